@@ -1,0 +1,772 @@
+/*
+ * vafr_oracle.c -- plain, slow FP64 CPU oracle of the VaFR ray-casting hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline / reference leg load this library.  The product
+ * (the CUDA library) never calls it, and the two share no code, header, table
+ * or constant generator.
+ *
+ * Method: "Visual Acuity Consistent Foveated Rendering towards Retinal
+ * Resolution" (Zhang, Gai, Li; arXiv 2503.23410).  Equation numbers follow the
+ * paper's order of display equations:
+ *   Eq. 2  linear MAR model  omega(e) = m e + omega0,  f = 1/omega   (Sec. 3.2.1)
+ *   Eq. 3  r = tan(e)/c_r = |(x,y) - (x0,y0)|, trig in degrees      (Sec. 3.2.1)
+ *   Eq. 4  du/de = 2 f(e)
+ *   Eq. 5  u(e) = 2 ln(m e + omega0)/m + c0
+ *   Eq. 6  tangential rate = radial rate,  r dtheta/dv = dr/du
+ *   Eq. 7  de/dr = c_r cos^2(e) 180/pi
+ *   Eq. 8  v(e, theta) = theta sin(2e)/(m e + omega0)
+ *   Eq. 9  l(e) = v(e, 360 deg)                        (shading height)
+ *   Eq. 10 e = (exp((u - c0) m/2) - omega0)/m           (Sec. 3.2.3)
+ *   Eq. 11 x = r cos(v/l(e) 360) + x0, y = r sin(v/l(e) 360) + y0
+ *   Eq. 12 the four-segment form of Eqs. 5 and 8        (Sec. 3.3)
+ *   Eq. 13 SR(e) = f(e) = (1/2) du/de                   (Sec. 4.1)
+ * Ray-casting pipeline: Sec. 6.1 (one ray per LP texel, closest-hit shading,
+ * miss shading, inverse mapping to the display; GT = one ray per pixel).
+ *
+ * Readings of points the paper leaves open (each also listed in the design
+ * notes): integration constants c_i fixed by u(0) = 0 and continuity at the
+ * pivots; texel (c, j) sits at u = c + 0.5 and angle (j + 0.5) 360/n_c with
+ * n_c = max(1, floor(l(e_c) + 0.5)); the angle is atan2 in display pixel
+ * coordinates (y down) wrapped to [0, 360); eccentricity is clamped to e_max
+ * in reconstruction; reconstruction is bilinear in (u, angle) with per-column
+ * angular wrap; Lambert shading with ambient 0.1 and a sky gradient on miss;
+ * two-sided watertight triangle test, closest t > 0, equal t -> lowest id.
+ * The LBVH part (30-bit Morton codes, sort, Karras radix tree, bounds) is not
+ * in the paper; it follows Karras 2012 "Maximizing Parallelism in the
+ * Construction of BVHs, Octrees, and k-d Trees".
+ *
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared (contraction off so
+ * the FP32 Morton quantisation is one IEEE op at a time on every host).
+ */
+
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_MAX_PIVOTS 9
+#define OR_DEG (M_PI / 180.0)
+
+/* ------------------------------------------------------------------------- */
+/* Acuity model and the segmented log-polar mapping (Eqs. 2, 5, 8-10, 12)     */
+
+typedef struct {
+    int    n_seg;                 /* pivots - 1                               */
+    double E[OR_MAX_PIVOTS];      /* pivot eccentricities (deg)               */
+    double f[OR_MAX_PIVOTS];      /* acuity at the pivots (cycles/deg)        */
+    double m[OR_MAX_PIVOTS];      /* MAR slope of segment i (Eq. 2)           */
+    double w0[OR_MAX_PIVOTS];     /* MAR intercept omega_i of segment i       */
+    double c[OR_MAX_PIVOTS];      /* integration constant c_i (Eq. 12)        */
+} or_acuity;
+
+/* u on segment i in the paper's literal form 2 ln(m_i e + w_i)/m_i + c_i,
+ * or its m -> 0 limit 2 e / w_i + c_i (constant acuity on the segment). */
+static double seg_u(const or_acuity* a, int i, double e) {
+    if (a->m[i] == 0.0) return 2.0 * e / a->w0[i] + a->c[i];
+    return 2.0 * log(a->m[i] * e + a->w0[i]) / a->m[i] + a->c[i];
+}
+
+/* Segment table from the pivots (Eq. 12, Sec. 3.3): MAR omega = 1/f is taken
+ * piecewise linear through the pivots (E_k, 1/f_k); c_1 makes u(0) = 0 and
+ * each later c_i makes u continuous at E_{i-1}.  Returns 0 or -1 on bad input. */
+int or_acuity_init(or_acuity* a, const double* E, const double* f, int n_piv) {
+    if (n_piv < 2 || n_piv > OR_MAX_PIVOTS) return -1;
+    memset(a, 0, sizeof(*a));
+    a->n_seg = n_piv - 1;
+    for (int k = 0; k < n_piv; ++k) {
+        if (!(f[k] > 0.0)) return -1;
+        if (k > 0 && !(E[k] > E[k - 1])) return -1;
+        a->E[k] = E[k];
+        a->f[k] = f[k];
+    }
+    if (E[0] != 0.0) return -1;
+    for (int i = 0; i < a->n_seg; ++i) {
+        double w_lo = 1.0 / f[i], w_hi = 1.0 / f[i + 1];
+        a->m[i] = (w_hi - w_lo) / (E[i + 1] - E[i]);
+        a->w0[i] = w_lo - a->m[i] * E[i];
+    }
+    /* u(0) = 0 on segment 0; continuity at every inner pivot. */
+    a->c[0] = 0.0;
+    a->c[0] = -seg_u(a, 0, 0.0);
+    for (int i = 1; i < a->n_seg; ++i) {
+        double u_end = seg_u(a, i - 1, E[i]);
+        a->c[i] = 0.0;
+        a->c[i] = u_end - seg_u(a, i, E[i]);
+    }
+    return 0;
+}
+
+/* Segment holding eccentricity e: [E_i, E_{i+1}); beyond the last pivot the
+ * last segment's formula is extended. */
+static int seg_of_e(const or_acuity* a, double e) {
+    for (int i = 0; i < a->n_seg - 1; ++i)
+        if (e < a->E[i + 1]) return i;
+    return a->n_seg - 1;
+}
+
+/* MAR omega(e) (deg/cycle), Eq. 2 per segment. */
+double or_omega(const or_acuity* a, double e) {
+    int i = seg_of_e(a, e);
+    return a->m[i] * e + a->w0[i];
+}
+
+/* Acuity f(e) = 1/omega(e) (cycles/deg), Eq. 2. */
+double or_acuity_f(const or_acuity* a, double e) { return 1.0 / or_omega(a, e); }
+
+/* LP horizontal coordinate u(e), Eqs. 5 / 12. */
+double or_u_of_e(const or_acuity* a, double e) { return seg_u(a, seg_of_e(a, e), e); }
+
+/* Inverse, Eq. 10 per segment: e = (exp((u - c_i) m_i / 2) - omega_i) / m_i. */
+double or_e_of_u(const or_acuity* a, double u) {
+    int i = a->n_seg - 1;
+    for (int k = 0; k < a->n_seg - 1; ++k) {
+        if (u < seg_u(a, k, a->E[k + 1])) { i = k; break; }
+    }
+    if (a->m[i] == 0.0) return (u - a->c[i]) * a->w0[i] / 2.0;
+    return (exp((u - a->c[i]) * a->m[i] / 2.0) - a->w0[i]) / a->m[i];
+}
+
+/* v(e, theta) = theta sin(2e)/(m e + omega), Eq. 8 / 12 (theta in degrees). */
+double or_v_of_e_theta(const or_acuity* a, double e, double theta_deg) {
+    return theta_deg * sin(2.0 * e * OR_DEG) / or_omega(a, e);
+}
+
+/* Shading height l(e) = v(e, 360 deg), Eq. 9. */
+double or_l_of_e(const or_acuity* a, double e) { return or_v_of_e_theta(a, e, 360.0); }
+
+/* Vectorised helpers for the Python side. */
+void or_eval(const or_acuity* a, int what, const double* in, double* out, int64_t n) {
+    for (int64_t k = 0; k < n; ++k) {
+        switch (what) {
+            case 0: out[k] = or_u_of_e(a, in[k]); break;
+            case 1: out[k] = or_e_of_u(a, in[k]); break;
+            case 2: out[k] = or_l_of_e(a, in[k]); break;
+            case 3: out[k] = or_acuity_f(a, in[k]); break;
+            default: out[k] = NAN;
+        }
+    }
+}
+
+int64_t or_sizeof_acuity(void) { return (int64_t)sizeof(or_acuity); }
+
+void or_acuity_get(const or_acuity* a, double* m, double* w0, double* c) {
+    for (int i = 0; i < a->n_seg; ++i) { m[i] = a->m[i]; w0[i] = a->w0[i]; c[i] = a->c[i]; }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Discrete LP layout (Sec. 3.2.2): columns at u = c + 0.5 for c + 0.5 < u(e_max);
+ * column c holds n_c = max(1, round(l(e_c))) texels at angles (j+0.5) 360/n_c.
+ * Texels are stored column after column: texel (c, j) at offset_c + j.
+ * Returns the column count, or -1 if it would exceed cap. */
+int or_lp_layout(const or_acuity* a, double e_max, int cap,
+                 double* e_col, int32_t* n_col, int64_t* off_col, int64_t* total) {
+    double u_max = or_u_of_e(a, e_max);
+    int C = 0;
+    while ((double)C + 0.5 < u_max) ++C;
+    if (C > cap) return -1;
+    int64_t acc = 0;
+    for (int c = 0; c < C; ++c) {
+        double e = or_e_of_u(a, (double)c + 0.5);
+        double l = or_l_of_e(a, e);
+        int32_t n = (int32_t)floor(l + 0.5);
+        if (n < 1) n = 1;
+        e_col[c] = e;
+        n_col[c] = n;
+        off_col[c] = acc;
+        acc += n;
+    }
+    *total = acc;
+    return C;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Views: pinhole camera, pose [R | t] camera -> world (x right, y up, z fwd). */
+
+typedef struct {
+    double width, height;   /* display size in pixels                        */
+    double fov_v_deg;       /* vertical field of view                        */
+    double x0, y0;          /* gaze point (display pixels, y down)           */
+    double pose[12];        /* row-major 3x4                                 */
+} or_view;
+
+/* c_r (Sec. 3.2.1): film height / focal length / display height in pixels. */
+static double view_cr(const or_view* v) {
+    return 2.0 * tan(0.5 * v->fov_v_deg * OR_DEG) / v->height;
+}
+
+/* Primary ray through display point (x, y) (continuous pixel coordinates). */
+static void view_ray(const or_view* v, double x, double y, double o[3], double d[3]) {
+    double cr = view_cr(v);
+    double dc[3] = {cr * (x - 0.5 * v->width), cr * (0.5 * v->height - y), 1.0};
+    for (int k = 0; k < 3; ++k) {
+        d[k] = v->pose[4 * k + 0] * dc[0] + v->pose[4 * k + 1] * dc[1] + v->pose[4 * k + 2] * dc[2];
+        o[k] = v->pose[4 * k + 3];
+    }
+}
+
+/* Screen point of LP texel (c, j) by the inverse mapping (Eqs. 3, 10, 11):
+ * e_c from the layout, r = tan(e_c)/c_r, angle = (j + 0.5)/n_c * 360 deg. */
+static void texel_screen_point(const or_view* v, double e_c, int32_t n_c, int64_t j,
+                               double* x, double* y) {
+    double r = tan(e_c * OR_DEG) / view_cr(v);
+    double ang = ((double)j + 0.5) / (double)n_c * 360.0;
+    *x = r * cos(ang * OR_DEG) + v->x0;
+    *y = r * sin(ang * OR_DEG) + v->y0;
+}
+
+/* Rays for a list of LP texels given by global texel index (Sec. 6.1). */
+void or_lp_rays(const or_view* v, const double* e_col, const int32_t* n_col,
+                const int64_t* off_col, int n_cols, const int64_t* texels, int64_t n,
+                double* orig, double* dir, double* screen_xy) {
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t t = texels[k];
+        int lo = 0, hi = n_cols - 1;           /* column with off_col[c] <= t */
+        while (lo < hi) {
+            int mid = (lo + hi + 1) / 2;
+            if (off_col[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        double x, y;
+        texel_screen_point(v, e_col[lo], n_col[lo], t - off_col[lo], &x, &y);
+        view_ray(v, x, y, orig + 3 * k, dir + 3 * k);
+        if (screen_xy) { screen_xy[2 * k] = x; screen_xy[2 * k + 1] = y; }
+    }
+}
+
+/* Rays through display pixel centres (x + 0.5, y + 0.5), pixel id = y W + x. */
+void or_pixel_rays(const or_view* v, const int64_t* pix, int64_t n, double* orig, double* dir) {
+    int64_t W = (int64_t)v->width;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n; ++k) {
+        double x = (double)(pix[k] % W) + 0.5, y = (double)(pix[k] / W) + 0.5;
+        view_ray(v, x, y, orig + 3 * k, dir + 3 * k);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Watertight ray / triangle test (Woop, Benthin, Wald 2013, JCGT 2(1)),
+ * two-sided, in FP64.  Hit iff all edge functions share a sign (zero counts
+ * as inside, so a ray through a shared edge hits both neighbours), the
+ * determinant is non-zero and t > 0. */
+
+typedef struct { int kx, ky, kz; double Sx, Sy, Sz; double o[3]; } or_wray;
+
+static void wray_init(or_wray* r, const double o[3], const double d[3]) {
+    double ax = fabs(d[0]), ay = fabs(d[1]), az = fabs(d[2]);
+    int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+    int kx = (kz + 1) % 3, ky = (kx + 1) % 3;
+    if (d[kz] < 0.0) { int s = kx; kx = ky; ky = s; }
+    r->kx = kx; r->ky = ky; r->kz = kz;
+    r->Sx = d[kx] / d[kz];
+    r->Sy = d[ky] / d[kz];
+    r->Sz = 1.0 / d[kz];
+    r->o[0] = o[0]; r->o[1] = o[1]; r->o[2] = o[2];
+}
+
+static int wray_hit(const or_wray* r, const float* tri, double* t_out) {
+    double A[3], B[3], C[3];
+    for (int k = 0; k < 3; ++k) {
+        A[k] = (double)tri[k] - r->o[k];
+        B[k] = (double)tri[3 + k] - r->o[k];
+        C[k] = (double)tri[6 + k] - r->o[k];
+    }
+    double Ax = A[r->kx] - r->Sx * A[r->kz], Ay = A[r->ky] - r->Sy * A[r->kz];
+    double Bx = B[r->kx] - r->Sx * B[r->kz], By = B[r->ky] - r->Sy * B[r->kz];
+    double Cx = C[r->kx] - r->Sx * C[r->kz], Cy = C[r->ky] - r->Sy * C[r->kz];
+    double U = Cx * By - Cy * Bx;
+    double V = Ax * Cy - Ay * Cx;
+    double W = Bx * Ay - By * Ax;
+    if ((U < 0.0 || V < 0.0 || W < 0.0) && (U > 0.0 || V > 0.0 || W > 0.0)) return 0;
+    double det = U + V + W;
+    if (det == 0.0) return 0;
+    double Az = r->Sz * A[r->kz], Bz = r->Sz * B[r->kz], Cz = r->Sz * C[r->kz];
+    double T = U * Az + V * Bz + W * Cz;
+    double t = T / det;
+    if (!(t > 0.0)) return 0;
+    *t_out = t;
+    return 1;
+}
+
+/* Signed distance-like margin of the ray from the triangle's boundary in the
+ * sheared 2-D frame: min over edges of (edge function / edge length), signed
+ * so that > 0 means inside.  Used by tests to classify edge ties. */
+double or_edge_margin(const double* o, const double* d, const float* tri) {
+    or_wray r;
+    wray_init(&r, o, d);
+    double P[3][2];
+    for (int v = 0; v < 3; ++v) {
+        double a[3];
+        for (int k = 0; k < 3; ++k) a[k] = (double)tri[3 * v + k] - o[k];
+        P[v][0] = a[r.kx] - r.Sx * a[r.kz];
+        P[v][1] = a[r.ky] - r.Sy * a[r.kz];
+    }
+    double area = (P[1][0] - P[0][0]) * (P[2][1] - P[0][1]) - (P[1][1] - P[0][1]) * (P[2][0] - P[0][0]);
+    double sgn = area >= 0.0 ? 1.0 : -1.0;
+    double best = INFINITY;
+    for (int e = 0; e < 3; ++e) {
+        const double* p = P[e];
+        const double* q = P[(e + 1) % 3];
+        double ex = q[0] - p[0], ey = q[1] - p[1];
+        double len = sqrt(ex * ex + ey * ey);
+        double fn = (ex * (0.0 - p[1]) - ey * (0.0 - p[0])) * sgn;
+        double dist = len > 0.0 ? fn / len : -INFINITY;
+        if (dist < best) best = dist;
+    }
+    return best;
+}
+
+/* Closest hit by brute force over all triangles: closest t > 0, equal t ->
+ * lowest triangle id (loop in id order, strict comparison).  -1 on a miss. */
+void or_cast_brute(const float* tris, int64_t n_tris, const double* orig, const double* dir,
+                   int64_t n_rays, int32_t* hit_id, double* hit_t) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n_rays; ++k) {
+        or_wray r;
+        wray_init(&r, orig + 3 * k, dir + 3 * k);
+        int32_t best = -1;
+        double bt = INFINITY;
+        for (int64_t i = 0; i < n_tris; ++i) {
+            double t;
+            if (wray_hit(&r, tris + 9 * i, &t) && t < bt) { bt = t; best = (int32_t)i; }
+        }
+        hit_id[k] = best;
+        hit_t[k] = best >= 0 ? bt : INFINITY;
+    }
+}
+
+/* t of a ray against one given triangle (INFINITY if no hit). */
+void or_ray_tri_t(const float* tris, const int32_t* ids, const double* orig, const double* dir,
+                  int64_t n, double* t_out) {
+    for (int64_t k = 0; k < n; ++k) {
+        or_wray r;
+        double t;
+        wray_init(&r, orig + 3 * k, dir + 3 * k);
+        t_out[k] = (ids[k] >= 0 && wray_hit(&r, tris + 9 * (int64_t)ids[k], &t)) ? t : INFINITY;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* CPU BVH (object-median split, FP64 padded boxes).  Speeds up large scenes;
+ * its result equals brute force exactly because boxes are conservative and
+ * triangles use the same test and tie rule. */
+
+typedef struct {
+    double lo[3], hi[3];
+    int32_t left, right;      /* children (internal) or -1                   */
+    int32_t first, count;     /* triangle range in `order` for leaves         */
+} or_bnode;
+
+typedef struct {
+    const float* tris;
+    int64_t n_tris;
+    int32_t* order;
+    or_bnode* nodes;
+    int32_t n_nodes;
+    double* cen;
+} or_bvh;
+
+static void tri_box(const float* t, double lo[3], double hi[3]) {
+    for (int k = 0; k < 3; ++k) {
+        double a = t[k], b = t[3 + k], c = t[6 + k];
+        lo[k] = fmin(a, fmin(b, c));
+        hi[k] = fmax(a, fmax(b, c));
+    }
+}
+
+static const double* g_sort_cen;
+static int g_sort_axis;
+static int cmp_cen(const void* pa, const void* pb) {
+    int32_t a = *(const int32_t*)pa, b = *(const int32_t*)pb;
+    double ca = g_sort_cen[3 * a + g_sort_axis], cb = g_sort_cen[3 * b + g_sort_axis];
+    if (ca < cb) return -1;
+    if (ca > cb) return 1;
+    return (a > b) - (a < b);
+}
+
+static int32_t bvh_build_rec(or_bvh* b, int32_t first, int32_t count) {
+    int32_t id = b->n_nodes++;
+    or_bnode* nd = &b->nodes[id];
+    for (int k = 0; k < 3; ++k) { nd->lo[k] = INFINITY; nd->hi[k] = -INFINITY; }
+    double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int32_t i = first; i < first + count; ++i) {
+        double lo[3], hi[3];
+        int32_t t = b->order[i];
+        tri_box(b->tris + 9 * (int64_t)t, lo, hi);
+        for (int k = 0; k < 3; ++k) {
+            nd->lo[k] = fmin(nd->lo[k], lo[k]);
+            nd->hi[k] = fmax(nd->hi[k], hi[k]);
+            clo[k] = fmin(clo[k], b->cen[3 * t + k]);
+            chi[k] = fmax(chi[k], b->cen[3 * t + k]);
+        }
+    }
+    for (int k = 0; k < 3; ++k) {          /* pad so FP64 slab tests stay conservative */
+        double pad = 1e-9 * (1.0 + fabs(nd->lo[k]) + fabs(nd->hi[k]));
+        nd->lo[k] -= pad;
+        nd->hi[k] += pad;
+    }
+    if (count <= 4) {
+        nd->left = nd->right = -1;
+        nd->first = first;
+        nd->count = count;
+        return id;
+    }
+    int axis = 0;
+    for (int k = 1; k < 3; ++k)
+        if (chi[k] - clo[k] > chi[axis] - clo[axis]) axis = k;
+    g_sort_cen = b->cen;
+    g_sort_axis = axis;
+    qsort(b->order + first, (size_t)count, sizeof(int32_t), cmp_cen);
+    int32_t half = count / 2;
+    int32_t l = bvh_build_rec(b, first, half);
+    int32_t r = bvh_build_rec(b, first + half, count - half);
+    nd = &b->nodes[id];
+    nd->left = l;
+    nd->right = r;
+    nd->first = -1;
+    nd->count = 0;
+    return id;
+}
+
+void* or_bvh_build(const float* tris, int64_t n_tris) {
+    or_bvh* b = (or_bvh*)calloc(1, sizeof(or_bvh));
+    b->tris = tris;
+    b->n_tris = n_tris;
+    b->order = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_tris > 0 ? n_tris : 1));
+    b->nodes = (or_bnode*)malloc(sizeof(or_bnode) * (size_t)(2 * n_tris + 1));
+    b->cen = (double*)malloc(sizeof(double) * 3 * (size_t)(n_tris > 0 ? n_tris : 1));
+    for (int64_t i = 0; i < n_tris; ++i) {
+        b->order[i] = (int32_t)i;
+        for (int k = 0; k < 3; ++k)
+            b->cen[3 * i + k] = ((double)tris[9 * i + k] + tris[9 * i + 3 + k] + tris[9 * i + 6 + k]) / 3.0;
+    }
+    if (n_tris > 0) bvh_build_rec(b, 0, (int32_t)n_tris);
+    free(b->cen);
+    b->cen = NULL;
+    return b;
+}
+
+void or_bvh_free(void* p) {
+    or_bvh* b = (or_bvh*)p;
+    if (!b) return;
+    free(b->order);
+    free(b->nodes);
+    free(b);
+}
+
+static int box_enter(const or_bnode* nd, const double o[3], const double inv[3], double tmax) {
+    double t0 = 0.0, t1 = tmax;
+    for (int k = 0; k < 3; ++k) {
+        double a = (nd->lo[k] - o[k]) * inv[k], c = (nd->hi[k] - o[k]) * inv[k];
+        if (isnan(a) || isnan(c)) {                 /* ray parallel, origin on the slab */
+            if (o[k] < nd->lo[k] || o[k] > nd->hi[k]) return 0;
+            continue;
+        }
+        double lo = fmin(a, c), hi = fmax(a, c);
+        if (lo > t0) t0 = lo;
+        if (hi < t1) t1 = hi;
+    }
+    return t0 <= t1 * (1.0 + 1e-12);
+}
+
+void or_cast_bvh(void* p, const double* orig, const double* dir, int64_t n_rays,
+                 int32_t* hit_id, double* hit_t) {
+    const or_bvh* b = (const or_bvh*)p;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n_rays; ++k) {
+        or_wray r;
+        const double* o = orig + 3 * k;
+        const double* d = dir + 3 * k;
+        wray_init(&r, o, d);
+        double inv[3] = {1.0 / d[0], 1.0 / d[1], 1.0 / d[2]};
+        int32_t best = -1;
+        double bt = INFINITY;
+        int32_t stack[128];
+        int sp = 0;
+        if (b->n_tris > 0) stack[sp++] = 0;
+        while (sp > 0) {
+            const or_bnode* nd = &b->nodes[stack[--sp]];
+            if (!box_enter(nd, o, inv, bt)) continue;
+            if (nd->left < 0) {
+                for (int32_t i = nd->first; i < nd->first + nd->count; ++i) {
+                    int32_t tid = b->order[i];
+                    double t;
+                    if (wray_hit(&r, b->tris + 9 * (int64_t)tid, &t) &&
+                        (t < bt || (t == bt && tid < best))) {
+                        bt = t;
+                        best = tid;
+                    }
+                }
+            } else if (sp + 2 <= 128) {
+                stack[sp++] = nd->right;
+                stack[sp++] = nd->left;
+            }
+        }
+        hit_id[k] = best;
+        hit_t[k] = best >= 0 ? bt : INFINITY;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Shading (Sec. 6.1: closest-hit and miss shaders; the paper does not print
+ * its shading code).  Lambert with a directional light and ambient k_a:
+ *   rgb = albedo (k_a + (1 - k_a) max(0, n . (-L))),
+ * n = geometric unit normal turned to face the ray origin; a miss returns the
+ * sky gradient lerp((1,1,1), (0.5,0.7,1.0), (dhat_y + 1)/2).  Alpha = 1. */
+
+#define OR_KA 0.1
+
+void or_shade(const float* tris, const float* albedo, const double* light_dir,
+              const double* dir, const int32_t* hit_id, int64_t n, double* rgba) {
+    double L[3] = {light_dir[0], light_dir[1], light_dir[2]};
+    double ln = sqrt(L[0] * L[0] + L[1] * L[1] + L[2] * L[2]);
+    for (int k = 0; k < 3; ++k) L[k] /= ln;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n; ++k) {
+        const double* d = dir + 3 * k;
+        double* out = rgba + 4 * k;
+        if (hit_id[k] < 0) {
+            double dl = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double s = 0.5 * (d[1] / dl + 1.0);
+            out[0] = (1.0 - s) * 1.0 + s * 0.5;
+            out[1] = (1.0 - s) * 1.0 + s * 0.7;
+            out[2] = (1.0 - s) * 1.0 + s * 1.0;
+            out[3] = 1.0;
+            continue;
+        }
+        const float* t = tris + 9 * (int64_t)hit_id[k];
+        double e1[3], e2[3], nrm[3];
+        for (int a = 0; a < 3; ++a) {
+            e1[a] = (double)t[3 + a] - t[a];
+            e2[a] = (double)t[6 + a] - t[a];
+        }
+        nrm[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        nrm[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        nrm[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        double nl = sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+        for (int a = 0; a < 3; ++a) nrm[a] /= nl;
+        if (nrm[0] * d[0] + nrm[1] * d[1] + nrm[2] * d[2] > 0.0)
+            for (int a = 0; a < 3; ++a) nrm[a] = -nrm[a];
+        double lam = -(nrm[0] * L[0] + nrm[1] * L[1] + nrm[2] * L[2]);
+        if (lam < 0.0) lam = 0.0;
+        double s = OR_KA + (1.0 - OR_KA) * lam;
+        const float* al = albedo + 3 * (int64_t)hit_id[k];
+        out[0] = al[0] * s;
+        out[1] = al[1] * s;
+        out[2] = al[2] * s;
+        out[3] = 1.0;
+    }
+}
+
+/* |n_hat . d_hat| of the hit triangle (grazing-ray classifier for tests). */
+void or_grazing(const float* tris, const double* dir, const int32_t* hit_id, int64_t n, double* out) {
+    for (int64_t k = 0; k < n; ++k) {
+        if (hit_id[k] < 0) { out[k] = 1.0; continue; }
+        const float* t = tris + 9 * (int64_t)hit_id[k];
+        const double* d = dir + 3 * k;
+        double e1[3], e2[3], nrm[3];
+        for (int a = 0; a < 3; ++a) { e1[a] = (double)t[3 + a] - t[a]; e2[a] = (double)t[6 + a] - t[a]; }
+        nrm[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        nrm[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        nrm[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        double nl = sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+        double dl = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        out[k] = fabs(nrm[0] * d[0] + nrm[1] * d[1] + nrm[2] * d[2]) / (nl * dl);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Reconstruction (Sec. 3.4 inverse-mapping pass; Eqs. 3, 5/12 forward map).
+ * For a display point (x, y): r = |(x,y) - (x0,y0)|, e = atan(c_r r) (deg,
+ * clamped to e_max), u = u(e), angle = atan2(y - y0, x - x0) in [0, 360).
+ * Bilinear filter: columns floor(u - 0.5) and +1 (clamped to [0, C-1]); in
+ * each column rows floor(angle n_c/360 - 0.5) and +1, wrapped modulo n_c. */
+
+static void column_sample(const double* lp, int nch, int64_t off, int32_t n, double ang,
+                          double* acc, double w) {
+    double v = ang / 360.0 * (double)n - 0.5;
+    double j0f = floor(v);
+    double wv = v - j0f;
+    int64_t j0 = (int64_t)j0f;
+    int64_t j1 = j0 + 1;
+    j0 = ((j0 % n) + n) % n;
+    j1 = ((j1 % n) + n) % n;
+    for (int ch = 0; ch < nch; ++ch)
+        acc[ch] += w * ((1.0 - wv) * lp[(off + j0) * nch + ch] + wv * lp[(off + j1) * nch + ch]);
+}
+
+void or_reconstruct_points(const or_acuity* a, double e_max, const or_view* v,
+                           const int32_t* n_col, const int64_t* off_col, int n_cols,
+                           const double* lp, int nch, const double* pts, int64_t n, double* out) {
+    double cr = view_cr(v);
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n; ++k) {
+        double dx = pts[2 * k] - v->x0, dy = pts[2 * k + 1] - v->y0;
+        double r = sqrt(dx * dx + dy * dy);
+        double e = atan(cr * r) / OR_DEG;
+        if (e > e_max) e = e_max;
+        double u = or_u_of_e(a, e);
+        double ang = atan2(dy, dx) / OR_DEG;
+        if (ang < 0.0) ang += 360.0;
+        double uf = u - 0.5;
+        if (uf < 0.0) uf = 0.0;
+        if (uf > (double)(n_cols - 1)) uf = (double)(n_cols - 1);
+        int c0 = (int)floor(uf);
+        double wu = uf - c0;
+        int c1 = c0 + 1 < n_cols ? c0 + 1 : n_cols - 1;
+        double acc[8] = {0};
+        column_sample(lp, nch, off_col[c0], n_col[c0], ang, acc, 1.0 - wu);
+        column_sample(lp, nch, off_col[c1], n_col[c1], ang, acc, wu);
+        for (int ch = 0; ch < nch; ++ch) out[k * nch + ch] = acc[ch];
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* LBVH reference (Karras 2012).  Morton codes from the centroid sum
+ * s = (v0 + v1) + v2 in FP32, quantised against the scene's s-bounds with
+ * one IEEE FP32 op at a time: q = min((uint)((s - lo)/(hi - lo) * 1024), 1023)
+ * (q = 0 on a degenerate axis); 10 bits per axis interleaved x-major
+ * (x bit b -> code bit 3b+2, y -> 3b+1, z -> 3b). */
+
+static uint32_t spread10(uint32_t q) {
+    uint32_t out = 0;
+    for (int b = 0; b < 10; ++b) out |= ((q >> b) & 1u) << (3 * b);
+    return out;
+}
+
+void or_morton(const float* tris, int64_t n, uint32_t* codes) {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float* s = (float*)malloc(sizeof(float) * 3 * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) {
+            volatile float a = tris[9 * i + k] + tris[9 * i + 3 + k];
+            float v = a + tris[9 * i + 6 + k];
+            s[3 * i + k] = v;
+            if (v < lo[k]) lo[k] = v;
+            if (v > hi[k]) hi[k] = v;
+        }
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t q[3];
+        for (int k = 0; k < 3; ++k) {
+            volatile float ext = hi[k] - lo[k];
+            if (!(ext > 0.0f)) { q[k] = 0; continue; }
+            volatile float num = s[3 * i + k] - lo[k];
+            volatile float t = num / ext;
+            volatile float sc = t * 1024.0f;
+            uint32_t qi = (uint32_t)sc;
+            q[k] = qi > 1023u ? 1023u : qi;
+        }
+        codes[i] = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+    }
+    free(s);
+}
+
+/* Sort by (code, id): qsort with a total order on the pair. */
+static const uint32_t* g_codes;
+static int cmp_code(const void* pa, const void* pb) {
+    int32_t a = *(const int32_t*)pa, b = *(const int32_t*)pb;
+    if (g_codes[a] != g_codes[b]) return g_codes[a] < g_codes[b] ? -1 : 1;
+    return (a > b) - (a < b);
+}
+
+/* Key of sorted position i: code in the high word, position in the low word,
+ * so equal codes still give distinct keys (Karras 2012, Sec. 4). */
+static uint64_t rkey(const uint32_t* sc, int64_t i) { return ((uint64_t)sc[i] << 32) | (uint64_t)i; }
+
+static int hibit64(uint64_t x) { int b = 63; while (!((x >> b) & 1u)) --b; return b; }
+
+/* Top-down binary radix tree over sorted keys.  Range [f, l] (f < l) splits
+ * at the highest bit where keys f and l differ: the left child takes the keys
+ * with that bit 0.  Node numbering (Karras 2012): the root is internal node 0;
+ * a child covering [a, b] is leaf a when a == b, else internal node gamma for
+ * the left child and gamma + 1 for the right child, gamma the split.
+ * child refs: >= 0 internal node, < 0 leaf ~k (k = sorted position). */
+static void radix_rec(const uint32_t* sc, int64_t f, int64_t l, int32_t node,
+                      int32_t* child, int32_t* parent_of_node, int32_t* range) {
+    uint64_t kf = rkey(sc, f), kl = rkey(sc, l);
+    int b = hibit64(kf ^ kl);
+    int64_t lo = f, hi = l;                  /* last index with bit b == 0 */
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) / 2;
+        if ((rkey(sc, mid) >> b) & 1u) hi = mid - 1; else lo = mid;
+    }
+    int64_t g = lo;
+    range[2 * node] = (int32_t)f;
+    range[2 * node + 1] = (int32_t)l;
+    int32_t L = (g == f) ? ~(int32_t)g : (int32_t)g;
+    int32_t R = (g + 1 == l) ? ~(int32_t)(g + 1) : (int32_t)(g + 1);
+    child[2 * node] = L;
+    child[2 * node + 1] = R;
+    if (L >= 0) { parent_of_node[L] = node; radix_rec(sc, f, g, L, child, parent_of_node, range); }
+    if (R >= 0) { parent_of_node[R] = node; radix_rec(sc, g + 1, l, R, child, parent_of_node, range); }
+}
+
+/* Full LBVH reference: codes (input order), sorted ids, child refs of the
+ * n - 1 internal nodes, per-internal-node and per-leaf FP32 bounds
+ * (lo xyz, hi xyz).  Returns 0 or -1. */
+int or_lbvh(const float* tris, int64_t n, uint32_t* codes, int32_t* sorted_ids,
+            int32_t* child, float* node_box, float* leaf_box, int32_t* range) {
+    if (n <= 0) return 0;
+    or_morton(tris, n, codes);
+    for (int64_t i = 0; i < n; ++i) sorted_ids[i] = (int32_t)i;
+    g_codes = codes;
+    qsort(sorted_ids, (size_t)n, sizeof(int32_t), cmp_code);
+    uint32_t* sc = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) sc[i] = codes[sorted_ids[i]];
+    for (int64_t i = 0; i < n; ++i) {
+        const float* t = tris + 9 * (int64_t)sorted_ids[i];
+        for (int k = 0; k < 3; ++k) {
+            float a = t[k], b = t[3 + k], c = t[6 + k];
+            float lo = a < b ? a : b; lo = lo < c ? lo : c;
+            float hi = a > b ? a : b; hi = hi > c ? hi : c;
+            leaf_box[6 * i + k] = lo;
+            leaf_box[6 * i + 3 + k] = hi;
+        }
+    }
+    if (n == 1) { free(sc); return 0; }
+    int32_t* par = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    par[0] = -1;
+    radix_rec(sc, 0, n - 1, 0, child, par, range);
+    /* bounds: an internal node's box is the union of its children's boxes;
+     * evaluate children first (post-order by descending range size works). */
+    int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n - 1));
+    int32_t* stk = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n - 1));
+    int64_t no = 0, sp = 0;
+    stk[sp++] = 0;
+    while (sp > 0) {                          /* pre-order; reversed = children first */
+        int32_t v = stk[--sp];
+        order[no++] = v;
+        for (int s = 0; s < 2; ++s)
+            if (child[2 * v + s] >= 0) stk[sp++] = child[2 * v + s];
+    }
+    for (int64_t q = no - 1; q >= 0; --q) {
+        int32_t v = order[q];
+        float* box = node_box + 6 * (int64_t)v;
+        for (int k = 0; k < 3; ++k) { box[k] = INFINITY; box[3 + k] = -INFINITY; }
+        for (int s = 0; s < 2; ++s) {
+            int32_t ch = child[2 * v + s];
+            const float* cb = ch >= 0 ? node_box + 6 * (int64_t)ch : leaf_box + 6 * (int64_t)(~ch);
+            for (int k = 0; k < 3; ++k) {
+                if (cb[k] < box[k]) box[k] = cb[k];
+                if (cb[3 + k] > box[3 + k]) box[3 + k] = cb[3 + k];
+            }
+        }
+    }
+    free(order);
+    free(stk);
+    free(par);
+    free(sc);
+    return 0;
+}
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

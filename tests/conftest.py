@@ -1,0 +1,32 @@
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs through the C-ABI library)")
+    config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+@pytest.fixture(scope="session")
+def golden():
+    with open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")) as f:
+        return json.load(f)
+
+
+@pytest.fixture(scope="session")
+def acuity():
+    import oracle
+    return oracle.Acuity()
+
+
+@pytest.fixture(scope="session")
+def layout(acuity):
+    import oracle
+    return oracle.lp_layout(acuity)
