@@ -1,0 +1,457 @@
+"""Benchmark of the VaFR ray-casting hot path on one GB300 (or N, one per rank).
+
+Workload (default ``terrain4k``): 3840x2160 monocular display, 100 deg vertical
+FOV, a 240-frame seeded saccade gaze trajectory, a 1,069,506-triangle scene
+(fBm terrain 512x1024 + 2,000 boxes), FP32 LP buffer and FP32 display.
+
+A step is one frame: the FP64 gaze set-up, the LP render (one ray per LP
+texel: generation + LBVH traversal + shading) and the reconstruction of the
+full-resolution display.  Inputs (scene, BVH, buffers) are resident in HBM
+before timing.  L2 is flushed (256 MiB write) between steps, outside the
+per-step CUDA events.  The GPU's own full-resolution ray cast (the paper's GT,
+one ray per display pixel) is timed the same way for the speedup.
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm here) on the
+host cores: each step renders a bounded random sample of one frame's LP texels
+and display pixels, extrapolated to a whole frame.
+
+Prints one JSON line (rank 0).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "display Mpix/s (VaFR frame: LP render + reconstruct)"
+UNIT = "Mpix/s"
+HERE_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+FP32_LANES_PER_SM = 128
+# FP32 operations per traversal step, counted from the kernel source: a node
+# visit is two slab tests (6 sub + 6 mul + 10 min/max + 1 mul + 1 cmp each);
+# a triangle test is 9 sub + 18 shear ops + 9 (U,V,W) + 2 (det) + 9 (z) + 3
+# (T) + 1 div + 7 compares; ray set-up + generation + shading ~ 60.
+OPS_PER_NODE = 48
+OPS_PER_TRI = 58
+OPS_PER_RAY = 60
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(HERE_PEAKS) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic(kernel: str, src: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for ln in open(path):
+            f = ln.split()
+            if len(f) >= 4 and f[0] == kernel and f[1] == sha:
+                return float(f[2]), f[3]
+    except OSError:
+        pass
+    return None, None
+
+
+def _workload_desc(w):
+    d = w.displays[0]
+    return (f"{w.name}: {d.width}x{d.height} x {len(d.poses)} eye(s), {d.fov_v_deg:g} deg FOV, "
+            f"{w.frames}-frame seeded gaze trajectory, {w.scene.n_tris:,} triangles "
+            f"({w.scene.name}), LP {'FP16' if w.lp_fp16 else 'FP32'}, display "
+            f"{'FP16' if w.display_fp16 else 'FP32'}")
+
+
+# ---------------------------------------------------------------------------
+# reference arm / CPU baseline: the FP64 oracle on the host cores
+
+
+def oracle_frame_sample(w, frame, n_tex, n_pix, bvh, lay, rng):
+    """Seconds to render n_tex LP texels + reconstruct n_pix pixels of one frame,
+    and the same scaled to a whole frame."""
+    import oracle
+    d = w.displays[0]
+    eyes = len(d.poses)
+    t_lp = t_rec = 0.0
+    for e in range(eyes):
+        gaze = d.gaze[frame % len(d.gaze), e]
+        tex = np.sort(rng.choice(lay.total, n_tex, replace=False))
+        t0 = time.perf_counter()
+        rgba, ids, _, _, _ = oracle.render_lp(w.scene.tris, w.scene.albedo, w.scene.light_dir, lay,
+                                              d.width, d.height, d.fov_v_deg, gaze, d.poses[e],
+                                              texels=tex, bvh=bvh)
+        t_lp += time.perf_counter() - t0
+        lp = np.zeros((lay.total, 4))
+        lp[tex] = rgba
+        pix = rng.choice(d.width * d.height, n_pix, replace=False)
+        t0 = time.perf_counter()
+        oracle.reconstruct(lp, lay, d.width, d.height, d.fov_v_deg, gaze, pix)
+        t_rec += time.perf_counter() - t0
+    frame_s = t_lp * lay.total / n_tex + t_rec * d.width * d.height / n_pix
+    return t_lp + t_rec, frame_s
+
+
+def run_reference(args, w):
+    import oracle
+    oracle.build()
+    d = w.displays[0]
+    eyes = len(d.poses)
+    lay = oracle.lp_layout()
+    t0 = time.perf_counter()
+    bvh = oracle.CpuBVH(w.scene.tris)
+    build_s = time.perf_counter() - t0
+    rng = np.random.default_rng(123)
+    n_tex, n_pix = args.ref_texels, args.ref_pixels
+    for k in range(args.warmup):
+        oracle_frame_sample(w, k, n_tex, n_pix, bvh, lay, rng)
+    frame_times, cpu_s = [], 0.0
+    for k in range(args.steps):
+        s, f = oracle_frame_sample(w, args.warmup + k, n_tex, n_pix, bvh, lay, rng)
+        cpu_s += s
+        frame_times.append(f)
+    ft = np.array(frame_times)
+    value = d.width * d.height * eyes / 1e6 / ft.mean()
+    sample = (f"per step: {n_tex} random LP texels/eye (CPU BVH, FP64) + {n_pix} random display "
+              f"pixels/eye reconstructed, extrapolated to the frame's {lay.total:,} texels and "
+              f"{d.width * d.height:,} pixels per eye; BVH build {build_s:.1f} s excluded")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(ft.mean() * 1e3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": _workload_desc(w)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "p50_frame_ms": float(np.percentile(ft, 50) * 1e3),
+        "p99_frame_ms": float(np.percentile(ft, 99) * 1e3),
+        "cpu_seconds_measured": cpu_s,
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# the CUDA path
+
+
+def run_gpu(args, w):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2503_23410_gb300 import build as B
+    if rank == 0 or ws == 1:
+        B.build()
+    if dist:
+        dist.barrier()
+    from paper_2503_23410_gb300 import vafr as V
+    V.load()
+    peaks, peak_kind = _peaks()
+
+    d = w.displays[0]
+    eyes = len(d.poses)
+    W_, H_ = d.width, d.height
+    tris = torch.from_numpy(np.ascontiguousarray(w.scene.tris.reshape(-1, 9))).cuda()
+    alb = torch.from_numpy(np.ascontiguousarray(w.scene.albedo)).cuda()
+    scene = V.vafr_build_scene(tris, alb, w.scene.light_dir)
+    lp_fmt = V.FMT_RGBA16F if w.lp_fp16 else V.FMT_RGBA32F
+    dp_fmt = V.FMT_RGBA16F if w.display_fp16 else V.FMT_RGBA32F
+    sess = V.vafr_session_create(V.make_session_desc(W_, H_, d.fov_v_deg, d.poses, lp_fmt, dp_fmt))
+    lp_b, dp_b = V.vafr_session_sizes(sess)
+    lp = torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda")
+    disp = torch.empty(eyes * dp_b, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    nf = len(d.gaze)
+    mask = (1 << eyes) - 1
+
+    def frame(k, evs=None):
+        g = d.gaze[k % nf]
+        for e in range(eyes):
+            V.vafr_set_gaze(sess, e, g[e, 0], g[e, 1])
+        if evs:
+            evs[0].record()
+        V.vafr_render_lp(scene, sess, mask, lp)
+        if evs:
+            evs[1].record()
+        for e in range(eyes):
+            V.vafr_reconstruct(sess, e, lp[e * lp_b:], disp[e * dp_b:])
+        if evs:
+            evs[2].record()
+
+    def gt_frame(k, evs=None):
+        if evs:
+            evs[0].record()
+        for e in range(eyes):
+            V.vafr_render_full_gt(scene, sess, e, disp[e * dp_b:])
+        if evs:
+            evs[1].record()
+
+    def timed(fn, K, n_ev):
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(K)]
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = V.vafr_kernel_launch_count()
+        t0 = time.perf_counter()
+        for k in range(K):
+            flush.fill_(k & 0xff)
+            fn(args.warmup + k, evs[k])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if dist:
+            dist.barrier()
+        launches = V.vafr_kernel_launch_count() - l0
+        per = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(n_ev - 1)]
+                        for k in range(K)])
+        return per, wall, launches
+
+    for k in range(args.warmup):
+        frame(k)
+        gt_frame(k)
+    torch.cuda.synchronize()
+    assert V.vafr_session_check(sess) == 0
+
+    with ClockSampler(local) as clk:
+        per, wall, launches = timed(frame, args.steps, 3)
+        gt_steps = max(3, min(args.steps, args.gt_steps))
+        gper, gwall, _ = timed(gt_frame, gt_steps, 2)
+        # end to end through the C ABI with HOST buffers: render_frame copies the
+        # display to pinned host memory every step (and synchronises)
+        host = torch.empty(eyes * dp_b, dtype=torch.uint8, pin_memory=True)
+        e2e_steps = max(3, min(args.steps, args.e2e_steps))
+        for k in range(2):
+            V.vafr_render_frame(scene, sess, host)
+        torch.cuda.synchronize()
+        te = time.perf_counter()
+        for k in range(e2e_steps):
+            g = d.gaze[k % nf]
+            for e in range(eyes):
+                V.vafr_set_gaze(sess, e, g[e, 0], g[e, 1])
+            V.vafr_render_frame(scene, sess, host)
+        e2e_s = time.perf_counter() - te
+    assert V.vafr_session_check(sess) == 0
+
+    step_ms = per.sum(1)
+    render_ms, recon_ms = per[:, 0], per[:, 1]
+    gt_ms = gper[:, 0]
+    total_s = step_ms.sum() / 1e3
+    if dist:
+        t = torch.tensor([total_s, e2e_s, gt_ms.mean()], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s, e2e_s, gt_mean = [float(x) for x in t.cpu()]
+    else:
+        gt_mean = float(gt_ms.mean())
+    mpix_frame = W_ * H_ * eyes / 1e6
+    value = mpix_frame * args.steps * ws / total_s
+    e2e_value = mpix_frame * e2e_steps * ws / e2e_s
+
+    # roofline of the dominant kernel
+    stats = V.vafr_traversal_stats(scene, sess, 0)
+    rays = stats["rays"] * eyes
+    ops = (stats["nodes"] * OPS_PER_NODE + stats["tri_tests"] * OPS_PER_TRI
+           + stats["rays"] * OPS_PER_RAY) * eyes
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = n_sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12      # T FP32 ops/s
+    render_s = float(render_ms.mean()) / 1e3
+    recon_s = float(recon_ms.mean()) / 1e3
+    lp_bytes = lp_b * eyes
+    recon_bytes = dp_b * eyes + lp_bytes                            # display write + LP read once
+    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    csrc = os.path.join(ROOT, "paper_2503_23410_gb300", "csrc")
+    tr_render, _ = _traffic("render_lp", os.path.join(csrc, "render.cu"))
+    tr_recon, _ = _traffic("reconstruct", os.path.join(csrc, "reconstruct.cu"))
+    roof_render = {"kernel": "k_render_lp", "bound": "alu", "achieved": ops / render_s / 1e12,
+                   "peak": alu_peak, "unit": "TFLOP/s", "frac": ops / render_s / 1e12 / alu_peak,
+                   "traffic": tr_render,
+                   "peak_kind": f"derived: {n_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                f"{sm_mhz:g} MHz (1 op/lane/clk)",
+                   "ops_per_launch": ops, "rays_per_launch": rays,
+                   "nodes_per_ray": stats["nodes"] / max(stats["rays"], 1),
+                   "tri_tests_per_ray": stats["tri_tests"] / max(stats["rays"], 1),
+                   "mrays_per_s": rays / render_s / 1e6, "avg_ms": render_s * 1e3}
+    roof_recon = {"kernel": "k_reconstruct", "bound": "hbm",
+                  "achieved": recon_bytes / recon_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                  "frac": recon_bytes / recon_s / 1e9 / hbm_peak, "traffic": tr_recon,
+                  "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured"
+                  else "fallback 6.8 TB/s",
+                  "bytes_per_launch": recon_bytes, "avg_ms": recon_s * 1e3}
+    dominant = roof_render if render_s >= recon_s else roof_recon
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": _workload_desc(w),
+                   "l2": "flushed between steps (256 MiB write outside the per-step events)",
+                   "parallelism": f"replicas x{ws} (independent sessions, no collective)"},
+        "fps": 1e3 / float(step_ms.mean()),
+        "p50_frame_ms": float(np.percentile(step_ms, 50)),
+        "p99_frame_ms": float(np.percentile(step_ms, 99)),
+        "gt": {"fps": 1e3 / gt_mean, "ms_per_frame": gt_mean,
+               "mpix_per_s": mpix_frame * 1e3 / gt_mean, "rays_per_frame": W_ * H_ * eyes,
+               "steps": gt_steps},
+        "speedup_vs_gt": gt_mean / float(step_ms.mean()),
+        "stage_ms": {"render_lp": float(render_ms.mean()), "reconstruct": float(recon_ms.mean())},
+        "roofline": dominant,
+        "roofline_other": roof_recon if dominant is roof_render else roof_render,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * eyes,
+                "d2h_bytes_per_step": dp_b * eyes, "steps": e2e_steps,
+                "path": "vafr_render_frame into pinned host memory (C ABI, synchronous)"},
+        "gpu_launches": int(launches),
+        "wall_s_timed_loop": wall,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(args, w)
+    if rank == 0:
+        print(json.dumps(line))
+    V.vafr_session_destroy(sess)
+    V.vafr_scene_destroy(scene)
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(args, w):
+    import oracle
+    oracle.build()
+    lay = oracle.lp_layout()
+    d = w.displays[0]
+    eyes = len(d.poses)
+    bvh = oracle.CpuBVH(w.scene.tris)
+    rng = np.random.default_rng(7)
+    cpu_s, frames = 0.0, []
+    t_start = time.perf_counter()
+    k = 0
+    while k < 3 or (time.perf_counter() - t_start < args.cpu_seconds and k < 50):
+        s, f = oracle_frame_sample(w, k, args.ref_texels, args.ref_pixels, bvh, lay, rng)
+        cpu_s += s
+        frames.append(f)
+        k += 1
+    ft = float(np.mean(frames))
+    return {"value": d.width * d.height * eyes / 1e6 / ft, "unit": UNIT,
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{k} frames x ({args.ref_texels} LP texels via CPU BVH + {args.ref_pixels} "
+                      f"display pixels) per eye, FP64, extrapolated to whole frames; "
+                      f"{cpu_s:.1f} s of sampled work"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=240)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="vafr", choices=["vafr", "reference"])
+    ap.add_argument("--workload", default="terrain4k",
+                    choices=["random1k", "terrain4k", "objects8k"])
+    ap.add_argument("--gt-steps", type=int, default=60)
+    ap.add_argument("--e2e-steps", type=int, default=60)
+    ap.add_argument("--ref-texels", type=int, default=65536)
+    ap.add_argument("--ref-pixels", type=int, default=524288)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    from workloads import workload
+    ws, rank, _ = _dist()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, workload(args.workload, frames=max(args.steps + args.warmup, 1)))
+        return
+    run_gpu(args, workload(args.workload))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,259 @@
+/*
+ * vafr.h -- C ABI of the GB300 (sm_103a) VaFR ray-casting library (libvafr.so).
+ *
+ * The library implements the data-parallel hot path of "Visual Acuity
+ * Consistent Foveated Rendering towards Retinal Resolution" (Zhang, Gai, Li;
+ * arXiv 2503.23410) for its ray-casting pipeline (Sec. 6.1): one primary ray
+ * per texel of the constant-size log-polar (LP) buffer generated through the
+ * inverse mapping (Eqs. 3, 10, 11 with the segmented mapping of Eq. 12),
+ * closest-hit / miss shading into the LP buffer, and the inverse-mapping pass
+ * that reconstructs the full-resolution display (Sec. 3.4).  The "GT" of the
+ * paper's evaluation (one ray per display pixel, Sec. 5.2.1 and Table 1) is
+ * provided as the baseline.
+ *
+ * Conventions (every entry point):
+ *  - Return value: VAFR_OK (0) or a negative VAFR_ERR_* code.  No C++
+ *    exception crosses this boundary.  vafr_last_error_message() gives a
+ *    human-readable detail for the calling thread's last failure.
+ *  - Work is asynchronous on the given CUDA stream (passed as void*, a
+ *    cudaStream_t; NULL = legacy default stream).  Device-side faults of the
+ *    method (traversal stack overflow, watchdog) set a per-object status word
+ *    that vafr_session_check / vafr_scene_check read after a stream sync.
+ *  - Ownership: the caller owns every buffer it passes (LP buffers, display
+ *    buffers, hit-id buffers).  The library owns the scene's acceleration
+ *    structure, each session's tables and each batch's graph.
+ *  - Pointers documented "device" must be device memory of the current device.
+ *    Pointers documented "host or device" are classified with
+ *    cudaPointerGetAttributes.
+ *  - Coordinates: display pixels, x right, y down, pixel (i, j) centred at
+ *    (i + 0.5, j + 0.5).  Camera: x right, y up, z forward; a pose is a
+ *    row-major 3x4 [R | t] taking camera to world coordinates.
+ *  - Colours: RGBA, alpha = 1.  VAFR_FMT_RGBA32F = 4 x float (16 B),
+ *    VAFR_FMT_RGBA16F = 4 x IEEE half, round-to-nearest-even (8 B).
+ */
+#ifndef VAFR_H
+#define VAFR_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VAFR_API __attribute__((visibility("default")))
+#else
+#define VAFR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define VAFR_OK               0
+#define VAFR_ERR_INVALID_ARG (-1) /* bad pointer, size, format, eye, NaN gaze  */
+#define VAFR_ERR_OOM         (-2) /* device or host allocation failed          */
+#define VAFR_ERR_CUDA        (-3) /* a CUDA runtime call failed                */
+#define VAFR_ERR_TIMEOUT     (-4) /* a device watchdog (iteration limit) fired */
+#define VAFR_ERR_BUDGET      (-5) /* request exceeds a configured memory budget */
+#define VAFR_ERR_DEVICE      (-6) /* device status word reports a fault        */
+#define VAFR_ERR_UNSUPPORTED (-7) /* no usable sm_103 device                   */
+
+#define VAFR_FMT_RGBA32F 0
+#define VAFR_FMT_RGBA16F 1
+
+#define VAFR_MAX_PIVOTS 9
+#define VAFR_MAX_BATCH  128   /* frame-eyes per batched launch */
+
+typedef struct vafr_scene vafr_scene;
+typedef struct vafr_session vafr_session;
+typedef struct vafr_batch vafr_batch;
+
+/* Acuity pivots of the segmented mapping (Sec. 3.3, Eq. 12): MAR = 1/f is
+ * piecewise linear through (pivot_ecc_deg[k], 1/pivot_cpd[k]);
+ * pivot_ecc_deg[0] must be 0 and strictly increasing; e_max_deg is the
+ * maximum perceivable eccentricity (Sec. 3.2.2). */
+typedef struct {
+    int32_t n_pivots;
+    double  pivot_ecc_deg[VAFR_MAX_PIVOTS];
+    double  pivot_cpd[VAFR_MAX_PIVOTS];
+    double  e_max_deg;
+} vafr_acuity;
+
+/* Fills the paper's pivots: f = 40, 10, 6, 5, 4 cpd at 0, 10, 20, 30, 60 deg
+ * and e_max = 60 deg (Sec. 3.3 and Sec. 3.2.2). */
+VAFR_API void vafr_acuity_default(vafr_acuity* a);
+
+/* A display + viewer.  n_eyes 1 (mono) or 2 (binocular, VaFR_Dup of Sec. 5.1:
+ * each eye rendered independently).  fov_v_deg is the vertical field of view;
+ * c_r = 2 tan(fov_v/2) / height (Sec. 3.2.1). */
+typedef struct {
+    int32_t     width, height;
+    double      fov_v_deg;
+    int32_t     n_eyes;
+    double      eye_pose[2][12];
+    int32_t     lp_format;       /* VAFR_FMT_* of the LP buffer             */
+    int32_t     display_format;  /* VAFR_FMT_* of the reconstructed display */
+    vafr_acuity acuity;
+} vafr_session_desc;
+
+/* One frame-eye of a batched launch. */
+typedef struct {
+    vafr_session* session;
+    int32_t       eye;
+    void*         lp;        /* device, LP buffer of that eye (see vafr_render_lp) */
+    void*         display;   /* device, height x width pixels of display_format     */
+} vafr_frame_desc;
+
+/* ---- errors -------------------------------------------------------------- */
+VAFR_API const char* vafr_error_string(int code);
+VAFR_API const char* vafr_last_error_message(void);
+/* Library version (major*10000 + minor*100 + patch) and the number of
+ * kernels this library launched so far on this process (all devices). */
+VAFR_API int32_t vafr_version(void);
+VAFR_API int64_t vafr_kernel_launch_count(void);
+
+/* ---- scene ---------------------------------------------------------------
+ * vafr_build_scene: builds the ray-casting acceleration structure of a
+ * triangle soup (the paper's closest-hit stage, Sec. 6.1, leaves the
+ * acceleration structure to the API; this library builds an LBVH after
+ * Karras 2012: 30-bit Morton codes of centroids, stable radix sort, binary
+ * radix tree, bottom-up FP32 bounds).
+ *   tri_xyz    host or device, n_tris x 3 vertices x 3 floats (xyz).
+ *   albedo_rgb host or device, n_tris x 3 floats in [0, 1]; NULL = 0.8 grey.
+ *   n_tris     0 <= n_tris < 2^30 (0 gives an empty scene: every ray misses).
+ *   light_dir  host, 3 floats, direction the light travels (normalised here).
+ *   stream     stream for the build; the scene is usable on any stream after
+ *              the build's work on `stream` completes.
+ *   out        receives the handle (library-owned; vafr_scene_destroy).
+ * Errors: INVALID_ARG (NULL tri_xyz with n_tris > 0, n_tris out of range,
+ * non-finite light), OOM, CUDA. */
+VAFR_API int vafr_build_scene(const float* tri_xyz, const float* albedo_rgb, int64_t n_tris,
+                     const float light_dir[3], void* stream, vafr_scene** out);
+VAFR_API int vafr_scene_destroy(vafr_scene* scene);
+/* Triangle count and device bytes held by the scene. */
+VAFR_API int vafr_scene_info(const vafr_scene* scene, int64_t* n_tris, int64_t* device_bytes);
+/* Copies the LBVH build products to HOST buffers (any may be NULL):
+ *   codes      n     uint32 Morton codes, input triangle order
+ *   sorted_ids n     int32 triangle ids in sorted (leaf) order
+ *   child      n-1 x 2 int32: >= 0 internal node, < 0 leaf ~k (k = leaf index)
+ *   node_box   n-1 x 6 float (lo xyz, hi xyz) of internal nodes
+ *   leaf_box   n   x 6 float of leaves (sorted order)
+ * Synchronises the device.  Errors: INVALID_ARG, CUDA. */
+VAFR_API int vafr_scene_export_lbvh(const vafr_scene* scene, uint32_t* codes, int32_t* sorted_ids,
+                           int32_t* child, float* node_box, float* leaf_box);
+/* Synchronises `stream` and reads + clears the scene's device status word.
+ * Returns VAFR_OK, VAFR_ERR_DEVICE or VAFR_ERR_TIMEOUT. */
+VAFR_API int vafr_scene_check(const vafr_scene* scene, void* stream);
+
+/* ---- session --------------------------------------------------------------
+ * vafr_session_create: validates the description and builds, in FP64 on the
+ * host, the discrete LP layout of the acuity model: columns c at
+ * u = c + 0.5 < u(e_max) (Eq. 12), eccentricity e_c by the inverse mapping
+ * (Eq. 10), n_c = max(1, round(l(e_c))) texels per column (Eq. 9), texel
+ * (c, j) at angle (j + 0.5) 360/n_c (Eq. 11).  The layout does not depend on
+ * the display size (Sec. 3.2.2).
+ * Errors: INVALID_ARG (size <= 0 or > 32768, fov outside (0, 170), n_eyes
+ * not 1 or 2, bad pivots, non-finite pose, unknown format), OOM, CUDA. */
+VAFR_API int vafr_session_create(const vafr_session_desc* desc, vafr_session** out);
+VAFR_API int vafr_session_destroy(vafr_session* session);
+/* Copies the LP layout to HOST buffers (any may be NULL): n_cols, n_texels
+ * (per eye), col_counts[n_cols], col_offsets[n_cols] (first texel of each
+ * column; texels are stored column after column), col_ecc_deg[n_cols]
+ * (FP32 eccentricity of each column centre).  Errors: INVALID_ARG. */
+VAFR_API int vafr_lp_layout(const vafr_session* session, int32_t* n_cols, int64_t* n_texels,
+                   int32_t* col_counts, int64_t* col_offsets, float* col_ecc_deg);
+/* Bytes of one eye's LP buffer and of one eye's display in the session's formats. */
+VAFR_API int vafr_session_sizes(const vafr_session* session, int64_t* lp_bytes_per_eye,
+                       int64_t* display_bytes_per_eye);
+/* Reads (set = 0) or writes (set = 1) the kernel variants used by this
+ * session's single-session calls: cfg[0] render variant, cfg[1] reconstruct
+ * tile shape (see vafr_tuning_space).  Results do not depend on the choice.
+ * Errors: INVALID_ARG (NULL, variant out of range). */
+VAFR_API int vafr_session_tuning(vafr_session* session, int32_t set, int32_t cfg[2]);
+/* Sets the gaze point (x0, y0) in display pixels of one eye (Eq. 3).  Any
+ * finite value is accepted (gaze outside the display is legal).  The FP64
+ * per-frame set-up (c_r, gaze tangent offsets, the integer/fraction split of
+ * the gaze used by reconstruction) is done here on the host; the next render
+ * or reconstruct call on the session uses it.  Errors: INVALID_ARG (eye out
+ * of range, NaN/inf). */
+VAFR_API int vafr_set_gaze(vafr_session* session, int32_t eye, double x0, double y0);
+/* Synchronises `stream` and reads + clears the session's device status word. */
+VAFR_API int vafr_session_check(vafr_session* session, void* stream);
+
+/* ---- the hot path ----------------------------------------------------------
+ * vafr_render_lp: for every texel of the eyes in eye_mask (bit e = eye e),
+ * casts the primary ray through the texel's screen point (Eqs. 3, 10, 11),
+ * finds the closest hit (two-sided watertight test, closest t > 0, equal t ->
+ * lower triangle id) and shades it (Lambert, ambient 0.1; sky gradient on a
+ * miss) -- the ray-generation / closest-hit / miss shaders of Sec. 6.1.
+ *   lp_out      device, [popcount(eye_mask)][n_texels] pixels of lp_format,
+ *               eyes in increasing order, texel (c, j) at col_offsets[c] + j.
+ *   hit_ids_out device or NULL, [popcount(eye_mask)][n_texels] int32 triangle
+ *               id of the hit, -1 on a miss.
+ * Errors: INVALID_ARG (NULL lp_out, eye_mask not a subset of the session's
+ * eyes or empty, gaze never set), CUDA. */
+VAFR_API int vafr_render_lp(const vafr_scene* scene, vafr_session* session, int32_t eye_mask,
+                   void* lp_out, int32_t* hit_ids_out, void* stream);
+/* vafr_reconstruct: inverse-mapping pass (Sec. 3.4): every display pixel
+ * (x + 0.5, y + 0.5) maps forward to (u, angle) with r = |p - gaze|,
+ * e = atan(c_r r) clamped to e_max (Eq. 3), u = u(e) (Eq. 12), angle =
+ * atan2(y - y0, x - x0) in [0, 360); the colour is the bilinear blend of
+ * columns floor(u - 0.5), +1 (clamped) and, in each, of rows
+ * floor(angle n_c/360 - 0.5), +1 wrapped modulo n_c.  FP32 arithmetic.
+ *   lp       device, one eye's LP buffer (n_texels pixels of lp_format).
+ *   display  device, height x width pixels of display_format, row-major.
+ * Errors: INVALID_ARG, CUDA. */
+VAFR_API int vafr_reconstruct(vafr_session* session, int32_t eye, const void* lp, void* display_out,
+                     void* stream);
+/* vafr_render_full_gt: the paper's GT (Sec. 5.2.1, Table 1): one ray per
+ * display pixel centre, same traversal and shading, written straight to the
+ * display (display_format).  hit_ids_out: device or NULL, height x width int32.
+ * Errors: INVALID_ARG, CUDA. */
+VAFR_API int vafr_render_full_gt(const vafr_scene* scene, vafr_session* session, int32_t eye,
+                        void* display_out, int32_t* hit_ids_out, void* stream);
+/* vafr_render_frame: one whole frame of the session (render_lp of every eye
+ * into a session-owned LP buffer, then reconstruct every eye).
+ *   display_out  host or device, [n_eyes][height][width] of display_format.
+ *                Host memory (pinned or pageable) is filled by a device->host
+ *                copy on `stream`; the call then synchronises `stream`.
+ * Errors: as vafr_render_lp / vafr_reconstruct, OOM. */
+VAFR_API int vafr_render_frame(const vafr_scene* scene, vafr_session* session, void* display_out,
+                      void* stream);
+/* Traversal statistics of one eye's LP render (an instrumented copy of the
+ * render kernel, never the timed one): out[0] = rays, out[1] = internal
+ * nodes visited, out[2] = triangle tests, out[3] = hits.  Host out[4]. */
+VAFR_API int vafr_traversal_stats(const vafr_scene* scene, vafr_session* session, int32_t eye,
+                         int64_t out[4], void* stream);
+
+/* ---- batching --------------------------------------------------------------
+ * A batch renders many frame-eyes (any mix of sessions, eyes and display
+ * sizes, all on one scene) with ONE persistent render launch over all LP
+ * texels and ONE persistent reconstruct launch over all display tiles.  The
+ * LP and reconstruct work of a frame-eye is the same as vafr_render_lp /
+ * vafr_reconstruct on its session.
+ *   vafr_batch_create   max_frames <= VAFR_MAX_BATCH.
+ *   vafr_batch_render   launches the two kernels directly (no graph).
+ *   vafr_batch_capture  records the two launches for `frames` into a CUDA
+ *                       graph (replaces any earlier graph of the batch).
+ *   vafr_batch_replay   re-reads every captured session's current gaze,
+ *                       patches the graph's kernel parameters and launches it.
+ *   vafr_batch_autotune times the candidate render block shapes and
+ *                       reconstruct tile shapes on `frames` (iters launches
+ *                       each, CUDA events) and keeps the fastest.
+ *   vafr_batch_tuning   reads (set = 0) or writes (set = 1) the choice:
+ *                       cfg[0] render variant, cfg[1] reconstruct variant.
+ * Errors: INVALID_ARG (n out of range, frame with a NULL buffer, eye out of
+ * range, session never given a gaze), CUDA. */
+VAFR_API int vafr_batch_create(const vafr_scene* scene, int32_t max_frames, vafr_batch** out);
+VAFR_API int vafr_batch_destroy(vafr_batch* batch);
+VAFR_API int vafr_batch_render(vafr_batch* batch, const vafr_frame_desc* frames, int32_t n, void* stream);
+VAFR_API int vafr_batch_capture(vafr_batch* batch, const vafr_frame_desc* frames, int32_t n, void* stream);
+VAFR_API int vafr_batch_replay(vafr_batch* batch, void* stream);
+VAFR_API int vafr_batch_autotune(vafr_batch* batch, const vafr_frame_desc* frames, int32_t n,
+                        void* stream, int32_t iters);
+VAFR_API int vafr_batch_tuning(vafr_batch* batch, int32_t set, int32_t cfg[2]);
+/* Number of render / reconstruct variants the autotuner chooses between. */
+VAFR_API int vafr_tuning_space(int32_t* n_render, int32_t* n_reconstruct);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VAFR_H */

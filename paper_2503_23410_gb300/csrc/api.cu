@@ -1,0 +1,891 @@
+// api.cu -- the C ABI of libvafr.so (declared in include/vafr.h): object
+// lifetimes, argument checking, the FP64 host set-up of the log-polar layout
+// (Sec. 3.2.2, Eqs. 9, 10, 12) and of each frame's gaze parameters (Eq. 3),
+// batching, CUDA-graph capture and the tile-shape autotuner.
+#include "vafr_internal.cuh"
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits.h>
+#include <string>
+#include <vector>
+
+using namespace vafr;
+
+namespace vafr {
+static std::atomic<long long> g_launches{0};
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace vafr
+
+namespace {
+
+thread_local std::string g_msg;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_msg = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? VAFR_ERR_OOM : VAFR_ERR_CUDA,  \
+                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int check_device(int* sms) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    cudaDeviceProp p;
+    CUDA_TRY(cudaGetDeviceProperties(&p, dev));
+    if (!(p.major == 10 && p.minor == 3))
+        return fail(VAFR_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a",
+                    dev, p.major, p.minor);
+    if (sms) *sms = p.multiProcessorCount;
+    return VAFR_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int bytes_per_px(int fmt) { return fmt == VAFR_FMT_RGBA16F ? 8 : 16; }
+
+// ---- the acuity mapping, FP64 host side ----------------------------------------
+// MAR omega is piecewise linear through the pivots (E_k, 1/f_k) (Eq. 2 per
+// segment, Sec. 3.3).  On segment i: u(e) = U_i + (2/m_i) ln(1 + m_i (e - E_i) /
+// omega(E_i)) (Eq. 12 with the constants fixed by u(0) = 0 and continuity),
+// e(u) its inverse (Eq. 10), l(e) = 360 sin(2e)/omega(e) (Eq. 9).
+struct Mapping {
+    int n_seg = 0;
+    double E[VAFR_MAX_PIVOTS], m[VAFR_MAX_PIVOTS], w[VAFR_MAX_PIVOTS], U[VAFR_MAX_PIVOTS + 1];
+    double e_max = 60.0;
+
+    int init(const vafr_acuity& a) {
+        if (a.n_pivots < 2 || a.n_pivots > VAFR_MAX_PIVOTS) return -1;
+        if (a.pivot_ecc_deg[0] != 0.0) return -1;
+        for (int k = 0; k < a.n_pivots; ++k) {
+            if (!std::isfinite(a.pivot_ecc_deg[k]) || !(a.pivot_cpd[k] > 0.0) ||
+                !std::isfinite(a.pivot_cpd[k]))
+                return -1;
+            if (k > 0 && !(a.pivot_ecc_deg[k] > a.pivot_ecc_deg[k - 1])) return -1;
+        }
+        if (!(a.e_max_deg > 0.0) || !(a.e_max_deg < 90.0)) return -1;
+        n_seg = a.n_pivots - 1;
+        e_max = a.e_max_deg;
+        U[0] = 0.0;
+        for (int i = 0; i < n_seg; ++i) {
+            E[i] = a.pivot_ecc_deg[i];
+            const double w_lo = 1.0 / a.pivot_cpd[i], w_hi = 1.0 / a.pivot_cpd[i + 1];
+            const double span = a.pivot_ecc_deg[i + 1] - E[i];
+            m[i] = (w_hi - w_lo) / span;
+            w[i] = w_lo - m[i] * E[i];
+            U[i + 1] = U[i] + du(i, span);
+        }
+        E[n_seg] = a.pivot_ecc_deg[n_seg];
+        return 0;
+    }
+    // u gained over `de` degrees from the start of segment i
+    double du(int i, double de) const {
+        const double om0 = m[i] * E[i] + w[i];
+        if (m[i] == 0.0) return 2.0 * de / w[i];
+        return 2.0 / m[i] * std::log1p(m[i] * de / om0);
+    }
+    int seg_e(double e) const {
+        int i = 0;
+        while (i + 1 < n_seg && e >= E[i + 1]) ++i;
+        return i;
+    }
+    double u_of_e(double e) const {
+        const int i = seg_e(e);
+        return U[i] + du(i, e - E[i]);
+    }
+    double e_of_u(double u) const {
+        int i = 0;
+        while (i + 1 < n_seg && u >= U[i + 1]) ++i;
+        const double om0 = m[i] * E[i] + w[i];
+        if (m[i] == 0.0) return E[i] + (u - U[i]) * w[i] / 2.0;
+        return E[i] + std::expm1(m[i] * (u - U[i]) / 2.0) * om0 / m[i];
+    }
+    double l_of_e(double e) const {
+        const int i = seg_e(e);
+        return 360.0 * std::sin(2.0 * e * M_PI / 180.0) / (m[i] * e + w[i]);
+    }
+};
+
+}  // namespace
+
+// ---- objects ----------------------------------------------------------------------
+struct vafr_scene {
+    int device = 0;
+    int sms = 0;
+    int64_t n = 0;
+    std::vector<void*> allocs;
+    int64_t bytes = 0;
+    LbvhBuffers buf{};
+    SceneDev dev{};
+    unsigned* status = nullptr;
+
+    template <class T>
+    int alloc(T** p, size_t count) {
+        const size_t b = sizeof(T) * (count ? count : 1);
+        void* q = nullptr;
+        CUDA_TRY(cudaMalloc(&q, b));
+        allocs.push_back(q);
+        bytes += (int64_t)b;
+        *p = reinterpret_cast<T*>(q);
+        return VAFR_OK;
+    }
+    ~vafr_scene() {
+        for (void* p : allocs) cudaFree(p);
+    }
+};
+
+struct vafr_session {
+    int device = 0;
+    int sms = 0;
+    vafr_session_desc desc{};
+    Mapping map;
+    int n_cols = 0;
+    int64_t n_texels = 0;
+    std::vector<double> e_col;
+    std::vector<int32_t> n_col;
+    std::vector<int64_t> off_col;
+    float* d_tan_e = nullptr;
+    int2* d_col = nullptr;
+    SegTable* d_seg = nullptr;
+    unsigned* d_status = nullptr;
+    unsigned long long* d_counter = nullptr;
+    unsigned long long* d_stats = nullptr;
+    bool gaze_set[2] = {false, false};
+    FrameDesc fd[2]{};
+    void* lp_internal = nullptr;       // render_frame's LP buffer
+    void* disp_internal = nullptr;     // render_frame's device display for host output
+    int recon_variant = 0;
+    int render_variant = 0;
+
+    ~vafr_session() {
+        cudaFree(d_tan_e);
+        cudaFree(d_col);
+        cudaFree(d_seg);
+        cudaFree(d_status);
+        cudaFree(d_counter);
+        cudaFree(d_stats);
+        cudaFree(lp_internal);
+        cudaFree(disp_internal);
+    }
+};
+
+struct vafr_batch {
+    const vafr_scene* scene = nullptr;
+    int max_frames = 0;
+    int render_variant = 0;
+    int recon_variant = 0;
+    unsigned long long* d_counter = nullptr;
+    // captured graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t render_node = nullptr, recon_node = nullptr;
+    cudaKernelNodeParams render_params{}, recon_params{};
+    std::vector<vafr_frame_desc> captured;
+    BigBatch* host_batch = nullptr;  // parameters of the captured launches
+
+    ~vafr_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaFree(d_counter);
+        delete host_batch;
+    }
+};
+
+namespace {
+
+// FP64 per-frame set-up of one eye (Eq. 3): c_r, gaze offsets, gaze split.
+void setup_gaze(vafr_session* s, int eye, double x0, double y0) {
+    const vafr_session_desc& d = s->desc;
+    const double cr = 2.0 * std::tan(0.5 * d.fov_v_deg * M_PI / 180.0) / d.height;
+    FrameDesc& f = s->fd[eye];
+    f.gx = (float)(cr * (x0 - 0.5 * d.width));
+    f.gy = (float)(cr * (0.5 * d.height - y0));
+    const double fx = std::floor(x0), fy = std::floor(y0);
+    f.gxi = (int)fx;
+    f.gyi = (int)fy;
+    f.gxf = (float)(0.5 - (x0 - fx));
+    f.gyf = (float)(0.5 - (y0 - fy));
+    s->gaze_set[eye] = true;
+}
+
+void fill_static(vafr_session* s, int eye) {
+    const vafr_session_desc& d = s->desc;
+    FrameDesc& f = s->fd[eye];
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) f.R[3 * r + c] = (float)d.eye_pose[eye][4 * r + c];
+        f.org[r] = (float)d.eye_pose[eye][4 * r + 3];
+    }
+    const double cr = 2.0 * std::tan(0.5 * d.fov_v_deg * M_PI / 180.0) / d.height;
+    f.cr = (float)cr;
+    f.px0 = (float)(cr * (0.5 - 0.5 * d.width));
+    f.py0 = (float)(cr * (0.5 * d.height - 0.5));
+    f.W = d.width;
+    f.H = d.height;
+    f.lp_fmt = d.lp_format;
+    f.disp_fmt = d.display_format;
+    f.seg = s->d_seg;
+    f.tan_e = s->d_tan_e;
+    f.col = s->d_col;
+    f.n_cols = s->n_cols;
+    f.n_texels = (int)s->n_texels;
+    f.status = s->d_status;
+    f.lp = nullptr;
+    f.disp = nullptr;
+    f.hit_ids = nullptr;
+}
+
+long long recon_tiles(const FrameDesc& f, int variant) {
+    const ReconShape sh = recon_shape(variant);
+    return (long long)((f.W + sh.tw - 1) / sh.tw) * ((f.H + sh.th - 1) / sh.th);
+}
+
+long long gt_items(const FrameDesc& f) {
+    return (long long)((f.W + 7) / 8) * ((f.H + 3) / 4) * 32;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+const char* vafr_error_string(int code) {
+    switch (code) {
+        case VAFR_OK: return "ok";
+        case VAFR_ERR_INVALID_ARG: return "invalid argument";
+        case VAFR_ERR_OOM: return "out of memory";
+        case VAFR_ERR_CUDA: return "CUDA error";
+        case VAFR_ERR_TIMEOUT: return "device watchdog fired";
+        case VAFR_ERR_BUDGET: return "memory budget exceeded";
+        case VAFR_ERR_DEVICE: return "device fault reported";
+        case VAFR_ERR_UNSUPPORTED: return "unsupported device";
+        default: return "unknown error";
+    }
+}
+
+const char* vafr_last_error_message(void) { return g_msg.c_str(); }
+
+int32_t vafr_version(void) { return 10000; }
+
+int64_t vafr_kernel_launch_count(void) { return g_launches.load(); }
+
+void vafr_acuity_default(vafr_acuity* a) {
+    if (!a) return;
+    std::memset(a, 0, sizeof(*a));
+    const double E[5] = {0, 10, 20, 30, 60}, f[5] = {40, 10, 6, 5, 4};
+    a->n_pivots = 5;
+    for (int k = 0; k < 5; ++k) { a->pivot_ecc_deg[k] = E[k]; a->pivot_cpd[k] = f[k]; }
+    a->e_max_deg = 60.0;
+}
+
+// ---- scene ---------------------------------------------------------------------------
+int vafr_build_scene(const float* tri_xyz, const float* albedo_rgb, int64_t n_tris,
+                     const float light_dir[3], void* stream, vafr_scene** out) {
+    if (!out) return fail(VAFR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_tris < 0 || n_tris >= (1ll << 30)) return fail(VAFR_ERR_INVALID_ARG, "n_tris out of range");
+    if (n_tris > 0 && !tri_xyz) return fail(VAFR_ERR_INVALID_ARG, "tri_xyz is NULL");
+    if (!light_dir) return fail(VAFR_ERR_INVALID_ARG, "light_dir is NULL");
+    const double ll = std::sqrt((double)light_dir[0] * light_dir[0] + (double)light_dir[1] * light_dir[1] +
+                                (double)light_dir[2] * light_dir[2]);
+    if (!std::isfinite(ll) || !(ll > 0.0)) return fail(VAFR_ERR_INVALID_ARG, "light_dir not finite/non-zero");
+    int sms = 0;
+    int rc = check_device(&sms);
+    if (rc) return rc;
+    cudaStream_t s = as_stream(stream);
+    auto* sc = new vafr_scene();
+    cudaGetDevice(&sc->device);
+    sc->sms = sms;
+    sc->n = n_tris;
+    const int n = (int)n_tris;
+    LbvhBuffers& b = sc->buf;
+    b.n = n;
+    float* tris = nullptr;
+    float* alb = nullptr;
+    const size_t nb = lbvh_sort_blocks(n);
+#define ALLOC(p, c)                              \
+    do {                                         \
+        int r_ = sc->alloc(&(p), (size_t)(c));   \
+        if (r_) { delete sc; return r_; }        \
+    } while (0)
+    ALLOC(sc->status, 1);
+    if (n > 0) {
+        ALLOC(tris, 9ll * n);
+        if (albedo_rgb) ALLOC(alb, 3ll * n);
+        ALLOC(b.codes, n);
+        ALLOC(b.keys_tmp, n);
+        ALLOC(b.ids, n);
+        ALLOC(b.ids_tmp, n);
+        ALLOC(b.keys_sorted, n);
+        ALLOC(b.hist, 256 * nb);
+        ALLOC(b.part_bounds, 6 * 304);
+        ALLOC(b.scene_bounds, 6);
+        ALLOC(b.child, n > 1 ? n - 1 : 1);
+        ALLOC(b.parent, 2ll * n);
+        ALLOC(b.flags, n > 1 ? n - 1 : 1);
+        ALLOC(b.node_box, 6ll * (n > 1 ? n - 1 : 1));
+        ALLOC(b.leaf_box, 6ll * n);
+        ALLOC(b.nodes, 4ll * (n > 1 ? n - 1 : 1));
+        ALLOC(b.leaves, 3ll * n);
+        ALLOC(b.albedo4, n);
+    }
+#undef ALLOC
+    auto bail = [&](int code) { delete sc; return code; };
+    if (cudaMemsetAsync(sc->status, 0, sizeof(unsigned), s) != cudaSuccess)
+        return bail(fail(VAFR_ERR_CUDA, "memset status"));
+    if (n > 0) {
+        const cudaMemcpyKind k1 = is_device_ptr(tri_xyz) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        cudaError_t e = cudaMemcpyAsync(tris, tri_xyz, sizeof(float) * 9ull * n, k1, s);
+        if (e == cudaSuccess && albedo_rgb) {
+            const cudaMemcpyKind k2 = is_device_ptr(albedo_rgb) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+            e = cudaMemcpyAsync(alb, albedo_rgb, sizeof(float) * 3ull * n, k2, s);
+        }
+        if (e != cudaSuccess) return bail(fail(VAFR_ERR_CUDA, "input copy: %s", cudaGetErrorString(e)));
+        b.tris = tris;
+        b.albedo = alb;
+        e = lbvh_build(b, s);
+        if (e != cudaSuccess) return bail(fail(VAFR_ERR_CUDA, "lbvh build: %s", cudaGetErrorString(e)));
+    }
+    SceneDev& d = sc->dev;
+    d.nodes = b.nodes;
+    d.leaves = b.leaves;
+    d.albedo = b.albedo4;
+    d.n_tris = n;
+    d.root = n == 0 ? INT_MIN : (n == 1 ? ~0 : 0);
+    for (int k = 0; k < 3; ++k) d.light[k] = (float)(light_dir[k] / ll);
+    d.status = sc->status;
+    *out = sc;
+    return VAFR_OK;
+}
+
+int vafr_scene_destroy(vafr_scene* scene) {
+    if (!scene) return VAFR_OK;
+    cudaDeviceSynchronize();
+    delete scene;
+    return VAFR_OK;
+}
+
+int vafr_scene_info(const vafr_scene* scene, int64_t* n_tris, int64_t* device_bytes) {
+    if (!scene) return fail(VAFR_ERR_INVALID_ARG, "scene is NULL");
+    if (n_tris) *n_tris = scene->n;
+    if (device_bytes) *device_bytes = scene->bytes;
+    return VAFR_OK;
+}
+
+int vafr_scene_export_lbvh(const vafr_scene* scene, uint32_t* codes, int32_t* sorted_ids,
+                           int32_t* child, float* node_box, float* leaf_box) {
+    if (!scene) return fail(VAFR_ERR_INVALID_ARG, "scene is NULL");
+    const int64_t n = scene->n;
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (n == 0) return VAFR_OK;
+    const LbvhBuffers& b = scene->buf;
+    if (codes) CUDA_TRY(cudaMemcpy(codes, b.codes, 4ull * n, cudaMemcpyDeviceToHost));
+    if (sorted_ids) CUDA_TRY(cudaMemcpy(sorted_ids, b.ids, 4ull * n, cudaMemcpyDeviceToHost));
+    if (n > 1 && child) CUDA_TRY(cudaMemcpy(child, b.child, 8ull * (n - 1), cudaMemcpyDeviceToHost));
+    if (n > 1 && node_box) CUDA_TRY(cudaMemcpy(node_box, b.node_box, 24ull * (n - 1), cudaMemcpyDeviceToHost));
+    if (leaf_box) CUDA_TRY(cudaMemcpy(leaf_box, b.leaf_box, 24ull * n, cudaMemcpyDeviceToHost));
+    return VAFR_OK;
+}
+
+int vafr_scene_check(const vafr_scene* scene, void* stream) {
+    if (!scene) return fail(VAFR_ERR_INVALID_ARG, "scene is NULL");
+    CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    unsigned st = 0;
+    CUDA_TRY(cudaMemcpy(&st, scene->status, sizeof(st), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(scene->status, 0, sizeof(unsigned)));
+    if (st & kFaultWatchdog) return fail(VAFR_ERR_TIMEOUT, "scene status 0x%x", st);
+    if (st) return fail(VAFR_ERR_DEVICE, "scene status 0x%x", st);
+    return VAFR_OK;
+}
+
+// ---- session -------------------------------------------------------------------------
+int vafr_session_create(const vafr_session_desc* desc, vafr_session** out) {
+    if (!desc || !out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    const vafr_session_desc& d = *desc;
+    if (d.width <= 0 || d.height <= 0 || d.width > 32768 || d.height > 32768)
+        return fail(VAFR_ERR_INVALID_ARG, "display size %dx%d out of range", d.width, d.height);
+    if (!(d.fov_v_deg > 0.0 && d.fov_v_deg < 170.0)) return fail(VAFR_ERR_INVALID_ARG, "fov out of range");
+    if (d.n_eyes != 1 && d.n_eyes != 2) return fail(VAFR_ERR_INVALID_ARG, "n_eyes must be 1 or 2");
+    if ((d.lp_format != VAFR_FMT_RGBA32F && d.lp_format != VAFR_FMT_RGBA16F) ||
+        (d.display_format != VAFR_FMT_RGBA32F && d.display_format != VAFR_FMT_RGBA16F))
+        return fail(VAFR_ERR_INVALID_ARG, "unknown format");
+    for (int e = 0; e < d.n_eyes; ++e)
+        for (int k = 0; k < 12; ++k)
+            if (!std::isfinite(d.eye_pose[e][k])) return fail(VAFR_ERR_INVALID_ARG, "pose not finite");
+    int sms = 0;
+    int rc = check_device(&sms);
+    if (rc) return rc;
+    auto* s = new vafr_session();
+    cudaGetDevice(&s->device);
+    s->sms = sms;
+    s->desc = d;
+    if (s->map.init(d.acuity) != 0) {
+        delete s;
+        return fail(VAFR_ERR_INVALID_ARG, "bad acuity pivots");
+    }
+    // discrete layout (Sec. 3.2.2): columns at u = c + 0.5 < u(e_max)
+    const double u_max = s->map.u_of_e(s->map.e_max);
+    int64_t acc = 0;
+    for (int c = 0; (double)c + 0.5 < u_max; ++c) {
+        const double e = s->map.e_of_u((double)c + 0.5);
+        int32_t nc = (int32_t)std::floor(s->map.l_of_e(e) + 0.5);
+        if (nc < 1) nc = 1;
+        s->e_col.push_back(e);
+        s->n_col.push_back(nc);
+        s->off_col.push_back(acc);
+        acc += nc;
+        if (acc > (1ll << 30)) {
+            delete s;
+            return fail(VAFR_ERR_INVALID_ARG, "LP layout too large");
+        }
+    }
+    s->n_cols = (int)s->e_col.size();
+    s->n_texels = acc;
+    if (s->n_cols == 0) {
+        delete s;
+        return fail(VAFR_ERR_INVALID_ARG, "empty LP layout");
+    }
+    std::vector<float> tan_e(s->n_cols);
+    std::vector<int2> col(s->n_cols);
+    for (int c = 0; c < s->n_cols; ++c) {
+        tan_e[c] = (float)std::tan(s->e_col[c] * M_PI / 180.0);
+        col[c] = make_int2((int)s->off_col[c], s->n_col[c]);
+    }
+    SegTable seg{};
+    seg.n_seg = s->map.n_seg;
+    for (int i = 0; i < s->map.n_seg; ++i) {
+        const double om0 = s->map.m[i] * s->map.E[i] + s->map.w[i];
+        seg.seg_e0[i] = (float)s->map.E[i];
+        seg.seg_u0[i] = (float)s->map.U[i];
+        if (s->map.m[i] == 0.0) {
+            seg.seg_k[i] = 0.0f;
+            seg.seg_a[i] = 0.0f;
+            seg.seg_b[i] = (float)(2.0 / s->map.w[i]);
+        } else {
+            seg.seg_k[i] = (float)(2.0 * M_LN2 / s->map.m[i]);
+            seg.seg_a[i] = (float)(s->map.m[i] / om0);
+            seg.seg_b[i] = 0.0f;
+        }
+    }
+    seg.e_max = (float)s->map.e_max;
+    auto bail = [&](cudaError_t e) {
+        delete s;
+        return fail(e == cudaErrorMemoryAllocation ? VAFR_ERR_OOM : VAFR_ERR_CUDA, "session: %s",
+                    cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&s->d_tan_e, sizeof(float) * s->n_cols)) != cudaSuccess) return bail(e);
+    if ((e = cudaMalloc(&s->d_col, sizeof(int2) * s->n_cols)) != cudaSuccess) return bail(e);
+    if ((e = cudaMalloc(&s->d_seg, sizeof(SegTable))) != cudaSuccess) return bail(e);
+    if ((e = cudaMalloc(&s->d_status, sizeof(unsigned))) != cudaSuccess) return bail(e);
+    if ((e = cudaMalloc(&s->d_counter, sizeof(unsigned long long))) != cudaSuccess) return bail(e);
+    if ((e = cudaMalloc(&s->d_stats, 4 * sizeof(unsigned long long))) != cudaSuccess) return bail(e);
+    if ((e = cudaMemcpy(s->d_tan_e, tan_e.data(), sizeof(float) * s->n_cols, cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e);
+    if ((e = cudaMemcpy(s->d_col, col.data(), sizeof(int2) * s->n_cols, cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e);
+    if ((e = cudaMemcpy(s->d_seg, &seg, sizeof(SegTable), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e);
+    if ((e = cudaMemset(s->d_status, 0, sizeof(unsigned))) != cudaSuccess) return bail(e);
+    for (int eye = 0; eye < d.n_eyes; ++eye) fill_static(s, eye);
+    *out = s;
+    return VAFR_OK;
+}
+
+int vafr_session_destroy(vafr_session* session) {
+    if (!session) return VAFR_OK;
+    cudaDeviceSynchronize();
+    delete session;
+    return VAFR_OK;
+}
+
+int vafr_lp_layout(const vafr_session* s, int32_t* n_cols, int64_t* n_texels, int32_t* col_counts,
+                   int64_t* col_offsets, float* col_ecc_deg) {
+    if (!s) return fail(VAFR_ERR_INVALID_ARG, "session is NULL");
+    if (n_cols) *n_cols = s->n_cols;
+    if (n_texels) *n_texels = s->n_texels;
+    for (int c = 0; c < s->n_cols; ++c) {
+        if (col_counts) col_counts[c] = s->n_col[c];
+        if (col_offsets) col_offsets[c] = s->off_col[c];
+        if (col_ecc_deg) col_ecc_deg[c] = (float)s->e_col[c];
+    }
+    return VAFR_OK;
+}
+
+int vafr_session_sizes(const vafr_session* s, int64_t* lp_bytes, int64_t* disp_bytes) {
+    if (!s) return fail(VAFR_ERR_INVALID_ARG, "session is NULL");
+    if (lp_bytes) *lp_bytes = s->n_texels * bytes_per_px(s->desc.lp_format);
+    if (disp_bytes) *disp_bytes = (int64_t)s->desc.width * s->desc.height * bytes_per_px(s->desc.display_format);
+    return VAFR_OK;
+}
+
+int vafr_session_tuning(vafr_session* s, int32_t set, int32_t cfg[2]) {
+    if (!s || !cfg) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    if (set) {
+        if (cfg[0] < 0 || cfg[0] >= kNumRenderVariants || cfg[1] < 0 || cfg[1] >= kNumReconVariants)
+            return fail(VAFR_ERR_INVALID_ARG, "variant out of range");
+        s->render_variant = cfg[0];
+        s->recon_variant = cfg[1];
+    } else {
+        cfg[0] = s->render_variant;
+        cfg[1] = s->recon_variant;
+    }
+    return VAFR_OK;
+}
+
+int vafr_set_gaze(vafr_session* s, int32_t eye, double x0, double y0) {
+    if (!s) return fail(VAFR_ERR_INVALID_ARG, "session is NULL");
+    if (eye < 0 || eye >= s->desc.n_eyes) return fail(VAFR_ERR_INVALID_ARG, "eye %d out of range", eye);
+    if (!std::isfinite(x0) || !std::isfinite(y0) || std::fabs(x0) > 1e7 || std::fabs(y0) > 1e7)
+        return fail(VAFR_ERR_INVALID_ARG, "gaze must be finite and |gaze| <= 1e7");
+    setup_gaze(s, eye, x0, y0);
+    return VAFR_OK;
+}
+
+int vafr_session_check(vafr_session* s, void* stream) {
+    if (!s) return fail(VAFR_ERR_INVALID_ARG, "session is NULL");
+    CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    unsigned st = 0;
+    CUDA_TRY(cudaMemcpy(&st, s->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(s->d_status, 0, sizeof(unsigned)));
+    if (st & kFaultWatchdog) return fail(VAFR_ERR_TIMEOUT, "session status 0x%x", st);
+    if (st) return fail(VAFR_ERR_DEVICE, "session status 0x%x", st);
+    return VAFR_OK;
+}
+
+// ---- hot path ---------------------------------------------------------------------------
+int vafr_render_lp(const vafr_scene* scene, vafr_session* s, int32_t eye_mask, void* lp_out,
+                   int32_t* hit_ids_out, void* stream) {
+    if (!scene || !s || !lp_out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    const int all = (1 << s->desc.n_eyes) - 1;
+    if (eye_mask <= 0 || (eye_mask & ~all)) return fail(VAFR_ERR_INVALID_ARG, "bad eye_mask %d", eye_mask);
+    if (!aligned(lp_out, 16) || !aligned(hit_ids_out, 4)) return fail(VAFR_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    SmallBatch b{};
+    b.work_counter = s->d_counter;
+    const int bpp = bytes_per_px(s->desc.lp_format);
+    for (int eye = 0; eye < s->desc.n_eyes; ++eye) {
+        if (!(eye_mask & (1 << eye))) continue;
+        if (!s->gaze_set[eye]) return fail(VAFR_ERR_INVALID_ARG, "gaze of eye %d never set", eye);
+        FrameDesc f = s->fd[eye];
+        f.lp = static_cast<char*>(lp_out) + (size_t)b.n * s->n_texels * bpp;
+        f.hit_ids = hit_ids_out ? hit_ids_out + (size_t)b.n * s->n_texels : nullptr;
+        f.work_begin = b.total_work;
+        b.total_work += s->n_texels;
+        b.d[b.n++] = f;
+    }
+    CUDA_TRY(launch_render_lp(scene->dev, b, s->render_variant, as_stream(stream), s->sms));
+    return VAFR_OK;
+}
+
+int vafr_reconstruct(vafr_session* s, int32_t eye, const void* lp, void* display_out, void* stream) {
+    if (!s || !lp || !display_out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    if (eye < 0 || eye >= s->desc.n_eyes) return fail(VAFR_ERR_INVALID_ARG, "eye %d out of range", eye);
+    if (!s->gaze_set[eye]) return fail(VAFR_ERR_INVALID_ARG, "gaze of eye %d never set", eye);
+    if (!aligned(lp, 16) || !aligned(display_out, 16)) return fail(VAFR_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    SmallBatch b{};
+    FrameDesc f = s->fd[eye];
+    f.lp = const_cast<void*>(lp);
+    f.disp = display_out;
+    f.tile_begin = 0;
+    b.d[0] = f;
+    b.n = 1;
+    b.total_tiles = recon_tiles(f, s->recon_variant);
+    CUDA_TRY(launch_reconstruct(b, s->recon_variant, as_stream(stream)));
+    return VAFR_OK;
+}
+
+int vafr_render_full_gt(const vafr_scene* scene, vafr_session* s, int32_t eye, void* display_out,
+                        int32_t* hit_ids_out, void* stream) {
+    if (!scene || !s || !display_out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    if (eye < 0 || eye >= s->desc.n_eyes) return fail(VAFR_ERR_INVALID_ARG, "eye %d out of range", eye);
+    if (!aligned(display_out, 16) || !aligned(hit_ids_out, 4)) return fail(VAFR_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    SmallBatch b{};
+    b.work_counter = s->d_counter;
+    FrameDesc f = s->fd[eye];   // GT needs no gaze: c_r and the pose only
+    f.disp = display_out;
+    f.hit_ids = hit_ids_out;
+    f.work_begin = 0;
+    b.d[0] = f;
+    b.n = 1;
+    b.total_work = gt_items(f);
+    CUDA_TRY(launch_render_gt(scene->dev, b, s->render_variant, as_stream(stream), s->sms));
+    return VAFR_OK;
+}
+
+int vafr_render_frame(const vafr_scene* scene, vafr_session* s, void* display_out, void* stream) {
+    if (!scene || !s || !display_out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    const int eyes = s->desc.n_eyes;
+    int64_t lpb = 0, dpb = 0;
+    vafr_session_sizes(s, &lpb, &dpb);
+    if (!s->lp_internal) CUDA_TRY(cudaMalloc(&s->lp_internal, (size_t)lpb * eyes));
+    const bool host = !is_device_ptr(display_out);
+    if (host && !s->disp_internal) CUDA_TRY(cudaMalloc(&s->disp_internal, (size_t)dpb * eyes));
+    if (!host && !aligned(display_out, 16)) return fail(VAFR_ERR_INVALID_ARG, "display must be 16-byte aligned");
+    void* disp = host ? s->disp_internal : display_out;
+    int rc = vafr_render_lp(scene, s, (1 << eyes) - 1, s->lp_internal, nullptr, stream);
+    if (rc) return rc;
+    for (int e = 0; e < eyes; ++e) {
+        rc = vafr_reconstruct(s, e, static_cast<char*>(s->lp_internal) + (size_t)e * lpb,
+                              static_cast<char*>(disp) + (size_t)e * dpb, stream);
+        if (rc) return rc;
+    }
+    if (host) {
+        CUDA_TRY(cudaMemcpyAsync(display_out, disp, (size_t)dpb * eyes, cudaMemcpyDeviceToHost,
+                                 as_stream(stream)));
+        CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    }
+    return VAFR_OK;
+}
+
+int vafr_traversal_stats(const vafr_scene* scene, vafr_session* s, int32_t eye, int64_t out[4],
+                         void* stream) {
+    if (!scene || !s || !out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    if (eye < 0 || eye >= s->desc.n_eyes || !s->gaze_set[eye])
+        return fail(VAFR_ERR_INVALID_ARG, "bad eye or gaze not set");
+    SmallBatch b{};
+    FrameDesc f = s->fd[eye];
+    f.work_begin = 0;
+    b.d[0] = f;
+    b.n = 1;
+    b.total_work = s->n_texels;
+    cudaStream_t st = as_stream(stream);
+    CUDA_TRY(launch_render_stats(scene->dev, b, s->d_stats, st, s->sms));
+    unsigned long long h[4];
+    CUDA_TRY(cudaMemcpyAsync(h, s->d_stats, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int k = 0; k < 4; ++k) out[k] = (int64_t)h[k];
+    return VAFR_OK;
+}
+
+// ---- batching ----------------------------------------------------------------------------
+static int build_batch(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, BigBatch* b) {
+    if (!frames || n <= 0 || n > bt->max_frames)
+        return fail(VAFR_ERR_INVALID_ARG, "frame count %d out of range (max %d)", n, bt->max_frames);
+    std::memset(b, 0, sizeof(*b));
+    b->work_counter = bt->d_counter;
+    for (int i = 0; i < n; ++i) {
+        const vafr_frame_desc& fr = frames[i];
+        vafr_session* s = fr.session;
+        if (!s || !fr.lp || !fr.display) return fail(VAFR_ERR_INVALID_ARG, "frame %d: NULL session/buffer", i);
+        if (fr.eye < 0 || fr.eye >= s->desc.n_eyes) return fail(VAFR_ERR_INVALID_ARG, "frame %d: bad eye", i);
+        if (!s->gaze_set[fr.eye]) return fail(VAFR_ERR_INVALID_ARG, "frame %d: gaze never set", i);
+        if (!aligned(fr.lp, 16) || !aligned(fr.display, 16)) return fail(VAFR_ERR_INVALID_ARG, "frame %d: unaligned buffer", i);
+        FrameDesc f = s->fd[fr.eye];
+        f.lp = fr.lp;
+        f.disp = fr.display;
+        f.hit_ids = nullptr;
+        f.work_begin = b->total_work;
+        f.tile_begin = b->total_tiles;
+        b->total_work += s->n_texels;
+        b->total_tiles += recon_tiles(f, bt->recon_variant);
+        b->d[i] = f;
+    }
+    b->n = n;
+    return VAFR_OK;
+}
+
+static int launch_batch(vafr_batch* bt, const BigBatch& b, cudaStream_t st) {
+    CUDA_TRY(launch_render_lp(bt->scene->dev, b, bt->render_variant, st, bt->scene->sms));
+    CUDA_TRY(launch_reconstruct(b, bt->recon_variant, st));
+    return VAFR_OK;
+}
+
+int vafr_batch_create(const vafr_scene* scene, int32_t max_frames, vafr_batch** out) {
+    if (!scene || !out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    if (max_frames <= 0 || max_frames > VAFR_MAX_BATCH)
+        return fail(VAFR_ERR_INVALID_ARG, "max_frames out of range");
+    auto* bt = new vafr_batch();
+    bt->scene = scene;
+    bt->max_frames = max_frames;
+    if (cudaMalloc(&bt->d_counter, sizeof(unsigned long long)) != cudaSuccess) {
+        delete bt;
+        return fail(VAFR_ERR_OOM, "batch counter");
+    }
+    bt->host_batch = new BigBatch();
+    *out = bt;
+    return VAFR_OK;
+}
+
+int vafr_batch_destroy(vafr_batch* batch) {
+    if (!batch) return VAFR_OK;
+    cudaDeviceSynchronize();
+    delete batch;
+    return VAFR_OK;
+}
+
+int vafr_batch_render(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream) {
+    if (!bt) return fail(VAFR_ERR_INVALID_ARG, "batch is NULL");
+    BigBatch* b = new BigBatch();
+    int rc = build_batch(bt, frames, n, b);
+    if (!rc) rc = launch_batch(bt, *b, as_stream(stream));
+    delete b;
+    return rc;
+}
+
+int vafr_batch_capture(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream) {
+    if (!bt) return fail(VAFR_ERR_INVALID_ARG, "batch is NULL");
+    int rc = build_batch(bt, frames, n, bt->host_batch);
+    if (rc) return rc;
+    if (bt->exec) { cudaGraphExecDestroy(bt->exec); bt->exec = nullptr; }
+    if (bt->graph) { cudaGraphDestroy(bt->graph); bt->graph = nullptr; }
+    cudaStream_t cs = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = launch_batch(bt, *bt->host_batch, cs);
+        e = cudaStreamEndCapture(cs, &bt->graph);
+    }
+    cudaStreamDestroy(cs);
+    if (rc) return rc;
+    CUDA_TRY(e);
+    CUDA_TRY(cudaGraphInstantiate(&bt->exec, bt->graph, 0));
+    // locate the two kernel nodes (capture order: memset -> render -> reconstruct)
+    size_t nn = 0;
+    CUDA_TRY(cudaGraphGetNodes(bt->graph, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    CUDA_TRY(cudaGraphGetNodes(bt->graph, nodes.data(), &nn));
+    bt->render_node = bt->recon_node = nullptr;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        CUDA_TRY(cudaGraphNodeGetType(nd, &ty));
+        if (ty != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams p{};
+        CUDA_TRY(cudaGraphKernelNodeGetParams(nd, &p));
+        size_t ndep = 0;
+        CUDA_TRY(cudaGraphNodeGetDependencies(nd, nullptr, nullptr, &ndep));
+        std::vector<cudaGraphNode_t> deps(ndep);
+        if (ndep) CUDA_TRY(cudaGraphNodeGetDependencies(nd, deps.data(), nullptr, &ndep));
+        bool after_kernel = false;
+        for (cudaGraphNode_t dn : deps) {
+            cudaGraphNodeType dt;
+            CUDA_TRY(cudaGraphNodeGetType(dn, &dt));
+            if (dt == cudaGraphNodeTypeKernel) after_kernel = true;
+        }
+        if (after_kernel) { bt->recon_node = nd; bt->recon_params = p; }
+        else { bt->render_node = nd; bt->render_params = p; }
+    }
+    if (!bt->render_node || !bt->recon_node) return fail(VAFR_ERR_CUDA, "graph: kernel nodes not found");
+    bt->captured.assign(frames, frames + n);
+    return VAFR_OK;
+}
+
+int vafr_batch_replay(vafr_batch* bt, void* stream) {
+    if (!bt || !bt->exec) return fail(VAFR_ERR_INVALID_ARG, "batch has no captured graph");
+    // refresh the per-frame gaze fields from the sessions (FP64 set-up already
+    // done by vafr_set_gaze), keep everything else as captured
+    BigBatch* b = bt->host_batch;
+    for (int i = 0; i < b->n; ++i) {
+        const vafr_frame_desc& fr = bt->captured[i];
+        const FrameDesc& src = fr.session->fd[fr.eye];
+        FrameDesc& f = b->d[i];
+        f.gx = src.gx; f.gy = src.gy;
+        f.gxi = src.gxi; f.gyi = src.gyi; f.gxf = src.gxf; f.gyf = src.gyf;
+    }
+    SceneDev sc = bt->scene->dev;
+    void* rargs[2] = {&sc, b};
+    void* cargs[1] = {b};
+    cudaKernelNodeParams rp = bt->render_params, cp = bt->recon_params;
+    rp.kernelParams = rargs;
+    rp.extra = nullptr;
+    cp.kernelParams = cargs;
+    cp.extra = nullptr;
+    CUDA_TRY(cudaGraphExecKernelNodeSetParams(bt->exec, bt->render_node, &rp));
+    CUDA_TRY(cudaGraphExecKernelNodeSetParams(bt->exec, bt->recon_node, &cp));
+    CUDA_TRY(cudaGraphLaunch(bt->exec, as_stream(stream)));
+    count_launch(2);
+    return VAFR_OK;
+}
+
+int vafr_tuning_space(int32_t* n_render, int32_t* n_reconstruct) {
+    if (n_render) *n_render = kNumRenderVariants;
+    if (n_reconstruct) *n_reconstruct = kNumReconVariants;
+    return VAFR_OK;
+}
+
+int vafr_batch_tuning(vafr_batch* bt, int32_t set, int32_t cfg[2]) {
+    if (!bt || !cfg) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    if (set) {
+        if (cfg[0] < 0 || cfg[0] >= kNumRenderVariants || cfg[1] < 0 || cfg[1] >= kNumReconVariants)
+            return fail(VAFR_ERR_INVALID_ARG, "variant out of range");
+        bt->render_variant = cfg[0];
+        bt->recon_variant = cfg[1];
+    } else {
+        cfg[0] = bt->render_variant;
+        cfg[1] = bt->recon_variant;
+    }
+    return VAFR_OK;
+}
+
+int vafr_batch_autotune(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream,
+                        int32_t iters) {
+    if (!bt) return fail(VAFR_ERR_INVALID_ARG, "batch is NULL");
+    if (iters <= 0) iters = 3;
+    cudaStream_t st = as_stream(stream);
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    BigBatch* b = new BigBatch();
+    int rc = VAFR_OK;
+    auto time_it = [&](auto&& launch) -> float {
+        if (launch() != cudaSuccess) return INFINITY;
+        cudaEventRecord(e0, st);
+        for (int i = 0; i < iters; ++i) launch();
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    float best = INFINITY;
+    int best_v = 0;
+    const int keep_recon = bt->recon_variant;
+    for (int v = 0; v < kNumRenderVariants && !rc; ++v) {
+        rc = build_batch(bt, frames, n, b);
+        if (rc) break;
+        const float ms = time_it([&] { return launch_render_lp(bt->scene->dev, *b, v, st, bt->scene->sms); });
+        if (ms < best) { best = ms; best_v = v; }
+    }
+    bt->render_variant = best_v;
+    best = INFINITY;
+    best_v = keep_recon;
+    for (int v = 0; v < kNumReconVariants && !rc; ++v) {
+        bt->recon_variant = v;
+        rc = build_batch(bt, frames, n, b);
+        if (rc) break;
+        const float ms = time_it([&] { return launch_reconstruct(*b, v, st); });
+        if (ms < best) { best = ms; best_v = v; }
+    }
+    bt->recon_variant = best_v;
+    delete b;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = fail(VAFR_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+    }
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,360 @@
+// lbvh.cu -- LBVH construction on the GPU (Karras 2012, "Maximizing Parallelism
+// in the Construction of BVHs, Octrees, and k-d Trees"):
+//   1. scene bounds of the triangle centroid sums s = (v0 + v1) + v2,
+//   2. 30-bit Morton codes of s quantised to 1024 cells per axis,
+//   3. stable LSD radix sort of (code, triangle id), 4 passes of 8 bits,
+//   4. binary radix tree: one thread per internal node,
+//   5. bottom-up FP32 bounds with one arrival counter per internal node,
+//   6. packing into the 64-byte two-child traversal node + 48-byte leaves.
+// The quantisation uses explicitly rounded intrinsics (no FMA contraction) so
+// the codes are bit-identical to any IEEE FP32 evaluation of the same sequence.
+// No kernel here waits on another thread: there is nothing that can spin.
+#include "vafr_internal.cuh"
+
+#include <float.h>
+
+namespace vafr {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kBoundsBlocks = 304;
+
+__device__ __forceinline__ float centroid_sum(const float* t, int k) {
+    return __fadd_rn(__fadd_rn(t[k], t[3 + k]), t[6 + k]);
+}
+
+__global__ void k_bounds_partial(const float* __restrict__ tris, int n, float* __restrict__ part) {
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float* t = tris + 9ll * i;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float s = centroid_sum(t, k);
+            lo[k] = fminf(lo[k], s);
+            hi[k] = fmaxf(hi[k], s);
+        }
+    }
+    __shared__ float red[6][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    }
+    if (lane == 0) {
+        for (int k = 0; k < 3; ++k) { red[k][warp] = lo[k]; red[3 + k][warp] = hi[k]; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        float v = red[k][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            v = k < 3 ? fminf(v, red[k][w]) : fmaxf(v, red[k][w]);
+        part[6 * blockIdx.x + k] = v;
+    }
+}
+
+__global__ void k_bounds_final(const float* __restrict__ part, int nb, float* __restrict__ out) {
+    const int k = threadIdx.x;
+    if (k >= 6) return;
+    float v = part[k];
+    for (int b = 1; b < nb; ++b) v = k < 3 ? fminf(v, part[6 * b + k]) : fmaxf(v, part[6 * b + k]);
+    out[k] = v;
+}
+
+// 10 bits spread to every third bit position (bit b -> bit 3b).
+__device__ __forceinline__ uint32_t spread3(uint32_t x) {
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000ffu;
+    x = (x | (x << 8)) & 0x0300f00fu;
+    x = (x | (x << 4)) & 0x030c30c3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+__global__ void k_morton(const float* __restrict__ tris, int n, const float* __restrict__ bounds,
+                         uint32_t* __restrict__ codes) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* t = tris + 9ll * i;
+    uint32_t q[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float lo = bounds[k], hi = bounds[3 + k];
+        const float ext = __fsub_rn(hi, lo);
+        if (!(ext > 0.0f)) { q[k] = 0u; continue; }
+        const float s = centroid_sum(t, k);
+        const float u = __fdiv_rn(__fsub_rn(s, lo), ext);
+        const uint32_t c = __float2uint_rz(__fmul_rn(u, 1024.0f));
+        q[k] = c > 1023u ? 1023u : c;
+    }
+    codes[i] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+}
+
+// ---- stable LSD radix sort ----------------------------------------------------
+// Pass = histogram (per tile) -> exclusive scan in (digit, tile) order ->
+// scatter.  The scatter ranks keys of a tile stably with warp multi-split:
+// every warp owns a contiguous run of the tile and walks it 32 keys at a time
+// in index order; __match_any_sync groups equal digits, and a per-(warp,
+// digit) counter accumulates ranks; a prefix over warps then orders warps.
+
+__global__ void k_radix_hist(const uint32_t* __restrict__ keys, int n, int shift,
+                             unsigned* __restrict__ hist, int nblocks) {
+    __shared__ unsigned h[256];
+    h[threadIdx.x] = 0u;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kSortTile;
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const long long i = base + it * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of `total` counters by one block of 1024 threads.
+__global__ void k_radix_scan(unsigned* __restrict__ hist, int total) {
+    __shared__ unsigned part[1024];
+    const int per = (total + 1023) / 1024;
+    const int b = threadIdx.x * per;
+    unsigned s = 0;
+    for (int i = 0; i < per; ++i)
+        if (b + i < total) s += hist[b + i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        unsigned v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned run = part[threadIdx.x] - s;   // exclusive prefix of this chunk
+    for (int i = 0; i < per; ++i) {
+        if (b + i < total) {
+            unsigned v = hist[b + i];
+            hist[b + i] = run;
+            run += v;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_scatter(const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin,
+                uint32_t* __restrict__ kout, int32_t* __restrict__ vout, int n, int shift,
+                const unsigned* __restrict__ hist, int nblocks) {
+    __shared__ unsigned cnt[kSortWarps][256];
+    __shared__ unsigned gbase[256];
+    for (int i = threadIdx.x; i < kSortWarps * 256; i += kSortThreads) (&cnt[0][0])[i] = 0u;
+    gbase[threadIdx.x] = hist[threadIdx.x * nblocks + blockIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const long long base = (long long)blockIdx.x * kSortTile + (long long)warp * (32 * kSortItems);
+    uint32_t key[kSortItems];
+    int32_t val[kSortItems];
+    unsigned rank[kSortItems], dig[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const long long i = base + r * 32 + lane;
+        const bool valid = i < n;
+        key[r] = valid ? kin[i] : 0u;
+        val[r] = valid ? (vin ? vin[i] : (int32_t)i) : 0;
+        const unsigned d = valid ? ((key[r] >> shift) & 255u) : 256u + lane;
+        dig[r] = d;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned before = 0u;
+        if (valid) before = cnt[warp][d];
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) cnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+        rank[r] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;   // kSortThreads == 256 digits
+        unsigned run = 0u;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            const unsigned c = cnt[w][d];
+            cnt[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const long long i = base + r * 32 + lane;
+        if (i < n) {
+            const unsigned d = dig[r];
+            const unsigned dst = gbase[d] + cnt[warp][d] + rank[r];
+            kout[dst] = key[r];
+            vout[dst] = val[r];
+        }
+    }
+}
+
+// ---- Karras hierarchy -----------------------------------------------------------
+// delta(i, j): common prefix length of the keys (code, index); -1 out of range.
+__device__ __forceinline__ int delta(const uint32_t* __restrict__ k, int n, int i, int j, uint32_t ki) {
+    if (j < 0 || j >= n) return -1;
+    const uint32_t kj = k[j];
+    if (kj == ki) return 32 + __clz((unsigned)(i ^ j));
+    return __clz(ki ^ kj);
+}
+
+__global__ void k_karras(const uint32_t* __restrict__ keys, int n, int2* __restrict__ child,
+                         int32_t* __restrict__ parent) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const uint32_t ki = keys[i];
+    const int d = (delta(keys, n, i, i + 1, ki) - delta(keys, n, i, i - 1, ki)) >= 0 ? 1 : -1;
+    const int dmin = delta(keys, n, i, i - d, ki);
+    int lmax = 2;
+    while (delta(keys, n, i, i + lmax * d, ki) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(keys, n, i, i + (l + t) * d, ki) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = delta(keys, n, i, j, ki);
+    int s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(keys, n, i, i + (s + t) * d, ki) > dnode) s += t;
+    } while (t > 1);
+    const int gamma = i + s * d + min(d, 0);
+    const int lo = min(i, j), hi = max(i, j);
+    const int L = (lo == gamma) ? ~gamma : gamma;
+    const int R = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+    child[i] = make_int2(L, R);
+    parent[L >= 0 ? L : (n - 1) + ~L] = i;
+    parent[R >= 0 ? R : (n - 1) + ~R] = i;
+    if (i == 0) parent[0] = -1;
+}
+
+__device__ __forceinline__ void load_box(const float* p, float b[6]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) b[k] = __ldcg(p + k);
+}
+
+// Bottom-up bounds: each leaf thread writes its box and climbs; at every
+// internal node the first arrival stops and the second (which then sees both
+// children's boxes) writes the union and continues.
+__global__ void k_refit(const float* __restrict__ tris, const int32_t* __restrict__ ids, int n,
+                        const int2* __restrict__ child, const int32_t* __restrict__ parent,
+                        unsigned* __restrict__ flags, float* __restrict__ node_box,
+                        float* __restrict__ leaf_box) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float* t = tris + 9ll * ids[k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        leaf_box[6ll * k + a] = fminf(fminf(t[a], t[3 + a]), t[6 + a]);
+        leaf_box[6ll * k + 3 + a] = fmaxf(fmaxf(t[a], t[3 + a]), t[6 + a]);
+    }
+    if (n == 1) return;
+    int node = parent[(n - 1) + k];
+    // a binary radix tree over 30-bit codes + 32-bit positions is at most 64
+    // levels deep; the bound only guards against a malformed parent array
+    for (int climb = 0; node >= 0 && climb < 96; ++climb) {
+        __threadfence();
+        if (atomicAdd(&flags[node], 1u) == 0u) return;
+        __threadfence();
+        const int2 c = child[node];
+        float a[6], b[6];
+        load_box(c.x >= 0 ? node_box + 6ll * c.x : leaf_box + 6ll * ~c.x, a);
+        load_box(c.y >= 0 ? node_box + 6ll * c.y : leaf_box + 6ll * ~c.y, b);
+        float* o = node_box + 6ll * node;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            __stcg(o + q, fminf(a[q], b[q]));
+            __stcg(o + 3 + q, fmaxf(a[3 + q], b[3 + q]));
+        }
+        node = parent[node];
+    }
+}
+
+__global__ void k_pack_nodes(const int2* __restrict__ child, const float* __restrict__ node_box,
+                             const float* __restrict__ leaf_box, int n, float4* __restrict__ nodes) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int2 c = child[i];
+    const float* a = c.x >= 0 ? node_box + 6ll * c.x : leaf_box + 6ll * ~c.x;
+    const float* b = c.y >= 0 ? node_box + 6ll * c.y : leaf_box + 6ll * ~c.y;
+    nodes[4ll * i + 0] = make_float4(a[0], a[3], a[1], a[4]);
+    nodes[4ll * i + 1] = make_float4(b[0], b[3], b[1], b[4]);
+    nodes[4ll * i + 2] = make_float4(a[2], a[5], b[2], b[5]);
+    nodes[4ll * i + 3] = make_float4(__int_as_float(c.x), __int_as_float(c.y), 0.0f, 0.0f);
+}
+
+__global__ void k_pack_leaves(const float* __restrict__ tris, const float* __restrict__ albedo,
+                              const int32_t* __restrict__ ids, int n, float4* __restrict__ leaves,
+                              float4* __restrict__ albedo4) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int id = ids[k];
+    const float* t = tris + 9ll * id;
+    leaves[3ll * k + 0] = make_float4(t[0], t[1], t[2], __int_as_float(id));
+    leaves[3ll * k + 1] = make_float4(t[3], t[4], t[5], 0.0f);
+    leaves[3ll * k + 2] = make_float4(t[6], t[7], t[8], 0.0f);
+    // albedo in original order (thread k writes triangle k's albedo)
+    if (albedo)
+        albedo4[k] = make_float4(albedo[3ll * k], albedo[3ll * k + 1], albedo[3ll * k + 2], 0.0f);
+    else
+        albedo4[k] = make_float4(0.8f, 0.8f, 0.8f, 0.0f);
+}
+
+inline int blocks_for(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
+
+}  // namespace
+
+size_t lbvh_sort_blocks(int n) { return (size_t)((n + kSortTile - 1) / kSortTile); }
+
+cudaError_t lbvh_build(const LbvhBuffers& b, cudaStream_t s) {
+    const int n = b.n;
+    if (n <= 0) return cudaSuccess;
+    const int nb_bounds = min(kBoundsBlocks, blocks_for(n, 256));
+    k_bounds_partial<<<nb_bounds, 256, 0, s>>>(b.tris, n, b.part_bounds);
+    k_bounds_final<<<1, 32, 0, s>>>(b.part_bounds, nb_bounds, b.scene_bounds);
+    k_morton<<<blocks_for(n, 256), 256, 0, s>>>(b.tris, n, b.scene_bounds, b.codes);
+    count_launch(3);
+    const int nblocks = (int)lbvh_sort_blocks(n);
+    // ping-pong: codes -> tmp -> sorted -> tmp -> sorted
+    const uint32_t* kin = b.codes;
+    const int32_t* vin = nullptr;
+    for (int pass = 0; pass < 4; ++pass) {
+        uint32_t* kout = (pass & 1) ? b.keys_sorted : b.keys_tmp;
+        int32_t* vout = (pass & 1) ? b.ids : b.ids_tmp;
+        k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(kin, n, 8 * pass, b.hist, nblocks);
+        k_radix_scan<<<1, 1024, 0, s>>>(b.hist, 256 * nblocks);
+        k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, 8 * pass,
+                                                         b.hist, nblocks);
+        count_launch(3);
+        kin = kout;
+        vin = vout;
+    }
+    if (n > 1) {
+        cudaMemsetAsync(b.flags, 0, sizeof(unsigned) * (size_t)(n - 1), s);
+        k_karras<<<blocks_for(n - 1, 256), 256, 0, s>>>(b.keys_sorted, n, b.child, b.parent);
+        count_launch(1);
+    }
+    k_refit<<<blocks_for(n, 256), 256, 0, s>>>(b.tris, b.ids, n, b.child, b.parent, b.flags,
+                                               b.node_box, b.leaf_box);
+    count_launch(1);
+    if (n > 1) {
+        k_pack_nodes<<<blocks_for(n - 1, 256), 256, 0, s>>>(b.child, b.node_box, b.leaf_box, n,
+                                                            b.nodes);
+        count_launch(1);
+    }
+    k_pack_leaves<<<blocks_for(n, 256), 256, 0, s>>>(b.tris, b.albedo, b.ids, n, b.leaves,
+                                                     b.albedo4);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+}  // namespace vafr

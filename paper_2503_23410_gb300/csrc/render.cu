@@ -1,0 +1,402 @@
+// render.cu -- ray generation, LBVH traversal and shading (the ray-casting
+// pipeline of Sec. 6.1: ray-generation shader dispatched over the LP buffer,
+// closest-hit shader, miss shader; and the GT dispatch over display pixels).
+//
+// Kernels are persistent: a grid of (SMs x resident blocks) whose warps pull
+// chunks of work items from one global atomic counter until the batch is done,
+// so uneven frames and uneven rays balance dynamically.
+//
+// Traversal: single-triangle LBVH leaves; each 64-byte node holds both child
+// boxes.  Box tests follow Ize 2013 ("Robust BVH Ray Traversal"): slab
+// distances (b - o) * (1/d) and the far distance scaled by 1 + 2 gamma_3 so no
+// box the ray touches is culled by rounding.  Triangle test: Woop, Benthin,
+// Wald 2013 ("Watertight Ray/Triangle Intersection"), two-sided, with the
+// 2-D edge functions evaluated without FMA contraction so that a shared edge
+// gets exactly opposite values in the two neighbouring triangles.
+// Hit rule: closest t > 0; equal t -> lower triangle id.
+#include "vafr_internal.cuh"
+
+#include <float.h>
+#include <limits.h>
+
+namespace vafr {
+namespace {
+
+constexpr float kAmbient = 0.1f;
+constexpr float kFarScale = 1.0000003576278687f;   // 1 + 2 gamma_3 in FP32 (gamma_3 = 3u/(1-3u))
+constexpr float kDirEps = 1e-30f;
+
+struct Ray {
+    float ox, oy, oz;
+    float dx, dy, dz;
+    float ix, iy, iz;            // 1/d with zero components clamped (box tests only)
+    float mx0, mx1, mx2;         // shear rows: A'x = Mx . A, A'y = My . A, A'z = Mz . A
+    float my0, my1, my2;
+    float mz0, mz1, mz2;
+};
+
+__device__ __forceinline__ float safe_inv(float d) {
+    if (fabsf(d) < kDirEps) d = copysignf(kDirEps, d);
+    return 1.0f / d;
+}
+
+__device__ __forceinline__ void ray_setup(Ray& r) {
+    r.ix = safe_inv(r.dx);
+    r.iy = safe_inv(r.dy);
+    r.iz = safe_inv(r.dz);
+    const float ax = fabsf(r.dx), ay = fabsf(r.dy), az = fabsf(r.dz);
+    const int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    const float dkz = kz == 0 ? r.dx : (kz == 1 ? r.dy : r.dz);
+    if (dkz < 0.0f) { const int s = kx; kx = ky; ky = s; }
+    const float dkx = kx == 0 ? r.dx : (kx == 1 ? r.dy : r.dz);
+    const float dky = ky == 0 ? r.dx : (ky == 1 ? r.dy : r.dz);
+    const float Sx = dkx / dkz, Sy = dky / dkz, Sz = 1.0f / dkz;
+    // Mx has 1 at kx and -Sx at kz; My has 1 at ky and -Sy at kz; Mz has Sz at kz.
+    r.mx0 = kx == 0 ? 1.0f : (kz == 0 ? -Sx : 0.0f);
+    r.mx1 = kx == 1 ? 1.0f : (kz == 1 ? -Sx : 0.0f);
+    r.mx2 = kx == 2 ? 1.0f : (kz == 2 ? -Sx : 0.0f);
+    r.my0 = ky == 0 ? 1.0f : (kz == 0 ? -Sy : 0.0f);
+    r.my1 = ky == 1 ? 1.0f : (kz == 1 ? -Sy : 0.0f);
+    r.my2 = ky == 2 ? 1.0f : (kz == 2 ? -Sy : 0.0f);
+    r.mz0 = kz == 0 ? Sz : 0.0f;
+    r.mz1 = kz == 1 ? Sz : 0.0f;
+    r.mz2 = kz == 2 ? Sz : 0.0f;
+}
+
+// Child boxes of a node: returns entry distance (or +inf when missed).
+__device__ __forceinline__ float slab(float lox, float hix, float loy, float hiy, float loz,
+                                      float hiz, const Ray& r, float tmax) {
+    const float tx0 = __fmul_rn(__fsub_rn(lox, r.ox), r.ix), tx1 = __fmul_rn(__fsub_rn(hix, r.ox), r.ix);
+    const float ty0 = __fmul_rn(__fsub_rn(loy, r.oy), r.iy), ty1 = __fmul_rn(__fsub_rn(hiy, r.oy), r.iy);
+    const float tz0 = __fmul_rn(__fsub_rn(loz, r.oz), r.iz), tz1 = __fmul_rn(__fsub_rn(hiz, r.oz), r.iz);
+    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    return tn <= tf * kFarScale ? tn : INFINITY;
+}
+
+// Watertight test; returns t or +inf.
+__device__ __forceinline__ float tri_test(const Ray& r, float4 a, float4 b, float4 c) {
+    const float Ax0 = __fsub_rn(a.x, r.ox), Ax1 = __fsub_rn(a.y, r.oy), Ax2 = __fsub_rn(a.z, r.oz);
+    const float Bx0 = __fsub_rn(b.x, r.ox), Bx1 = __fsub_rn(b.y, r.oy), Bx2 = __fsub_rn(b.z, r.oz);
+    const float Cx0 = __fsub_rn(c.x, r.ox), Cx1 = __fsub_rn(c.y, r.oy), Cx2 = __fsub_rn(c.z, r.oz);
+    const float Ax = fmaf(r.mx0, Ax0, fmaf(r.mx1, Ax1, __fmul_rn(r.mx2, Ax2)));
+    const float Ay = fmaf(r.my0, Ax0, fmaf(r.my1, Ax1, __fmul_rn(r.my2, Ax2)));
+    const float Bx = fmaf(r.mx0, Bx0, fmaf(r.mx1, Bx1, __fmul_rn(r.mx2, Bx2)));
+    const float By = fmaf(r.my0, Bx0, fmaf(r.my1, Bx1, __fmul_rn(r.my2, Bx2)));
+    const float Cx = fmaf(r.mx0, Cx0, fmaf(r.mx1, Cx1, __fmul_rn(r.mx2, Cx2)));
+    const float Cy = fmaf(r.my0, Cx0, fmaf(r.my1, Cx1, __fmul_rn(r.my2, Cx2)));
+    const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return INFINITY;
+    const float det = __fadd_rn(__fadd_rn(U, V), W);
+    if (det == 0.0f) return INFINITY;
+    const float Az = fmaf(r.mz0, Ax0, fmaf(r.mz1, Ax1, __fmul_rn(r.mz2, Ax2)));
+    const float Bz = fmaf(r.mz0, Bx0, fmaf(r.mz1, Bx1, __fmul_rn(r.mz2, Bx2)));
+    const float Cz = fmaf(r.mz0, Cx0, fmaf(r.mz1, Cx1, __fmul_rn(r.mz2, Cx2)));
+    const float T = fmaf(U, Az, fmaf(V, Bz, __fmul_rn(W, Cz)));
+    const float t = __fdiv_rn(T, det);
+    return t > 0.0f ? t : INFINITY;
+}
+
+struct Hit {
+    float t;
+    int leaf;   // sorted leaf index, -1 = miss
+    int id;     // triangle id
+};
+
+template <bool STATS>
+__device__ __forceinline__ void test_leaf(const SceneDev& sc, const Ray& r, int k, Hit& h,
+                                          unsigned long long* tri_tests) {
+    const float4 a = __ldg(sc.leaves + 3ll * k);
+    const float4 b = __ldg(sc.leaves + 3ll * k + 1);
+    const float4 c = __ldg(sc.leaves + 3ll * k + 2);
+    if (STATS) ++*tri_tests;
+    const float t = tri_test(r, a, b, c);
+    const int id = __float_as_int(a.w);
+    if (t < h.t || (t == h.t && t < INFINITY && id < h.id)) {
+        h.t = t;
+        h.leaf = k;
+        h.id = id;
+    }
+}
+
+// Closest hit through the LBVH.  Returns a fault bit (0 = fine).
+template <bool STATS>
+__device__ unsigned traverse(const SceneDev& sc, const Ray& r, Hit& h,
+                             unsigned long long* node_visits, unsigned long long* tri_tests) {
+    h.t = INFINITY;
+    h.leaf = -1;
+    h.id = INT_MAX;
+    if (sc.n_tris <= 0) return 0u;
+    if (sc.root < 0) {   // single triangle
+        test_leaf<STATS>(sc, r, 0, h, tri_tests);
+        return 0u;
+    }
+    int stack[kStackSize];
+    float stack_t[kStackSize];
+    int sp = 0;
+    int node = sc.root;
+    const int n_inner = sc.n_tris - 1;
+    unsigned budget = 4u * (unsigned)sc.n_tris + 64u;
+    while (true) {
+        if (--budget == 0u) return kFaultWatchdog;
+        if ((unsigned)node >= (unsigned)n_inner) return kFaultBadNode;
+        if (STATS) ++*node_visits;
+        const float4* nd = sc.nodes + 4ll * node;
+        const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+        const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
+        float tl = slab(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, r, h.t);
+        float tr = slab(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, r, h.t);
+        if (tl < INFINITY && cl < 0) {
+            if ((unsigned)~cl >= (unsigned)sc.n_tris) return kFaultBadNode;
+            test_leaf<STATS>(sc, r, ~cl, h, tri_tests);
+            tl = INFINITY;
+        }
+        if (tr < INFINITY && cr < 0) {
+            if ((unsigned)~cr >= (unsigned)sc.n_tris) return kFaultBadNode;
+            test_leaf<STATS>(sc, r, ~cr, h, tri_tests);
+            tr = INFINITY;
+        }
+        const bool hl = tl < INFINITY, hr = tr < INFINITY;
+        if (hl && hr) {
+            if (sp >= kStackSize) return kFaultStack;
+            const bool left_first = tl <= tr;
+            stack[sp] = left_first ? cr : cl;
+            stack_t[sp] = left_first ? tr : tl;
+            ++sp;
+            node = left_first ? cl : cr;
+        } else if (hl) {
+            node = cl;
+        } else if (hr) {
+            node = cr;
+        } else {
+            // pop, skipping entries that start beyond the current closest hit
+            while (true) {
+                if (sp == 0) return 0u;
+                --sp;
+                if (stack_t[sp] <= h.t * kFarScale) break;
+            }
+            node = stack[sp];
+        }
+    }
+}
+
+__device__ __forceinline__ float4 shade(const SceneDev& sc, const Ray& r, const Hit& h) {
+    if (h.leaf < 0) {
+        const float inv = rsqrtf(fmaf(r.dx, r.dx, fmaf(r.dy, r.dy, r.dz * r.dz)));
+        const float s = 0.5f * fmaf(r.dy, inv, 1.0f);
+        return make_float4(1.0f - 0.5f * s, 1.0f - 0.3f * s, 1.0f, 1.0f);
+    }
+    const float4 a = __ldg(sc.leaves + 3ll * h.leaf);
+    const float4 b = __ldg(sc.leaves + 3ll * h.leaf + 1);
+    const float4 c = __ldg(sc.leaves + 3ll * h.leaf + 2);
+    const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
+    const float e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
+    float nx = e1y * e2z - e1z * e2y;
+    float ny = e1z * e2x - e1x * e2z;
+    float nz = e1x * e2y - e1y * e2x;
+    const float inv = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+    nx *= inv; ny *= inv; nz *= inv;
+    if (fmaf(nx, r.dx, fmaf(ny, r.dy, nz * r.dz)) > 0.0f) { nx = -nx; ny = -ny; nz = -nz; }
+    const float lam = fmaxf(0.0f, -fmaf(nx, sc.light[0], fmaf(ny, sc.light[1], nz * sc.light[2])));
+    const float s = fmaf(1.0f - kAmbient, lam, kAmbient);
+    const float4 al = __ldg(sc.albedo + h.id);
+    return make_float4(al.x * s, al.y * s, al.z * s, 1.0f);
+}
+
+__device__ __forceinline__ void store_px(void* base, long long idx, int fmt, float4 v) {
+    if (fmt == VAFR_FMT_RGBA16F) {
+        const __half2 lo = __floats2half2_rn(v.x, v.y), hi = __floats2half2_rn(v.z, v.w);
+        uint2 p;
+        p.x = *reinterpret_cast<const unsigned*>(&lo);
+        p.y = *reinterpret_cast<const unsigned*>(&hi);
+        reinterpret_cast<uint2*>(base)[idx] = p;
+    } else {
+        reinterpret_cast<float4*>(base)[idx] = v;
+    }
+}
+
+__device__ __forceinline__ void world_ray(const FrameDesc& f, float cx, float cy, Ray& r) {
+    // camera direction (cx, cy, 1) -> world
+    r.dx = fmaf(f.R[0], cx, fmaf(f.R[1], cy, f.R[2]));
+    r.dy = fmaf(f.R[3], cx, fmaf(f.R[4], cy, f.R[5]));
+    r.dz = fmaf(f.R[6], cx, fmaf(f.R[7], cy, f.R[8]));
+    r.ox = f.org[0];
+    r.oy = f.org[1];
+    r.oz = f.org[2];
+}
+
+template <class B>
+__device__ __forceinline__ int find_frame(const B& b, long long w, bool tiles) {
+    int lo = 0, hi = b.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const long long beg = tiles ? b.d[mid].tile_begin : b.d[mid].work_begin;
+        if (beg <= w) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// LP ray of texel t of frame f (Eqs. 3, 10, 11): the screen point at distance
+// r = tan(e_c)/c_r from the gaze at angle (j + 0.5) 360/n_c, unprojected:
+// camera direction (tan(e_c) cos(phi) + gx, -tan(e_c) sin(phi) + gy, 1).
+__device__ __forceinline__ void lp_ray(const FrameDesc& f, int t, Ray& r) {
+    int lo = 0, hi = f.n_cols - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&f.col[mid].x) <= t) lo = mid; else hi = mid - 1;
+    }
+    const int2 cc = __ldg(&f.col[lo]);
+    const int j = t - cc.x;
+    const float te = __ldg(&f.tan_e[lo]);
+    float sp, cp;
+    sincospif(__fdiv_rn((float)(2 * j + 1), (float)cc.y), &sp, &cp);
+    world_ray(f, fmaf(te, cp, f.gx), fmaf(-te, sp, f.gy), r);
+}
+
+template <int TPB, int FETCH, class B>
+__global__ void __launch_bounds__(TPB)
+k_render_lp(const SceneDev sc, const __grid_constant__ B b) {
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        unsigned long long base = 0ull;
+        if (lane == 0) base = atomicAdd(b.work_counter, (unsigned long long)FETCH);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((long long)base >= b.total_work) break;
+#pragma unroll 1
+        for (int k = 0; k < FETCH; k += 32) {
+            const long long w = (long long)base + k + lane;
+            if (w >= b.total_work) break;
+            const int fi = find_frame(b, w, false);
+            const FrameDesc& f = b.d[fi];
+            const int t = (int)(w - f.work_begin);
+            Ray r;
+            lp_ray(f, t, r);
+            ray_setup(r);
+            Hit h;
+            const unsigned fault = traverse<false>(sc, r, h, nullptr, nullptr);
+            if (fault) { atomicOr(f.status, fault); h.leaf = -1; h.id = -1; }
+            store_px(f.lp, t, f.lp_fmt, shade(sc, r, h));
+            if (f.hit_ids) f.hit_ids[t] = h.leaf >= 0 ? h.id : -1;
+        }
+    }
+}
+
+// GT: work item = (tile of 8 x 4 pixels, lane); pixel centre rays.
+template <int TPB, int FETCH, class B>
+__global__ void __launch_bounds__(TPB)
+k_render_gt(const SceneDev sc, const __grid_constant__ B b) {
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        unsigned long long base = 0ull;
+        if (lane == 0) base = atomicAdd(b.work_counter, (unsigned long long)FETCH);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((long long)base >= b.total_work) break;
+#pragma unroll 1
+        for (int k = 0; k < FETCH; k += 32) {
+            const long long w = (long long)base + k + lane;
+            if (w >= b.total_work) break;
+            const int fi = find_frame(b, w, false);
+            const FrameDesc& f = b.d[fi];
+            const long long local = w - f.work_begin;
+            const long long tile = local >> 5;
+            const int tiles_x = (f.W + 7) >> 3;
+            const int x = (int)(tile % tiles_x) * 8 + (lane & 7);
+            const int y = (int)(tile / tiles_x) * 4 + (lane >> 3);
+            if (x >= f.W || y >= f.H) continue;
+            const float cx = f.cr * ((float)x + 0.5f - 0.5f * (float)f.W);
+            const float cy = f.cr * (0.5f * (float)f.H - ((float)y + 0.5f));
+            Ray r;
+            world_ray(f, cx, cy, r);
+            ray_setup(r);
+            Hit h;
+            const unsigned fault = traverse<false>(sc, r, h, nullptr, nullptr);
+            if (fault) { atomicOr(f.status, fault); h.leaf = -1; h.id = -1; }
+            const long long p = (long long)y * f.W + x;
+            store_px(f.disp, p, f.disp_fmt, shade(sc, r, h));
+            if (f.hit_ids) f.hit_ids[p] = h.leaf >= 0 ? h.id : -1;
+        }
+    }
+}
+
+// Instrumented copy (never timed): counts rays, nodes, triangle tests, hits.
+__global__ void __launch_bounds__(128)
+k_render_stats(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned long long* out) {
+    unsigned long long nodes = 0, tris = 0, rays = 0, hits = 0;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < b.total_work;
+         w += (long long)gridDim.x * blockDim.x) {
+        const FrameDesc& f = b.d[find_frame(b, w, false)];
+        Ray r;
+        lp_ray(f, (int)(w - f.work_begin), r);
+        ray_setup(r);
+        Hit h;
+        traverse<true>(sc, r, h, &nodes, &tris);
+        ++rays;
+        hits += h.leaf >= 0;
+    }
+    atomicAdd(out + 0, rays);
+    atomicAdd(out + 1, nodes);
+    atomicAdd(out + 2, tris);
+    atomicAdd(out + 3, hits);
+}
+
+template <int TPB, int FETCH, bool GT, class B>
+cudaError_t launch_one(const SceneDev& sc, const B& b, cudaStream_t s, int num_sms) {
+    auto kern = GT ? k_render_gt<TPB, FETCH, B> : k_render_lp<TPB, FETCH, B>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    e = cudaMemsetAsync(b.work_counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    long long want_warps = (b.total_work + FETCH - 1) / FETCH;
+    long long grid = (long long)per_sm * num_sms;
+    const long long need = (want_warps * 32 + TPB - 1) / TPB;
+    if (need < grid) grid = need < 1 ? 1 : need;
+    kern<<<(unsigned)grid, TPB, 0, s>>>(sc, b);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <bool GT, class B>
+cudaError_t launch_variant(const SceneDev& sc, const B& b, int variant, cudaStream_t s, int sms) {
+    if (b.total_work <= 0) return cudaSuccess;
+    switch (variant) {
+        case 0: return launch_one<128, 32, GT>(sc, b, s, sms);
+        case 1: return launch_one<256, 32, GT>(sc, b, s, sms);
+        case 2: return launch_one<128, 64, GT>(sc, b, s, sms);
+        default: return launch_one<64, 32, GT>(sc, b, s, sms);
+    }
+}
+
+}  // namespace
+
+template <class B>
+cudaError_t launch_render_lp(const SceneDev& scene, const B& batch, int variant, cudaStream_t s,
+                             int num_sms) {
+    return launch_variant<false>(scene, batch, variant, s, num_sms);
+}
+template <class B>
+cudaError_t launch_render_gt(const SceneDev& scene, const B& batch, int variant, cudaStream_t s,
+                             int num_sms) {
+    return launch_variant<true>(scene, batch, variant, s, num_sms);
+}
+
+template cudaError_t launch_render_lp<SmallBatch>(const SceneDev&, const SmallBatch&, int, cudaStream_t, int);
+template cudaError_t launch_render_lp<BigBatch>(const SceneDev&, const BigBatch&, int, cudaStream_t, int);
+template cudaError_t launch_render_gt<SmallBatch>(const SceneDev&, const SmallBatch&, int, cudaStream_t, int);
+template cudaError_t launch_render_gt<BigBatch>(const SceneDev&, const BigBatch&, int, cudaStream_t, int);
+
+cudaError_t launch_render_stats(const SceneDev& scene, const SmallBatch& batch,
+                                unsigned long long* counters, cudaStream_t s, int num_sms) {
+    cudaError_t e = cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_render_stats<<<num_sms * 4, 128, 0, s>>>(scene, batch, counters);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+}  // namespace vafr

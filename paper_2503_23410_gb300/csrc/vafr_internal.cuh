@@ -1,0 +1,142 @@
+// vafr_internal.cuh -- device data layouts and launch interfaces shared by the
+// CUDA translation units of libvafr.so (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/vafr.h"
+
+namespace vafr {
+
+// ---- device status words --------------------------------------------------
+enum DeviceFault : unsigned {
+    kFaultStack = 1u,     // traversal stack would overflow
+    kFaultWatchdog = 2u,  // traversal iteration limit reached
+    kFaultBadNode = 4u,   // child reference out of range
+};
+
+constexpr int kStackSize = 64;
+constexpr int kMaxSeg = VAFR_MAX_PIVOTS - 1;
+
+// ---- scene (LBVH) in traversal layout ----------------------------------------
+// Internal node i (64 B, four float4):
+//   n[0] = (L.lo.x, L.hi.x, L.lo.y, L.hi.y)
+//   n[1] = (R.lo.x, R.hi.x, R.lo.y, R.hi.y)
+//   n[2] = (L.lo.z, L.hi.z, R.lo.z, R.hi.z)
+//   n[3] = (L ref, R ref, -, -) as int bits; ref >= 0 internal, < 0 leaf ~k
+// Leaf k (sorted order): three float4 (v0.xyz | id), (v1.xyz | 0), (v2.xyz | 0).
+struct SceneDev {
+    const float4* nodes;
+    const float4* leaves;
+    const float4* albedo;   // original triangle order (rgb, 0)
+    int root;               // 0 (internal), ~0 (single leaf) or INT_MIN (empty)
+    int n_tris;
+    float light[3];         // unit light travel direction
+    unsigned* status;       // device status word
+};
+
+// ---- per session: forward-map constants -------------------------------------
+// Immutable after session creation; lives in device memory and is reached
+// through FrameDesc::seg.  u(e) on segment s (e in [e0_s, e0_{s+1})):
+//   u = u0 + k log2(1 + a (e - e0)) + b (e - e0)
+// (k, a, b) = (2 ln2 / m, m / (m e0 + w), 0) for a sloped MAR segment and
+// (0, 0, 2 / w) for a flat one (Eq. 12 and its m -> 0 limit).
+struct SegTable {
+    int n_seg;
+    float seg_e0[kMaxSeg];
+    float seg_u0[kMaxSeg];
+    float seg_k[kMaxSeg];
+    float seg_a[kMaxSeg];
+    float seg_b[kMaxSeg];
+    float e_max;            // deg
+};
+
+// ---- one frame-eye of work (kernel parameter; filled on the host in FP64,
+// rounded to FP32) ------------------------------------------------------------
+struct FrameDesc {
+    float R[9];             // camera -> world rotation, row-major
+    float org[3];           // eye position
+    float gx, gy;           // gaze tangent offsets: c_r (x0 - W/2), c_r (H/2 - y0)
+    float cr;               // c_r
+    float px0, py0;         // c_r (0.5 - W/2), c_r (H/2 - 0.5): GT ray of pixel (0,0)
+    int gxi, gyi;           // floor of the gaze point
+    float gxf, gyf;         // 0.5 - fractional part of the gaze point
+    int W, H;
+    int lp_fmt, disp_fmt;
+    const SegTable* seg;    // device
+    const float* tan_e;     // device [C] tan(e_c) of the column centres
+    const int2* col;        // device [C] (first texel, texel count)
+    int n_cols;
+    int n_texels;
+    void* lp;
+    void* disp;
+    int* hit_ids;
+    unsigned* status;
+    long long work_begin;   // first global work item (render) of this frame
+    long long tile_begin;   // first global tile (reconstruct) of this frame
+};
+
+template <int MAXD>
+struct Batch {
+    int n;
+    long long total_work;   // sum of render work items
+    long long total_tiles;  // sum of reconstruct tiles
+    unsigned long long* work_counter;  // device counter (persistent fetch)
+    FrameDesc d[MAXD];
+};
+
+using SmallBatch = Batch<2>;
+using BigBatch = Batch<VAFR_MAX_BATCH>;
+// kernel parameters (scene + batch) must fit the 32,764-byte parameter space
+static_assert(sizeof(BigBatch) + sizeof(SceneDev) <= 32764, "batch too large for kernel params");
+
+// ---- launch interfaces ---------------------------------------------------------
+// Render variants: (threads per block, rays per warp fetch).
+constexpr int kNumRenderVariants = 4;
+// Reconstruct variants: tile shapes.
+constexpr int kNumReconVariants = 4;
+
+struct ReconShape { int tw, th; int px; };   // tile width/height in pixels, pixels per thread
+ReconShape recon_shape(int variant);
+
+template <class B>
+cudaError_t launch_render_lp(const SceneDev& scene, const B& batch, int variant,
+                             cudaStream_t s, int num_sms);
+template <class B>
+cudaError_t launch_render_gt(const SceneDev& scene, const B& batch, int variant,
+                             cudaStream_t s, int num_sms);
+template <class B>
+cudaError_t launch_reconstruct(const B& batch, int variant, cudaStream_t s);
+cudaError_t launch_render_stats(const SceneDev& scene, const SmallBatch& batch,
+                                unsigned long long* counters, cudaStream_t s, int num_sms);
+
+// LBVH build (lbvh.cu).  All device pointers are owned by the caller.
+struct LbvhBuffers {
+    const float* tris;      // n x 9 input (device)
+    const float* albedo;    // n x 3 (device) or nullptr
+    int n;
+    uint32_t* codes;        // n  Morton codes, input order
+    uint32_t* keys_tmp;     // n  sort scratch
+    int32_t* ids;           // n  sorted triangle ids
+    int32_t* ids_tmp;       // n  sort scratch
+    uint32_t* keys_sorted;  // n
+    unsigned* hist;         // 256 * blocks
+    float* part_bounds;     // 6 * blocks
+    float* scene_bounds;    // 6
+    int2* child;            // n-1
+    int32_t* parent;        // (n-1) + n: parents of internal nodes then leaves
+    unsigned* flags;        // n-1 refit arrival counters
+    float* node_box;        // (n-1) x 6
+    float* leaf_box;        // n x 6
+    float4* nodes;          // (n-1) x 4
+    float4* leaves;         // n x 3
+    float4* albedo4;        // n
+};
+size_t lbvh_sort_blocks(int n);
+cudaError_t lbvh_build(const LbvhBuffers& b, cudaStream_t s);
+
+void count_launch(int k = 1);
+
+}  // namespace vafr

@@ -30,3 +30,23 @@ def acuity():
 def layout(acuity):
     import oracle
     return oracle.lp_layout(acuity)
+
+
+@pytest.fixture(scope="session")
+def V():
+    """The C-ABI binding, built in-tree (GPU tests only)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_23410_gb300 import build
+    build.build()
+    from paper_2503_23410_gb300 import vafr
+    vafr.load()
+    torch.cuda.set_device(0)
+    return vafr
+
+
+@pytest.fixture(scope="session")
+def torch_mod():
+    import torch
+    return torch

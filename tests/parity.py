@@ -1,0 +1,75 @@
+"""Shared helpers of the GPU parity tests: device set-up through the C ABI and the
+classification of hit-id mismatches as ray-edge / depth ties.
+
+A mismatch between the GPU's hit triangle (FP32 ray, FP32 watertight test) and
+the oracle's (FP64 ray, FP64 test) is a tie when the FP64 ray passes within
+``rel`` x (distance along the ray) of an edge of the oracle's triangle, or when
+the GPU's triangle is within that distance of being hit by the FP64 ray and
+its plane lies no farther than the oracle's hit (relative 1e-5).  Anything
+else is a genuine error.  A colour comparison skips rays that graze their
+triangle (|n.d| < 1e-5), where the face-forward flip is ambiguous.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+
+def device_scene(V, scene, torch):
+    tris = torch.from_numpy(np.ascontiguousarray(scene.tris.reshape(-1, 9))).cuda()
+    alb = torch.from_numpy(np.ascontiguousarray(scene.albedo)).cuda()
+    h = V.vafr_build_scene(tris if scene.n_tris else None, alb if scene.n_tris else None,
+                           scene.light_dir)
+    return h, (tris, alb)
+
+
+def _plane_t(tri, o, d):
+    v0, v1, v2 = tri.astype(np.float64)
+    n = np.cross(v1 - v0, v2 - v0)
+    den = float(n @ d)
+    if den == 0.0:
+        return np.inf
+    return float(n @ (v0 - o)) / den
+
+
+def classify(tris, o, d, gpu_ids, ora_ids, ora_t, rel=1e-5):
+    """Returns (n_ties, n_errors, error_indices) over the mismatching rays."""
+    mism = np.flatnonzero(gpu_ids != ora_ids)
+    ties, errs = 0, []
+    for k in mism:
+        dist_scale = np.linalg.norm(d[k])
+        tie = False
+        if ora_ids[k] >= 0:
+            m = oracle.edge_margin(tris[ora_ids[k]], o[k], d[k])
+            delta = rel * ora_t[k] * dist_scale
+            if abs(m) < delta:
+                tie = True
+        if not tie and gpu_ids[k] >= 0:
+            tg = _plane_t(tris[gpu_ids[k]], o[k], d[k])
+            delta = rel * max(tg, 1e-30) * dist_scale
+            m = oracle.edge_margin(tris[gpu_ids[k]], o[k], d[k])
+            if m > -delta and tg > 0 and (ora_ids[k] < 0 or tg <= ora_t[k] * (1 + 1e-5)):
+                tie = True
+        if tie:
+            ties += 1
+        else:
+            errs.append(k)
+    return ties, len(errs), np.array(errs, dtype=np.int64)
+
+
+def compare_hits_and_colours(tris, o, d, gpu_ids, gpu_rgba, ora_ids, ora_t, ora_rgba,
+                             colour_tol, tie_budget=1e-4):
+    ties, n_err, err_idx = classify(tris, o, d, gpu_ids, ora_ids, ora_t)
+    n = len(gpu_ids)
+    same = gpu_ids == ora_ids
+    graze = oracle.grazing(tris, d, ora_ids) < 1e-5
+    ok = same & ~graze
+    cerr = np.abs(gpu_rgba[ok].astype(np.float64) - ora_rgba[ok]).max(initial=0.0)
+    summary = dict(n=n, mismatches=int((~same).sum()), ties=ties, errors=n_err,
+                   tie_frac=(ties + int((same & graze).sum())) / max(n, 1), colour_err=float(cerr))
+    assert n_err == 0, f"{n_err} non-tie hit mismatches, e.g. rays {err_idx[:8]}: {summary}"
+    assert summary["tie_frac"] <= tie_budget, f"too many ties: {summary}"
+    assert cerr <= colour_tol, f"colour error {cerr} > {colour_tol}: {summary}"
+    return summary

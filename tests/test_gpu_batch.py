@@ -1,0 +1,123 @@
+"""Batched launches (one persistent render launch over all frame-eyes + one
+reconstruct launch over all display tiles), CUDA-graph capture/replay and the
+autotuner: every result equals the single-session path bitwise."""
+
+import numpy as np
+import pytest
+
+from parity import device_scene
+from workloads import random_triangles_scene
+from workloads.views import eye_pair_poses, look_at_pose
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup(V, torch_mod):
+    sc = random_triangles_scene(2000, seed=21)
+    h, keep = device_scene(V, sc, torch_mod)
+    poses = eye_pair_poses(look_at_pose((0.0, 0.3, -3.2), (0, 0, 0)), 0.063)
+    sizes = [(640, 360, 0, 0), (1280, 720, 1, 1), (333, 211, 0, 1), (1920, 1080, 1, 0)]
+    sessions = []
+    for k, (W, H, lf, df) in enumerate(sizes):
+        s = V.vafr_session_create(V.make_session_desc(W, H, 100.0, poses, lf, df))
+        for e in range(2):
+            V.vafr_set_gaze(s, e, W * (0.3 + 0.1 * k + 0.2 * e), H * (0.6 - 0.1 * k))
+        lpb, dpb = V.vafr_session_sizes(s)
+        bufs = [(torch_mod.zeros(lpb, dtype=torch_mod.uint8, device="cuda"),
+                 torch_mod.zeros(dpb, dtype=torch_mod.uint8, device="cuda")) for _ in range(2)]
+        sessions.append((s, bufs, lpb, dpb))
+    yield h, sessions, keep
+    for s, *_ in sessions:
+        V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)
+
+
+def _single(V, torch, h, sessions):
+    """Reference: each session rendered alone through render_lp + reconstruct."""
+    outs = []
+    for s, bufs, lpb, dpb in sessions:
+        lp = torch.empty(2 * lpb, dtype=torch.uint8, device="cuda")
+        V.vafr_render_lp(h, s, 3, lp)
+        for e in range(2):
+            d = torch.empty(dpb, dtype=torch.uint8, device="cuda")
+            V.vafr_reconstruct(s, e, lp[e * lpb:], d)
+            outs.append((lp[e * lpb:(e + 1) * lpb].clone(), d))
+    torch.cuda.synchronize()
+    return [(a.cpu().numpy(), b.cpu().numpy()) for a, b in outs]
+
+
+def _frames(sessions):
+    fr = []
+    for s, bufs, lpb, dpb in sessions:
+        for e in range(2):
+            fr.append((s, e, bufs[e][0], bufs[e][1]))
+    return fr
+
+
+def _read(sessions):
+    out = []
+    for s, bufs, lpb, dpb in sessions:
+        for e in range(2):
+            out.append((bufs[e][0].cpu().numpy(), bufs[e][1].cpu().numpy()))
+    return out
+
+
+def test_batch_equals_single(V, torch_mod, setup):
+    h, sessions, _ = setup
+    ref = _single(V, torch_mod, h, sessions)
+    b = V.vafr_batch_create(h, 16)
+    for cfg in [(0, 0), (1, 2), (2, 3), (3, 1)]:
+        V.vafr_batch_tuning(b, cfg)
+        V.vafr_batch_render(b, _frames(sessions))
+        torch_mod.cuda.synchronize()
+        for (lp, d), (rlp, rd) in zip(_read(sessions), ref):
+            assert np.array_equal(lp, rlp)
+            assert np.array_equal(d, rd)
+    V.vafr_batch_destroy(b)
+
+
+def test_graph_replay_follows_gaze(V, torch_mod, setup):
+    h, sessions, _ = setup
+    b = V.vafr_batch_create(h, 16)
+    V.vafr_batch_capture(b, _frames(sessions))
+    for it in range(3):
+        for k, (s, bufs, lpb, dpb) in enumerate(sessions):
+            V.vafr_set_gaze(s, 0, 50.0 + 37 * it + k, 40.0 + 11 * it)
+            V.vafr_set_gaze(s, 1, 90.0 + 13 * it, 70.0 + 5 * it + k)
+        V.vafr_batch_replay(b)
+        torch_mod.cuda.synchronize()
+        got = _read(sessions)
+        ref = _single(V, torch_mod, h, sessions)
+        for (lp, d), (rlp, rd) in zip(got, ref):
+            assert np.array_equal(lp, rlp)
+            assert np.array_equal(d, rd)
+    V.vafr_batch_destroy(b)
+
+
+def test_autotune_picks_valid_variant(V, torch_mod, setup):
+    h, sessions, _ = setup
+    b = V.vafr_batch_create(h, 16)
+    V.vafr_batch_autotune(b, _frames(sessions), iters=2)
+    nr, nc = V.vafr_tuning_space()
+    r, c = V.vafr_batch_tuning(b)
+    assert 0 <= r < nr and 0 <= c < nc
+    V.vafr_batch_render(b, _frames(sessions))
+    torch_mod.cuda.synchronize()
+    ref = _single(V, torch_mod, h, sessions)
+    for (lp, d), (rlp, rd) in zip(_read(sessions), ref):
+        assert np.array_equal(d, rd)
+    V.vafr_batch_destroy(b)
+
+
+def test_batch_rejects_bad_frames(V, torch_mod, setup):
+    h, sessions, _ = setup
+    b = V.vafr_batch_create(h, 2)
+    with pytest.raises(V.VafrError):
+        V.vafr_batch_render(b, _frames(sessions))        # 8 frames > max 2
+    s, bufs, lpb, dpb = sessions[0]
+    with pytest.raises(V.VafrError):
+        V.vafr_batch_render(b, [(s, 5, bufs[0][0], bufs[0][1])])
+    with pytest.raises(V.VafrError):
+        V.vafr_batch_replay(b)                            # nothing captured
+    V.vafr_batch_destroy(b)

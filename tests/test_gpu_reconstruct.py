@@ -1,0 +1,124 @@
+"""GPU inverse-mapping reconstruction against the FP64 oracle, on seeded LP inputs
+(never on CUDA-produced data), and the whole VaFR frame end to end."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from parity import device_scene
+from workloads import workload
+from workloads.views import look_at_pose
+
+pytestmark = pytest.mark.gpu
+
+POSE = look_at_pose((0.0, 0.0, -3.0), (0, 0, 0))
+
+
+@pytest.fixture(scope="module")
+def lay():
+    return oracle.lp_layout()
+
+
+def _recon(V, torch, W, H, fov, gaze, lp_np, lp_fmt=0, disp_fmt=0, variant=None):
+    s = V.vafr_session_create(V.make_session_desc(W, H, fov, [POSE], lp_fmt, disp_fmt))
+    V.vafr_set_gaze(s, 0, *gaze)
+    dt = torch.float16 if lp_fmt else torch.float32
+    lp = torch.from_numpy(np.ascontiguousarray(lp_np)).to(dt).cuda()
+    out = torch.empty((H, W, 4), dtype=torch.float16 if disp_fmt else torch.float32, device="cuda")
+    if variant is not None:
+        V.vafr_session_tuning(s, (0, variant))
+    V.vafr_reconstruct(s, 0, lp, out)
+    torch.cuda.synchronize()
+    res = out.float().cpu().numpy().reshape(-1, 4)
+    V.vafr_session_destroy(s)
+    return res
+
+
+@pytest.mark.parametrize("W,H,gaze", [(640, 360, (200.3, 100.9)), (641, 357, (320.5, 178.5)),
+                                      (500, 300, (0.0, 0.0)), (500, 300, (-120.0, 410.25)),
+                                      (512, 512, (512.0, 512.0))])
+def test_random_lp_all_pixels(V, torch_mod, lay, W, H, gaze):
+    rng = np.random.default_rng(W * 7 + H)
+    lp = rng.uniform(0, 1, (lay.total, 4)).astype(np.float32)
+    got = _recon(V, torch_mod, W, H, 100.0, gaze, lp)
+    ref = oracle.reconstruct(lp.astype(np.float64), lay, W, H, 100.0, gaze)
+    err = np.abs(got - ref).max()
+    print(f"recon {W}x{H} gaze {gaze}: max err {err:.2e}")
+    assert err < 1e-3
+
+
+def test_constant_lp_is_exact(V, torch_mod, lay):
+    lp = np.tile(np.float32([0.25, 0.5, 0.75, 1.0]), (lay.total, 1))
+    got = _recon(V, torch_mod, 777, 333, 90.0, (100.0, 200.0), lp)
+    assert np.array_equal(got, np.broadcast_to(lp[0], got.shape))
+
+
+def test_analytic_texture(V, torch_mod, lay):
+    # F(e, phi) at texel centres: the smooth field reconstructs to 1e-5 of the oracle
+    e_c = np.repeat(lay.e_col, lay.n_col)
+    col = np.repeat(np.arange(lay.n_cols), lay.n_col)
+    j = np.arange(lay.total) - lay.off_col[col]
+    phi = np.radians((j + 0.5) / lay.n_col[col] * 360.0)
+    lp = np.stack([e_c / 60, 0.5 + 0.5 * np.cos(phi), 0.5 + 0.5 * np.sin(phi),
+                   np.ones_like(phi)], 1)
+    W, H, gaze = 1280, 720, (700.25, 300.75)
+    got = _recon(V, torch_mod, W, H, 100.0, gaze, lp.astype(np.float32))
+    ref = oracle.reconstruct(lp.astype(np.float32).astype(np.float64), lay, W, H, 100.0, gaze)
+    assert np.abs(got - ref).max() < 1e-5
+
+
+def test_fp16_formats(V, torch_mod, lay):
+    rng = np.random.default_rng(9)
+    lp = rng.uniform(0, 1, (lay.total, 4)).astype(np.float16)
+    W, H, gaze = 960, 540, (480.0, 270.0)
+    got = _recon(V, torch_mod, W, H, 100.0, gaze, lp, lp_fmt=1, disp_fmt=1)
+    ref = oracle.reconstruct(lp.astype(np.float64), lay, W, H, 100.0, gaze)
+    assert np.abs(got - ref).max() < 1e-3 + 2.0 ** -11
+
+
+def test_tile_variants_identical(V, torch_mod, lay):
+    rng = np.random.default_rng(4)
+    lp = rng.uniform(0, 1, (lay.total, 4)).astype(np.float32)
+    outs = [_recon(V, torch_mod, 803, 451, 100.0, (400.0, 225.0), lp, variant=v) for v in range(4)]
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+@pytest.mark.parametrize("W,H", [(3840, 2160), (7680, 4320)])
+def test_full_size_sampled(V, torch_mod, lay, W, H):
+    rng = np.random.default_rng(W)
+    lp = rng.uniform(0, 1, (lay.total, 4)).astype(np.float32)
+    gaze = (W * 0.37, H * 0.61)
+    got = _recon(V, torch_mod, W, H, 100.0, gaze, lp)
+    pix = rng.choice(W * H, 65536, replace=False)
+    ref = oracle.reconstruct(lp.astype(np.float64), lay, W, H, 100.0, gaze, pix)
+    assert np.abs(got[pix] - ref).max() < 1e-3
+
+
+def test_whole_frame_random1k(V, torch_mod, lay):
+    """render_frame (LP render + reconstruct) vs the oracle's LP render + reconstruct;
+    pixels whose filter footprint touches a tie texel are excluded."""
+    w = workload("random1k")
+    d, sc = w.displays[0], w.scene
+    h, keep = device_scene(V, sc, torch_mod)
+    s = V.vafr_session_create(V.make_session_desc(d.width, d.height, d.fov_v_deg, d.poses))
+    gaze = d.gaze[0, 0]
+    V.vafr_set_gaze(s, 0, *gaze)
+    host = np.zeros((d.height, d.width, 4), np.float32)
+    V.vafr_render_frame(h, s, host)                        # host output: D2H inside the call
+    lp = torch_mod.empty((lay.total, 4), device="cuda")
+    ids = torch_mod.empty(lay.total, dtype=torch_mod.int32, device="cuda")
+    V.vafr_render_lp(h, s, 1, lp, ids)
+    torch_mod.cuda.synchronize()
+    rgba, oid, _, _, _ = oracle.render_lp(sc.tris, sc.albedo, sc.light_dir, lay, d.width,
+                                          d.height, d.fov_v_deg, gaze, d.poses[0])
+    ref = oracle.reconstruct(rgba, lay, d.width, d.height, d.fov_v_deg, gaze)
+    bad = (ids.cpu().numpy() != oid).astype(np.float64)[:, None]
+    touch = oracle.reconstruct(bad, lay, d.width, d.height, d.fov_v_deg, gaze)[:, 0] > 0
+    got = host.reshape(-1, 4)
+    assert touch.mean() < 0.01
+    assert np.abs(got[~touch] - ref[~touch]).max() < 1e-3
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)

@@ -1,0 +1,214 @@
+"""GPU LP render (ray generation + traversal + shading) and GT render against the
+FP64 oracle: hit triangle ids bit-exact except classified ray-edge / depth ties
+(<= 0.01 % of rays), colours within 1e-3 (FP32) or the FP16 bound + 1e-3."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from parity import compare_hits_and_colours, device_scene
+from workloads import random_triangles_scene, tiny_scene, workload
+from workloads.views import look_at_pose
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lay():
+    return oracle.lp_layout()
+
+
+def _session(V, W, H, fov, poses, lp_fmt=0, disp_fmt=0, acuity=None):
+    return V.vafr_session_create(V.make_session_desc(W, H, fov, poses, lp_fmt, disp_fmt, acuity))
+
+
+def _render_lp(V, torch, scene_h, sess, n_tex, eye_mask=1, fp16=False):
+    eyes = bin(eye_mask).count("1")
+    dt = torch.float16 if fp16 else torch.float32
+    lp = torch.empty((eyes * n_tex, 4), dtype=dt, device="cuda")
+    ids = torch.empty(eyes * n_tex, dtype=torch.int32, device="cuda")
+    V.vafr_render_lp(scene_h, sess, eye_mask, lp, ids)
+    torch.cuda.synchronize()
+    assert V.vafr_session_check(sess) == 0
+    return lp.float().cpu().numpy(), ids.cpu().numpy()
+
+
+def test_layout_matches_oracle(V, lay):
+    pose = look_at_pose((0, 0, -3), (0, 0, 0))
+    for W, H in [(512, 512), (7680, 4320)]:
+        s = _session(V, W, H, 90.0, [pose])
+        counts, offs, ecc, n_tex = V.vafr_lp_layout(s)
+        assert n_tex == lay.total
+        assert np.array_equal(counts, lay.n_col)
+        assert np.array_equal(offs, lay.off_col)
+        np.testing.assert_allclose(ecc, lay.e_col, rtol=1e-6)
+        V.vafr_session_destroy(s)
+
+
+def test_lp_frame_random1k_full(V, torch_mod, lay):
+    w = workload("random1k")
+    d, sc = w.displays[0], w.scene
+    h, keep = device_scene(V, sc, torch_mod)
+    s = _session(V, d.width, d.height, d.fov_v_deg, d.poses)
+    gaze = d.gaze[0, 0]
+    V.vafr_set_gaze(s, 0, *gaze)
+    lp, ids = _render_lp(V, torch_mod, h, s, lay.total)
+    rgba, oid, ot, o, dd = oracle.render_lp(sc.tris, sc.albedo, sc.light_dir, lay, d.width,
+                                            d.height, d.fov_v_deg, gaze, d.poses[0])
+    summ = compare_hits_and_colours(sc.tris, o, dd, ids, lp, oid, ot, rgba, 1e-3)
+    assert 0.2 < (ids >= 0).mean() < 0.95
+    st = V.vafr_traversal_stats(h, s, 0)
+    assert st["rays"] == lay.total and st["hits"] == int((ids >= 0).sum())
+    print("random1k LP", summ, st)
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)
+
+
+def test_gt_random1k_full(V, torch_mod):
+    w = workload("random1k")
+    d, sc = w.displays[0], w.scene
+    h, keep = device_scene(V, sc, torch_mod)
+    s = _session(V, d.width, d.height, d.fov_v_deg, d.poses)
+    out = torch_mod.empty((d.height, d.width, 4), dtype=torch_mod.float32, device="cuda")
+    ids = torch_mod.empty(d.height * d.width, dtype=torch_mod.int32, device="cuda")
+    V.vafr_render_full_gt(h, s, 0, out, ids)
+    torch_mod.cuda.synchronize()
+    rgba, oid, ot, o, dd = oracle.render_gt(sc.tris, sc.albedo, sc.light_dir, d.width, d.height,
+                                            d.fov_v_deg, d.poses[0])
+    compare_hits_and_colours(sc.tris, o, dd, ids.cpu().numpy(), out.cpu().numpy().reshape(-1, 4),
+                             oid, ot, rgba, 1e-3)
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)
+
+
+@pytest.mark.parametrize("kind", ["empty", "single", "quad", "fan", "stack", "axis"])
+def test_lp_tiny_scenes(V, torch_mod, lay, kind):
+    sc = tiny_scene(kind)
+    pose = look_at_pose((0.0, 0.0, -3.0), (0, 0, 0))
+    h, keep = device_scene(V, sc, torch_mod)
+    s = _session(V, 640, 480, 90.0, [pose])
+    V.vafr_set_gaze(s, 0, 320.0, 240.0)
+    lp, ids = _render_lp(V, torch_mod, h, s, lay.total)
+    rgba, oid, ot, o, dd = oracle.render_lp(sc.tris, sc.albedo, sc.light_dir, lay, 640, 480, 90.0,
+                                            (320.0, 240.0), pose)
+    compare_hits_and_colours(sc.tris, o, dd, ids, lp, oid, ot, rgba, 1e-3)
+    if kind == "empty":
+        assert (ids == -1).all()
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def terrain(V, torch_mod):
+    w = workload("terrain4k", frames=240)
+    h, keep = device_scene(V, w.scene, torch_mod)
+    bvh = oracle.CpuBVH(w.scene.tris)
+    yield w, h, bvh
+    V.vafr_scene_destroy(h)
+
+
+@pytest.mark.parametrize("frame", [0, 120, 239])
+def test_lp_terrain_full_size_sampled(V, torch_mod, lay, terrain, frame):
+    w, h, bvh = terrain
+    d, sc = w.displays[0], w.scene
+    s = _session(V, d.width, d.height, d.fov_v_deg, d.poses)
+    gaze = d.gaze[frame, 0]
+    V.vafr_set_gaze(s, 0, *gaze)
+    lp, ids = _render_lp(V, torch_mod, h, s, lay.total)
+    rng = np.random.default_rng(frame)
+    tex = np.sort(rng.choice(lay.total, 65536, replace=False))
+    rgba, oid, ot, o, dd = oracle.render_lp(sc.tris, sc.albedo, sc.light_dir, lay, d.width,
+                                            d.height, d.fov_v_deg, gaze, d.poses[0], texels=tex,
+                                            bvh=bvh)
+    compare_hits_and_colours(sc.tris, o, dd, ids[tex], lp[tex], oid, ot, rgba, 1e-3)
+    V.vafr_session_destroy(s)
+
+
+def test_gt_terrain_full_size_sampled(V, torch_mod, terrain):
+    w, h, bvh = terrain
+    d, sc = w.displays[0], w.scene
+    s = _session(V, d.width, d.height, d.fov_v_deg, d.poses)
+    out = torch_mod.empty((d.height * d.width, 4), dtype=torch_mod.float32, device="cuda")
+    ids = torch_mod.empty(d.height * d.width, dtype=torch_mod.int32, device="cuda")
+    V.vafr_render_full_gt(h, s, 0, out, ids)
+    torch_mod.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    pix = np.sort(rng.choice(d.width * d.height, 65536, replace=False))
+    rgba, oid, ot, o, dd = oracle.render_gt(sc.tris, sc.albedo, sc.light_dir, d.width, d.height,
+                                            d.fov_v_deg, d.poses[0], pixels=pix, bvh=bvh)
+    compare_hits_and_colours(sc.tris, o, dd, ids.cpu().numpy()[pix], out.cpu().numpy()[pix], oid,
+                             ot, rgba, 1e-3)
+    V.vafr_session_destroy(s)
+
+
+def test_lp_fp16_binocular_and_gaze_outside(V, torch_mod, lay):
+    sc = random_triangles_scene(1024, seed=1001)
+    head = look_at_pose((0.0, 0.2, -3.0), (0, 0, 0))
+    from workloads.views import eye_pair_poses
+    poses = eye_pair_poses(head, 0.063)
+    W, H = 1920, 1080
+    h, keep = device_scene(V, sc, torch_mod)
+    s = _session(V, W, H, 100.0, poses, lp_fmt=1, disp_fmt=1)
+    gazes = [(-250.0, 1300.5), (W + 0.25, -3.75)]   # both outside the display
+    for e, g in enumerate(gazes):
+        V.vafr_set_gaze(s, e, *g)
+    lp, ids = _render_lp(V, torch_mod, h, s, lay.total, eye_mask=3, fp16=True)
+    rng = np.random.default_rng(11)
+    for e in range(2):
+        tex = np.sort(rng.choice(lay.total, 50000, replace=False))
+        rgba, oid, ot, o, dd = oracle.render_lp(sc.tris, sc.albedo, sc.light_dir, lay, W, H, 100.0,
+                                                gazes[e], poses[e], texels=tex)
+        # FP16 RNE: relative 2^-11 of values <= 1, plus the FP32 1e-3
+        compare_hits_and_colours(sc.tris, o, dd, ids[e * lay.total + tex],
+                                 lp[e * lay.total + tex], oid, ot, rgba, 1e-3 + 2.0 ** -11)
+    # each eye alone is bitwise the same as both together
+    for e in range(2):
+        lp1, ids1 = _render_lp(V, torch_mod, h, s, lay.total, eye_mask=1 << e, fp16=True)
+        assert np.array_equal(ids1, ids[e * lay.total:(e + 1) * lay.total])
+        assert np.array_equal(lp1, lp[e * lay.total:(e + 1) * lay.total])
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)
+
+
+def test_lp_independent_of_resolution(V, torch_mod, lay):
+    # Sec. 3.2.2: same FOV, pose and gaze direction -> same LP buffer at 1080p and 8K
+    sc = random_triangles_scene(1024, seed=1001)
+    pose = look_at_pose((0.0, 0.0, -3.0), (0, 0, 0))
+    h, keep = device_scene(V, sc, torch_mod)
+    outs = []
+    for W, H, g in [(1920, 1080, (1060.0, 490.0)), (7680, 4320, (4240.0, 1960.0))]:
+        s = _session(V, W, H, 100.0, [pose])
+        V.vafr_set_gaze(s, 0, *g)
+        outs.append(_render_lp(V, torch_mod, h, s, lay.total))
+        V.vafr_session_destroy(s)
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][0], outs[1][0])
+    V.vafr_scene_destroy(h)
+
+
+def test_invalid_arguments(V, torch_mod):
+    pose = look_at_pose((0.0, 0.0, -3.0), (0, 0, 0))
+    with pytest.raises(V.VafrError):
+        _session(V, 0, 100, 90.0, [pose])
+    with pytest.raises(V.VafrError):
+        _session(V, 100, 100, 180.0, [pose])
+    bad = V.make_acuity([0, 10, 5], [40, 10, 6])
+    with pytest.raises(V.VafrError):
+        _session(V, 100, 100, 90.0, [pose], acuity=bad)
+    s = _session(V, 100, 100, 90.0, [pose])
+    with pytest.raises(V.VafrError):
+        V.vafr_set_gaze(s, 0, math.nan, 1.0)
+    with pytest.raises(V.VafrError):
+        V.vafr_set_gaze(s, 1, 1.0, 1.0)
+    lp = torch_mod.empty((10, 4), device="cuda")
+    sc = random_triangles_scene(8, seed=1)
+    h, keep = device_scene(V, sc, torch_mod)
+    with pytest.raises(V.VafrError):   # gaze never set
+        V.vafr_render_lp(h, s, 1, lp)
+    V.vafr_set_gaze(s, 0, 50.0, 50.0)
+    with pytest.raises(V.VafrError):   # eye mask outside the session
+        V.vafr_render_lp(h, s, 2, lp)
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)

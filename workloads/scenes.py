@@ -75,7 +75,8 @@ def tiny_scene(kind: str, seed: int = 7) -> Scene:
         raise ValueError(kind)
     n = tris.shape[0]
     albedo = rng.uniform(0.2, 1.0, size=(n, 3)).astype(np.float32)
-    return Scene(tris.reshape(n, 3, 3), albedo, _unit(DEFAULT_LIGHT), f"tiny-{kind}")
+    return Scene(np.ascontiguousarray(tris.reshape(n, 3, 3), dtype=np.float32), albedo,
+                 _unit(DEFAULT_LIGHT), f"tiny-{kind}")
 
 
 # --------------------------------------------------------------------------
