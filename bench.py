@@ -325,12 +325,8 @@ def run_gpu(args, w):
     render_ms, recon_ms = per[:, 0], per[:, 1]
     gt_ms = gper[:, 0]
     total_s = step_ms.sum() / 1e3
-    if dist:
-        t = torch.tensor([total_s, e2e_s, gt_ms.mean()], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s, e2e_s, gt_mean = [float(x) for x in t.cpu()]
-    else:
-        gt_mean = float(gt_ms.mean())
+    from paper_2503_23410_gb300.dist import max_over_ranks
+    total_s, e2e_s, gt_mean = max_over_ranks([total_s, e2e_s, float(gt_ms.mean())], "cuda")
     mpix_frame = W_ * H_ * eyes / 1e6
     value = mpix_frame * args.steps * ws / total_s
     e2e_value = mpix_frame * e2e_steps * ws / e2e_s

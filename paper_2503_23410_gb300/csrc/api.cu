@@ -2,6 +2,7 @@
 // lifetimes, argument checking, the FP64 host set-up of the log-polar layout
 // (Sec. 3.2.2, Eqs. 9, 10, 12) and of each frame's gaze parameters (Eq. 3),
 // batching, CUDA-graph capture and the tile-shape autotuner.
+#include "layout.h"
 #include "vafr_internal.cuh"
 
 #include <atomic>
@@ -10,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits.h>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -67,68 +69,6 @@ bool is_device_ptr(const void* p) {
 
 int bytes_per_px(int fmt) { return fmt == VAFR_FMT_RGBA16F ? 8 : 16; }
 
-// ---- the acuity mapping, FP64 host side ----------------------------------------
-// MAR omega is piecewise linear through the pivots (E_k, 1/f_k) (Eq. 2 per
-// segment, Sec. 3.3).  On segment i: u(e) = U_i + (2/m_i) ln(1 + m_i (e - E_i) /
-// omega(E_i)) (Eq. 12 with the constants fixed by u(0) = 0 and continuity),
-// e(u) its inverse (Eq. 10), l(e) = 360 sin(2e)/omega(e) (Eq. 9).
-struct Mapping {
-    int n_seg = 0;
-    double E[VAFR_MAX_PIVOTS], m[VAFR_MAX_PIVOTS], w[VAFR_MAX_PIVOTS], U[VAFR_MAX_PIVOTS + 1];
-    double e_max = 60.0;
-
-    int init(const vafr_acuity& a) {
-        if (a.n_pivots < 2 || a.n_pivots > VAFR_MAX_PIVOTS) return -1;
-        if (a.pivot_ecc_deg[0] != 0.0) return -1;
-        for (int k = 0; k < a.n_pivots; ++k) {
-            if (!std::isfinite(a.pivot_ecc_deg[k]) || !(a.pivot_cpd[k] > 0.0) ||
-                !std::isfinite(a.pivot_cpd[k]))
-                return -1;
-            if (k > 0 && !(a.pivot_ecc_deg[k] > a.pivot_ecc_deg[k - 1])) return -1;
-        }
-        if (!(a.e_max_deg > 0.0) || !(a.e_max_deg < 90.0)) return -1;
-        n_seg = a.n_pivots - 1;
-        e_max = a.e_max_deg;
-        U[0] = 0.0;
-        for (int i = 0; i < n_seg; ++i) {
-            E[i] = a.pivot_ecc_deg[i];
-            const double w_lo = 1.0 / a.pivot_cpd[i], w_hi = 1.0 / a.pivot_cpd[i + 1];
-            const double span = a.pivot_ecc_deg[i + 1] - E[i];
-            m[i] = (w_hi - w_lo) / span;
-            w[i] = w_lo - m[i] * E[i];
-            U[i + 1] = U[i] + du(i, span);
-        }
-        E[n_seg] = a.pivot_ecc_deg[n_seg];
-        return 0;
-    }
-    // u gained over `de` degrees from the start of segment i
-    double du(int i, double de) const {
-        const double om0 = m[i] * E[i] + w[i];
-        if (m[i] == 0.0) return 2.0 * de / w[i];
-        return 2.0 / m[i] * std::log1p(m[i] * de / om0);
-    }
-    int seg_e(double e) const {
-        int i = 0;
-        while (i + 1 < n_seg && e >= E[i + 1]) ++i;
-        return i;
-    }
-    double u_of_e(double e) const {
-        const int i = seg_e(e);
-        return U[i] + du(i, e - E[i]);
-    }
-    double e_of_u(double u) const {
-        int i = 0;
-        while (i + 1 < n_seg && u >= U[i + 1]) ++i;
-        const double om0 = m[i] * E[i] + w[i];
-        if (m[i] == 0.0) return E[i] + (u - U[i]) * w[i] / 2.0;
-        return E[i] + std::expm1(m[i] * (u - U[i]) / 2.0) * om0 / m[i];
-    }
-    double l_of_e(double e) const {
-        const int i = seg_e(e);
-        return 360.0 * std::sin(2.0 * e * M_PI / 180.0) / (m[i] * e + w[i]);
-    }
-};
-
 }  // namespace
 
 // ---- objects ----------------------------------------------------------------------
@@ -161,15 +101,9 @@ struct vafr_session {
     int device = 0;
     int sms = 0;
     vafr_session_desc desc{};
-    Mapping map;
+    std::shared_ptr<const LayoutTables> lay;   // shared by sessions with the same acuity
     int n_cols = 0;
     int64_t n_texels = 0;
-    std::vector<double> e_col;
-    std::vector<int32_t> n_col;
-    std::vector<int64_t> off_col;
-    float* d_tan_e = nullptr;
-    int2* d_col = nullptr;
-    SegTable* d_seg = nullptr;
     unsigned* d_status = nullptr;
     unsigned long long* d_counter = nullptr;
     unsigned long long* d_stats = nullptr;
@@ -181,9 +115,6 @@ struct vafr_session {
     int render_variant = 0;
 
     ~vafr_session() {
-        cudaFree(d_tan_e);
-        cudaFree(d_col);
-        cudaFree(d_seg);
         cudaFree(d_status);
         cudaFree(d_counter);
         cudaFree(d_stats);
@@ -246,9 +177,14 @@ void fill_static(vafr_session* s, int eye) {
     f.H = d.height;
     f.lp_fmt = d.lp_format;
     f.disp_fmt = d.display_format;
-    f.seg = s->d_seg;
-    f.tan_e = s->d_tan_e;
-    f.col = s->d_col;
+    const LayoutTables& L = *s->lay;
+    f.tan_e = L.d_tan_e;
+    f.col = L.d_col;
+    f.col_pair = L.d_col_pair;
+    f.u_tab = L.d_u_tab;
+    f.work = L.d_work;
+    f.u_n = kUTable;
+    f.u_inv_h = (float)L.u_inv_h;
     f.n_cols = s->n_cols;
     f.n_texels = (int)s->n_texels;
     f.status = s->d_status;
@@ -440,74 +376,26 @@ int vafr_session_create(const vafr_session_desc* desc, vafr_session** out) {
     int sms = 0;
     int rc = check_device(&sms);
     if (rc) return rc;
+    std::shared_ptr<const LayoutTables> lay;
+    std::string why;
+    rc = get_layout(d.acuity, &lay, &why);
+    if (rc) return fail(rc, "%s", why.c_str());
     auto* s = new vafr_session();
     cudaGetDevice(&s->device);
     s->sms = sms;
     s->desc = d;
-    if (s->map.init(d.acuity) != 0) {
-        delete s;
-        return fail(VAFR_ERR_INVALID_ARG, "bad acuity pivots");
-    }
-    // discrete layout (Sec. 3.2.2): columns at u = c + 0.5 < u(e_max)
-    const double u_max = s->map.u_of_e(s->map.e_max);
-    int64_t acc = 0;
-    for (int c = 0; (double)c + 0.5 < u_max; ++c) {
-        const double e = s->map.e_of_u((double)c + 0.5);
-        int32_t nc = (int32_t)std::floor(s->map.l_of_e(e) + 0.5);
-        if (nc < 1) nc = 1;
-        s->e_col.push_back(e);
-        s->n_col.push_back(nc);
-        s->off_col.push_back(acc);
-        acc += nc;
-        if (acc > (1ll << 30)) {
-            delete s;
-            return fail(VAFR_ERR_INVALID_ARG, "LP layout too large");
-        }
-    }
-    s->n_cols = (int)s->e_col.size();
-    s->n_texels = acc;
-    if (s->n_cols == 0) {
-        delete s;
-        return fail(VAFR_ERR_INVALID_ARG, "empty LP layout");
-    }
-    std::vector<float> tan_e(s->n_cols);
-    std::vector<int2> col(s->n_cols);
-    for (int c = 0; c < s->n_cols; ++c) {
-        tan_e[c] = (float)std::tan(s->e_col[c] * M_PI / 180.0);
-        col[c] = make_int2((int)s->off_col[c], s->n_col[c]);
-    }
-    SegTable seg{};
-    seg.n_seg = s->map.n_seg;
-    for (int i = 0; i < s->map.n_seg; ++i) {
-        const double om0 = s->map.m[i] * s->map.E[i] + s->map.w[i];
-        seg.seg_e0[i] = (float)s->map.E[i];
-        seg.seg_u0[i] = (float)s->map.U[i];
-        if (s->map.m[i] == 0.0) {
-            seg.seg_k[i] = 0.0f;
-            seg.seg_a[i] = 0.0f;
-            seg.seg_b[i] = (float)(2.0 / s->map.w[i]);
-        } else {
-            seg.seg_k[i] = (float)(2.0 * M_LN2 / s->map.m[i]);
-            seg.seg_a[i] = (float)(s->map.m[i] / om0);
-            seg.seg_b[i] = 0.0f;
-        }
-    }
-    seg.e_max = (float)s->map.e_max;
+    s->lay = lay;
+    s->n_cols = lay->n_cols;
+    s->n_texels = lay->n_texels;
     auto bail = [&](cudaError_t e) {
         delete s;
         return fail(e == cudaErrorMemoryAllocation ? VAFR_ERR_OOM : VAFR_ERR_CUDA, "session: %s",
                     cudaGetErrorString(e));
     };
     cudaError_t e;
-    if ((e = cudaMalloc(&s->d_tan_e, sizeof(float) * s->n_cols)) != cudaSuccess) return bail(e);
-    if ((e = cudaMalloc(&s->d_col, sizeof(int2) * s->n_cols)) != cudaSuccess) return bail(e);
-    if ((e = cudaMalloc(&s->d_seg, sizeof(SegTable))) != cudaSuccess) return bail(e);
     if ((e = cudaMalloc(&s->d_status, sizeof(unsigned))) != cudaSuccess) return bail(e);
     if ((e = cudaMalloc(&s->d_counter, sizeof(unsigned long long))) != cudaSuccess) return bail(e);
     if ((e = cudaMalloc(&s->d_stats, 4 * sizeof(unsigned long long))) != cudaSuccess) return bail(e);
-    if ((e = cudaMemcpy(s->d_tan_e, tan_e.data(), sizeof(float) * s->n_cols, cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e);
-    if ((e = cudaMemcpy(s->d_col, col.data(), sizeof(int2) * s->n_cols, cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e);
-    if ((e = cudaMemcpy(s->d_seg, &seg, sizeof(SegTable), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e);
     if ((e = cudaMemset(s->d_status, 0, sizeof(unsigned))) != cudaSuccess) return bail(e);
     for (int eye = 0; eye < d.n_eyes; ++eye) fill_static(s, eye);
     *out = s;
@@ -526,10 +414,11 @@ int vafr_lp_layout(const vafr_session* s, int32_t* n_cols, int64_t* n_texels, in
     if (!s) return fail(VAFR_ERR_INVALID_ARG, "session is NULL");
     if (n_cols) *n_cols = s->n_cols;
     if (n_texels) *n_texels = s->n_texels;
+    const LayoutTables& L = *s->lay;
     for (int c = 0; c < s->n_cols; ++c) {
-        if (col_counts) col_counts[c] = s->n_col[c];
-        if (col_offsets) col_offsets[c] = s->off_col[c];
-        if (col_ecc_deg) col_ecc_deg[c] = (float)s->e_col[c];
+        if (col_counts) col_counts[c] = L.n_col[c];
+        if (col_offsets) col_offsets[c] = L.off_col[c];
+        if (col_ecc_deg) col_ecc_deg[c] = (float)L.e_col[c];
     }
     return VAFR_OK;
 }

@@ -292,6 +292,14 @@ __global__ void k_pack_nodes(const int2* __restrict__ child, const float* __rest
     nodes[4ll * i + 3] = make_float4(__int_as_float(c.x), __int_as_float(c.y), 0.0f, 0.0f);
 }
 
+__device__ __forceinline__ bool lex_less(float ax, float ay, float az, float bx, float by, float bz) {
+    return ax < bx || (ax == bx && (ay < by || (ay == by && az < bz)));
+}
+
+// Leaves store their vertices in lexicographic (x, y, z) order.  The
+// intersection test is two-sided, so the order carries no meaning, and
+// identical triangles given with different vertex orders then evaluate to
+// bit-identical t: the lower-id rule, not rounding, decides between them.
 __global__ void k_pack_leaves(const float* __restrict__ tris, const float* __restrict__ albedo,
                               const int32_t* __restrict__ ids, int n, float4* __restrict__ leaves,
                               float4* __restrict__ albedo4) {
@@ -299,9 +307,23 @@ __global__ void k_pack_leaves(const float* __restrict__ tris, const float* __res
     if (k >= n) return;
     const int id = ids[k];
     const float* t = tris + 9ll * id;
-    leaves[3ll * k + 0] = make_float4(t[0], t[1], t[2], __int_as_float(id));
-    leaves[3ll * k + 1] = make_float4(t[3], t[4], t[5], 0.0f);
-    leaves[3ll * k + 2] = make_float4(t[6], t[7], t[8], 0.0f);
+    float v[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[a][c] = t[3 * a + c];
+    // three-element sorting network
+#define VAFR_CSWAP(i, j)                                                                      \
+    if (lex_less(v[j][0], v[j][1], v[j][2], v[i][0], v[i][1], v[i][2])) {                     \
+        for (int c = 0; c < 3; ++c) { const float q = v[i][c]; v[i][c] = v[j][c]; v[j][c] = q; } \
+    }
+    VAFR_CSWAP(0, 1)
+    VAFR_CSWAP(1, 2)
+    VAFR_CSWAP(0, 1)
+#undef VAFR_CSWAP
+    leaves[3ll * k + 0] = make_float4(v[0][0], v[0][1], v[0][2], __int_as_float(id));
+    leaves[3ll * k + 1] = make_float4(v[1][0], v[1][1], v[1][2], 0.0f);
+    leaves[3ll * k + 2] = make_float4(v[2][0], v[2][1], v[2][2], 0.0f);
     // albedo in original order (thread k writes triangle k's albedo)
     if (albedo)
         albedo4[k] = make_float4(albedo[3ll * k], albedo[3ll * k + 1], albedo[3ll * k + 2], 0.0f);

@@ -4,21 +4,23 @@
 // Per pixel centre p = (x + 0.5, y + 0.5):
 //   d = p - gaze, computed as (x - floor(x0)) + (0.5 - frac(x0)) so the FP32
 //       offset is exact near the gaze even at 16K;
-//   e = atan(c_r |d|) in degrees, clamped to e_max (Eq. 3);
-//   u = u0 + k log2(1 + a (e - e0)) + b (e - e0) on e's segment (Eq. 12);
-//   angle fraction = atan2(dy, dx) / 2pi wrapped to [0, 1);
-//   columns c0 = floor(u - 0.5), c1 = c0 + 1 clamped to [0, C-1]; in each
-//   column rows floor(frac n_c - 0.5) and +1 wrapped modulo n_c.
+//   z = c_r |d| = tan(e) (Eq. 3), clamped to tan(e_max);
+//   u = u(e(z)) (Eq. 12) from a per-session table of cubic Hermite pieces on
+//       2,048 uniform intervals of z, built in FP64 on the host from the exact
+//       u(e) and du/dz (interpolation error < 1e-5 texel, below FP32 rounding);
+//   angle fraction = atan2(dy, dx) / 2pi in [0, 1), by octant reduction and an
+//       odd degree-15 polynomial for atan(t)/2pi on [0, 1] (near-minimax fit by
+//       Lawson's reweighted least squares, csrc/fit_atan.py; |err| < 3e-8);
+//   columns c0 = floor(u - 0.5), c1 = c0 + 1 clamped to [0, C-1] (one 16-byte
+//   load of the column-pair table); in each column rows floor(frac n_c - 0.5)
+//   and +1 wrapped modulo n_c; bilinear blend in FP32.
 // One block per display tile; a thread computes `PX` horizontally adjacent
-// pixels and writes them with one or two 16-byte streaming stores.  The LP
-// buffer (8-17 MB per eye) stays L2-resident; display writes go to HBM.
+// pixels and writes them with 16-byte streaming stores.  The LP buffer (8-17 MB
+// per eye) and the tables stay cache-resident; display writes go to HBM.
 #include "vafr_internal.cuh"
 
 namespace vafr {
 namespace {
-
-constexpr float kRad2Deg = 57.295779513082320876f;
-constexpr float kInv2Pi = 0.15915494309189533577f;
 
 __device__ __forceinline__ float4 load_lp(const void* lp, int fmt, int idx) {
     if (fmt == VAFR_FMT_RGBA16F) {
@@ -35,54 +37,70 @@ __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float w) {
                        fmaf(w, b.w - a.w, a.w));
 }
 
-__device__ __forceinline__ float4 column_sample(const void* lp, int fmt, int2 cc, float frac) {
-    const float v = fmaf(frac, (float)cc.y, -0.5f);
+// atan2(dy, dx) / 2pi wrapped to [0, 1); (0, 0) -> 0.
+__device__ __forceinline__ float angle_fraction(float dy, float dx) {
+    const float ax = fabsf(dx), ay = fabsf(dy);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float t = mx > 0.0f ? __fdividef(mn, mx) : 0.0f;
+    const float s = t * t;
+    float p = -0.0006453031091950834f;
+    p = fmaf(p, s, 0.0034795934334397316f);
+    p = fmaf(p, s, -0.008898717351257801f);
+    p = fmaf(p, s, 0.01534602977335453f);
+    p = fmaf(p, s, -0.022136269137263298f);
+    p = fmaf(p, s, 0.031745944172143936f);
+    p = fmaf(p, s, -0.05304612219333649f);
+    p = fmaf(p, s, 0.15915483236312866f);
+    float a = p * t;                       // first-octant fraction in [0, 1/8]
+    a = ay > ax ? 0.25f - a : a;           // first quadrant
+    a = dx < 0.0f ? 0.5f - a : a;          // upper half plane
+    a = dy < 0.0f ? 1.0f - a : a;          // full turn
+    return a;
+}
+
+__device__ __forceinline__ float4 column_sample(const void* lp, int fmt, int off, int n, float frac) {
+    const float v = fmaf(frac, (float)n, -0.5f);
     const float j0f = floorf(v);
     const float wv = v - j0f;
     int j0 = (int)j0f;
     int j1 = j0 + 1;
-    if (j0 < 0) j0 += cc.y;
-    if (j1 >= cc.y) j1 -= cc.y;
-    const float4 a = load_lp(lp, fmt, cc.x + j0);
-    const float4 b = load_lp(lp, fmt, cc.x + j1);
-    return lerp4(a, b, wv);
+    j0 = j0 < 0 ? j0 + n : j0;
+    j1 = j1 >= n ? j1 - n : j1;
+    return lerp4(load_lp(lp, fmt, off + j0), load_lp(lp, fmt, off + j1), wv);
 }
 
-struct SegRegs {
-    int n;
-    float e0[kMaxSeg], u0[kMaxSeg], k[kMaxSeg], a[kMaxSeg], b[kMaxSeg];
-    float e_max;
-};
-
-__device__ __forceinline__ float4 recon_pixel(const FrameDesc& f, const SegRegs& sg, int x, int y) {
+__device__ __forceinline__ float4 recon_pixel(const FrameDesc& f, int x, int y) {
     const float dx = (float)(x - f.gxi) + f.gxf;
     const float dy = (float)(y - f.gyi) + f.gyf;
-    const float r = sqrtf(fmaf(dx, dx, dy * dy));
-    const float e = fminf(atanf(f.cr * r) * kRad2Deg, sg.e_max);
-    int s = 0;
-#pragma unroll
-    for (int q = 1; q < kMaxSeg; ++q)
-        if (q < sg.n && e >= sg.e0[q]) s = q;
-    const float de = e - sg.e0[s];
-    const float u = sg.u0[s] + fmaf(sg.k[s], log2f(fmaf(sg.a[s], de, 1.0f)), sg.b[s] * de);
-    float frac = atan2f(dy, dx) * kInv2Pi;
-    if (frac < 0.0f) frac += 1.0f;
+    const float z = f.cr * sqrtf(fmaf(dx, dx, dy * dy));
+    const float s = fminf(z * f.u_inv_h, (float)f.u_n);
+    const int i = min((int)s, f.u_n - 1);
+    const float t = s - (float)i;
+    const float4 c = __ldg(f.u_tab + i);
+    const float u = fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
+    const float frac = angle_fraction(dy, dx);
     const float uf = fminf(fmaxf(u - 0.5f, 0.0f), (float)(f.n_cols - 1));
     const int c0 = (int)uf;
     const float wu = uf - (float)c0;
-    const int c1 = min(c0 + 1, f.n_cols - 1);
-    const int2 cc0 = __ldg(f.col + c0), cc1 = __ldg(f.col + c1);
-    const float4 v0 = column_sample(f.lp, f.lp_fmt, cc0, frac);
-    const float4 v1 = column_sample(f.lp, f.lp_fmt, cc1, frac);
+    const int4 cp = __ldg(f.col_pair + c0);  // (offset, count) of c0 and of min(c0 + 1, C - 1)
+    const float4 v0 = column_sample(f.lp, f.lp_fmt, cp.x, cp.y, frac);
+    const float4 v1 = column_sample(f.lp, f.lp_fmt, cp.z, cp.w, frac);
     return lerp4(v0, v1, wu);
+}
+
+__device__ __forceinline__ uint2 pack_half4(float4 p) {
+    const __half2 a = __floats2half2_rn(p.x, p.y), c = __floats2half2_rn(p.z, p.w);
+    uint2 q;
+    q.x = *reinterpret_cast<const unsigned*>(&a);
+    q.y = *reinterpret_cast<const unsigned*>(&c);
+    return q;
 }
 
 template <int TW, int TH, int PX, class B>
 __global__ void __launch_bounds__((TW / PX) * TH)
 k_reconstruct(const __grid_constant__ B b) {
-    __shared__ SegRegs sseg;
     __shared__ int sfi;
-    const long long tile = blockIdx.x;
+    const int tile = (int)blockIdx.x;
     if (threadIdx.x == 0) {
         int lo = 0, hi = b.n - 1;
         while (lo < hi) {
@@ -90,51 +108,30 @@ k_reconstruct(const __grid_constant__ B b) {
             if (b.d[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
         }
         sfi = lo;
-        const SegTable* g = b.d[lo].seg;
-        sseg.n = g->n_seg;
-        for (int q = 0; q < kMaxSeg; ++q) {
-            sseg.e0[q] = g->seg_e0[q];
-            sseg.u0[q] = g->seg_u0[q];
-            sseg.k[q] = g->seg_k[q];
-            sseg.a[q] = g->seg_a[q];
-            sseg.b[q] = g->seg_b[q];
-        }
-        sseg.e_max = g->e_max;
     }
     __syncthreads();
     const FrameDesc& f = b.d[sfi];
-    const SegRegs& sg = sseg;
-    const long long local = tile - f.tile_begin;
+    const int local = tile - (int)f.tile_begin;
     const int tiles_x = (f.W + TW - 1) / TW;
-    const int tx = (int)(local % tiles_x), ty = (int)(local / tiles_x);
+    const int ty = local / tiles_x;
+    const int tx = local - ty * tiles_x;
     constexpr int TX = TW / PX;
     const int x0 = tx * TW + (int)(threadIdx.x % TX) * PX;
     const int y = ty * TH + (int)(threadIdx.x / TX);
     if (y >= f.H) return;
     const long long row = (long long)y * f.W;
     if (f.disp_fmt == VAFR_FMT_RGBA16F) {
-        // PX pixels of 8 bytes
         if (PX == 2 && x0 + 1 < f.W && ((row + x0) & 1) == 0) {
-            const float4 p0 = recon_pixel(f, sg, x0, y), p1 = recon_pixel(f, sg, x0 + 1, y);
-            const __half2 a = __floats2half2_rn(p0.x, p0.y), c = __floats2half2_rn(p0.z, p0.w);
-            const __half2 d = __floats2half2_rn(p1.x, p1.y), e = __floats2half2_rn(p1.z, p1.w);
-            uint4 pk;
-            pk.x = *reinterpret_cast<const unsigned*>(&a);
-            pk.y = *reinterpret_cast<const unsigned*>(&c);
-            pk.z = *reinterpret_cast<const unsigned*>(&d);
-            pk.w = *reinterpret_cast<const unsigned*>(&e);
-            __stcs(reinterpret_cast<uint4*>(reinterpret_cast<uint2*>(f.disp) + row + x0), pk);
+            const uint2 a = pack_half4(recon_pixel(f, x0, y));
+            const uint2 c = pack_half4(recon_pixel(f, x0 + 1, y));
+            __stcs(reinterpret_cast<uint4*>(reinterpret_cast<uint2*>(f.disp) + row + x0),
+                   make_uint4(a.x, a.y, c.x, c.y));
         } else {
 #pragma unroll
             for (int q = 0; q < PX; ++q) {
                 const int x = x0 + q;
                 if (x >= f.W) break;
-                const float4 p = recon_pixel(f, sg, x, y);
-                const __half2 a = __floats2half2_rn(p.x, p.y), c = __floats2half2_rn(p.z, p.w);
-                uint2 pk;
-                pk.x = *reinterpret_cast<const unsigned*>(&a);
-                pk.y = *reinterpret_cast<const unsigned*>(&c);
-                __stcs(reinterpret_cast<uint2*>(f.disp) + row + x, pk);
+                __stcs(reinterpret_cast<uint2*>(f.disp) + row + x, pack_half4(recon_pixel(f, x, y)));
             }
         }
     } else {
@@ -142,7 +139,7 @@ k_reconstruct(const __grid_constant__ B b) {
         for (int q = 0; q < PX; ++q) {
             const int x = x0 + q;
             if (x >= f.W) break;
-            __stcs(reinterpret_cast<float4*>(f.disp) + row + x, recon_pixel(f, sg, x, y));
+            __stcs(reinterpret_cast<float4*>(f.disp) + row + x, recon_pixel(f, x, y));
         }
     }
 }
@@ -158,8 +155,7 @@ cudaError_t launch_shape(const B& b, cudaStream_t s) {
 }  // namespace
 
 // Tile shapes the autotuner chooses between (pixels).  The 16-byte FP16 pair
-// store needs an even pixel offset: every tile width is even and PX = 2 tiles
-// start at even x.
+// store needs an even pixel offset, checked per thread.
 ReconShape recon_shape(int variant) {
     switch (variant) {
         case 0: return {64, 8, 2};

@@ -240,21 +240,20 @@ __device__ __forceinline__ int find_frame(const B& b, long long w, bool tiles) {
     return lo;
 }
 
-// LP ray of texel t of frame f (Eqs. 3, 10, 11): the screen point at distance
-// r = tan(e_c)/c_r from the gaze at angle (j + 0.5) 360/n_c, unprojected:
-// camera direction (tan(e_c) cos(phi) + gx, -tan(e_c) sin(phi) + gy, 1).
-__device__ __forceinline__ void lp_ray(const FrameDesc& f, int t, Ray& r) {
-    int lo = 0, hi = f.n_cols - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(&f.col[mid].x) <= t) lo = mid; else hi = mid - 1;
-    }
-    const int2 cc = __ldg(&f.col[lo]);
-    const int j = t - cc.x;
-    const float te = __ldg(&f.tan_e[lo]);
+// LP ray of the frame's work item k (Eqs. 3, 10, 11): work items visit the
+// texels in screen-space Morton order; texel t = (c, j) sits at distance
+// r = tan(e_c)/c_r from the gaze at angle phi = (j + 0.5) 360/n_c, so its
+// camera direction is (tan(e_c) cos(phi) + gx, -tan(e_c) sin(phi) + gy, 1).
+// Returns the texel index.
+__device__ __forceinline__ int lp_ray(const FrameDesc& f, int k, Ray& r) {
+    const int2 tc = __ldg(f.work + k);
+    const int2 cc = __ldg(&f.col[tc.y]);
+    const int j = tc.x - cc.x;
+    const float te = __ldg(&f.tan_e[tc.y]);
     float sp, cp;
     sincospif(__fdiv_rn((float)(2 * j + 1), (float)cc.y), &sp, &cp);
     world_ray(f, fmaf(te, cp, f.gx), fmaf(-te, sp, f.gy), r);
+    return tc.x;
 }
 
 template <int TPB, int FETCH, class B>
@@ -272,9 +271,8 @@ k_render_lp(const SceneDev sc, const __grid_constant__ B b) {
             if (w >= b.total_work) break;
             const int fi = find_frame(b, w, false);
             const FrameDesc& f = b.d[fi];
-            const int t = (int)(w - f.work_begin);
             Ray r;
-            lp_ray(f, t, r);
+            const int t = lp_ray(f, (int)(w - f.work_begin), r);
             ray_setup(r);
             Hit h;
             const unsigned fault = traverse<false>(sc, r, h, nullptr, nullptr);

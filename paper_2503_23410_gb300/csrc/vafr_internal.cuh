@@ -37,21 +37,11 @@ struct SceneDev {
     unsigned* status;       // device status word
 };
 
-// ---- per session: forward-map constants -------------------------------------
-// Immutable after session creation; lives in device memory and is reached
-// through FrameDesc::seg.  u(e) on segment s (e in [e0_s, e0_{s+1})):
-//   u = u0 + k log2(1 + a (e - e0)) + b (e - e0)
-// (k, a, b) = (2 ln2 / m, m / (m e0 + w), 0) for a sloped MAR segment and
-// (0, 0, 2 / w) for a flat one (Eq. 12 and its m -> 0 limit).
-struct SegTable {
-    int n_seg;
-    float seg_e0[kMaxSeg];
-    float seg_u0[kMaxSeg];
-    float seg_k[kMaxSeg];
-    float seg_a[kMaxSeg];
-    float seg_b[kMaxSeg];
-    float e_max;            // deg
-};
+// ---- per session: forward-map table ------------------------------------------
+// u as a function of z = tan(e) = c_r r on [0, tan(e_max)] (Eqs. 3, 12): kUTable
+// uniform intervals, interval i holding the cubic Hermite piece
+// u = c.x + t (c.y + t (c.z + t c.w)), t in [0, 1].
+constexpr int kUTable = 2048;
 
 // ---- one frame-eye of work (kernel parameter; filled on the host in FP64,
 // rounded to FP32) ------------------------------------------------------------
@@ -65,9 +55,13 @@ struct FrameDesc {
     float gxf, gyf;         // 0.5 - fractional part of the gaze point
     int W, H;
     int lp_fmt, disp_fmt;
-    const SegTable* seg;    // device
     const float* tan_e;     // device [C] tan(e_c) of the column centres
     const int2* col;        // device [C] (first texel, texel count)
+    const int4* col_pair;   // device [C] (first, count) of c and of min(c + 1, C - 1)
+    const float4* u_tab;    // device [u_n] cubic pieces of u(z)
+    const int2* work;       // device [n_texels] (texel, column) in processing order
+    int u_n;                // number of pieces
+    float u_inv_h;          // u_n / tan(e_max)
     int n_cols;
     int n_texels;
     void* lp;
