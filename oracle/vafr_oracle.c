@@ -268,12 +268,28 @@ static void wray_init(or_wray* r, const double o[3], const double d[3]) {
     r->o[0] = o[0]; r->o[1] = o[1]; r->o[2] = o[2];
 }
 
+/* Vertices in lexicographic (x, y, z) order: the two-sided test and the hit
+ * rule do not depend on vertex order, so evaluating every triangle in one
+ * canonical order makes identical triangles tie exactly in FP64 as well. */
+static void canonical_vertices(const float* tri, const float* v[3]) {
+    v[0] = tri; v[1] = tri + 3; v[2] = tri + 6;
+    for (int pass = 0; pass < 3; ++pass) {
+        int i = pass == 1 ? 1 : 0, j = i + 1;
+        const float* a = v[i];
+        const float* b = v[j];
+        int b_first = b[0] < a[0] || (b[0] == a[0] && (b[1] < a[1] || (b[1] == a[1] && b[2] < a[2])));
+        if (b_first) { v[i] = b; v[j] = a; }
+    }
+}
+
 static int wray_hit(const or_wray* r, const float* tri, double* t_out) {
+    const float* v[3];
+    canonical_vertices(tri, v);
     double A[3], B[3], C[3];
     for (int k = 0; k < 3; ++k) {
-        A[k] = (double)tri[k] - r->o[k];
-        B[k] = (double)tri[3 + k] - r->o[k];
-        C[k] = (double)tri[6 + k] - r->o[k];
+        A[k] = (double)v[0][k] - r->o[k];
+        B[k] = (double)v[1][k] - r->o[k];
+        C[k] = (double)v[2][k] - r->o[k];
     }
     double Ax = A[r->kx] - r->Sx * A[r->kz], Ay = A[r->ky] - r->Sy * A[r->kz];
     double Bx = B[r->kx] - r->Sx * B[r->kz], By = B[r->ky] - r->Sy * B[r->kz];
@@ -627,10 +643,13 @@ void or_reconstruct_points(const or_acuity* a, double e_max, const or_view* v,
 
 /* ------------------------------------------------------------------------- */
 /* LBVH reference (Karras 2012).  Morton codes from the centroid sum
- * s = (v0 + v1) + v2 in FP32, quantised against the scene's s-bounds with
- * one IEEE FP32 op at a time: q = min((uint)((s - lo)/(hi - lo) * 1024), 1023)
- * (q = 0 on a degenerate axis); 10 bits per axis interleaved x-major
- * (x bit b -> code bit 3b+2, y -> 3b+1, z -> 3b). */
+ * s = (v0 + v1) + v2 in FP32, quantised on a cubic grid spanning the largest
+ * extent of the scene's s-bounds, one IEEE FP32 op at a time:
+ *   ext = max over axes of (hi - lo),  q = min((uint)((s - lo)/ext * 1024), 1023)
+ * (q = 0 for every axis when ext = 0); 10 bits per axis interleaved x-major
+ * (x bit b -> code bit 3b+2, y -> 3b+1, z -> 3b).  A cubic grid splits long
+ * axes before short ones (a terrain is not cut along its thin height axis
+ * as often as along its extent). */
 
 static uint32_t spread10(uint32_t q) {
     uint32_t out = 0;
@@ -649,10 +668,14 @@ void or_morton(const float* tris, int64_t n, uint32_t* codes) {
             if (v < lo[k]) lo[k] = v;
             if (v > hi[k]) hi[k] = v;
         }
+    volatile float ext = 0.0f;
+    for (int k = 0; k < 3; ++k) {
+        volatile float e = hi[k] - lo[k];
+        if (e > ext) ext = e;
+    }
     for (int64_t i = 0; i < n; ++i) {
         uint32_t q[3];
         for (int k = 0; k < 3; ++k) {
-            volatile float ext = hi[k] - lo[k];
             if (!(ext > 0.0f)) { q[k] = 0; continue; }
             volatile float num = s[3 * i + k] - lo[k];
             volatile float t = num / ext;

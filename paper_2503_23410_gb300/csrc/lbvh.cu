@@ -1,7 +1,8 @@
 // lbvh.cu -- LBVH construction on the GPU (Karras 2012, "Maximizing Parallelism
 // in the Construction of BVHs, Octrees, and k-d Trees"):
 //   1. scene bounds of the triangle centroid sums s = (v0 + v1) + v2,
-//   2. 30-bit Morton codes of s quantised to 1024 cells per axis,
+//   2. 30-bit Morton codes of s on a cubic grid of 1024 cells along the
+//      largest extent of the bounds,
 //   3. stable LSD radix sort of (code, triangle id), 4 passes of 8 bits,
 //   4. binary radix tree: one thread per internal node,
 //   5. bottom-up FP32 bounds with one arrival counter per internal node,
@@ -82,11 +83,13 @@ __global__ void k_morton(const float* __restrict__ tris, int n, const float* __r
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float* t = tris + 9ll * i;
+    // cubic grid: every axis is scaled by the largest extent of the bounds
+    const float ext = fmaxf(fmaxf(__fsub_rn(bounds[3], bounds[0]), __fsub_rn(bounds[4], bounds[1])),
+                            __fsub_rn(bounds[5], bounds[2]));
     uint32_t q[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float lo = bounds[k], hi = bounds[3 + k];
-        const float ext = __fsub_rn(hi, lo);
+        const float lo = bounds[k];
         if (!(ext > 0.0f)) { q[k] = 0u; continue; }
         const float s = centroid_sum(t, k);
         const float u = __fdiv_rn(__fsub_rn(s, lo), ext);

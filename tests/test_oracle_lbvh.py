@@ -26,6 +26,15 @@ def test_morton_hand_computed():
     assert codes.tolist() == want
 
 
+def test_morton_cubic_grid():
+    # centroid-sum extents 3072 (x) and 1536 (y): every axis is scaled by the
+    # largest extent, so t = 3p / 3072 = p / 1024 and q = p (1023 at 1024)
+    codes = oracle.morton(_point_tris([[0, 0, 0], [1024, 512, 0], [0, 512, 0], [256, 256, 0]]))
+    # (0,0,0) -> 0; (1023,512,0): x bits all set, y bit 9 -> 0x24924924 | 2**28;
+    # (0,512,0) -> y bit 9 -> bit 28; (256,256,0) -> x bit 8 (bit 26) + y bit 8 (bit 25)
+    assert codes.tolist() == [0, 0x24924924 | 2**28, 2**28, 2**26 + 2**25]
+
+
 def test_morton_degenerate_axis():
     # y and z have zero extent (q = 0 there): only the x bits 2, 5, ..., 29 can be set
     codes = oracle.morton(_point_tris([[0, 5, 0], [1024, 5, 0], [512, 5, 0]]))
