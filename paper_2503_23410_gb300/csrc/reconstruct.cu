@@ -4,7 +4,7 @@
 // Per pixel centre p = (x + 0.5, y + 0.5):
 //   d = p - gaze, computed as (x - floor(x0)) + (0.5 - frac(x0)) so the FP32
 //       offset is exact near the gaze even at 16K;
-//   z = c_r |d| = tan(e) (Eq. 3), clamped to tan(e_max);
+//   z = c_r |d| = tan(e) (Eq. 3; |d| = d.d rsqrt(d.d)), clamped to tan(e_max);
 //   u = u(e(z)) (Eq. 12) from a per-session table of cubic Hermite pieces on
 //       2,048 uniform intervals of z, built in FP64 on the host from the exact
 //       u(e) and du/dz (interpolation error < 1e-5 texel, below FP32 rounding);
@@ -69,17 +69,49 @@ __device__ __forceinline__ float4 column_sample(const void* lp, int fmt, int off
     return lerp4(load_lp(lp, fmt, off + j0), load_lp(lp, fmt, off + j1), wv);
 }
 
-__device__ __forceinline__ float4 recon_pixel(const FrameDesc& f, int x, int y) {
+// Frame parameters copied to registers once per thread: the descriptor lives in
+// parameter space, and the compiler cannot prove that display stores leave it
+// unchanged, so reading it per pixel would reload every field.
+struct ReconRegs {
+    int gxi, gyi;
+    float gxf, gyf, cr, u_inv_h, u_nf, cmax;
+    int u_last;
+    const float4* u_tab;
+    const int4* col_pair;
+    const void* lp;
+    int lp_fmt;
+};
+
+__device__ __forceinline__ ReconRegs load_regs(const FrameDesc& f) {
+    ReconRegs r;
+    r.gxi = f.gxi;
+    r.gyi = f.gyi;
+    r.gxf = f.gxf;
+    r.gyf = f.gyf;
+    r.cr = f.cr;
+    r.u_inv_h = f.u_inv_h;
+    r.u_nf = (float)f.u_n;
+    r.u_last = f.u_n - 1;
+    r.cmax = (float)(f.n_cols - 1);
+    r.u_tab = f.u_tab;
+    r.col_pair = f.col_pair;
+    r.lp = f.lp;
+    r.lp_fmt = f.lp_fmt;
+    return r;
+}
+
+__device__ __forceinline__ float4 recon_pixel(const ReconRegs& f, int x, int y) {
     const float dx = (float)(x - f.gxi) + f.gxf;
     const float dy = (float)(y - f.gyi) + f.gyf;
-    const float z = f.cr * sqrtf(fmaf(dx, dx, dy * dy));
-    const float s = fminf(z * f.u_inv_h, (float)f.u_n);
-    const int i = min((int)s, f.u_n - 1);
+    const float r2 = fmaf(dx, dx, dy * dy);
+    const float z = r2 > 0.0f ? f.cr * (r2 * rsqrtf(r2)) : 0.0f;   // c_r |d| = tan(e)
+    const float s = fminf(z * f.u_inv_h, f.u_nf);
+    const int i = min((int)s, f.u_last);
     const float t = s - (float)i;
     const float4 c = __ldg(f.u_tab + i);
     const float u = fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
     const float frac = angle_fraction(dy, dx);
-    const float uf = fminf(fmaxf(u - 0.5f, 0.0f), (float)(f.n_cols - 1));
+    const float uf = fminf(fmaxf(u - 0.5f, 0.0f), f.cmax);
     const int c0 = (int)uf;
     const float wu = uf - (float)c0;
     const int4 cp = __ldg(f.col_pair + c0);  // (offset, count) of c0 and of min(c0 + 1, C - 1)
@@ -110,36 +142,39 @@ k_reconstruct(const __grid_constant__ B b) {
         sfi = lo;
     }
     __syncthreads();
-    const FrameDesc& f = b.d[sfi];
-    const int local = tile - (int)f.tile_begin;
-    const int tiles_x = (f.W + TW - 1) / TW;
+    const FrameDesc& fd = b.d[sfi];
+    const ReconRegs f = load_regs(fd);
+    const int W = fd.W, H = fd.H;
+    void* const disp = fd.disp;
+    const int local = tile - (int)fd.tile_begin;
+    const int tiles_x = (W + TW - 1) / TW;
     const int ty = local / tiles_x;
     const int tx = local - ty * tiles_x;
     constexpr int TX = TW / PX;
     const int x0 = tx * TW + (int)(threadIdx.x % TX) * PX;
     const int y = ty * TH + (int)(threadIdx.x / TX);
-    if (y >= f.H) return;
-    const long long row = (long long)y * f.W;
-    if (f.disp_fmt == VAFR_FMT_RGBA16F) {
-        if (PX == 2 && x0 + 1 < f.W && ((row + x0) & 1) == 0) {
+    if (y >= H) return;
+    const long long row = (long long)y * W;
+    if (fd.disp_fmt == VAFR_FMT_RGBA16F) {
+        if (PX == 2 && x0 + 1 < W && ((row + x0) & 1) == 0) {
             const uint2 a = pack_half4(recon_pixel(f, x0, y));
             const uint2 c = pack_half4(recon_pixel(f, x0 + 1, y));
-            __stcs(reinterpret_cast<uint4*>(reinterpret_cast<uint2*>(f.disp) + row + x0),
+            __stcs(reinterpret_cast<uint4*>(reinterpret_cast<uint2*>(disp) + row + x0),
                    make_uint4(a.x, a.y, c.x, c.y));
         } else {
 #pragma unroll
             for (int q = 0; q < PX; ++q) {
                 const int x = x0 + q;
-                if (x >= f.W) break;
-                __stcs(reinterpret_cast<uint2*>(f.disp) + row + x, pack_half4(recon_pixel(f, x, y)));
+                if (x >= W) break;
+                __stcs(reinterpret_cast<uint2*>(disp) + row + x, pack_half4(recon_pixel(f, x, y)));
             }
         }
     } else {
 #pragma unroll
         for (int q = 0; q < PX; ++q) {
             const int x = x0 + q;
-            if (x >= f.W) break;
-            __stcs(reinterpret_cast<float4*>(f.disp) + row + x, recon_pixel(f, x, y));
+            if (x >= W) break;
+            __stcs(reinterpret_cast<float4*>(disp) + row + x, recon_pixel(f, x, y));
         }
     }
 }
