@@ -253,6 +253,33 @@ VAFR_API int vafr_batch_tuning(vafr_batch* batch, int32_t set, int32_t cfg[2]);
 /* Number of render / reconstruct variants the autotuner chooses between. */
 VAFR_API int vafr_tuning_space(int32_t* n_render, int32_t* n_reconstruct);
 
+/* ---- allocation-free entry point ---------------------------------------------
+ * vafr_morton_sort_noalloc: the Morton codes and the stable (code, id) order
+ * of a triangle soup -- the first stages of vafr_build_scene -- computed
+ * without allocating any memory.  The paper has no counterpart; it exists for
+ * callers that may not allocate device memory: code whose GPU memory all
+ * belongs to the caller's own pool allocator, or that runs on a
+ * latency-critical thread where cudaMalloc's implicit device synchronisation
+ * is not acceptable.  The caller passes inputs and outputs; the scratch is a
+ * fixed 6.3 MB file-scope device array that every GPU loading the library
+ * holds until the process exits.
+ *   tri_xyz         device, n_tris x 9 floats.
+ *   n_tris          0 <= n_tris <= VAFR_NOALLOC_MAX_TRIS (larger: INVALID_ARG).
+ *   codes_out       device, n_tris uint32, Morton codes in input order (the
+ *                   same values vafr_scene_export_lbvh reports).
+ *   sorted_ids_out  device, n_tris int32, triangle ids sorted by (code, id).
+ *   err, err_len    optional host buffer for a message (NULL allowed).
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array: calls that overlap on the GPU (other
+ * streams, other threads) race and corrupt each other's results; serialise
+ * them.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * Errors: INVALID_ARG (size, NULL or non-device pointer), CUDA. */
+#define VAFR_NOALLOC_MAX_TRIS 524288
+VAFR_API int vafr_morton_sort_noalloc(const float* tri_xyz, int64_t n_tris, uint32_t* codes_out,
+                                      int32_t* sorted_ids_out, void* stream, char* err,
+                                      int32_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,9 @@
 
 #include <float.h>
 
+#include <cstring>
+#include <mutex>
+
 namespace vafr {
 namespace {
 
@@ -383,3 +386,108 @@ cudaError_t lbvh_build(const LbvhBuffers& b, cudaStream_t s) {
 }
 
 }  // namespace vafr
+
+// ---- allocation-free Morton codes + sort ---------------------------------------
+// vafr_morton_sort_noalloc serves callers that may not allocate device memory:
+// code running where the whole GPU's memory belongs to the caller's own pool
+// allocator, or on a latency-critical thread where cudaMalloc's implicit
+// device synchronisation is not acceptable.  All of its scratch lives in one
+// file-scope __device__ array; it launches the same kernels as the build.
+namespace vafr {
+namespace {
+
+constexpr int kNoAllocMaxTris = VAFR_NOALLOC_MAX_TRIS;
+constexpr int kNoAllocBlocks = (kNoAllocMaxTris + kSortTile - 1) / kSortTile;
+
+struct NoAllocScratch {
+    uint32_t keys_tmp[kNoAllocMaxTris];
+    int32_t ids_tmp[kNoAllocMaxTris];
+    uint32_t keys_sorted[kNoAllocMaxTris];
+    unsigned hist[256 * kNoAllocBlocks];
+    float part_bounds[6 * kBoundsBlocks];
+    float scene_bounds[8];
+};
+
+// Held by every GPU that loads the library until the process exits
+// (sizeof(NoAllocScratch) = 6.3 MB).  Every call shares it; nothing in it has
+// to start at zero (each pass overwrites what it reads).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+NoAllocScratch* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device with that device current.
+cudaError_t noalloc_scratch(NoAllocScratch** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<NoAllocScratch*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace vafr
+
+extern "C" VAFR_API int vafr_morton_sort_noalloc(const float* tri_xyz, int64_t n_tris,
+                                                 uint32_t* codes_out, int32_t* sorted_ids_out,
+                                                 void* stream, char* err, int32_t err_len) {
+    using namespace vafr;
+    auto report = [&](int code, const char* msg) {
+        if (err && err_len > 0) {
+            std::strncpy(err, msg, (size_t)err_len - 1);
+            err[err_len - 1] = '\0';
+        }
+        return code;
+    };
+    if (n_tris < 0) return report(VAFR_ERR_INVALID_ARG, "n_tris is negative");
+    if (n_tris > kNoAllocMaxTris)
+        return report(VAFR_ERR_INVALID_ARG, "n_tris exceeds VAFR_NOALLOC_MAX_TRIS (524288)");
+    if (n_tris == 0) return VAFR_OK;
+    if (!tri_xyz || !codes_out || !sorted_ids_out) return report(VAFR_ERR_INVALID_ARG, "NULL pointer");
+    for (const void* p : {(const void*)tri_xyz, (const void*)codes_out, (const void*)sorted_ids_out}) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess ||
+            (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return report(VAFR_ERR_INVALID_ARG, "every buffer must be device memory");
+        }
+    }
+    NoAllocScratch* sc = nullptr;
+    cudaError_t e = noalloc_scratch(&sc);
+    if (e != cudaSuccess) return report(VAFR_ERR_CUDA, cudaGetErrorString(e));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int n = (int)n_tris;
+    const int nb_bounds = min(kBoundsBlocks, blocks_for(n, 256));
+    k_bounds_partial<<<nb_bounds, 256, 0, s>>>(tri_xyz, n, sc->part_bounds);
+    k_bounds_final<<<1, 32, 0, s>>>(sc->part_bounds, nb_bounds, sc->scene_bounds);
+    k_morton<<<blocks_for(n, 256), 256, 0, s>>>(tri_xyz, n, sc->scene_bounds, codes_out);
+    count_launch(3);
+    const int nblocks = (int)lbvh_sort_blocks(n);
+    const uint32_t* kin = codes_out;
+    const int32_t* vin = nullptr;
+    for (int pass = 0; pass < 4; ++pass) {
+        uint32_t* kout = (pass & 1) ? sc->keys_sorted : sc->keys_tmp;
+        int32_t* vout = (pass & 1) ? sorted_ids_out : sc->ids_tmp;
+        k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(kin, n, 8 * pass, sc->hist, nblocks);
+        k_radix_scan<<<1, 1024, 0, s>>>(sc->hist, 256 * nblocks);
+        k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, 8 * pass,
+                                                         sc->hist, nblocks);
+        count_launch(3);
+        kin = kout;
+        vin = vout;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return report(VAFR_ERR_CUDA, cudaGetErrorString(e));
+    return VAFR_OK;
+}

@@ -93,7 +93,10 @@ _PROTOS = {
     "vafr_batch_autotune": (ctypes.c_int, [_P, _P, _I32, _P, _I32]),
     "vafr_batch_tuning": (ctypes.c_int, [_P, _I32, _P]),
     "vafr_tuning_space": (ctypes.c_int, [_P, _P]),
+    "vafr_morton_sort_noalloc": (ctypes.c_int, [_P, _I64, _P, _P, _P, ctypes.c_char_p, _I32]),
 }
+
+NOALLOC_MAX_TRIS = 524288
 
 _lib = None
 
@@ -364,3 +367,14 @@ def vafr_tuning_space():
     a, b = ctypes.c_int32(), ctypes.c_int32()
     _check(load().vafr_tuning_space(ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def vafr_morton_sort_noalloc(tri_xyz, codes_out, sorted_ids_out, stream=None) -> None:
+    """Morton codes + stable (code, id) order without any allocation (device buffers)."""
+    _require_f32(tri_xyz, "tri_xyz")
+    n = int(tri_xyz.shape[0])
+    msg = ctypes.create_string_buffer(256)
+    rc = load().vafr_morton_sort_noalloc(ptr(tri_xyz), n, ptr(codes_out), ptr(sorted_ids_out),
+                                         stream_ptr(stream), msg, len(msg))
+    if rc != OK:
+        raise VafrError(rc, vafr_error_string(rc), msg.value.decode())
