@@ -211,9 +211,12 @@ VAFR_API int vafr_render_full_gt(const vafr_scene* scene, vafr_session* session,
                         void* display_out, int32_t* hit_ids_out, void* stream);
 /* vafr_render_frame: one whole frame of the session (render_lp of every eye
  * into a session-owned LP buffer, then reconstruct every eye).
- *   display_out  host or device, [n_eyes][height][width] of display_format.
- *                Host memory (pinned or pageable) is filled by a device->host
- *                copy on `stream`; the call then synchronises `stream`.
+ *   display_out  host or device, [n_eyes][height][width] of display_format,
+ *                16-byte aligned.  Pinned host memory (page-locked or
+ *                registered) is written directly by the reconstruction kernel
+ *                through its device alias; pageable host memory is filled by a
+ *                device->host copy.  For host memory the call synchronises
+ *                `stream` before returning.
  * Errors: as vafr_render_lp / vafr_reconstruct, OOM. */
 VAFR_API int vafr_render_frame(const vafr_scene* scene, vafr_session* session, void* display_out,
                       void* stream);

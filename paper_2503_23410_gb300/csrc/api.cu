@@ -529,22 +529,39 @@ int vafr_render_frame(const vafr_scene* scene, vafr_session* s, void* display_ou
     int64_t lpb = 0, dpb = 0;
     vafr_session_sizes(s, &lpb, &dpb);
     if (!s->lp_internal) CUDA_TRY(cudaMalloc(&s->lp_internal, (size_t)lpb * eyes));
-    const bool host = !is_device_ptr(display_out);
-    if (host && !s->disp_internal) CUDA_TRY(cudaMalloc(&s->disp_internal, (size_t)dpb * eyes));
-    if (!host && !aligned(display_out, 16)) return fail(VAFR_ERR_INVALID_ARG, "display must be 16-byte aligned");
-    void* disp = host ? s->disp_internal : display_out;
+    // Where the display goes: device memory as is; pinned (page-locked or
+    // registered) host memory through its device alias, so the reconstruction
+    // kernel writes it directly over the CPU-GPU link; pageable host memory
+    // through a device buffer and one device-to-host copy.
+    cudaPointerAttributes pa;
+    void* target = nullptr;
+    bool copy_out = false;
+    if (cudaPointerGetAttributes(&pa, display_out) != cudaSuccess) {
+        cudaGetLastError();
+        pa.type = cudaMemoryTypeUnregistered;
+    }
+    if (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) {
+        target = display_out;
+    } else if (pa.type == cudaMemoryTypeHost && pa.devicePointer != nullptr) {
+        target = pa.devicePointer;
+    } else {
+        if (!s->disp_internal) CUDA_TRY(cudaMalloc(&s->disp_internal, (size_t)dpb * eyes));
+        target = s->disp_internal;
+        copy_out = true;
+    }
+    if (!aligned(target, 16)) return fail(VAFR_ERR_INVALID_ARG, "display must be 16-byte aligned");
     int rc = vafr_render_lp(scene, s, (1 << eyes) - 1, s->lp_internal, nullptr, stream);
     if (rc) return rc;
     for (int e = 0; e < eyes; ++e) {
         rc = vafr_reconstruct(s, e, static_cast<char*>(s->lp_internal) + (size_t)e * lpb,
-                              static_cast<char*>(disp) + (size_t)e * dpb, stream);
+                              static_cast<char*>(target) + (size_t)e * dpb, stream);
         if (rc) return rc;
     }
-    if (host) {
-        CUDA_TRY(cudaMemcpyAsync(display_out, disp, (size_t)dpb * eyes, cudaMemcpyDeviceToHost,
+    if (copy_out)
+        CUDA_TRY(cudaMemcpyAsync(display_out, target, (size_t)dpb * eyes, cudaMemcpyDeviceToHost,
                                  as_stream(stream)));
+    if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)
         CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
-    }
     return VAFR_OK;
 }
 

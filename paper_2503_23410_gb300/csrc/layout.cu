@@ -88,8 +88,10 @@ LayoutTables::~LayoutTables() {
 
 namespace {
 
-// Cubic Hermite pieces of u(z), z = tan(e), on kUTable uniform intervals of
-// [0, tan(e_max)], from the exact u and du/dz = du/de (180/pi) / (1 + z^2).
+// Cubic Hermite pieces of u(z) - 1/2 (the bilinear filter's column
+// coordinate), z = tan(e), on kUTable uniform intervals of [0, tan(e_max)],
+// from the exact u and du/dz = du/de (180/pi) / (1 + z^2), plus one constant
+// entry u(e_max) - 1/2 for the clamp.
 void build_u_table(const Mapping& mp, std::vector<float4>& tab, double& inv_h) {
     const int N = kUTable;
     const double z_max = std::tan(mp.e_max * M_PI / 180.0);
@@ -101,12 +103,13 @@ void build_u_table(const Mapping& mp, std::vector<float4>& tab, double& inv_h) {
         p[k] = mp.u_of_e(e);
         d[k] = mp.du_de(e) * (180.0 / M_PI) / (1.0 + z * z) * h;
     }
-    tab.resize(N);
+    tab.resize(N + 1);
     for (int k = 0; k < N; ++k) {
         const double c2 = 3.0 * (p[k + 1] - p[k]) - 2.0 * d[k] - d[k + 1];
         const double c3 = 2.0 * (p[k] - p[k + 1]) + d[k] + d[k + 1];
-        tab[k] = make_float4((float)p[k], (float)d[k], (float)c2, (float)c3);
+        tab[k] = make_float4((float)(p[k] - 0.5), (float)d[k], (float)c2, (float)c3);
     }
+    tab[N] = make_float4((float)(p[N] - 0.5), 0.0f, 0.0f, 0.0f);   // z >= tan(e_max): u(e_max)
     inv_h = N / z_max;
 }
 

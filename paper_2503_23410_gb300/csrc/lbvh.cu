@@ -292,9 +292,11 @@ __global__ void k_pack_nodes(const int2* __restrict__ child, const float* __rest
     const int2 c = child[i];
     const float* a = c.x >= 0 ? node_box + 6ll * c.x : leaf_box + 6ll * ~c.x;
     const float* b = c.y >= 0 ? node_box + 6ll * c.y : leaf_box + 6ll * ~c.y;
-    nodes[4ll * i + 0] = make_float4(a[0], a[3], a[1], a[4]);
-    nodes[4ll * i + 1] = make_float4(b[0], b[3], b[1], b[4]);
-    nodes[4ll * i + 2] = make_float4(a[2], a[5], b[2], b[5]);
+    // per axis: (left lo, right lo, left hi, right hi), so both children's slabs
+    // are computed with paired FP32 instructions
+    nodes[4ll * i + 0] = make_float4(a[0], b[0], a[3], b[3]);
+    nodes[4ll * i + 1] = make_float4(a[1], b[1], a[4], b[4]);
+    nodes[4ll * i + 2] = make_float4(a[2], b[2], a[5], b[5]);
     nodes[4ll * i + 3] = make_float4(__int_as_float(c.x), __int_as_float(c.y), 0.0f, 0.0f);
 }
 

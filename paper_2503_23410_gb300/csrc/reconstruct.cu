@@ -5,7 +5,7 @@
 //   d = p - gaze, computed as (x - floor(x0)) + (0.5 - frac(x0)) so the FP32
 //       offset is exact near the gaze even at 16K;
 //   z = c_r |d| = tan(e) (Eq. 3; |d| = d.d rsqrt(d.d)), clamped to tan(e_max);
-//   u = u(e(z)) (Eq. 12) from a per-session table of cubic Hermite pieces on
+//   u(e(z)) - 1/2 (Eq. 12) from a per-acuity table of cubic Hermite pieces on
 //       2,048 uniform intervals of z, built in FP64 on the host from the exact
 //       u(e) and du/dz (interpolation error < 1e-5 texel, below FP32 rounding);
 //   angle fraction = atan2(dy, dx) / 2pi in [0, 1), by octant reduction and an
@@ -22,19 +22,32 @@
 namespace vafr {
 namespace {
 
-__device__ __forceinline__ float4 load_lp(const void* lp, int fmt, int idx) {
+// Texel as two channel pairs, so the filter runs on paired FP32 instructions.
+struct px2 {
+    float2 rg, ba;
+};
+
+__device__ __forceinline__ px2 load_lp(const void* lp, int fmt, int idx) {
+    px2 r;
     if (fmt == VAFR_FMT_RGBA16F) {
         const uint2 p = __ldg(reinterpret_cast<const uint2*>(lp) + idx);
-        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&p.x));
-        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&p.y));
-        return make_float4(a.x, a.y, b.x, b.y);
+        r.rg = __half22float2(*reinterpret_cast<const __half2*>(&p.x));
+        r.ba = __half22float2(*reinterpret_cast<const __half2*>(&p.y));
+    } else {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(lp) + idx);
+        r.rg = make_float2(q.x, q.y);
+        r.ba = make_float2(q.z, q.w);
     }
-    return __ldg(reinterpret_cast<const float4*>(lp) + idx);
+    return r;
 }
 
-__device__ __forceinline__ float4 lerp4(float4 a, float4 b, float w) {
-    return make_float4(fmaf(w, b.x - a.x, a.x), fmaf(w, b.y - a.y, a.y), fmaf(w, b.z - a.z, a.z),
-                       fmaf(w, b.w - a.w, a.w));
+// a + w (b - a): exact when a == b (a constant LP reconstructs exactly).
+__device__ __forceinline__ px2 lerp2(px2 a, px2 b, float w) {
+    const float2 w2 = make_float2(w, w);
+    px2 r;
+    r.rg = __ffma2_rn(w2, __fadd2_rn(b.rg, make_float2(-a.rg.x, -a.rg.y)), a.rg);
+    r.ba = __ffma2_rn(w2, __fadd2_rn(b.ba, make_float2(-a.ba.x, -a.ba.y)), a.ba);
+    return r;
 }
 
 // atan2(dy, dx) / 2pi wrapped to [0, 1); (0, 0) -> 0.
@@ -58,7 +71,7 @@ __device__ __forceinline__ float angle_fraction(float dy, float dx) {
     return a;
 }
 
-__device__ __forceinline__ float4 column_sample(const void* lp, int fmt, int off, int n, float frac) {
+__device__ __forceinline__ px2 column_sample(const void* lp, int fmt, int off, int n, float frac) {
     const float v = fmaf(frac, (float)n, -0.5f);
     const float j0f = floorf(v);
     const float wv = v - j0f;
@@ -66,72 +79,61 @@ __device__ __forceinline__ float4 column_sample(const void* lp, int fmt, int off
     int j1 = j0 + 1;
     j0 = j0 < 0 ? j0 + n : j0;
     j1 = j1 >= n ? j1 - n : j1;
-    return lerp4(load_lp(lp, fmt, off + j0), load_lp(lp, fmt, off + j1), wv);
+    return lerp2(load_lp(lp, fmt, off + j0), load_lp(lp, fmt, off + j1), wv);
 }
 
-// Frame parameters copied to registers once per thread: the descriptor lives in
-// parameter space, and the compiler cannot prove that display stores leave it
-// unchanged, so reading it per pixel would reload every field.
+// Frame parameters, staged through shared memory by one thread and then held
+// in registers: read-only parameter-space values may otherwise be reloaded
+// at every use.
 struct ReconRegs {
-    int gxi, gyi;
-    float gxf, gyf, cr, u_inv_h, u_nf, cmax;
-    int u_last;
+    float zs;        // c_r * u_n / tan(e_max): radius in pixels -> table coordinate
+    float u_nf;      // u_n (the clamp entry)
+    float cmax;      // C - 1
     const float4* u_tab;
     const int4* col_pair;
     const void* lp;
     int lp_fmt;
 };
 
-__device__ __forceinline__ ReconRegs load_regs(const FrameDesc& f) {
+struct ReconShared {
     ReconRegs r;
-    r.gxi = f.gxi;
-    r.gyi = f.gyi;
-    r.gxf = f.gxf;
-    r.gyf = f.gyf;
-    r.cr = f.cr;
-    r.u_inv_h = f.u_inv_h;
-    r.u_nf = (float)f.u_n;
-    r.u_last = f.u_n - 1;
-    r.cmax = (float)(f.n_cols - 1);
-    r.u_tab = f.u_tab;
-    r.col_pair = f.col_pair;
-    r.lp = f.lp;
-    r.lp_fmt = f.lp_fmt;
-    return r;
-}
+    int gxi, gyi;
+    float gxf, gyf;
+    int W, H, disp_fmt, tile_begin;
+    void* disp;
+};
 
-__device__ __forceinline__ float4 recon_pixel(const ReconRegs& f, int x, int y) {
-    const float dx = (float)(x - f.gxi) + f.gxf;
-    const float dy = (float)(y - f.gyi) + f.gyf;
-    const float r2 = fmaf(dx, dx, dy * dy);
-    const float z = r2 > 0.0f ? f.cr * (r2 * rsqrtf(r2)) : 0.0f;   // c_r |d| = tan(e)
-    const float s = fminf(z * f.u_inv_h, f.u_nf);
-    const int i = min((int)s, f.u_last);
+// One pixel of a row: dx is its gaze offset, dy2 the row's squared offset.
+__device__ __forceinline__ px2 recon_pixel(const ReconRegs& f, float dx, float dy, float dy2) {
+    const float r2 = fmaf(dx, dx, dy2);
+    // c_r |d| = tan(e) scaled to the table; the 1e-30 bias keeps rsqrt finite at d = 0
+    const float s = fminf(f.zs * (r2 * rsqrtf(r2 + 1e-30f)), f.u_nf);
+    const int i = (int)s;
     const float t = s - (float)i;
     const float4 c = __ldg(f.u_tab + i);
-    const float u = fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
+    const float uf = fminf(fmaxf(fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x), 0.0f), f.cmax);  // u - 0.5
     const float frac = angle_fraction(dy, dx);
-    const float uf = fminf(fmaxf(u - 0.5f, 0.0f), f.cmax);
     const int c0 = (int)uf;
     const float wu = uf - (float)c0;
     const int4 cp = __ldg(f.col_pair + c0);  // (offset, count) of c0 and of min(c0 + 1, C - 1)
-    const float4 v0 = column_sample(f.lp, f.lp_fmt, cp.x, cp.y, frac);
-    const float4 v1 = column_sample(f.lp, f.lp_fmt, cp.z, cp.w, frac);
-    return lerp4(v0, v1, wu);
+    const px2 v0 = column_sample(f.lp, f.lp_fmt, cp.x, cp.y, frac);
+    const px2 v1 = column_sample(f.lp, f.lp_fmt, cp.z, cp.w, frac);
+    return lerp2(v0, v1, wu);
 }
 
-__device__ __forceinline__ uint2 pack_half4(float4 p) {
-    const __half2 a = __floats2half2_rn(p.x, p.y), c = __floats2half2_rn(p.z, p.w);
-    uint2 q;
-    q.x = *reinterpret_cast<const unsigned*>(&a);
-    q.y = *reinterpret_cast<const unsigned*>(&c);
-    return q;
+__device__ __forceinline__ unsigned pack_half2(float2 p) {
+    const __half2 h = __floats2half2_rn(p.x, p.y);
+    return *reinterpret_cast<const unsigned*>(&h);
 }
 
+// Tile of TW x TH pixels; TW / PX threads per row, each thread PX pixels of one
+// row.  FP32 display: pixel q of a thread is x = x_tile + q TW/PX + tx, so each
+// 16-byte store of a warp is contiguous.  FP16 display: a thread takes PX
+// adjacent pixels (pairs share one 16-byte store).
 template <int TW, int TH, int PX, class B>
 __global__ void __launch_bounds__((TW / PX) * TH)
 k_reconstruct(const __grid_constant__ B b) {
-    __shared__ int sfi;
+    __shared__ ReconShared sh;
     const int tile = (int)blockIdx.x;
     if (threadIdx.x == 0) {
         int lo = 0, hi = b.n - 1;
@@ -139,42 +141,67 @@ k_reconstruct(const __grid_constant__ B b) {
             const int mid = (lo + hi + 1) >> 1;
             if (b.d[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
         }
-        sfi = lo;
+        const FrameDesc& fd = b.d[lo];
+        sh.r.zs = fd.cr * fd.u_inv_h;
+        sh.r.u_nf = (float)fd.u_n;
+        sh.r.cmax = (float)(fd.n_cols - 1);
+        sh.r.u_tab = fd.u_tab;
+        sh.r.col_pair = fd.col_pair;
+        sh.r.lp = fd.lp;
+        sh.r.lp_fmt = fd.lp_fmt;
+        sh.gxi = fd.gxi;
+        sh.gyi = fd.gyi;
+        sh.gxf = fd.gxf;
+        sh.gyf = fd.gyf;
+        sh.W = fd.W;
+        sh.H = fd.H;
+        sh.disp_fmt = fd.disp_fmt;
+        sh.tile_begin = (int)fd.tile_begin;
+        sh.disp = fd.disp;
     }
     __syncthreads();
-    const FrameDesc& fd = b.d[sfi];
-    const ReconRegs f = load_regs(fd);
-    const int W = fd.W, H = fd.H;
-    void* const disp = fd.disp;
-    const int local = tile - (int)fd.tile_begin;
+    const ReconRegs f = sh.r;
+    const int W = sh.W, H = sh.H;
+    void* const disp = sh.disp;
+    const int local = tile - sh.tile_begin;
     const int tiles_x = (W + TW - 1) / TW;
     const int ty = local / tiles_x;
-    const int tx = local - ty * tiles_x;
+    const int tx_tile = local - ty * tiles_x;
     constexpr int TX = TW / PX;
-    const int x0 = tx * TW + (int)(threadIdx.x % TX) * PX;
+    const int tx = (int)(threadIdx.x % TX);
     const int y = ty * TH + (int)(threadIdx.x / TX);
     if (y >= H) return;
+    const float dy = (float)(y - sh.gyi) + sh.gyf;
+    const float dy2 = dy * dy;
     const long long row = (long long)y * W;
-    if (fd.disp_fmt == VAFR_FMT_RGBA16F) {
+    const int xt = tx_tile * TW;
+    const int gxi = sh.gxi;
+    const float gxf = sh.gxf;
+    if (sh.disp_fmt == VAFR_FMT_RGBA16F) {
+        const int x0 = xt + tx * PX;
+        const float dx0 = (float)(x0 - gxi) + gxf;
         if (PX == 2 && x0 + 1 < W && ((row + x0) & 1) == 0) {
-            const uint2 a = pack_half4(recon_pixel(f, x0, y));
-            const uint2 c = pack_half4(recon_pixel(f, x0 + 1, y));
+            const px2 a = recon_pixel(f, dx0, dy, dy2);
+            const px2 c = recon_pixel(f, dx0 + 1.0f, dy, dy2);
             __stcs(reinterpret_cast<uint4*>(reinterpret_cast<uint2*>(disp) + row + x0),
-                   make_uint4(a.x, a.y, c.x, c.y));
+                   make_uint4(pack_half2(a.rg), pack_half2(a.ba), pack_half2(c.rg), pack_half2(c.ba)));
         } else {
 #pragma unroll
             for (int q = 0; q < PX; ++q) {
                 const int x = x0 + q;
                 if (x >= W) break;
-                __stcs(reinterpret_cast<uint2*>(disp) + row + x, pack_half4(recon_pixel(f, x, y)));
+                const px2 a = recon_pixel(f, (float)(x - gxi) + gxf, dy, dy2);
+                __stcs(reinterpret_cast<uint2*>(disp) + row + x,
+                       make_uint2(pack_half2(a.rg), pack_half2(a.ba)));
             }
         }
     } else {
 #pragma unroll
         for (int q = 0; q < PX; ++q) {
-            const int x = x0 + q;
+            const int x = xt + q * TX + tx;
             if (x >= W) break;
-            __stcs(reinterpret_cast<float4*>(disp) + row + x, recon_pixel(f, x, y));
+            const px2 a = recon_pixel(f, (float)(x - gxi) + gxf, dy, dy2);
+            __stcs(reinterpret_cast<float4*>(disp) + row + x, make_float4(a.rg.x, a.rg.y, a.ba.x, a.ba.y));
         }
     }
 }

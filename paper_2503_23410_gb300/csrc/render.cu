@@ -7,9 +7,11 @@
 // so uneven frames and uneven rays balance dynamically.
 //
 // Traversal: single-triangle LBVH leaves; each 64-byte node holds both child
-// boxes.  Box tests follow Ize 2013 ("Robust BVH Ray Traversal"): slab
-// distances (b - o) * (1/d) and the far distance scaled by 1 + 2 gamma_3 so no
-// box the ray touches is culled by rounding.  Triangle test: Woop, Benthin,
+// boxes, laid out per axis as pairs so both slabs run on paired FP32
+// instructions.  Box tests are conservative (after Ize 2013, "Robust BVH Ray
+// Traversal"): slab distances as one FMA, b (1/d) - o (1/d), widened by a
+// per-ray slack covering the rounding of o (1/d), and the far distance scaled
+// by 1 + 2 gamma_3, so no box the ray touches is culled by rounding.  Triangle test: Woop, Benthin,
 // Wald 2013 ("Watertight Ray/Triangle Intersection"), two-sided, with the
 // 2-D edge functions evaluated without FMA contraction so that a shared edge
 // gets exactly opposite values in the two neighbouring triangles.
@@ -30,6 +32,8 @@ struct Ray {
     float ox, oy, oz;
     float dx, dy, dz;
     float ix, iy, iz;            // 1/d with zero components clamped (box tests only)
+    float nox, noy, noz;         // -o * (1/d), for t = b (1/d) - o (1/d) as one FMA
+    float slack;                 // absolute widening covering the rounding of o (1/d)
     float mx0, mx1, mx2;         // shear rows: A'x = Mx . A, A'y = My . A, A'z = Mz . A
     float my0, my1, my2;
     float mz0, mz1, mz2;
@@ -44,6 +48,12 @@ __device__ __forceinline__ void ray_setup(Ray& r) {
     r.ix = safe_inv(r.dx);
     r.iy = safe_inv(r.dy);
     r.iz = safe_inv(r.dz);
+    r.nox = -r.ox * r.ix;
+    r.noy = -r.oy * r.iy;
+    r.noz = -r.oz * r.iz;
+    // fma(b, 1/d, -o/d) is exact up to its final rounding plus the rounding of
+    // o/d (at most half an ulp of |o/d|); 2^-22 |o/d| bounds both with margin
+    r.slack = 2.384185791015625e-07f * fmaxf(fmaxf(fabsf(r.nox), fabsf(r.noy)), fabsf(r.noz));
     const float ax = fabsf(r.dx), ay = fabsf(r.dy), az = fabsf(r.dz);
     const int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
     int kx = kz == 2 ? 0 : kz + 1;
@@ -65,15 +75,24 @@ __device__ __forceinline__ void ray_setup(Ray& r) {
     r.mz2 = kz == 2 ? Sz : 0.0f;
 }
 
-// Child boxes of a node: returns entry distance (or +inf when missed).
-__device__ __forceinline__ float slab(float lox, float hix, float loy, float hiy, float loz,
-                                      float hiz, const Ray& r, float tmax) {
-    const float tx0 = __fmul_rn(__fsub_rn(lox, r.ox), r.ix), tx1 = __fmul_rn(__fsub_rn(hix, r.ox), r.ix);
-    const float ty0 = __fmul_rn(__fsub_rn(loy, r.oy), r.iy), ty1 = __fmul_rn(__fsub_rn(hiy, r.oy), r.iy);
-    const float tz0 = __fmul_rn(__fsub_rn(loz, r.oz), r.iz), tz1 = __fmul_rn(__fsub_rn(hiz, r.oz), r.iz);
-    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
-    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
-    return tn <= tf * kFarScale ? tn : INFINITY;
+// Both child boxes of a node at once (paired FP32).  Slab distances are
+// t = b (1/d) - o (1/d) as single FMAs; the interval is widened by the per-ray
+// slack on both ends and the far end scaled by 1 + 2 gamma_3 (Ize 2013), so a
+// box the ray touches is never culled by rounding.  Returns the entry
+// distances (left, right), +inf for a miss.
+__device__ __forceinline__ float2 slab2(float4 nx, float4 ny, float4 nz, const Ray& r, float tmax) {
+    const float2 ix = make_float2(r.ix, r.ix), iy = make_float2(r.iy, r.iy), iz = make_float2(r.iz, r.iz);
+    const float2 ox = make_float2(r.nox, r.nox), oy = make_float2(r.noy, r.noy), oz = make_float2(r.noz, r.noz);
+    const float2 x0 = __ffma2_rn(make_float2(nx.x, nx.y), ix, ox), x1 = __ffma2_rn(make_float2(nx.z, nx.w), ix, ox);
+    const float2 y0 = __ffma2_rn(make_float2(ny.x, ny.y), iy, oy), y1 = __ffma2_rn(make_float2(ny.z, ny.w), iy, oy);
+    const float2 z0 = __ffma2_rn(make_float2(nz.x, nz.y), iz, oz), z1 = __ffma2_rn(make_float2(nz.z, nz.w), iz, oz);
+    const float tlo = -r.slack;
+    const float tnl = fmaxf(fmaxf(fminf(x0.x, x1.x), fminf(y0.x, y1.x)), fmaxf(fminf(z0.x, z1.x), tlo));
+    const float tnr = fmaxf(fmaxf(fminf(x0.y, x1.y), fminf(y0.y, y1.y)), fmaxf(fminf(z0.y, z1.y), tlo));
+    const float tfl = fminf(fminf(fmaxf(x0.x, x1.x), fmaxf(y0.x, y1.x)), fminf(fmaxf(z0.x, z1.x), tmax));
+    const float tfr = fminf(fminf(fmaxf(x0.y, x1.y), fmaxf(y0.y, y1.y)), fminf(fmaxf(z0.y, z1.y), tmax));
+    return make_float2(tnl <= fmaf(tfl, kFarScale, 2.0f * r.slack) ? tnl : INFINITY,
+                       tnr <= fmaf(tfr, kFarScale, 2.0f * r.slack) ? tnr : INFINITY);
 }
 
 // Watertight test; returns t or +inf.
@@ -148,8 +167,8 @@ __device__ unsigned traverse(const SceneDev& sc, const Ray& r, Hit& h,
         const float4* nd = sc.nodes + 4ll * node;
         const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
         const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
-        float tl = slab(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, r, h.t);
-        float tr = slab(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, r, h.t);
+        const float2 tt = slab2(n0, n1, n2, r, h.t);
+        float tl = tt.x, tr = tt.y;
         if (tl < INFINITY && cl < 0) {
             if ((unsigned)~cl >= (unsigned)sc.n_tris) return kFaultBadNode;
             test_leaf<STATS>(sc, r, ~cl, h, tri_tests);
@@ -177,7 +196,7 @@ __device__ unsigned traverse(const SceneDev& sc, const Ray& r, Hit& h,
             while (true) {
                 if (sp == 0) return 0u;
                 --sp;
-                if (stack_t[sp] <= h.t * kFarScale) break;
+                if (stack_t[sp] <= fmaf(h.t, kFarScale, 2.0f * r.slack)) break;
             }
             node = stack[sp];
         }

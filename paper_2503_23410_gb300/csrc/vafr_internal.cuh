@@ -21,10 +21,10 @@ constexpr int kStackSize = 64;
 constexpr int kMaxSeg = VAFR_MAX_PIVOTS - 1;
 
 // ---- scene (LBVH) in traversal layout ----------------------------------------
-// Internal node i (64 B, four float4):
-//   n[0] = (L.lo.x, L.hi.x, L.lo.y, L.hi.y)
-//   n[1] = (R.lo.x, R.hi.x, R.lo.y, R.hi.y)
-//   n[2] = (L.lo.z, L.hi.z, R.lo.z, R.hi.z)
+// Internal node i (64 B, four float4), children L and R:
+//   n[0] = (L.lo.x, R.lo.x, L.hi.x, R.hi.x)
+//   n[1] = (L.lo.y, R.lo.y, L.hi.y, R.hi.y)
+//   n[2] = (L.lo.z, R.lo.z, L.hi.z, R.hi.z)
 //   n[3] = (L ref, R ref, -, -) as int bits; ref >= 0 internal, < 0 leaf ~k
 // Leaf k (sorted order): three float4 (v0.xyz | id), (v1.xyz | 0), (v2.xyz | 0).
 struct SceneDev {
@@ -38,9 +38,10 @@ struct SceneDev {
 };
 
 // ---- per session: forward-map table ------------------------------------------
-// u as a function of z = tan(e) = c_r r on [0, tan(e_max)] (Eqs. 3, 12): kUTable
-// uniform intervals, interval i holding the cubic Hermite piece
-// u = c.x + t (c.y + t (c.z + t c.w)), t in [0, 1].
+// u - 1/2 as a function of z = tan(e) = c_r r on [0, tan(e_max)] (Eqs. 3, 12):
+// kUTable uniform intervals, interval i holding the cubic Hermite piece
+// c.x + t (c.y + t (c.z + t c.w)), t in [0, 1]; entry kUTable is the constant
+// u(e_max) - 1/2 used for z >= tan(e_max).
 constexpr int kUTable = 2048;
 
 // ---- one frame-eye of work (kernel parameter; filled on the host in FP64,
@@ -58,7 +59,7 @@ struct FrameDesc {
     const float* tan_e;     // device [C] tan(e_c) of the column centres
     const int2* col;        // device [C] (first texel, texel count)
     const int4* col_pair;   // device [C] (first, count) of c and of min(c + 1, C - 1)
-    const float4* u_tab;    // device [u_n] cubic pieces of u(z)
+    const float4* u_tab;    // device [u_n + 1] cubic pieces of u(z)
     const int2* work;       // device [n_texels] (texel, column) in processing order
     int u_n;                // number of pieces
     float u_inv_h;          // u_n / tan(e_max)

@@ -122,3 +122,26 @@ def test_whole_frame_random1k(V, torch_mod, lay):
     assert np.abs(got[~touch] - ref[~touch]).max() < 1e-3
     V.vafr_session_destroy(s)
     V.vafr_scene_destroy(h)
+
+
+def test_render_frame_host_outputs_match_device(V, torch_mod, lay):
+    """vafr_render_frame into device memory, pinned host memory (written by the
+    kernel directly) and pageable host memory (copied): bitwise identical."""
+    torch = torch_mod
+    w = workload("random1k")
+    d, sc = w.displays[0], w.scene
+    h, keep = device_scene(V, sc, torch)
+    s = V.vafr_session_create(V.make_session_desc(d.width, d.height, d.fov_v_deg, d.poses))
+    V.vafr_set_gaze(s, 0, 200.25, 300.5)
+    dev = torch.empty((d.height, d.width, 4), dtype=torch.float32, device="cuda")
+    pinned = torch.zeros((d.height, d.width, 4), dtype=torch.float32, pin_memory=True)
+    pageable = np.zeros((d.height, d.width, 4), np.float32)
+    V.vafr_render_frame(h, s, dev)
+    V.vafr_render_frame(h, s, pinned)
+    V.vafr_render_frame(h, s, pageable)
+    torch.cuda.synchronize()
+    ref = dev.cpu().numpy()
+    assert np.array_equal(pinned.numpy(), ref)
+    assert np.array_equal(pageable, ref)
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)
