@@ -40,11 +40,11 @@ UNIT = "Mpix/s"
 HERE_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 FP32_LANES_PER_SM = 128
-# FP32 operations per traversal step, counted from the kernel source: a node
-# visit is two slab tests (6 sub + 6 mul + 10 min/max + 1 mul + 1 cmp each);
-# a triangle test is 9 sub + 18 shear ops + 9 (U,V,W) + 2 (det) + 9 (z) + 3
-# (T) + 1 div + 7 compares; ray set-up + generation + shading ~ 60.
-OPS_PER_NODE = 48
+# FP32 operations per traversal step, counted from the kernel source: a child
+# box test is 6 slab FMAs + 10 min/max + 1 FMA + 1 compare; a triangle test is
+# 9 sub + 18 shear ops + 9 (U,V,W) + 2 (det) + 9 (z) + 3 (T) + 1 div + 7
+# compares; ray set-up + generation + shading ~ 60.
+OPS_PER_BOX = 18
 OPS_PER_TRI = 58
 OPS_PER_RAY = 60
 
@@ -334,7 +334,7 @@ def run_gpu(args, w):
     # roofline of the dominant kernel
     stats = V.vafr_traversal_stats(scene, sess, 0)
     rays = stats["rays"] * eyes
-    ops = (stats["nodes"] * OPS_PER_NODE + stats["tri_tests"] * OPS_PER_TRI
+    ops = (stats["box_tests"] * OPS_PER_BOX + stats["tri_tests"] * OPS_PER_TRI
            + stats["rays"] * OPS_PER_RAY) * eyes
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -353,7 +353,8 @@ def run_gpu(args, w):
                    "peak_kind": f"derived: {n_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                 f"{sm_mhz:g} MHz (1 op/lane/clk)",
                    "ops_per_launch": ops, "rays_per_launch": rays,
-                   "nodes_per_ray": stats["nodes"] / max(stats["rays"], 1),
+                   "nodes4_per_ray": stats["nodes"] / max(stats["rays"], 1),
+                   "box_tests_per_ray": stats["box_tests"] / max(stats["rays"], 1),
                    "tri_tests_per_ray": stats["tri_tests"] / max(stats["rays"], 1),
                    "mrays_per_s": rays / render_s / 1e6, "avg_ms": render_s * 1e3}
     roof_recon = {"kernel": "k_reconstruct", "bound": "hbm",

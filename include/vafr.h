@@ -221,10 +221,11 @@ VAFR_API int vafr_render_full_gt(const vafr_scene* scene, vafr_session* session,
 VAFR_API int vafr_render_frame(const vafr_scene* scene, vafr_session* session, void* display_out,
                       void* stream);
 /* Traversal statistics of one eye's LP render (an instrumented copy of the
- * render kernel, never the timed one): out[0] = rays, out[1] = internal
- * nodes visited, out[2] = triangle tests, out[3] = hits.  Host out[4]. */
+ * render kernel's 4-wide traversal, never the timed one): out[0] = rays,
+ * out[1] = 4-wide nodes visited, out[2] = child boxes tested, out[3] =
+ * triangle tests, out[4] = hits.  Host out[5]. */
 VAFR_API int vafr_traversal_stats(const vafr_scene* scene, vafr_session* session, int32_t eye,
-                         int64_t out[4], void* stream);
+                         int64_t out[5], void* stream);
 
 /* ---- batching --------------------------------------------------------------
  * A batch renders many frame-eyes (any mix of sessions, eyes and display

@@ -95,6 +95,36 @@ __device__ __forceinline__ float2 slab2(float4 nx, float4 ny, float4 nz, const R
                        tnr <= fmaf(tfr, kFarScale, 2.0f * r.slack) ? tnr : INFINITY);
 }
 
+// The four child boxes of a 4-wide node (two pairs of paired-FP32 slabs), with
+// the same conservative widening as slab2.  Returns the entry distances,
+// +inf for a miss.
+__device__ __forceinline__ float4 slab4(const float4* __restrict__ nd, const Ray& r, float tmax) {
+    const float4 lx = __ldg(nd), hx = __ldg(nd + 1), ly = __ldg(nd + 2);
+    const float4 hy = __ldg(nd + 3), lz = __ldg(nd + 4), hz = __ldg(nd + 5);
+    const float2 ix = make_float2(r.ix, r.ix), iy = make_float2(r.iy, r.iy), iz = make_float2(r.iz, r.iz);
+    const float2 ox = make_float2(r.nox, r.nox), oy = make_float2(r.noy, r.noy), oz = make_float2(r.noz, r.noz);
+    const float2 xa0 = __ffma2_rn(make_float2(lx.x, lx.y), ix, ox), xb0 = __ffma2_rn(make_float2(lx.z, lx.w), ix, ox);
+    const float2 xa1 = __ffma2_rn(make_float2(hx.x, hx.y), ix, ox), xb1 = __ffma2_rn(make_float2(hx.z, hx.w), ix, ox);
+    const float2 ya0 = __ffma2_rn(make_float2(ly.x, ly.y), iy, oy), yb0 = __ffma2_rn(make_float2(ly.z, ly.w), iy, oy);
+    const float2 ya1 = __ffma2_rn(make_float2(hy.x, hy.y), iy, oy), yb1 = __ffma2_rn(make_float2(hy.z, hy.w), iy, oy);
+    const float2 za0 = __ffma2_rn(make_float2(lz.x, lz.y), iz, oz), zb0 = __ffma2_rn(make_float2(lz.z, lz.w), iz, oz);
+    const float2 za1 = __ffma2_rn(make_float2(hz.x, hz.y), iz, oz), zb1 = __ffma2_rn(make_float2(hz.z, hz.w), iz, oz);
+    const float lo = -r.slack;
+    const float far_pad = 2.0f * r.slack;
+#define VAFR_CHILD(X0, X1, Y0, Y1, Z0, Z1)                                                            \
+    ([&]() {                                                                                          \
+        const float tn = fmaxf(fmaxf(fminf(X0, X1), fminf(Y0, Y1)), fmaxf(fminf(Z0, Z1), lo));        \
+        const float tf = fminf(fminf(fmaxf(X0, X1), fmaxf(Y0, Y1)), fminf(fmaxf(Z0, Z1), tmax));      \
+        return tn <= fmaf(tf, kFarScale, far_pad) ? tn : INFINITY;                                    \
+    }())
+    const float t0 = VAFR_CHILD(xa0.x, xa1.x, ya0.x, ya1.x, za0.x, za1.x);
+    const float t1 = VAFR_CHILD(xa0.y, xa1.y, ya0.y, ya1.y, za0.y, za1.y);
+    const float t2 = VAFR_CHILD(xb0.x, xb1.x, yb0.x, yb1.x, zb0.x, zb1.x);
+    const float t3 = VAFR_CHILD(xb0.y, xb1.y, yb0.y, yb1.y, zb0.y, zb1.y);
+#undef VAFR_CHILD
+    return make_float4(t0, t1, t2, t3);
+}
+
 // Watertight test; returns t or +inf.
 __device__ __forceinline__ float tri_test(const Ray& r, float4 a, float4 b, float4 c) {
     const float Ax0 = __fsub_rn(a.x, r.ox), Ax1 = __fsub_rn(a.y, r.oy), Ax2 = __fsub_rn(a.z, r.oz);
@@ -142,10 +172,11 @@ __device__ __forceinline__ void test_leaf(const SceneDev& sc, const Ray& r, int 
     }
 }
 
-// Closest hit through the LBVH.  Returns a fault bit (0 = fine).
+// Closest hit through the binary LBVH.  Returns a fault bit (0 = fine).
 template <bool STATS>
-__device__ unsigned traverse(const SceneDev& sc, const Ray& r, Hit& h,
-                             unsigned long long* node_visits, unsigned long long* tri_tests) {
+__device__ unsigned traverse2(const SceneDev& sc, const Ray& r, Hit& h,
+                              unsigned long long* node_visits, unsigned long long* box_tests,
+                              unsigned long long* tri_tests) {
     h.t = INFINITY;
     h.leaf = -1;
     h.id = INT_MAX;
@@ -163,7 +194,7 @@ __device__ unsigned traverse(const SceneDev& sc, const Ray& r, Hit& h,
     while (true) {
         if (--budget == 0u) return kFaultWatchdog;
         if ((unsigned)node >= (unsigned)n_inner) return kFaultBadNode;
-        if (STATS) ++*node_visits;
+        if (STATS) { ++*node_visits; *box_tests += 2; }
         const float4* nd = sc.nodes + 4ll * node;
         const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
         const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
@@ -201,6 +232,107 @@ __device__ unsigned traverse(const SceneDev& sc, const Ray& r, Hit& h,
             node = stack[sp];
         }
     }
+}
+
+__device__ __forceinline__ void sort2(float& ta, int& ra, float& tb, int& rb) {
+    const bool sw = tb < ta;
+    const float t = sw ? tb : ta;
+    const int q = sw ? rb : ra;
+    tb = sw ? ta : tb;
+    rb = sw ? ra : rb;
+    ta = t;
+    ra = q;
+}
+
+// Closest hit through the 4-wide tree: test the four child boxes, test leaf
+// children at once, then continue with the nearest internal child and push the
+// others far-to-near.  Returns a fault bit (0 = fine).
+template <bool STATS>
+__device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
+                              unsigned long long* node_visits, unsigned long long* box_tests,
+                              unsigned long long* tri_tests) {
+    h.t = INFINITY;
+    h.leaf = -1;
+    h.id = INT_MAX;
+    if (sc.n_tris <= 0) return 0u;
+    if (sc.root < 0) {   // single triangle
+        test_leaf<STATS>(sc, r, 0, h, tri_tests);
+        return 0u;
+    }
+    int stack[kStackSize];
+    float stack_t[kStackSize];
+    int sp = 0;
+    int node = 0;
+    const int n_inner = sc.n_tris - 1;
+    unsigned budget = 4u * (unsigned)sc.n_tris + 64u;
+    while (true) {
+        if (--budget == 0u) return kFaultWatchdog;
+        if ((unsigned)node >= (unsigned)n_inner) return kFaultBadNode;
+        const float4* nd = sc.nodes4 + 8ll * node;
+        float4 t = slab4(nd, r, h.t);
+        const float4 rf = __ldg(nd + 6);
+        int c0 = __float_as_int(rf.x), c1 = __float_as_int(rf.y), c2 = __float_as_int(rf.z),
+            c3 = __float_as_int(rf.w);
+        if (STATS) {
+            ++*node_visits;
+            *box_tests += (c0 != kEmptyRef) + (c1 != kEmptyRef) + (c2 != kEmptyRef) + (c3 != kEmptyRef);
+        }
+#define VAFR_LEAF(T, C)                                                                   \
+        if (T < INFINITY && C < 0) {                                                      \
+            if (C != kEmptyRef) {                                                         \
+                if ((unsigned)~C >= (unsigned)sc.n_tris) return kFaultBadNode;            \
+                test_leaf<STATS>(sc, r, ~C, h, tri_tests);                                \
+            }                                                                             \
+            T = INFINITY;                                                                 \
+        }
+        VAFR_LEAF(t.x, c0)
+        VAFR_LEAF(t.y, c1)
+        VAFR_LEAF(t.z, c2)
+        VAFR_LEAF(t.w, c3)
+#undef VAFR_LEAF
+        // children entering beyond an updated closest hit are dropped
+        const float lim = fmaf(h.t, kFarScale, 2.0f * r.slack);
+        if (t.x > lim) t.x = INFINITY;
+        if (t.y > lim) t.y = INFINITY;
+        if (t.z > lim) t.z = INFINITY;
+        if (t.w > lim) t.w = INFINITY;
+        // ascending (t, ref): sorting network (0,1) (2,3) (0,2) (1,3) (1,2)
+        sort2(t.x, c0, t.y, c1);
+        sort2(t.z, c2, t.w, c3);
+        sort2(t.x, c0, t.z, c2);
+        sort2(t.y, c1, t.w, c3);
+        sort2(t.y, c1, t.z, c2);
+        if (t.x < INFINITY) {
+            if (t.w < INFINITY) {
+                if (sp >= kStackSize) return kFaultStack;
+                stack[sp] = c3; stack_t[sp] = t.w; ++sp;
+            }
+            if (t.z < INFINITY) {
+                if (sp >= kStackSize) return kFaultStack;
+                stack[sp] = c2; stack_t[sp] = t.z; ++sp;
+            }
+            if (t.y < INFINITY) {
+                if (sp >= kStackSize) return kFaultStack;
+                stack[sp] = c1; stack_t[sp] = t.y; ++sp;
+            }
+            node = c0;
+        } else {
+            while (true) {
+                if (sp == 0) return 0u;
+                --sp;
+                if (stack_t[sp] <= fmaf(h.t, kFarScale, 2.0f * r.slack)) break;
+            }
+            node = stack[sp];
+        }
+    }
+}
+
+template <int WIDE, bool STATS>
+__device__ __forceinline__ unsigned traverse(const SceneDev& sc, const Ray& r, Hit& h,
+                                             unsigned long long* nv, unsigned long long* bt,
+                                             unsigned long long* tt) {
+    if (WIDE == 4) return traverse4<STATS>(sc, r, h, nv, bt, tt);
+    return traverse2<STATS>(sc, r, h, nv, bt, tt);
 }
 
 __device__ __forceinline__ float4 shade(const SceneDev& sc, const Ray& r, const Hit& h) {
@@ -275,7 +407,7 @@ __device__ __forceinline__ int lp_ray(const FrameDesc& f, int k, Ray& r) {
     return tc.x;
 }
 
-template <int TPB, int FETCH, class B>
+template <int TPB, int FETCH, int WIDE, class B>
 __global__ void __launch_bounds__(TPB)
 k_render_lp(const SceneDev sc, const __grid_constant__ B b) {
     const int lane = threadIdx.x & 31;
@@ -294,7 +426,7 @@ k_render_lp(const SceneDev sc, const __grid_constant__ B b) {
             const int t = lp_ray(f, (int)(w - f.work_begin), r);
             ray_setup(r);
             Hit h;
-            const unsigned fault = traverse<false>(sc, r, h, nullptr, nullptr);
+            const unsigned fault = traverse<WIDE, false>(sc, r, h, nullptr, nullptr, nullptr);
             if (fault) { atomicOr(f.status, fault); h.leaf = -1; h.id = -1; }
             store_px(f.lp, t, f.lp_fmt, shade(sc, r, h));
             if (f.hit_ids) f.hit_ids[t] = h.leaf >= 0 ? h.id : -1;
@@ -303,7 +435,7 @@ k_render_lp(const SceneDev sc, const __grid_constant__ B b) {
 }
 
 // GT: work item = (tile of 8 x 4 pixels, lane); pixel centre rays.
-template <int TPB, int FETCH, class B>
+template <int TPB, int FETCH, int WIDE, class B>
 __global__ void __launch_bounds__(TPB)
 k_render_gt(const SceneDev sc, const __grid_constant__ B b) {
     const int lane = threadIdx.x & 31;
@@ -330,7 +462,7 @@ k_render_gt(const SceneDev sc, const __grid_constant__ B b) {
             world_ray(f, cx, cy, r);
             ray_setup(r);
             Hit h;
-            const unsigned fault = traverse<false>(sc, r, h, nullptr, nullptr);
+            const unsigned fault = traverse<WIDE, false>(sc, r, h, nullptr, nullptr, nullptr);
             if (fault) { atomicOr(f.status, fault); h.leaf = -1; h.id = -1; }
             const long long p = (long long)y * f.W + x;
             store_px(f.disp, p, f.disp_fmt, shade(sc, r, h));
@@ -339,10 +471,11 @@ k_render_gt(const SceneDev sc, const __grid_constant__ B b) {
     }
 }
 
-// Instrumented copy (never timed): counts rays, nodes, triangle tests, hits.
+// Instrumented copy (never timed): counts rays, node visits, box tests,
+// triangle tests and hits of the 4-wide traversal the render kernels use.
 __global__ void __launch_bounds__(128)
 k_render_stats(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned long long* out) {
-    unsigned long long nodes = 0, tris = 0, rays = 0, hits = 0;
+    unsigned long long nodes = 0, boxes = 0, tris = 0, rays = 0, hits = 0;
     for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < b.total_work;
          w += (long long)gridDim.x * blockDim.x) {
         const FrameDesc& f = b.d[find_frame(b, w, false)];
@@ -350,19 +483,20 @@ k_render_stats(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned
         lp_ray(f, (int)(w - f.work_begin), r);
         ray_setup(r);
         Hit h;
-        traverse<true>(sc, r, h, &nodes, &tris);
+        traverse<4, true>(sc, r, h, &nodes, &boxes, &tris);
         ++rays;
         hits += h.leaf >= 0;
     }
     atomicAdd(out + 0, rays);
     atomicAdd(out + 1, nodes);
-    atomicAdd(out + 2, tris);
-    atomicAdd(out + 3, hits);
+    atomicAdd(out + 2, boxes);
+    atomicAdd(out + 3, tris);
+    atomicAdd(out + 4, hits);
 }
 
-template <int TPB, int FETCH, bool GT, class B>
+template <int TPB, int FETCH, int WIDE, bool GT, class B>
 cudaError_t launch_one(const SceneDev& sc, const B& b, cudaStream_t s, int num_sms) {
-    auto kern = GT ? k_render_gt<TPB, FETCH, B> : k_render_lp<TPB, FETCH, B>;
+    auto kern = GT ? k_render_gt<TPB, FETCH, WIDE, B> : k_render_lp<TPB, FETCH, WIDE, B>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB, 0);
     if (e != cudaSuccess) return e;
@@ -382,10 +516,10 @@ template <bool GT, class B>
 cudaError_t launch_variant(const SceneDev& sc, const B& b, int variant, cudaStream_t s, int sms) {
     if (b.total_work <= 0) return cudaSuccess;
     switch (variant) {
-        case 0: return launch_one<128, 32, GT>(sc, b, s, sms);
-        case 1: return launch_one<256, 32, GT>(sc, b, s, sms);
-        case 2: return launch_one<128, 64, GT>(sc, b, s, sms);
-        default: return launch_one<64, 32, GT>(sc, b, s, sms);
+        case 0: return launch_one<128, 32, 4, GT>(sc, b, s, sms);
+        case 1: return launch_one<256, 32, 4, GT>(sc, b, s, sms);
+        case 2: return launch_one<128, 64, 4, GT>(sc, b, s, sms);
+        default: return launch_one<128, 32, 2, GT>(sc, b, s, sms);
     }
 }
 
@@ -409,7 +543,7 @@ template cudaError_t launch_render_gt<BigBatch>(const SceneDev&, const BigBatch&
 
 cudaError_t launch_render_stats(const SceneDev& scene, const SmallBatch& batch,
                                 unsigned long long* counters, cudaStream_t s, int num_sms) {
-    cudaError_t e = cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(counters, 0, 5 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     k_render_stats<<<num_sms * 4, 128, 0, s>>>(scene, batch, counters);
     count_launch(1);

@@ -17,7 +17,8 @@ enum DeviceFault : unsigned {
     kFaultBadNode = 4u,   // child reference out of range
 };
 
-constexpr int kStackSize = 64;
+constexpr int kStackSize = 96;
+constexpr int kEmptyRef = (int)0x80000000;   // unused slot of a 4-wide node
 constexpr int kMaxSeg = VAFR_MAX_PIVOTS - 1;
 
 // ---- scene (LBVH) in traversal layout ----------------------------------------
@@ -27,8 +28,12 @@ constexpr int kMaxSeg = VAFR_MAX_PIVOTS - 1;
 //   n[2] = (L.lo.z, R.lo.z, L.hi.z, R.hi.z)
 //   n[3] = (L ref, R ref, -, -) as int bits; ref >= 0 internal, < 0 leaf ~k
 // Leaf k (sorted order): three float4 (v0.xyz | id), (v1.xyz | 0), (v2.xyz | 0).
+// 4-wide node j (128 B, eight float4): lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of
+// children 0..3, then their refs (>= 0 4-wide node, < 0 leaf ~k, kEmptyRef
+// unused), then padding.  4-wide node 0 is the root.
 struct SceneDev {
     const float4* nodes;
+    const float4* nodes4;
     const float4* leaves;
     const float4* albedo;   // original triangle order (rgb, 0)
     int root;               // 0 (internal), ~0 (single leaf) or INT_MIN (empty)
@@ -126,6 +131,9 @@ struct LbvhBuffers {
     float* node_box;        // (n-1) x 6
     float* leaf_box;        // n x 6
     float4* nodes;          // (n-1) x 4
+    unsigned* head_flag;    // n-1: internal node at even depth
+    unsigned* head_idx;     // n-1: its 4-wide node index
+    float4* nodes4;         // (n-1) x 8 (upper bound on the 4-wide node count)
     float4* leaves;         // n x 3
     float4* albedo4;        // n
 };
