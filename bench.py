@@ -399,6 +399,145 @@ def run_gpu(args, w):
         dist.destroy_process_group()
 
 
+def _device_scene(V, torch, w):
+    tris = torch.from_numpy(np.ascontiguousarray(w.scene.tris.reshape(-1, 9))).cuda()
+    alb = torch.from_numpy(np.ascontiguousarray(w.scene.albedo)).cuda()
+    return V.vafr_build_scene(tris, alb, w.scene.light_dir), (tris, alb)
+
+
+def run_sweep(args):
+    """Resolution sweep (binocular, 1080p ... 16K per eye, FP16 LP and display):
+    all ten frame-eyes rendered by ONE batched render launch + ONE batched
+    reconstruct launch per frame; GT timed per resolution."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2503_23410_gb300 import build as B
+    B.build()
+    from paper_2503_23410_gb300 import vafr as V
+    from workloads import workload
+    V.load()
+    w = workload("sweep", frames=args.steps + args.warmup)
+    scene, keep = _device_scene(V, torch, w)
+    sess, bufs, frames = [], [], []
+    for d in w.displays:
+        s = V.vafr_session_create(V.make_session_desc(d.width, d.height, d.fov_v_deg, d.poses,
+                                                      V.FMT_RGBA16F, V.FMT_RGBA16F))
+        lpb, dpb = V.vafr_session_sizes(s)
+        lp = torch.empty(2 * lpb, dtype=torch.uint8, device="cuda")
+        dp = torch.empty(2 * dpb, dtype=torch.uint8, device="cuda")
+        sess.append(s)
+        bufs.append((lp, dp, lpb, dpb))
+        for e in range(2):
+            frames.append((s, e, lp[e * lpb:], dp[e * dpb:]))
+    batch = V.vafr_batch_create(scene, V.MAX_BATCH)
+
+    def set_gaze(k):
+        for s, d in zip(sess, w.displays):
+            for e in range(2):
+                V.vafr_set_gaze(s, e, *d.gaze[k % len(d.gaze), e])
+    set_gaze(0)
+    V.vafr_batch_autotune(batch, frames, iters=3)
+    V.vafr_batch_capture(batch, frames)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for k in range(args.warmup):
+        set_gaze(k)
+        V.vafr_batch_replay(batch)
+    torch.cuda.synchronize()
+    times = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        set_gaze(args.warmup + k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        V.vafr_batch_replay(batch)
+        e1.record()
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    batch_ms = np.array([a.elapsed_time(b) for a, b in times])
+    per_res = []
+    for (s, (lp, dp, lpb, dpb), d) in zip(sess, bufs, w.displays):
+        gts = []
+        for k in range(max(3, args.gt_steps // 4) + 2):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for e in range(2):
+                V.vafr_render_full_gt(scene, s, e, dp[e * dpb:])
+            e1.record()
+            torch.cuda.synchronize()
+            if k >= 2:
+                gts.append(e0.elapsed_time(e1))
+        vs = []
+        for k in range(8):
+            flush.fill_(2)
+            for e in range(2):
+                V.vafr_set_gaze(s, e, *d.gaze[k, e])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            V.vafr_render_lp(scene, s, 3, lp)
+            for e in range(2):
+                V.vafr_reconstruct(s, e, lp[e * lpb:], dp[e * dpb:])
+            e1.record()
+            torch.cuda.synchronize()
+            if k >= 2:
+                vs.append(e0.elapsed_time(e1))
+        _, _, _, n_tex = V.vafr_lp_layout(s)
+        per_res.append({"width": d.width, "height": d.height, "lp_rays": 2 * n_tex,
+                        "gt_rays": 2 * d.width * d.height, "vafr_ms": float(np.median(vs)),
+                        "gt_ms": float(np.median(gts)),
+                        "speedup_vs_gt": float(np.median(gts) / np.median(vs))})
+    mpix = sum(2 * d.width * d.height for d in w.displays) / 1e6
+    line = {"metric": "display Mpix/s, resolution sweep batched in one launch", "unit": "Mpix/s",
+            "value": mpix * 1e3 / float(batch_ms.mean()), "ms_per_step": float(batch_ms.mean()),
+            "p50_frame_ms": float(np.percentile(batch_ms, 50)),
+            "p99_frame_ms": float(np.percentile(batch_ms, 99)), "steps": args.steps,
+            "warmup": args.warmup, "n_gpus": 1, "higher_is_better": True, "dtype": "f16 store, f32 math",
+            "data": "synthetic", "config": {"workload": "sweep: terrain4k scene, binocular, per eye "
+            "1920x1080, 2560x1440, 3840x2160, 7680x4320, 15360x8640; FP16 LP + display; one CUDA "
+            "graph (render + reconstruct launch) per frame",
+            "l2": "flushed between steps"},
+            "tuning": V.vafr_batch_tuning(batch), "per_resolution": per_res}
+    print(json.dumps(line))
+    V.vafr_batch_destroy(batch)
+    for s in sess:
+        V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(scene)
+
+
+def run_serving(args):
+    """64 Poisson-arriving binocular sessions (1080p/1440p/4K/8K), admitted by
+    an 8 GB HBM budget and continuously batched on two streams."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2503_23410_gb300 import build as B
+    B.build()
+    from paper_2503_23410_gb300 import vafr as V
+    from paper_2503_23410_gb300.serve import Server, VafrBackend, poisson_requests
+    from workloads import workload
+    V.load()
+    w = workload("serving", frames=args.serve_frames)
+    scene, keep = _device_scene(V, torch, w)
+    reqs = poisson_requests(w, seed=1)
+    warm = poisson_requests(workload("serving", frames=3), seed=2, n_sessions=8)
+    be = VafrBackend(scene, n_slots=2, autotune=True)
+    Server(be, w.hbm_budget_bytes).run(warm)            # warm-up (tuning, allocator)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        st = Server(be, w.hbm_budget_bytes).run(reqs, time_limit_s=600)
+    be.close_all()
+    sm = st.summary()
+    line = {"metric": "served frames/s and p50/p99 frame latency, 64 Poisson sessions",
+            "unit": "frames/s", "value": sm["frames_per_s"], "higher_is_better": True,
+            "n_gpus": 1, "data": "synthetic", "dtype": "f16 store, f32 math",
+            "config": {"workload": f"serving: {len(reqs)} binocular sessions x {args.serve_frames} "
+                       "frames, resolution uniform over 1080p/1440p/4K/8K, Poisson arrivals "
+                       f"({w.poisson_rate_hz:.0f}/s), random-walk gaze, terrain4k scene, HBM "
+                       f"budget {w.hbm_budget_bytes >> 30} GB, 2 in-flight batches"},
+            "serving": sm, "clocks": clk.summary()}
+    print(json.dumps(line))
+    V.vafr_scene_destroy(scene)
+
+
 def cpu_baseline(args, w):
     import oracle
     oracle.build()
@@ -430,7 +569,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="vafr", choices=["vafr", "reference"])
     ap.add_argument("--workload", default="terrain4k",
-                    choices=["random1k", "terrain4k", "objects8k"])
+                    choices=["random1k", "terrain4k", "objects8k", "sweep", "serving"])
+    ap.add_argument("--serve-frames", type=int, default=60)
     ap.add_argument("--gt-steps", type=int, default=60)
     ap.add_argument("--e2e-steps", type=int, default=60)
     ap.add_argument("--ref-texels", type=int, default=65536)
@@ -447,7 +587,12 @@ def main():
             return
         run_reference(args, workload(args.workload, frames=max(args.steps + args.warmup, 1)))
         return
-    run_gpu(args, workload(args.workload))
+    if args.workload == "sweep":
+        run_sweep(args)
+    elif args.workload == "serving":
+        run_serving(args)
+    else:
+        run_gpu(args, workload(args.workload))
 
 
 if __name__ == "__main__":

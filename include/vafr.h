@@ -223,9 +223,10 @@ VAFR_API int vafr_render_frame(const vafr_scene* scene, vafr_session* session, v
 /* Traversal statistics of one eye's LP render (an instrumented copy of the
  * render kernel's 4-wide traversal, never the timed one): out[0] = rays,
  * out[1] = 4-wide nodes visited, out[2] = child boxes tested, out[3] =
- * triangle tests, out[4] = hits.  Host out[5]. */
+ * triangle tests, out[4] = hits, out[5] = most nodes visited by one ray.
+ * Host out[6]. */
 VAFR_API int vafr_traversal_stats(const vafr_scene* scene, vafr_session* session, int32_t eye,
-                         int64_t out[5], void* stream);
+                         int64_t out[6], void* stream);
 
 /* ---- batching --------------------------------------------------------------
  * A batch renders many frame-eyes (any mix of sessions, eyes and display

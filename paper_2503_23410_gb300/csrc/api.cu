@@ -399,7 +399,7 @@ int vafr_session_create(const vafr_session_desc* desc, vafr_session** out) {
     cudaError_t e;
     if ((e = cudaMalloc(&s->d_status, sizeof(unsigned))) != cudaSuccess) return bail(e);
     if ((e = cudaMalloc(&s->d_counter, sizeof(unsigned long long))) != cudaSuccess) return bail(e);
-    if ((e = cudaMalloc(&s->d_stats, 5 * sizeof(unsigned long long))) != cudaSuccess) return bail(e);
+    if ((e = cudaMalloc(&s->d_stats, 6 * sizeof(unsigned long long))) != cudaSuccess) return bail(e);
     if ((e = cudaMemset(s->d_status, 0, sizeof(unsigned))) != cudaSuccess) return bail(e);
     for (int eye = 0; eye < d.n_eyes; ++eye) fill_static(s, eye);
     *out = s;
@@ -569,7 +569,7 @@ int vafr_render_frame(const vafr_scene* scene, vafr_session* s, void* display_ou
     return VAFR_OK;
 }
 
-int vafr_traversal_stats(const vafr_scene* scene, vafr_session* s, int32_t eye, int64_t out[5],
+int vafr_traversal_stats(const vafr_scene* scene, vafr_session* s, int32_t eye, int64_t out[6],
                          void* stream) {
     if (!scene || !s || !out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
     if (eye < 0 || eye >= s->desc.n_eyes || !s->gaze_set[eye])
@@ -582,10 +582,10 @@ int vafr_traversal_stats(const vafr_scene* scene, vafr_session* s, int32_t eye, 
     b.total_work = s->n_texels;
     cudaStream_t st = as_stream(stream);
     CUDA_TRY(launch_render_stats(scene->dev, b, s->d_stats, st, s->sms));
-    unsigned long long h[5];
+    unsigned long long h[6];
     CUDA_TRY(cudaMemcpyAsync(h, s->d_stats, sizeof(h), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    for (int k = 0; k < 5; ++k) out[k] = (int64_t)h[k];
+    for (int k = 0; k < 6; ++k) out[k] = (int64_t)h[k];
     return VAFR_OK;
 }
 

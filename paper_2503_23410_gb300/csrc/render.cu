@@ -6,12 +6,11 @@
 // chunks of work items from one global atomic counter until the batch is done,
 // so uneven frames and uneven rays balance dynamically.
 //
-// Traversal: single-triangle LBVH leaves; each 64-byte node holds both child
-// boxes, laid out per axis as pairs so both slabs run on paired FP32
-// instructions.  Box tests are conservative (after Ize 2013, "Robust BVH Ray
-// Traversal"): slab distances as one FMA, b (1/d) - o (1/d), widened by a
-// per-ray slack covering the rounding of o (1/d), and the far distance scaled
-// by 1 + 2 gamma_3, so no box the ray touches is culled by rounding.  Triangle test: Woop, Benthin,
+// Traversal: single-triangle leaves.  Each binary node holds both child boxes
+// and each 4-wide node four, laid out per axis so the slabs run on paired FP32
+// instructions.  Box tests follow Ize 2013 ("Robust BVH Ray Traversal"): slab
+// distances (b - o) (1/d) and the far distance scaled by 1 + 2 gamma_3, so no
+// box the ray touches is culled by rounding.  Triangle test: Woop, Benthin,
 // Wald 2013 ("Watertight Ray/Triangle Intersection"), two-sided, with the
 // 2-D edge functions evaluated without FMA contraction so that a shared edge
 // gets exactly opposite values in the two neighbouring triangles.
@@ -32,8 +31,6 @@ struct Ray {
     float ox, oy, oz;
     float dx, dy, dz;
     float ix, iy, iz;            // 1/d with zero components clamped (box tests only)
-    float nox, noy, noz;         // -o * (1/d), for t = b (1/d) - o (1/d) as one FMA
-    float slack;                 // absolute widening covering the rounding of o (1/d)
     float mx0, mx1, mx2;         // shear rows: A'x = Mx . A, A'y = My . A, A'z = Mz . A
     float my0, my1, my2;
     float mz0, mz1, mz2;
@@ -48,12 +45,6 @@ __device__ __forceinline__ void ray_setup(Ray& r) {
     r.ix = safe_inv(r.dx);
     r.iy = safe_inv(r.dy);
     r.iz = safe_inv(r.dz);
-    r.nox = -r.ox * r.ix;
-    r.noy = -r.oy * r.iy;
-    r.noz = -r.oz * r.iz;
-    // fma(b, 1/d, -o/d) is exact up to its final rounding plus the rounding of
-    // o/d (at most half an ulp of |o/d|); 2^-22 |o/d| bounds both with margin
-    r.slack = 2.384185791015625e-07f * fmaxf(fmaxf(fabsf(r.nox), fabsf(r.noy)), fabsf(r.noz));
     const float ax = fabsf(r.dx), ay = fabsf(r.dy), az = fabsf(r.dz);
     const int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
     int kx = kz == 2 ? 0 : kz + 1;
@@ -76,46 +67,44 @@ __device__ __forceinline__ void ray_setup(Ray& r) {
 }
 
 // Both child boxes of a node at once (paired FP32).  Slab distances are
-// t = b (1/d) - o (1/d) as single FMAs; the interval is widened by the per-ray
-// slack on both ends and the far end scaled by 1 + 2 gamma_3 (Ize 2013), so a
-// box the ray touches is never culled by rounding.  Returns the entry
-// distances (left, right), +inf for a miss.
+// (b - o) (1/d) as in Ize 2013 ("Robust BVH Ray Traversal"): the subtraction
+// keeps the sign of b - o exact even for rays parallel to an axis, and the far
+// end is scaled by 1 + 2 gamma_3 so a box the ray touches is never culled by
+// rounding.  Returns the entry distances (left, right), +inf for a miss.
+__device__ __forceinline__ float2 sub2(float a, float b, float o) {
+    return __fadd2_rn(make_float2(a, b), make_float2(-o, -o));
+}
+
 __device__ __forceinline__ float2 slab2(float4 nx, float4 ny, float4 nz, const Ray& r, float tmax) {
     const float2 ix = make_float2(r.ix, r.ix), iy = make_float2(r.iy, r.iy), iz = make_float2(r.iz, r.iz);
-    const float2 ox = make_float2(r.nox, r.nox), oy = make_float2(r.noy, r.noy), oz = make_float2(r.noz, r.noz);
-    const float2 x0 = __ffma2_rn(make_float2(nx.x, nx.y), ix, ox), x1 = __ffma2_rn(make_float2(nx.z, nx.w), ix, ox);
-    const float2 y0 = __ffma2_rn(make_float2(ny.x, ny.y), iy, oy), y1 = __ffma2_rn(make_float2(ny.z, ny.w), iy, oy);
-    const float2 z0 = __ffma2_rn(make_float2(nz.x, nz.y), iz, oz), z1 = __ffma2_rn(make_float2(nz.z, nz.w), iz, oz);
-    const float tlo = -r.slack;
-    const float tnl = fmaxf(fmaxf(fminf(x0.x, x1.x), fminf(y0.x, y1.x)), fmaxf(fminf(z0.x, z1.x), tlo));
-    const float tnr = fmaxf(fmaxf(fminf(x0.y, x1.y), fminf(y0.y, y1.y)), fmaxf(fminf(z0.y, z1.y), tlo));
+    const float2 x0 = __fmul2_rn(sub2(nx.x, nx.y, r.ox), ix), x1 = __fmul2_rn(sub2(nx.z, nx.w, r.ox), ix);
+    const float2 y0 = __fmul2_rn(sub2(ny.x, ny.y, r.oy), iy), y1 = __fmul2_rn(sub2(ny.z, ny.w, r.oy), iy);
+    const float2 z0 = __fmul2_rn(sub2(nz.x, nz.y, r.oz), iz), z1 = __fmul2_rn(sub2(nz.z, nz.w, r.oz), iz);
+    const float tnl = fmaxf(fmaxf(fminf(x0.x, x1.x), fminf(y0.x, y1.x)), fmaxf(fminf(z0.x, z1.x), 0.0f));
+    const float tnr = fmaxf(fmaxf(fminf(x0.y, x1.y), fminf(y0.y, y1.y)), fmaxf(fminf(z0.y, z1.y), 0.0f));
     const float tfl = fminf(fminf(fmaxf(x0.x, x1.x), fmaxf(y0.x, y1.x)), fminf(fmaxf(z0.x, z1.x), tmax));
     const float tfr = fminf(fminf(fmaxf(x0.y, x1.y), fmaxf(y0.y, y1.y)), fminf(fmaxf(z0.y, z1.y), tmax));
-    return make_float2(tnl <= fmaf(tfl, kFarScale, 2.0f * r.slack) ? tnl : INFINITY,
-                       tnr <= fmaf(tfr, kFarScale, 2.0f * r.slack) ? tnr : INFINITY);
+    return make_float2(tnl <= tfl * kFarScale ? tnl : INFINITY, tnr <= tfr * kFarScale ? tnr : INFINITY);
 }
 
 // The four child boxes of a 4-wide node (two pairs of paired-FP32 slabs), with
-// the same conservative widening as slab2.  Returns the entry distances,
-// +inf for a miss.
+// the same robust evaluation as slab2.  Returns the entry distances, +inf for
+// a miss.
 __device__ __forceinline__ float4 slab4(const float4* __restrict__ nd, const Ray& r, float tmax) {
     const float4 lx = __ldg(nd), hx = __ldg(nd + 1), ly = __ldg(nd + 2);
     const float4 hy = __ldg(nd + 3), lz = __ldg(nd + 4), hz = __ldg(nd + 5);
     const float2 ix = make_float2(r.ix, r.ix), iy = make_float2(r.iy, r.iy), iz = make_float2(r.iz, r.iz);
-    const float2 ox = make_float2(r.nox, r.nox), oy = make_float2(r.noy, r.noy), oz = make_float2(r.noz, r.noz);
-    const float2 xa0 = __ffma2_rn(make_float2(lx.x, lx.y), ix, ox), xb0 = __ffma2_rn(make_float2(lx.z, lx.w), ix, ox);
-    const float2 xa1 = __ffma2_rn(make_float2(hx.x, hx.y), ix, ox), xb1 = __ffma2_rn(make_float2(hx.z, hx.w), ix, ox);
-    const float2 ya0 = __ffma2_rn(make_float2(ly.x, ly.y), iy, oy), yb0 = __ffma2_rn(make_float2(ly.z, ly.w), iy, oy);
-    const float2 ya1 = __ffma2_rn(make_float2(hy.x, hy.y), iy, oy), yb1 = __ffma2_rn(make_float2(hy.z, hy.w), iy, oy);
-    const float2 za0 = __ffma2_rn(make_float2(lz.x, lz.y), iz, oz), zb0 = __ffma2_rn(make_float2(lz.z, lz.w), iz, oz);
-    const float2 za1 = __ffma2_rn(make_float2(hz.x, hz.y), iz, oz), zb1 = __ffma2_rn(make_float2(hz.z, hz.w), iz, oz);
-    const float lo = -r.slack;
-    const float far_pad = 2.0f * r.slack;
+    const float2 xa0 = __fmul2_rn(sub2(lx.x, lx.y, r.ox), ix), xb0 = __fmul2_rn(sub2(lx.z, lx.w, r.ox), ix);
+    const float2 xa1 = __fmul2_rn(sub2(hx.x, hx.y, r.ox), ix), xb1 = __fmul2_rn(sub2(hx.z, hx.w, r.ox), ix);
+    const float2 ya0 = __fmul2_rn(sub2(ly.x, ly.y, r.oy), iy), yb0 = __fmul2_rn(sub2(ly.z, ly.w, r.oy), iy);
+    const float2 ya1 = __fmul2_rn(sub2(hy.x, hy.y, r.oy), iy), yb1 = __fmul2_rn(sub2(hy.z, hy.w, r.oy), iy);
+    const float2 za0 = __fmul2_rn(sub2(lz.x, lz.y, r.oz), iz), zb0 = __fmul2_rn(sub2(lz.z, lz.w, r.oz), iz);
+    const float2 za1 = __fmul2_rn(sub2(hz.x, hz.y, r.oz), iz), zb1 = __fmul2_rn(sub2(hz.z, hz.w, r.oz), iz);
 #define VAFR_CHILD(X0, X1, Y0, Y1, Z0, Z1)                                                            \
     ([&]() {                                                                                          \
-        const float tn = fmaxf(fmaxf(fminf(X0, X1), fminf(Y0, Y1)), fmaxf(fminf(Z0, Z1), lo));        \
+        const float tn = fmaxf(fmaxf(fminf(X0, X1), fminf(Y0, Y1)), fmaxf(fminf(Z0, Z1), 0.0f));      \
         const float tf = fminf(fminf(fmaxf(X0, X1), fmaxf(Y0, Y1)), fminf(fmaxf(Z0, Z1), tmax));      \
-        return tn <= fmaf(tf, kFarScale, far_pad) ? tn : INFINITY;                                    \
+        return tn <= tf * kFarScale ? tn : INFINITY;                                                  \
     }())
     const float t0 = VAFR_CHILD(xa0.x, xa1.x, ya0.x, ya1.x, za0.x, za1.x);
     const float t1 = VAFR_CHILD(xa0.y, xa1.y, ya0.y, ya1.y, za0.y, za1.y);
@@ -227,7 +216,7 @@ __device__ unsigned traverse2(const SceneDev& sc, const Ray& r, Hit& h,
             while (true) {
                 if (sp == 0) return 0u;
                 --sp;
-                if (stack_t[sp] <= fmaf(h.t, kFarScale, 2.0f * r.slack)) break;
+                if (stack_t[sp] <= h.t * kFarScale) break;
             }
             node = stack[sp];
         }
@@ -291,7 +280,7 @@ __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
         VAFR_LEAF(t.w, c3)
 #undef VAFR_LEAF
         // children entering beyond an updated closest hit are dropped
-        const float lim = fmaf(h.t, kFarScale, 2.0f * r.slack);
+        const float lim = h.t * kFarScale;
         if (t.x > lim) t.x = INFINITY;
         if (t.y > lim) t.y = INFINITY;
         if (t.z > lim) t.z = INFINITY;
@@ -320,7 +309,7 @@ __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
             while (true) {
                 if (sp == 0) return 0u;
                 --sp;
-                if (stack_t[sp] <= fmaf(h.t, kFarScale, 2.0f * r.slack)) break;
+                if (stack_t[sp] <= h.t * kFarScale) break;
             }
             node = stack[sp];
         }
@@ -475,7 +464,7 @@ k_render_gt(const SceneDev sc, const __grid_constant__ B b) {
 // triangle tests and hits of the 4-wide traversal the render kernels use.
 __global__ void __launch_bounds__(128)
 k_render_stats(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned long long* out) {
-    unsigned long long nodes = 0, boxes = 0, tris = 0, rays = 0, hits = 0;
+    unsigned long long nodes = 0, boxes = 0, tris = 0, rays = 0, hits = 0, worst = 0;
     for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < b.total_work;
          w += (long long)gridDim.x * blockDim.x) {
         const FrameDesc& f = b.d[find_frame(b, w, false)];
@@ -483,7 +472,9 @@ k_render_stats(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned
         lp_ray(f, (int)(w - f.work_begin), r);
         ray_setup(r);
         Hit h;
+        unsigned long long n0 = nodes;
         traverse<4, true>(sc, r, h, &nodes, &boxes, &tris);
+        worst = max(worst, nodes - n0);
         ++rays;
         hits += h.leaf >= 0;
     }
@@ -492,6 +483,7 @@ k_render_stats(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned
     atomicAdd(out + 2, boxes);
     atomicAdd(out + 3, tris);
     atomicAdd(out + 4, hits);
+    atomicMax(out + 5, worst);
 }
 
 template <int TPB, int FETCH, int WIDE, bool GT, class B>
@@ -543,7 +535,7 @@ template cudaError_t launch_render_gt<BigBatch>(const SceneDev&, const BigBatch&
 
 cudaError_t launch_render_stats(const SceneDev& scene, const SmallBatch& batch,
                                 unsigned long long* counters, cudaStream_t s, int num_sms) {
-    cudaError_t e = cudaMemsetAsync(counters, 0, 5 * sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(counters, 0, 6 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     k_render_stats<<<num_sms * 4, 128, 0, s>>>(scene, batch, counters);
     count_launch(1);

@@ -309,10 +309,10 @@ def vafr_render_frame(scene: int, session: int, display_out, stream=None) -> Non
 
 
 def vafr_traversal_stats(scene: int, session: int, eye: int = 0, stream=None):
-    out = np.zeros(5, np.int64)
+    out = np.zeros(6, np.int64)
     _check(load().vafr_traversal_stats(scene, session, int(eye), ptr(out), stream_ptr(stream)))
     return {"rays": int(out[0]), "nodes": int(out[1]), "box_tests": int(out[2]),
-            "tri_tests": int(out[3]), "hits": int(out[4])}
+            "tri_tests": int(out[3]), "hits": int(out[4]), "max_nodes": int(out[5])}
 
 
 def _frames(frames):

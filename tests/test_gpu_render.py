@@ -212,3 +212,25 @@ def test_invalid_arguments(V, torch_mod):
         V.vafr_render_lp(h, s, 2, lp)
     V.vafr_session_destroy(s)
     V.vafr_scene_destroy(h)
+
+
+def test_axis_parallel_rays_stay_cheap(V, torch_mod, lay, terrain):
+    """Rays exactly parallel to a world axis (cos phi = 0 at the centre gaze) from
+    an eye whose origin is off that axis's plane must still cull boxes: no ray
+    may wander through the whole tree (that once made one launch 7x slower)."""
+    w, h, bvh = terrain
+    d = w.displays[0]
+    from workloads.views import eye_pair_poses
+    left, _ = eye_pair_poses(d.poses[0], 0.063)
+    s = _session(V, d.width, d.height, d.fov_v_deg, [left])
+    V.vafr_set_gaze(s, 0, d.width / 2, d.height / 2)
+    st = V.vafr_traversal_stats(h, s, 0)
+    assert st["max_nodes"] < 2000, st
+    lp, ids = _render_lp(V, torch_mod, h, s, lay.total)
+    rng = np.random.default_rng(3)
+    tex = np.sort(rng.choice(lay.total, 20000, replace=False))
+    rgba, oid, ot, o, dd = oracle.render_lp(w.scene.tris, w.scene.albedo, w.scene.light_dir, lay,
+                                            d.width, d.height, d.fov_v_deg,
+                                            (d.width / 2, d.height / 2), left, texels=tex, bvh=bvh)
+    compare_hits_and_colours(w.scene.tris, o, dd, ids[tex], lp[tex], oid, ot, rgba, 1e-3)
+    V.vafr_session_destroy(s)
