@@ -127,12 +127,15 @@ __device__ __forceinline__ unsigned pack_half2(float2 p) {
 }
 
 // Tile of TW x TH pixels; TW / PX threads per row, each thread PX pixels of one
-// row.  FP32 display: pixel q of a thread is x = x_tile + q TW/PX + tx, so each
-// 16-byte store of a warp is contiguous.  FP16 display: a thread takes PX
-// adjacent pixels (pairs share one 16-byte store).
+// row, so the per-thread set-up (frame lookup, row offset) is shared by PX
+// pixels.  FP32 display: pixel q of a thread is x = x_tile + q TW/PX + tx, and
+// each 16-byte store of a warp is contiguous.  FP16 display: the thread takes
+// PX/2 pairs of adjacent pixels, pair q at x = x_tile + 2 (q TW/PX + tx), each
+// pair one 16-byte store, again contiguous across the warp.
 template <int TW, int TH, int PX, class B>
 __global__ void __launch_bounds__((TW / PX) * TH)
 k_reconstruct(const __grid_constant__ B b) {
+    static_assert(PX % 2 == 0, "pixels per thread must be even");
     __shared__ ReconShared sh;
     const int tile = (int)blockIdx.x;
     if (threadIdx.x == 0) {
@@ -175,30 +178,36 @@ k_reconstruct(const __grid_constant__ B b) {
     const float dy2 = dy * dy;
     const long long row = (long long)y * W;
     const int xt = tx_tile * TW;
+    // every pixel's gaze offset is one rounding of (x - floor(x0)) + (0.5 - frac(x0)),
+    // so results do not depend on the tile shape
     const int gxi = sh.gxi;
     const float gxf = sh.gxf;
     if (sh.disp_fmt == VAFR_FMT_RGBA16F) {
-        const int x0 = xt + tx * PX;
-        const float dx0 = (float)(x0 - gxi) + gxf;
-        if (PX == 2 && x0 + 1 < W && ((row + x0) & 1) == 0) {
-            const px2 a = recon_pixel(f, dx0, dy, dy2);
-            const px2 c = recon_pixel(f, dx0 + 1.0f, dy, dy2);
-            __stcs(reinterpret_cast<uint4*>(reinterpret_cast<uint2*>(disp) + row + x0),
-                   make_uint4(pack_half2(a.rg), pack_half2(a.ba), pack_half2(c.rg), pack_half2(c.ba)));
-        } else {
+        const bool pair_ok = (W & 1) == 0;   // 16-byte alignment of pixel pairs
 #pragma unroll
-            for (int q = 0; q < PX; ++q) {
-                const int x = x0 + q;
-                if (x >= W) break;
-                const px2 a = recon_pixel(f, (float)(x - gxi) + gxf, dy, dy2);
-                __stcs(reinterpret_cast<uint2*>(disp) + row + x,
-                       make_uint2(pack_half2(a.rg), pack_half2(a.ba)));
+        for (int q = 0; q < PX / 2; ++q) {
+            const int xo = 2 * (q * TX + tx);
+            const int x = xt + xo;
+            if (x >= W) break;
+            const px2 a = recon_pixel(f, (float)(x - gxi) + gxf, dy, dy2);
+            if (pair_ok && x + 1 < W) {
+                const px2 c = recon_pixel(f, (float)(x + 1 - gxi) + gxf, dy, dy2);
+                __stcs(reinterpret_cast<uint4*>(reinterpret_cast<uint2*>(disp) + row + x),
+                       make_uint4(pack_half2(a.rg), pack_half2(a.ba), pack_half2(c.rg), pack_half2(c.ba)));
+            } else {
+                __stcs(reinterpret_cast<uint2*>(disp) + row + x, make_uint2(pack_half2(a.rg), pack_half2(a.ba)));
+                if (x + 1 < W) {
+                    const px2 c = recon_pixel(f, (float)(x + 1 - gxi) + gxf, dy, dy2);
+                    __stcs(reinterpret_cast<uint2*>(disp) + row + x + 1,
+                           make_uint2(pack_half2(c.rg), pack_half2(c.ba)));
+                }
             }
         }
     } else {
 #pragma unroll
         for (int q = 0; q < PX; ++q) {
-            const int x = xt + q * TX + tx;
+            const int xo = q * TX + tx;
+            const int x = xt + xo;
             if (x >= W) break;
             const px2 a = recon_pixel(f, (float)(x - gxi) + gxf, dy, dy2);
             __stcs(reinterpret_cast<float4*>(disp) + row + x, make_float4(a.rg.x, a.rg.y, a.ba.x, a.ba.y));
@@ -216,24 +225,24 @@ cudaError_t launch_shape(const B& b, cudaStream_t s) {
 
 }  // namespace
 
-// Tile shapes the autotuner chooses between (pixels).  The 16-byte FP16 pair
-// store needs an even pixel offset, checked per thread.
+// Tile shapes the autotuner chooses between (pixels wide, rows, pixels per
+// thread).
 ReconShape recon_shape(int variant) {
     switch (variant) {
-        case 0: return {64, 8, 2};
-        case 1: return {32, 8, 1};
-        case 2: return {128, 4, 2};
-        default: return {32, 16, 2};
+        case 0: return {256, 4, 8};
+        case 1: return {128, 8, 4};
+        case 2: return {64, 8, 2};
+        default: return {128, 4, 4};
     }
 }
 
 template <class B>
 cudaError_t launch_reconstruct(const B& batch, int variant, cudaStream_t s) {
     switch (variant) {
-        case 0: return launch_shape<64, 8, 2>(batch, s);
-        case 1: return launch_shape<32, 8, 1>(batch, s);
-        case 2: return launch_shape<128, 4, 2>(batch, s);
-        default: return launch_shape<32, 16, 2>(batch, s);
+        case 0: return launch_shape<256, 4, 8>(batch, s);
+        case 1: return launch_shape<128, 8, 4>(batch, s);
+        case 2: return launch_shape<64, 8, 2>(batch, s);
+        default: return launch_shape<128, 4, 4>(batch, s);
     }
 }
 
