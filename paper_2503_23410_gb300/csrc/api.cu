@@ -308,6 +308,15 @@ int vafr_build_scene(const float* tri_xyz, const float* albedo_rgb, int64_t n_tr
         b.albedo = alb;
         e = lbvh_build(b, s);
         if (e != cudaSuccess) return bail(fail(VAFR_ERR_CUDA, "lbvh build: %s", cudaGetErrorString(e)));
+        if (n > 1) {
+            void* scratch = nullptr;
+            e = cudaMalloc(&scratch, tree4_scratch_bytes(n));
+            if (e != cudaSuccess) return bail(fail(VAFR_ERR_OOM, "traversal tree scratch"));
+            e = tree4_build(b, scratch, kPlocRadius, s);
+            cudaFree(scratch);
+            if (e != cudaSuccess)
+                return bail(fail(VAFR_ERR_CUDA, "traversal tree build: %s", cudaGetErrorString(e)));
+        }
     }
     SceneDev& d = sc->dev;
     d.nodes = b.nodes;

@@ -339,72 +339,6 @@ __global__ void k_pack_leaves(const float* __restrict__ tris, const float* __res
         albedo4[k] = make_float4(0.8f, 0.8f, 0.8f, 0.0f);
 }
 
-// ---- 4-wide traversal structure ------------------------------------------------
-// The binary tree is collapsed two levels at a time: every internal node at
-// even depth (the root is depth 0) becomes a 4-wide node whose children are
-// its children, with each internal child replaced by that child's own two
-// children.  Child boxes are the binary nodes' exact FP32 boxes.
-
-__global__ void k_depth_heads(const int32_t* __restrict__ parent, int n_inner,
-                              unsigned* __restrict__ head) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_inner) return;
-    int d = 0;
-    for (int p = parent[i]; p >= 0 && d < 96; p = parent[p]) ++d;
-    head[i] = (d & 1) == 0 ? 1u : 0u;
-}
-
-__device__ __forceinline__ void box_of(int ref, const float* __restrict__ node_box,
-                                       const float* __restrict__ leaf_box, float b[6]) {
-    const float* p = ref >= 0 ? node_box + 6ll * ref : leaf_box + 6ll * ~ref;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) b[k] = p[k];
-}
-
-// head_idx: exclusive scan of the head flags (4-wide node index of each head).
-__global__ void k_pack_nodes4(const int2* __restrict__ child, const float* __restrict__ node_box,
-                              const float* __restrict__ leaf_box, const unsigned* __restrict__ flag,
-                              const unsigned* __restrict__ head_idx, int n_inner,
-                              float4* __restrict__ nodes4) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_inner || !flag[i]) return;
-    int ref[4];
-    float box[4][6];
-    int m = 0;
-    const int2 c = child[i];
-    const int cs[2] = {c.x, c.y};
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const int ca = cs[a];
-        if (ca < 0) {
-            box_of(ca, node_box, leaf_box, box[m]);
-            ref[m++] = ca;
-        } else {
-            const int2 g = child[ca];
-            const int gs[2] = {g.x, g.y};
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                box_of(gs[q], node_box, leaf_box, box[m]);
-                ref[m++] = gs[q] < 0 ? gs[q] : (int)head_idx[gs[q]];
-            }
-        }
-    }
-    for (int k = m; k < 4; ++k) {
-        ref[k] = kEmptyRef;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) box[k][q] = 0.0f;
-    }
-    float4* o = nodes4 + 8ll * head_idx[i];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {   // lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the four children
-        const int comp = (q >> 1) + ((q & 1) ? 3 : 0);
-        o[q] = make_float4(box[0][comp], box[1][comp], box[2][comp], box[3][comp]);
-    }
-    o[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]),
-                       __int_as_float(ref[3]));
-    o[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-}
-
 inline int blocks_for(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
 
 }  // namespace
@@ -450,15 +384,6 @@ cudaError_t lbvh_build(const LbvhBuffers& b, cudaStream_t s) {
     k_pack_leaves<<<blocks_for(n, 256), 256, 0, s>>>(b.tris, b.albedo, b.ids, n, b.leaves,
                                                      b.albedo4);
     count_launch(1);
-    if (n > 1) {
-        k_depth_heads<<<blocks_for(n - 1, 256), 256, 0, s>>>(b.parent, n - 1, b.head_flag);
-        cudaMemcpyAsync(b.head_idx, b.head_flag, sizeof(unsigned) * (size_t)(n - 1),
-                        cudaMemcpyDeviceToDevice, s);
-        k_radix_scan<<<1, 1024, 0, s>>>(b.head_idx, n - 1);
-        k_pack_nodes4<<<blocks_for(n - 1, 256), 256, 0, s>>>(b.child, b.node_box, b.leaf_box,
-                                                             b.head_flag, b.head_idx, n - 1, b.nodes4);
-        count_launch(3);
-    }
     return cudaGetLastError();
 }
 

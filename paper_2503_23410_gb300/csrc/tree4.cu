@@ -1,0 +1,350 @@
+// tree4.cu -- the traversal tree: a binary tree of the scene's leaves built by
+// PLOC (Meister and Bittner 2018, "Parallel Locally-Ordered Clustering for
+// Bounding Volume Hierarchy Construction"), collapsed into 4-wide nodes.
+//
+// PLOC starts from the leaves in Morton order (the LBVH sort) and repeats:
+//   1. every cluster finds the cluster within +-radius positions whose
+//      merged box has the smallest surface area (ties: lower position);
+//   2. mutual nearest neighbours merge into a new internal node, which takes
+//      the lower position; the other position is dropped;
+//   3. the cluster array is compacted (exclusive scans; no atomics, so the
+//      tree is deterministic).
+// The pair of mutual neighbours with the smallest distance (lowest position on
+// ties) always exists, so every round merges at least once.  The tree is then
+// renumbered so its root is node 0 and collapsed two levels at a time: every
+// internal node at even depth becomes a 4-wide node whose children are its
+// children, internal children replaced by their own two children.  All boxes
+// are exact FP32 unions of the triangles' boxes.
+#include "vafr_internal.cuh"
+
+#include <utility>
+
+namespace vafr {
+namespace {
+
+constexpr int kPlocRadiusMax = 16;
+constexpr int kThreads = 256;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+inline int blocks_for(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
+
+// ---- multi-block exclusive scan of unsigned counters ----------------------------
+__global__ void k_scan_tiles(unsigned* __restrict__ v, int n, unsigned* __restrict__ sums) {
+    __shared__ unsigned part[kScanThreads];
+    const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+    unsigned x[kScanItems];
+    unsigned acc = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        x[k] = base + k < n ? v[base + k] : 0u;
+        acc += x[k];
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 1; o < kScanThreads; o <<= 1) {
+        const unsigned t = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += t;
+        __syncthreads();
+    }
+    unsigned run = part[threadIdx.x] - acc;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) v[base + k] = run;
+        run += x[k];
+    }
+    if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = part[threadIdx.x];
+}
+
+__global__ void k_scan_add(unsigned* __restrict__ v, int n, const unsigned* __restrict__ sums) {
+    const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+    if (i < n) v[i] += sums[i / kScanTile];
+}
+
+// Scratch `sums` needs scan_scratch_elems(n) entries.
+int scan_scratch_elems(int n) {
+    int total = 0;
+    for (int m = n; m > 1;) {
+        m = blocks_for(m, kScanTile);
+        total += m;
+    }
+    return total + 1;
+}
+
+cudaError_t exclusive_scan(unsigned* v, int n, unsigned* sums, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int nb = blocks_for(n, kScanTile);
+    k_scan_tiles<<<nb, kScanThreads, 0, s>>>(v, n, sums);
+    count_launch(1);
+    if (nb > 1) {
+        cudaError_t e = exclusive_scan(sums, nb, sums + nb, s);   // scan the tile sums
+        if (e != cudaSuccess) return e;
+        k_scan_add<<<blocks_for(n, kThreads), kThreads, 0, s>>>(v, n, sums);
+        count_launch(1);
+    }
+    return cudaGetLastError();
+}
+
+// ---- PLOC ---------------------------------------------------------------------------
+__device__ __forceinline__ float half_area(float4 lo, float4 hi) {
+    const float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return fmaf(dx, dy, fmaf(dy, dz, dz * dx));
+}
+
+__global__ void k_ploc_init(const float* __restrict__ leaf_box, int n, int* __restrict__ C,
+                            float4* __restrict__ lo, float4* __restrict__ hi) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* b = leaf_box + 6ll * i;
+    C[i] = ~i;
+    lo[i] = make_float4(b[0], b[1], b[2], 0.0f);
+    hi[i] = make_float4(b[3], b[4], b[5], 0.0f);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_ploc_nn(const float4* __restrict__ lo, const float4* __restrict__ hi, int m, int radius,
+          int* __restrict__ nbr) {
+    constexpr int R = kPlocRadiusMax;
+    __shared__ float4 slo[kThreads + 2 * R], shi[kThreads + 2 * R];
+    const int base = blockIdx.x * kThreads;
+    for (int k = threadIdx.x; k < kThreads + 2 * R; k += kThreads) {
+        const int j = base - R + k;
+        if (j >= 0 && j < m) {
+            slo[k] = lo[j];
+            shi[k] = hi[j];
+        }
+    }
+    __syncthreads();
+    const int i = base + threadIdx.x;
+    if (i >= m) return;
+    const float4 a = slo[threadIdx.x + R], A = shi[threadIdx.x + R];
+    float best = INFINITY;
+    int bj = -1;
+    for (int d = -radius; d <= radius; ++d) {
+        const int j = i + d;
+        if (d == 0 || j < 0 || j >= m) continue;
+        const float4 b = slo[threadIdx.x + R + d], B = shi[threadIdx.x + R + d];
+        const float c = half_area(make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), 0.0f),
+                                  make_float4(fmaxf(A.x, B.x), fmaxf(A.y, B.y), fmaxf(A.z, B.z), 0.0f));
+        if (c < best) {   // ascending j: ties keep the lower position
+            best = c;
+            bj = j;
+        }
+    }
+    nbr[i] = bj;
+}
+
+__global__ void k_ploc_flags(const int* __restrict__ nbr, int m, unsigned* __restrict__ keep,
+                             unsigned* __restrict__ merge) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int j = nbr[i];
+    const bool mutual = j >= 0 && nbr[j] == i;
+    keep[i] = (mutual && i > j) ? 0u : 1u;
+    merge[i] = (mutual && i < j) ? 1u : 0u;
+}
+
+__global__ void k_ploc_compact(const int* __restrict__ C, const float4* __restrict__ lo,
+                               const float4* __restrict__ hi, const int* __restrict__ nbr,
+                               const unsigned* __restrict__ keep_flag, const unsigned* __restrict__ pos,
+                               const unsigned* __restrict__ merge_flag, const unsigned* __restrict__ moff,
+                               int m, int node_base, int* __restrict__ C2, float4* __restrict__ lo2,
+                               float4* __restrict__ hi2, int2* __restrict__ child,
+                               float* __restrict__ node_box) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || !keep_flag[i]) return;
+    const unsigned p = pos[i];
+    if (merge_flag[i]) {
+        const int j = nbr[i];
+        const int id = node_base + (int)moff[i];
+        const float4 a = lo[i], b = lo[j], A = hi[i], B = hi[j];
+        const float4 l = make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), 0.0f);
+        const float4 h = make_float4(fmaxf(A.x, B.x), fmaxf(A.y, B.y), fmaxf(A.z, B.z), 0.0f);
+        child[id] = make_int2(C[i], C[j]);
+        float* nb = node_box + 6ll * id;
+        nb[0] = l.x; nb[1] = l.y; nb[2] = l.z; nb[3] = h.x; nb[4] = h.y; nb[5] = h.z;
+        C2[p] = id;
+        lo2[p] = l;
+        hi2[p] = h;
+    } else {
+        C2[p] = C[i];
+        lo2[p] = lo[i];
+        hi2[p] = hi[i];
+    }
+}
+
+// creation order puts the root last: node id -> n_inner - 1 - id puts it first
+__global__ void k_renumber(const int2* __restrict__ child, const float* __restrict__ node_box,
+                           int n_inner, int2* __restrict__ child2, float* __restrict__ node_box2,
+                           int32_t* __restrict__ parent2) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n_inner) return;
+    const int nid = n_inner - 1 - id;
+    int2 c = child[id];
+    c.x = c.x >= 0 ? n_inner - 1 - c.x : c.x;
+    c.y = c.y >= 0 ? n_inner - 1 - c.y : c.y;
+    child2[nid] = c;
+    if (c.x >= 0) parent2[c.x] = nid;
+    if (c.y >= 0) parent2[c.y] = nid;
+    if (nid == 0) parent2[0] = -1;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) node_box2[6ll * nid + k] = node_box[6ll * id + k];
+}
+
+// ---- collapse to 4-wide -------------------------------------------------------------
+__global__ void k_depth_heads(const int32_t* __restrict__ parent, int n_inner,
+                              unsigned* __restrict__ head) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inner) return;
+    int d = 0;
+    // a PLOC tree of 2^30 leaves can be deeper than a radix tree; the bound only
+    // guards against a malformed parent array
+    for (int p = parent[i]; p >= 0 && d < 4096; p = parent[p]) ++d;
+    head[i] = (d & 1) == 0 ? 1u : 0u;
+}
+
+__device__ __forceinline__ void box_of(int ref, const float* __restrict__ node_box,
+                                       const float* __restrict__ leaf_box, float b[6]) {
+    const float* p = ref >= 0 ? node_box + 6ll * ref : leaf_box + 6ll * ~ref;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) b[k] = p[k];
+}
+
+// head_idx: exclusive scan of the head flags (4-wide node index of each head).
+__global__ void k_pack_nodes4(const int2* __restrict__ child, const float* __restrict__ node_box,
+                              const float* __restrict__ leaf_box, const unsigned* __restrict__ flag,
+                              const unsigned* __restrict__ head_idx, int n_inner,
+                              float4* __restrict__ nodes4) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inner || !flag[i]) return;
+    int ref[4];
+    float box[4][6];
+    int m = 0;
+    const int2 c = child[i];
+    const int cs[2] = {c.x, c.y};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int ca = cs[a];
+        if (ca < 0) {
+            box_of(ca, node_box, leaf_box, box[m]);
+            ref[m++] = ca;
+        } else {
+            const int2 g = child[ca];
+            const int gs[2] = {g.x, g.y};
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                box_of(gs[q], node_box, leaf_box, box[m]);
+                ref[m++] = gs[q] < 0 ? gs[q] : (int)head_idx[gs[q]];
+            }
+        }
+    }
+    for (int k = m; k < 4; ++k) {
+        ref[k] = kEmptyRef;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) box[k][q] = 0.0f;
+    }
+    float4* o = nodes4 + 8ll * head_idx[i];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {   // lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the four children
+        const int comp = (q >> 1) + ((q & 1) ? 3 : 0);
+        o[q] = make_float4(box[0][comp], box[1][comp], box[2][comp], box[3][comp]);
+    }
+    o[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]),
+                       __int_as_float(ref[3]));
+    o[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+}  // namespace
+
+size_t tree4_scratch_bytes(int n) {
+    const size_t N = (size_t)(n > 1 ? n : 1);
+    return N * (2 * sizeof(int) + 4 * sizeof(float4) + sizeof(int) + 4 * sizeof(unsigned)) +
+           (size_t)(n > 1 ? n - 1 : 1) * (sizeof(int2) * 2 + 12 * sizeof(float) + sizeof(int32_t)) +
+           (size_t)scan_scratch_elems((int)N) * sizeof(unsigned) + 20 * 256;
+}
+
+cudaError_t tree4_build(const LbvhBuffers& b, void* scratch, int radius, cudaStream_t s) {
+    if (radius < 1 || radius > kPlocRadiusMax) return cudaErrorInvalidValue;
+    const int n = b.n;
+    if (n <= 1) return cudaSuccess;
+    const int n_inner = n - 1;
+    // carve the scratch block
+    char* p = static_cast<char*>(scratch);
+    auto take = [&](size_t bytes) {
+        char* q = p;
+        p += (bytes + 255) & ~(size_t)255;
+        return q;
+    };
+    int* C = reinterpret_cast<int*>(take(sizeof(int) * n));
+    int* C2 = reinterpret_cast<int*>(take(sizeof(int) * n));
+    float4* lo = reinterpret_cast<float4*>(take(sizeof(float4) * n));
+    float4* hi = reinterpret_cast<float4*>(take(sizeof(float4) * n));
+    float4* lo2 = reinterpret_cast<float4*>(take(sizeof(float4) * n));
+    float4* hi2 = reinterpret_cast<float4*>(take(sizeof(float4) * n));
+    int* nbr = reinterpret_cast<int*>(take(sizeof(int) * n));
+    unsigned* keep = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * n));
+    unsigned* pos = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * n));
+    unsigned* merge = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * n));
+    unsigned* moff = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * n));
+    int2* child = reinterpret_cast<int2*>(take(sizeof(int2) * n_inner));
+    int2* child2 = reinterpret_cast<int2*>(take(sizeof(int2) * n_inner));
+    float* nbox = reinterpret_cast<float*>(take(sizeof(float) * 6 * n_inner));
+    float* nbox2 = reinterpret_cast<float*>(take(sizeof(float) * 6 * n_inner));
+    int32_t* parent = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * n_inner));
+    unsigned* sums = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * scan_scratch_elems(n)));
+    unsigned* hostv = nullptr;
+    cudaError_t e = cudaMallocHost(&hostv, 4 * sizeof(unsigned));
+    if (e != cudaSuccess) return e;
+
+    k_ploc_init<<<blocks_for(n, kThreads), kThreads, 0, s>>>(b.leaf_box, n, C, lo, hi);
+    count_launch(1);
+    int m = n, node_base = 0, rounds = 0;
+    while (m > 1 && e == cudaSuccess) {
+        if (++rounds > 100000) { e = cudaErrorUnknown; break; }
+        const int g = blocks_for(m, kThreads);
+        k_ploc_nn<<<g, kThreads, 0, s>>>(lo, hi, m, radius, nbr);
+        k_ploc_flags<<<g, kThreads, 0, s>>>(nbr, m, keep, merge);
+        count_launch(2);
+        e = cudaMemcpyAsync(pos, keep, sizeof(unsigned) * m, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(moff, merge, sizeof(unsigned) * m, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = exclusive_scan(pos, m, sums, s);
+        if (e == cudaSuccess) e = exclusive_scan(moff, m, sums, s);
+        if (e != cudaSuccess) break;
+        k_ploc_compact<<<g, kThreads, 0, s>>>(C, lo, hi, nbr, keep, pos, merge, moff, m, node_base, C2,
+                                              lo2, hi2, child, nbox);
+        count_launch(1);
+        e = cudaMemcpyAsync(hostv + 0, pos + (m - 1), sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hostv + 1, keep + (m - 1), sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hostv + 2, moff + (m - 1), sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hostv + 3, merge + (m - 1), sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        const int m2 = (int)(hostv[0] + hostv[1]);
+        const int merged = (int)(hostv[2] + hostv[3]);
+        if (merged <= 0 || m2 != m - merged) { e = cudaErrorUnknown; break; }
+        node_base += merged;
+        m = m2;
+        std::swap(C, C2);
+        std::swap(lo, lo2);
+        std::swap(hi, hi2);
+    }
+    cudaFreeHost(hostv);
+    if (e != cudaSuccess) return e;
+    if (node_base != n_inner) return cudaErrorUnknown;
+    k_renumber<<<blocks_for(n_inner, kThreads), kThreads, 0, s>>>(child, nbox, n_inner, child2, nbox2, parent);
+    k_depth_heads<<<blocks_for(n_inner, kThreads), kThreads, 0, s>>>(parent, n_inner, b.head_flag);
+    count_launch(2);
+    e = cudaMemcpyAsync(b.head_idx, b.head_flag, sizeof(unsigned) * (size_t)n_inner, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = exclusive_scan(b.head_idx, n_inner, sums, s);
+    if (e != cudaSuccess) return e;
+    k_pack_nodes4<<<blocks_for(n_inner, kThreads), kThreads, 0, s>>>(child2, nbox2, b.leaf_box, b.head_flag,
+                                                                      b.head_idx, n_inner, b.nodes4);
+    count_launch(1);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the caller frees the scratch next
+    return e;
+}
+
+}  // namespace vafr

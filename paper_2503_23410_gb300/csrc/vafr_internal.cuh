@@ -139,6 +139,12 @@ struct LbvhBuffers {
 };
 size_t lbvh_sort_blocks(int n);
 cudaError_t lbvh_build(const LbvhBuffers& b, cudaStream_t s);
+// Traversal tree (tree4.cu): PLOC over the sorted leaves, collapsed to 4-wide
+// nodes in b.nodes4.  `scratch` holds tree4_scratch_bytes(n) device bytes and
+// may be freed when the call returns (it synchronises `s`).
+constexpr int kPlocRadius = 8;
+size_t tree4_scratch_bytes(int n);
+cudaError_t tree4_build(const LbvhBuffers& b, void* scratch, int radius, cudaStream_t s);
 
 void count_launch(int k = 1);
 
