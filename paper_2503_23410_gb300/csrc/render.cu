@@ -31,6 +31,7 @@ struct Ray {
     float ox, oy, oz;
     float dx, dy, dz;
     float ix, iy, iz;            // 1/d with zero components clamped (box tests only)
+    int nx, ny, nz;              // float4 index of each axis's near plane in a 4-wide node
     float mx0, mx1, mx2;         // shear rows: A'x = Mx . A, A'y = My . A, A'z = Mz . A
     float my0, my1, my2;
     float mz0, mz1, mz2;
@@ -45,6 +46,10 @@ __device__ __forceinline__ void ray_setup(Ray& r) {
     r.ix = safe_inv(r.dx);
     r.iy = safe_inv(r.dy);
     r.iz = safe_inv(r.dz);
+    // a 4-wide node stores lo then hi per axis: the near plane is hi when 1/d < 0
+    r.nx = r.ix < 0.0f ? 1 : 0;
+    r.ny = r.iy < 0.0f ? 3 : 2;
+    r.nz = r.iz < 0.0f ? 5 : 4;
     const float ax = fabsf(r.dx), ay = fabsf(r.dy), az = fabsf(r.dz);
     const int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
     int kx = kz == 2 ? 0 : kz + 1;
@@ -88,28 +93,32 @@ __device__ __forceinline__ float2 slab2(float4 nx, float4 ny, float4 nz, const R
 }
 
 // The four child boxes of a 4-wide node (two pairs of paired-FP32 slabs), with
-// the same robust evaluation as slab2.  Returns the entry distances, +inf for
-// a miss.
+// the same robust evaluation as slab2.  Each axis's near and far planes are
+// chosen per ray by the sign of 1/d (the near plane of every box is then its
+// lo side, or its hi side, for all four children at once), so each child needs
+// only the max of three near distances and the min of three far ones.
+// Returns the entry distances, +inf for a miss.
 __device__ __forceinline__ float4 slab4(const float4* __restrict__ nd, const Ray& r, float tmax) {
-    const float4 lx = __ldg(nd), hx = __ldg(nd + 1), ly = __ldg(nd + 2);
-    const float4 hy = __ldg(nd + 3), lz = __ldg(nd + 4), hz = __ldg(nd + 5);
+    const float4 nxp = __ldg(nd + r.nx), fxp = __ldg(nd + (r.nx ^ 1));
+    const float4 nyp = __ldg(nd + r.ny), fyp = __ldg(nd + (r.ny ^ 1));
+    const float4 nzp = __ldg(nd + r.nz), fzp = __ldg(nd + (r.nz ^ 1));
     const float2 ix = make_float2(r.ix, r.ix), iy = make_float2(r.iy, r.iy), iz = make_float2(r.iz, r.iz);
-    const float2 xa0 = __fmul2_rn(sub2(lx.x, lx.y, r.ox), ix), xb0 = __fmul2_rn(sub2(lx.z, lx.w, r.ox), ix);
-    const float2 xa1 = __fmul2_rn(sub2(hx.x, hx.y, r.ox), ix), xb1 = __fmul2_rn(sub2(hx.z, hx.w, r.ox), ix);
-    const float2 ya0 = __fmul2_rn(sub2(ly.x, ly.y, r.oy), iy), yb0 = __fmul2_rn(sub2(ly.z, ly.w, r.oy), iy);
-    const float2 ya1 = __fmul2_rn(sub2(hy.x, hy.y, r.oy), iy), yb1 = __fmul2_rn(sub2(hy.z, hy.w, r.oy), iy);
-    const float2 za0 = __fmul2_rn(sub2(lz.x, lz.y, r.oz), iz), zb0 = __fmul2_rn(sub2(lz.z, lz.w, r.oz), iz);
-    const float2 za1 = __fmul2_rn(sub2(hz.x, hz.y, r.oz), iz), zb1 = __fmul2_rn(sub2(hz.z, hz.w, r.oz), iz);
-#define VAFR_CHILD(X0, X1, Y0, Y1, Z0, Z1)                                                            \
-    ([&]() {                                                                                          \
-        const float tn = fmaxf(fmaxf(fminf(X0, X1), fminf(Y0, Y1)), fmaxf(fminf(Z0, Z1), 0.0f));      \
-        const float tf = fminf(fminf(fmaxf(X0, X1), fmaxf(Y0, Y1)), fminf(fmaxf(Z0, Z1), tmax));      \
-        return tn <= tf * kFarScale ? tn : INFINITY;                                                  \
+    const float2 xna = __fmul2_rn(sub2(nxp.x, nxp.y, r.ox), ix), xnb = __fmul2_rn(sub2(nxp.z, nxp.w, r.ox), ix);
+    const float2 xfa = __fmul2_rn(sub2(fxp.x, fxp.y, r.ox), ix), xfb = __fmul2_rn(sub2(fxp.z, fxp.w, r.ox), ix);
+    const float2 yna = __fmul2_rn(sub2(nyp.x, nyp.y, r.oy), iy), ynb = __fmul2_rn(sub2(nyp.z, nyp.w, r.oy), iy);
+    const float2 yfa = __fmul2_rn(sub2(fyp.x, fyp.y, r.oy), iy), yfb = __fmul2_rn(sub2(fyp.z, fyp.w, r.oy), iy);
+    const float2 zna = __fmul2_rn(sub2(nzp.x, nzp.y, r.oz), iz), znb = __fmul2_rn(sub2(nzp.z, nzp.w, r.oz), iz);
+    const float2 zfa = __fmul2_rn(sub2(fzp.x, fzp.y, r.oz), iz), zfb = __fmul2_rn(sub2(fzp.z, fzp.w, r.oz), iz);
+#define VAFR_CHILD(XN, XF, YN, YF, ZN, ZF)                                        \
+    ([&]() {                                                                      \
+        const float tn = fmaxf(fmaxf(XN, YN), fmaxf(ZN, 0.0f));                   \
+        const float tf = fminf(fminf(XF, YF), fminf(ZF, tmax));                   \
+        return tn <= tf * kFarScale ? tn : INFINITY;                              \
     }())
-    const float t0 = VAFR_CHILD(xa0.x, xa1.x, ya0.x, ya1.x, za0.x, za1.x);
-    const float t1 = VAFR_CHILD(xa0.y, xa1.y, ya0.y, ya1.y, za0.y, za1.y);
-    const float t2 = VAFR_CHILD(xb0.x, xb1.x, yb0.x, yb1.x, zb0.x, zb1.x);
-    const float t3 = VAFR_CHILD(xb0.y, xb1.y, yb0.y, yb1.y, zb0.y, zb1.y);
+    const float t0 = VAFR_CHILD(xna.x, xfa.x, yna.x, yfa.x, zna.x, zfa.x);
+    const float t1 = VAFR_CHILD(xna.y, xfa.y, yna.y, yfa.y, zna.y, zfa.y);
+    const float t2 = VAFR_CHILD(xnb.x, xfb.x, ynb.x, yfb.x, znb.x, zfb.x);
+    const float t3 = VAFR_CHILD(xnb.y, xfb.y, ynb.y, yfb.y, znb.y, zfb.y);
 #undef VAFR_CHILD
     return make_float4(t0, t1, t2, t3);
 }
