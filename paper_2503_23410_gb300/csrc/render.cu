@@ -245,7 +245,7 @@ __device__ __forceinline__ void sort2(float& ta, int& ra, float& tb, int& rb) {
 // Closest hit through the 4-wide tree: test the four child boxes, test leaf
 // children at once, then continue with the nearest internal child and push the
 // others far-to-near.  Returns a fault bit (0 = fine).
-template <bool STATS>
+template <bool STATS, int ORDER>
 __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
                               unsigned long long* node_visits, unsigned long long* box_tests,
                               unsigned long long* tri_tests) {
@@ -294,12 +294,19 @@ __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
         if (t.y > lim) t.y = INFINITY;
         if (t.z > lim) t.z = INFINITY;
         if (t.w > lim) t.w = INFINITY;
-        // ascending (t, ref): sorting network (0,1) (2,3) (0,2) (1,3) (1,2)
-        sort2(t.x, c0, t.y, c1);
-        sort2(t.z, c2, t.w, c3);
-        sort2(t.x, c0, t.z, c2);
-        sort2(t.y, c1, t.w, c3);
-        sort2(t.y, c1, t.z, c2);
+        if (ORDER == 0) {
+            // ascending (t, ref): sorting network (0,1) (2,3) (0,2) (1,3) (1,2)
+            sort2(t.x, c0, t.y, c1);
+            sort2(t.z, c2, t.w, c3);
+            sort2(t.x, c0, t.z, c2);
+            sort2(t.y, c1, t.w, c3);
+            sort2(t.y, c1, t.z, c2);
+        } else {
+            // nearest first, the rest in slot order: (0,1) (2,3) (0,2)
+            sort2(t.x, c0, t.y, c1);
+            sort2(t.z, c2, t.w, c3);
+            sort2(t.x, c0, t.z, c2);
+        }
         if (t.x < INFINITY) {
             if (t.w < INFINITY) {
                 if (sp >= kStackSize) return kFaultStack;
@@ -325,11 +332,13 @@ __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
     }
 }
 
-template <int WIDE, bool STATS>
+// WIDE: 4 (4-wide PLOC tree) or 2 (binary LBVH); ORDER (4-wide only): 0 pushes
+// children far-to-near after a full sort, 1 only puts the nearest first.
+template <int WIDE, bool STATS, int ORDER = 0>
 __device__ __forceinline__ unsigned traverse(const SceneDev& sc, const Ray& r, Hit& h,
                                              unsigned long long* nv, unsigned long long* bt,
                                              unsigned long long* tt) {
-    if (WIDE == 4) return traverse4<STATS>(sc, r, h, nv, bt, tt);
+    if (WIDE == 4) return traverse4<STATS, ORDER>(sc, r, h, nv, bt, tt);
     return traverse2<STATS>(sc, r, h, nv, bt, tt);
 }
 
@@ -405,8 +414,8 @@ __device__ __forceinline__ int lp_ray(const FrameDesc& f, int k, Ray& r) {
     return tc.x;
 }
 
-template <int TPB, int FETCH, int WIDE, class B>
-__global__ void __launch_bounds__(TPB)
+template <int TPB, int FETCH, int WIDE, int ORDER, int MINB, class B>
+__global__ void __launch_bounds__(TPB, MINB)
 k_render_lp(const SceneDev sc, const __grid_constant__ B b) {
     const int lane = threadIdx.x & 31;
     while (true) {
@@ -424,7 +433,7 @@ k_render_lp(const SceneDev sc, const __grid_constant__ B b) {
             const int t = lp_ray(f, (int)(w - f.work_begin), r);
             ray_setup(r);
             Hit h;
-            const unsigned fault = traverse<WIDE, false>(sc, r, h, nullptr, nullptr, nullptr);
+            const unsigned fault = traverse<WIDE, false, ORDER>(sc, r, h, nullptr, nullptr, nullptr);
             if (fault) { atomicOr(f.status, fault); h.leaf = -1; h.id = -1; }
             store_px(f.lp, t, f.lp_fmt, shade(sc, r, h));
             if (f.hit_ids) f.hit_ids[t] = h.leaf >= 0 ? h.id : -1;
@@ -433,8 +442,8 @@ k_render_lp(const SceneDev sc, const __grid_constant__ B b) {
 }
 
 // GT: work item = (tile of 8 x 4 pixels, lane); pixel centre rays.
-template <int TPB, int FETCH, int WIDE, class B>
-__global__ void __launch_bounds__(TPB)
+template <int TPB, int FETCH, int WIDE, int ORDER, int MINB, class B>
+__global__ void __launch_bounds__(TPB, MINB)
 k_render_gt(const SceneDev sc, const __grid_constant__ B b) {
     const int lane = threadIdx.x & 31;
     while (true) {
@@ -460,7 +469,7 @@ k_render_gt(const SceneDev sc, const __grid_constant__ B b) {
             world_ray(f, cx, cy, r);
             ray_setup(r);
             Hit h;
-            const unsigned fault = traverse<WIDE, false>(sc, r, h, nullptr, nullptr, nullptr);
+            const unsigned fault = traverse<WIDE, false, ORDER>(sc, r, h, nullptr, nullptr, nullptr);
             if (fault) { atomicOr(f.status, fault); h.leaf = -1; h.id = -1; }
             const long long p = (long long)y * f.W + x;
             store_px(f.disp, p, f.disp_fmt, shade(sc, r, h));
@@ -495,9 +504,10 @@ k_render_stats(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned
     atomicMax(out + 5, worst);
 }
 
-template <int TPB, int FETCH, int WIDE, bool GT, class B>
+template <int TPB, int FETCH, int WIDE, int ORDER, int MINB, bool GT, class B>
 cudaError_t launch_one(const SceneDev& sc, const B& b, cudaStream_t s, int num_sms) {
-    auto kern = GT ? k_render_gt<TPB, FETCH, WIDE, B> : k_render_lp<TPB, FETCH, WIDE, B>;
+    auto kern = GT ? k_render_gt<TPB, FETCH, WIDE, ORDER, MINB, B>
+                   : k_render_lp<TPB, FETCH, WIDE, ORDER, MINB, B>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB, 0);
     if (e != cudaSuccess) return e;
@@ -516,11 +526,14 @@ cudaError_t launch_one(const SceneDev& sc, const B& b, cudaStream_t s, int num_s
 template <bool GT, class B>
 cudaError_t launch_variant(const SceneDev& sc, const B& b, int variant, cudaStream_t s, int sms) {
     if (b.total_work <= 0) return cudaSuccess;
+    // (threads per block, rays per warp fetch, tree width, child order, min blocks/SM)
     switch (variant) {
-        case 0: return launch_one<128, 32, 4, GT>(sc, b, s, sms);
-        case 1: return launch_one<256, 32, 4, GT>(sc, b, s, sms);
-        case 2: return launch_one<128, 64, 4, GT>(sc, b, s, sms);
-        default: return launch_one<128, 32, 2, GT>(sc, b, s, sms);
+        case 0: return launch_one<128, 32, 4, 1, 1, GT>(sc, b, s, sms);
+        case 1: return launch_one<256, 32, 4, 0, 1, GT>(sc, b, s, sms);
+        case 2: return launch_one<128, 32, 4, 0, 1, GT>(sc, b, s, sms);
+        case 3: return launch_one<128, 32, 2, 0, 1, GT>(sc, b, s, sms);
+        case 4: return launch_one<128, 32, 4, 0, 10, GT>(sc, b, s, sms);
+        default: return launch_one<128, 32, 4, 1, 10, GT>(sc, b, s, sms);
     }
 }
 

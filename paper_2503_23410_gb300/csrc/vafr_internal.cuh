@@ -93,8 +93,8 @@ using BigBatch = Batch<VAFR_MAX_BATCH>;
 static_assert(sizeof(BigBatch) + sizeof(SceneDev) <= 32764, "batch too large for kernel params");
 
 // ---- launch interfaces ---------------------------------------------------------
-// Render variants: (threads per block, rays per warp fetch).
-constexpr int kNumRenderVariants = 4;
+// Render variants: threads per block, tree width, child order, register cap.
+constexpr int kNumRenderVariants = 6;
 // Reconstruct variants: tile shapes.
 constexpr int kNumReconVariants = 4;
 
