@@ -305,20 +305,48 @@ def run_gpu(args, w):
         per, wall, launches = timed(frame, args.steps, 3)
         gt_steps = max(3, min(args.steps, args.gt_steps))
         gper, gwall, _ = timed(gt_frame, gt_steps, 2)
-        # end to end through the C ABI with HOST buffers: render_frame copies the
-        # display to pinned host memory every step (and synchronises)
-        host = torch.empty(eyes * dp_b, dtype=torch.uint8, pin_memory=True)
+        # end to end through the C ABI with HOST buffers, two ways:
+        #  (a) vafr_render_frame into pinned host memory, one synchronous call
+        #      per frame;
+        #  (b) a 2-deep pipeline through the batch API: frame k renders on
+        #      stream k % 2 into pinned host buffer k % 2 (the reconstruction
+        #      writes the host memory directly), and a frame's buffer is
+        #      reused only after its stream has finished, so frame k + 1
+        #      computes while frame k crosses the CPU-GPU link.
         e2e_steps = max(3, min(args.steps, args.e2e_steps))
+        host = [torch.empty(eyes * dp_b, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
         for k in range(2):
-            V.vafr_render_frame(scene, sess, host)
+            V.vafr_render_frame(scene, sess, host[0])
         torch.cuda.synchronize()
         te = time.perf_counter()
         for k in range(e2e_steps):
             g = d.gaze[k % nf]
             for e in range(eyes):
                 V.vafr_set_gaze(sess, e, g[e, 0], g[e, 1])
-            V.vafr_render_frame(scene, sess, host)
+            V.vafr_render_frame(scene, sess, host[0])
+        e2e_sync_s = time.perf_counter() - te
+        lps = [torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda") for _ in range(2)]
+        streams = [torch.cuda.Stream() for _ in range(2)]
+        batches = [V.vafr_batch_create(scene, 2 * eyes) for _ in range(2)]
+
+        def frames_for(slot):
+            return [(sess, e, lps[slot][e * lp_b:], host[slot][e * dp_b:]) for e in range(eyes)]
+        for k in range(4):
+            V.vafr_batch_render(batches[k % 2], frames_for(k % 2), stream=streams[k % 2])
+        torch.cuda.synchronize()
+        te = time.perf_counter()
+        for k in range(e2e_steps):
+            slot = k % 2
+            streams[slot].synchronize()          # frame k - 2 has landed in host[slot]
+            g = d.gaze[k % nf]
+            for e in range(eyes):
+                V.vafr_set_gaze(sess, e, g[e, 0], g[e, 1])
+            V.vafr_batch_render(batches[slot], frames_for(slot), stream=streams[slot])
+        for st_ in streams:
+            st_.synchronize()
         e2e_s = time.perf_counter() - te
+        for bt in batches:
+            V.vafr_batch_destroy(bt)
     assert V.vafr_session_check(sess) == 0
 
     step_ms = per.sum(1)
@@ -326,10 +354,12 @@ def run_gpu(args, w):
     gt_ms = gper[:, 0]
     total_s = step_ms.sum() / 1e3
     from paper_2503_23410_gb300.dist import max_over_ranks
-    total_s, e2e_s, gt_mean = max_over_ranks([total_s, e2e_s, float(gt_ms.mean())], "cuda")
+    total_s, e2e_s, e2e_sync_s, gt_mean = max_over_ranks(
+        [total_s, e2e_s, e2e_sync_s, float(gt_ms.mean())], "cuda")
     mpix_frame = W_ * H_ * eyes / 1e6
     value = mpix_frame * args.steps * ws / total_s
     e2e_value = mpix_frame * e2e_steps * ws / e2e_s
+    e2e_sync_value = mpix_frame * e2e_steps * ws / e2e_sync_s
 
     # roofline of the dominant kernel
     stats = V.vafr_traversal_stats(scene, sess, 0)
@@ -384,7 +414,11 @@ def run_gpu(args, w):
         "roofline_other": roof_recon if dominant is roof_render else roof_render,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * eyes,
                 "d2h_bytes_per_step": dp_b * eyes, "steps": e2e_steps,
-                "path": "vafr_render_frame into pinned host memory (C ABI, synchronous)"},
+                "path": "vafr_batch_render into pinned host frames, 2 frames in flight on 2 "
+                        "streams (C ABI); gaze passed by value each step",
+                "sync_per_frame_value": e2e_sync_value,
+                "sync_per_frame_path": "vafr_render_frame into pinned host memory, one "
+                                       "synchronous call per frame"},
         "gpu_launches": int(launches),
         "wall_s_timed_loop": wall,
         "clocks": clk.summary(),
