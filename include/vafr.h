@@ -155,9 +155,14 @@ VAFR_API int vafr_scene_check(const vafr_scene* scene, void* stream);
 VAFR_API int vafr_session_create(const vafr_session_desc* desc, vafr_session** out);
 VAFR_API int vafr_session_destroy(vafr_session* session);
 /* Copies the LP layout to HOST buffers (any may be NULL): n_cols, n_texels
- * (per eye), col_counts[n_cols], col_offsets[n_cols] (first texel of each
- * column; texels are stored column after column), col_ecc_deg[n_cols]
- * (FP32 eccentricity of each column centre).  Errors: INVALID_ARG. */
+ * (texels = rays per eye), col_counts[n_cols], col_offsets[n_cols],
+ * col_ecc_deg[n_cols] (FP32 eccentricity of each column centre).
+ * LP buffer layout: columns are stored one after another, texel (c, j) in
+ * slot col_offsets[c] + j; each column is framed by two guard slots,
+ * col_offsets[c] - 1 holding a copy of texel (c, n_c - 1) and
+ * col_offsets[c] + n_c a copy of texel (c, 0) (the angular wrap), so one
+ * eye's buffer holds n_texels + 2 n_cols slots (vafr_session_sizes).
+ * Errors: INVALID_ARG. */
 VAFR_API int vafr_lp_layout(const vafr_session* session, int32_t* n_cols, int64_t* n_texels,
                    int32_t* col_counts, int64_t* col_offsets, float* col_ecc_deg);
 /* Bytes of one eye's LP buffer and of one eye's display in the session's formats. */
@@ -184,10 +189,11 @@ VAFR_API int vafr_session_check(vafr_session* session, void* stream);
  * finds the closest hit (two-sided watertight test, closest t > 0, equal t ->
  * lower triangle id) and shades it (Lambert, ambient 0.1; sky gradient on a
  * miss) -- the ray-generation / closest-hit / miss shaders of Sec. 6.1.
- *   lp_out      device, [popcount(eye_mask)][n_texels] pixels of lp_format,
- *               eyes in increasing order, texel (c, j) at col_offsets[c] + j.
- *   hit_ids_out device or NULL, [popcount(eye_mask)][n_texels] int32 triangle
- *               id of the hit, -1 on a miss.
+ *   lp_out      device, [popcount(eye_mask)][slots] pixels of lp_format,
+ *               eyes in increasing order, in the layout of vafr_lp_layout
+ *               (guard slots included; slots = lp_bytes_per_eye / pixel size).
+ *   hit_ids_out device or NULL, [popcount(eye_mask)][slots] int32 triangle
+ *               id of the hit, -1 on a miss, same layout.
  * Errors: INVALID_ARG (NULL lp_out, eye_mask not a subset of the session's
  * eyes or empty, gaze never set), CUDA. */
 VAFR_API int vafr_render_lp(const vafr_scene* scene, vafr_session* session, int32_t eye_mask,
@@ -198,7 +204,8 @@ VAFR_API int vafr_render_lp(const vafr_scene* scene, vafr_session* session, int3
  * atan2(y - y0, x - x0) in [0, 360); the colour is the bilinear blend of
  * columns floor(u - 0.5), +1 (clamped) and, in each, of rows
  * floor(angle n_c/360 - 0.5), +1 wrapped modulo n_c.  FP32 arithmetic.
- *   lp       device, one eye's LP buffer (n_texels pixels of lp_format).
+ *   lp       device, one eye's LP buffer (vafr_lp_layout, guard slots filled
+ *            as vafr_render_lp writes them).
  *   display  device, height x width pixels of display_format, row-major.
  * Errors: INVALID_ARG, CUDA. */
 VAFR_API int vafr_reconstruct(vafr_session* session, int32_t eye, const void* lp, void* display_out,

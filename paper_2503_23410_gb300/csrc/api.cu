@@ -103,7 +103,8 @@ struct vafr_session {
     vafr_session_desc desc{};
     std::shared_ptr<const LayoutTables> lay;   // shared by sessions with the same acuity
     int n_cols = 0;
-    int64_t n_texels = 0;
+    int64_t n_texels = 0;   // rays per eye
+    int64_t n_slots = 0;    // LP buffer texels per eye (texels + 2 guard slots per column)
     unsigned* d_status = nullptr;
     unsigned long long* d_counter = nullptr;
     unsigned long long* d_stats = nullptr;
@@ -400,6 +401,7 @@ int vafr_session_create(const vafr_session_desc* desc, vafr_session** out) {
     s->lay = lay;
     s->n_cols = lay->n_cols;
     s->n_texels = lay->n_texels;
+    s->n_slots = lay->n_slots;
     auto bail = [&](cudaError_t e) {
         delete s;
         return fail(e == cudaErrorMemoryAllocation ? VAFR_ERR_OOM : VAFR_ERR_CUDA, "session: %s",
@@ -438,7 +440,7 @@ int vafr_lp_layout(const vafr_session* s, int32_t* n_cols, int64_t* n_texels, in
 
 int vafr_session_sizes(const vafr_session* s, int64_t* lp_bytes, int64_t* disp_bytes) {
     if (!s) return fail(VAFR_ERR_INVALID_ARG, "session is NULL");
-    if (lp_bytes) *lp_bytes = s->n_texels * bytes_per_px(s->desc.lp_format);
+    if (lp_bytes) *lp_bytes = s->n_slots * bytes_per_px(s->desc.lp_format);
     if (disp_bytes) *disp_bytes = (int64_t)s->desc.width * s->desc.height * bytes_per_px(s->desc.display_format);
     return VAFR_OK;
 }
@@ -491,8 +493,8 @@ int vafr_render_lp(const vafr_scene* scene, vafr_session* s, int32_t eye_mask, v
         if (!(eye_mask & (1 << eye))) continue;
         if (!s->gaze_set[eye]) return fail(VAFR_ERR_INVALID_ARG, "gaze of eye %d never set", eye);
         FrameDesc f = s->fd[eye];
-        f.lp = static_cast<char*>(lp_out) + (size_t)b.n * s->n_texels * bpp;
-        f.hit_ids = hit_ids_out ? hit_ids_out + (size_t)b.n * s->n_texels : nullptr;
+        f.lp = static_cast<char*>(lp_out) + (size_t)b.n * s->n_slots * bpp;
+        f.hit_ids = hit_ids_out ? hit_ids_out + (size_t)b.n * s->n_slots : nullptr;
         f.work_begin = b.total_work;
         b.total_work += s->n_texels;
         b.d[b.n++] = f;

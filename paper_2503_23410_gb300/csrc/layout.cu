@@ -128,7 +128,9 @@ uint32_t spread16(uint32_t x) {
 // acuity model only, never on the display size or the gaze.
 void build_work_order(const LayoutTables& L, std::vector<int2>& work) {
     const double X = std::tan(L.map.e_max * M_PI / 180.0) * 1.0001;
-    std::vector<std::pair<uint32_t, int32_t>> key(L.n_texels);
+    // (Morton key, slot, column); the slot breaks ties, so the order is a function
+    std::vector<std::pair<uint32_t, int2>> key;
+    key.reserve(L.n_texels);
     for (int c = 0; c < L.n_cols; ++c) {
         const double te = std::tan(L.e_col[c] * M_PI / 180.0);
         for (int32_t j = 0; j < L.n_col[c]; ++j) {
@@ -136,16 +138,14 @@ void build_work_order(const LayoutTables& L, std::vector<int2>& work) {
             const double x = te * std::cos(ph), y = te * std::sin(ph);
             const uint32_t qx = (uint32_t)std::min(65535.0, std::max(0.0, (x + X) / (2 * X) * 65535.0));
             const uint32_t qy = (uint32_t)std::min(65535.0, std::max(0.0, (y + X) / (2 * X) * 65535.0));
-            const int64_t t = L.off_col[c] + j;
-            key[t] = {(spread16(qx) << 1) | spread16(qy), (int32_t)t};
+            key.push_back({(spread16(qx) << 1) | spread16(qy), make_int2((int)(L.off_col[c] + j), c)});
         }
     }
-    std::sort(key.begin(), key.end());
-    std::vector<int32_t> col_of(L.n_texels);
-    for (int c = 0; c < L.n_cols; ++c)
-        for (int32_t j = 0; j < L.n_col[c]; ++j) col_of[L.off_col[c] + j] = c;
+    std::sort(key.begin(), key.end(), [](const std::pair<uint32_t, int2>& a, const std::pair<uint32_t, int2>& b) {
+        return a.first != b.first ? a.first < b.first : a.second.x < b.second.x;
+    });
     work.resize(L.n_texels);
-    for (int64_t w = 0; w < L.n_texels; ++w) work[w] = make_int2(key[w].second, col_of[key[w].second]);
+    for (int64_t w = 0; w < L.n_texels; ++w) work[w] = key[w].second;
 }
 
 int build(const vafr_acuity& acuity, LayoutTables& L, std::string* err) {
@@ -153,23 +153,29 @@ int build(const vafr_acuity& acuity, LayoutTables& L, std::string* err) {
         *err = "bad acuity pivots (need E_0 = 0, increasing pivots, f > 0, 0 < e_max < 90, MAR > 0)";
         return VAFR_ERR_INVALID_ARG;
     }
+    // Column c occupies slots [off_c - 1, off_c + n_c]: its n_c texels plus a
+    // guard slot on each side holding a copy of the texel across the angular
+    // wrap (texel n_c - 1 before, texel 0 after), so a bilinear row pair is
+    // always two adjacent slots.
     const double u_max = L.map.u_of_e(L.map.e_max);
-    int64_t acc = 0;
+    int64_t acc = 0, slots = 0;
     for (int c = 0; (double)c + 0.5 < u_max; ++c) {
         const double e = L.map.e_of_u((double)c + 0.5);
         int32_t nc = (int32_t)std::floor(L.map.l_of_e(e) + 0.5);
         if (nc < 1) nc = 1;
         L.e_col.push_back(e);
         L.n_col.push_back(nc);
-        L.off_col.push_back(acc);
+        L.off_col.push_back(slots + 1);
         acc += nc;
-        if (acc > (1ll << 28) || L.e_col.size() > (1u << 20)) {
+        slots += nc + 2;
+        if (slots > (1ll << 28) || L.e_col.size() > (1u << 20)) {
             *err = "LP layout too large";
             return VAFR_ERR_INVALID_ARG;
         }
     }
     L.n_cols = (int)L.e_col.size();
     L.n_texels = acc;
+    L.n_slots = slots;
     if (L.n_cols == 0) {
         *err = "empty LP layout";
         return VAFR_ERR_INVALID_ARG;

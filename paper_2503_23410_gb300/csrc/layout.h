@@ -39,16 +39,17 @@ struct LayoutTables {
     int device = 0;
     Mapping map;
     int n_cols = 0;
-    int64_t n_texels = 0;
+    int64_t n_texels = 0;           // sum of n_c: rays per eye
+    int64_t n_slots = 0;            // LP buffer length: sum of (n_c + 2)
     std::vector<double> e_col;      // eccentricity of column centres u = c + 0.5
     std::vector<int32_t> n_col;     // texels per column
-    std::vector<int64_t> off_col;   // first texel of each column
+    std::vector<int64_t> off_col;   // slot of texel (c, 0); slots off - 1 and off + n_c are guards
     float* d_tan_e = nullptr;       // [C]
-    int2* d_col = nullptr;          // [C] (first texel, count)
-    int4* d_col_pair = nullptr;     // [C] (first, count) of c and min(c + 1, C - 1)
+    int2* d_col = nullptr;          // [C] (slot of texel 0, count)
+    int4* d_col_pair = nullptr;     // [C] (slot of texel 0, count) of c and min(c + 1, C - 1)
     float4* d_u_tab = nullptr;      // cubic pieces of u(z), z = tan(e)
     double u_inv_h = 0.0;
-    int2* d_work = nullptr;         // [n_texels] (texel, column) in screen-space Morton order
+    int2* d_work = nullptr;         // [n_texels] (slot, column) in screen-space Morton order
     ~LayoutTables();
 };
 

@@ -13,7 +13,8 @@
 //       Lawson's reweighted least squares, csrc/fit_atan.py; |err| < 3e-8);
 //   columns c0 = floor(u - 0.5), c1 = c0 + 1 clamped to [0, C-1] (one 16-byte
 //   load of the column-pair table); in each column rows floor(frac n_c - 0.5)
-//   and +1 wrapped modulo n_c; bilinear blend in FP32.
+//   and +1 wrapped modulo n_c -- two adjacent slots thanks to the column's
+//   guard slots; bilinear blend in FP32.
 // One block per display tile; a thread computes `PX` horizontally adjacent
 // pixels and writes them with 16-byte streaming stores.  The LP buffer (8-17 MB
 // per eye) and the tables stay cache-resident; display writes go to HBM.
@@ -41,29 +42,47 @@ __device__ __forceinline__ px2 load_lp(const void* lp, int fmt, int idx) {
     return r;
 }
 
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// b - a, one rounding (the FMA's product a * -1 is exact)
+__device__ __forceinline__ float2 sub2(float2 b, float2 a) { return __ffma2_rn(a, f2(-1.0f, -1.0f), b); }
+
 // a + w (b - a): exact when a == b (a constant LP reconstructs exactly).
 __device__ __forceinline__ px2 lerp2(px2 a, px2 b, float w) {
-    const float2 w2 = make_float2(w, w);
+    const float2 w2 = f2(w, w);
     px2 r;
-    r.rg = __ffma2_rn(w2, __fadd2_rn(b.rg, make_float2(-a.rg.x, -a.rg.y)), a.rg);
-    r.ba = __ffma2_rn(w2, __fadd2_rn(b.ba, make_float2(-a.ba.x, -a.ba.y)), a.ba);
+    r.rg = __ffma2_rn(w2, sub2(b.rg, a.rg), a.rg);
+    r.ba = __ffma2_rn(w2, sub2(b.ba, a.ba), a.ba);
     return r;
 }
 
-// atan2(dy, dx) / 2pi wrapped to [0, 1); (0, 0) -> 0.
+// Hardware reciprocal approximation (PTX rcp.approx, flush-to-zero); the
+// argument is kept >= 1e-30, so it is a normal number.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Odd polynomial for atan(t) / 2pi on [0, 1]: coefficients of t^15 ... t^1
+// (near-minimax fit by Lawson's reweighted least squares, csrc/fit_atan.py).
+#define VAFR_ATAN_COEFS                                                      \
+    -0.0006453031091950834f, 0.0034795934334397316f, -0.008898717351257801f, \
+        0.01534602977335453f, -0.022136269137263298f, 0.031745944172143936f, \
+        -0.05304612219333649f, 0.15915483236312866f
+
+// atan2(dy, dx) / 2pi wrapped to [0, 1); (0, 0) -> 0.  Octant reduction
+// t = min(|dx|, |dy|) / max(|dx|, |dy|), then the polynomial, then the octant
+// is undone as 0.25 - a, 0.5 - a, 1 - a.
 __device__ __forceinline__ float angle_fraction(float dy, float dx) {
+    constexpr float c[8] = {VAFR_ATAN_COEFS};
     const float ax = fabsf(dx), ay = fabsf(dy);
-    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-    const float t = mx > 0.0f ? __fdividef(mn, mx) : 0.0f;
+    const float mx = fmaxf(fmaxf(ax, ay), 1e-30f), mn = fminf(ax, ay);
+    const float t = mn * rcp_approx(mx);
     const float s = t * t;
-    float p = -0.0006453031091950834f;
-    p = fmaf(p, s, 0.0034795934334397316f);
-    p = fmaf(p, s, -0.008898717351257801f);
-    p = fmaf(p, s, 0.01534602977335453f);
-    p = fmaf(p, s, -0.022136269137263298f);
-    p = fmaf(p, s, 0.031745944172143936f);
-    p = fmaf(p, s, -0.05304612219333649f);
-    p = fmaf(p, s, 0.15915483236312866f);
+    float p = c[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) p = fmaf(p, s, c[k]);
     float a = p * t;                       // first-octant fraction in [0, 1/8]
     a = ay > ax ? 0.25f - a : a;           // first quadrant
     a = dx < 0.0f ? 0.5f - a : a;          // upper half plane
@@ -71,15 +90,22 @@ __device__ __forceinline__ float angle_fraction(float dy, float dx) {
     return a;
 }
 
-__device__ __forceinline__ px2 column_sample(const void* lp, int fmt, int off, int n, float frac) {
+// Row pair of column (off, n) that brackets the angle fraction: v = frac n_c
+// - 1/2, rows floor(v) in [-1, n_c - 1] and floor(v) + 1.  The column's guard
+// slots (off - 1 holds row n_c - 1, off + n_c holds row 0) make the pair the
+// two adjacent slots i0, i0 + 1 for every v; w is the weight of i0 + 1.
+__device__ __forceinline__ void column_index(int off, int n, float frac, int& i0, float& w) {
     const float v = fmaf(frac, (float)n, -0.5f);
     const float j0f = floorf(v);
-    const float wv = v - j0f;
-    int j0 = (int)j0f;
-    int j1 = j0 + 1;
-    j0 = j0 < 0 ? j0 + n : j0;
-    j1 = j1 >= n ? j1 - n : j1;
-    return lerp2(load_lp(lp, fmt, off + j0), load_lp(lp, fmt, off + j1), wv);
+    w = v - j0f;
+    i0 = off + (int)j0f;
+}
+
+__device__ __forceinline__ px2 column_sample(const void* lp, int fmt, int off, int n, float frac) {
+    int i0;
+    float w;
+    column_index(off, n, frac, i0, w);
+    return lerp2(load_lp(lp, fmt, i0), load_lp(lp, fmt, i0 + 1), w);
 }
 
 // Frame parameters, staged through shared memory by one thread and then held
@@ -102,6 +128,34 @@ struct ReconShared {
     int W, H, disp_fmt, tile_begin;
     void* disp;
 };
+
+// Thread 0 of a block finds the frame that owns display tile `tile` (binary
+// search over the frames' first tiles) and stages its parameters.
+template <class B>
+__device__ __forceinline__ void stage_frame(const B& b, int tile, ReconShared& sh) {
+    int lo = 0, hi = b.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.d[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+    }
+    const FrameDesc& fd = b.d[lo];
+    sh.r.zs = fd.cr * fd.u_inv_h;
+    sh.r.u_nf = (float)fd.u_n;
+    sh.r.cmax = (float)(fd.n_cols - 1);
+    sh.r.u_tab = fd.u_tab;
+    sh.r.col_pair = fd.col_pair;
+    sh.r.lp = fd.lp;
+    sh.r.lp_fmt = fd.lp_fmt;
+    sh.gxi = fd.gxi;
+    sh.gyi = fd.gyi;
+    sh.gxf = fd.gxf;
+    sh.gyf = fd.gyf;
+    sh.W = fd.W;
+    sh.H = fd.H;
+    sh.disp_fmt = fd.disp_fmt;
+    sh.tile_begin = (int)fd.tile_begin;
+    sh.disp = fd.disp;
+}
 
 // One pixel of a row: dx is its gaze offset, dy2 the row's squared offset.
 __device__ __forceinline__ px2 recon_pixel(const ReconRegs& f, float dx, float dy, float dy2) {
@@ -138,30 +192,7 @@ k_reconstruct(const __grid_constant__ B b) {
     static_assert(PX % 2 == 0, "pixels per thread must be even");
     __shared__ ReconShared sh;
     const int tile = (int)blockIdx.x;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = b.n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (b.d[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
-        }
-        const FrameDesc& fd = b.d[lo];
-        sh.r.zs = fd.cr * fd.u_inv_h;
-        sh.r.u_nf = (float)fd.u_n;
-        sh.r.cmax = (float)(fd.n_cols - 1);
-        sh.r.u_tab = fd.u_tab;
-        sh.r.col_pair = fd.col_pair;
-        sh.r.lp = fd.lp;
-        sh.r.lp_fmt = fd.lp_fmt;
-        sh.gxi = fd.gxi;
-        sh.gyi = fd.gyi;
-        sh.gxf = fd.gxf;
-        sh.gyf = fd.gyf;
-        sh.W = fd.W;
-        sh.H = fd.H;
-        sh.disp_fmt = fd.disp_fmt;
-        sh.tile_begin = (int)fd.tile_begin;
-        sh.disp = fd.disp;
-    }
+    if (threadIdx.x == 0) stage_frame(b, tile, sh);
     __syncthreads();
     const ReconRegs f = sh.r;
     const int W = sh.W, H = sh.H;
@@ -215,6 +246,142 @@ k_reconstruct(const __grid_constant__ B b) {
     }
 }
 
+// ---- column runs ---------------------------------------------------------------
+// A thread owns one display column x and R consecutive rows; the 32 lanes of a
+// warp take 32 consecutive x, so every row store of a warp is contiguous.  Down
+// the run the thread keeps the last u-table piece, column pair and the two LP
+// row pairs in registers and reloads each only when its index changes: away
+// from the gaze several display pixels fall into one LP cell (about 2.5 on
+// average at 4K, 100 degrees), so most of the per-pixel loads of the row
+// kernel disappear.  The arithmetic per pixel is the row kernel's, operation
+// for operation, so both produce identical bits.
+template <int LPF>
+__device__ __forceinline__ px2 load_lp_t(const void* lp, int idx) {
+    return load_lp(lp, LPF, idx);
+}
+
+template <int DF>
+__device__ __forceinline__ void store_px(void* disp, long long idx, px2 v) {
+    if (DF == VAFR_FMT_RGBA16F)
+        __stcs(reinterpret_cast<uint2*>(disp) + idx, make_uint2(pack_half2(v.rg), pack_half2(v.ba)));
+    else
+        __stcs(reinterpret_cast<float4*>(disp) + idx, make_float4(v.rg.x, v.rg.y, v.ba.x, v.ba.y));
+}
+
+// Predicated loads: when `p` is false nothing is read and `v` keeps its value,
+// without a branch (the index bookkeeping of a run is branch-free); FP16 LP
+// texels, which need widening after the load, take a branch instead.
+__device__ __forceinline__ void ld_if(bool p, const float4* ptr, float4& v) {
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+        "@q ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%5];\n\t}"
+        : "+f"(v.x), "+f"(v.y), "+f"(v.z), "+f"(v.w)
+        : "r"((int)p), "l"(ptr));
+}
+
+__device__ __forceinline__ void ld_if(bool p, const int4* ptr, int4& v) {
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+        "@q ld.global.nc.v4.b32 {%0, %1, %2, %3}, [%5];\n\t}"
+        : "+r"(v.x), "+r"(v.y), "+r"(v.z), "+r"(v.w)
+        : "r"((int)p), "l"(ptr));
+}
+
+// LP texel `idx` into `v` if `p`: FP32 RGBA, or FP16 RGBA widened exactly.
+template <int LPF>
+__device__ __forceinline__ void ld_texel_if(bool p, const void* lp, int idx, px2& v) {
+    if (LPF == VAFR_FMT_RGBA16F) {
+        // a branch: predicated-off widening instructions would still issue
+        if (p) v = load_lp(lp, LPF, idx);
+    } else {
+        asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+            "@q ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%5];\n\t}"
+            : "+f"(v.rg.x), "+f"(v.rg.y), "+f"(v.ba.x), "+f"(v.ba.y)
+            : "r"((int)p), "l"(reinterpret_cast<const float4*>(lp) + idx));
+    }
+}
+
+template <int R, int LPF, int DF>
+__device__ __forceinline__ void recon_run(const ReconRegs& f, void* disp, long long W, int x, int y0,
+                                          int nrows, float dx, int gyi, float gyf) {
+    int piece = -1, c0_held = -1, k0 = -1, k1 = -1;
+    float4 cf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    int4 cp = make_int4(0, 1, 0, 1);
+    px2 a0{}, b0{}, a1{}, b1{};
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        if (k >= nrows) break;
+        const int y = y0 + k;
+        const float dy = (float)(y - gyi) + gyf;
+        const float dy2 = dy * dy;
+        const float r2 = fmaf(dx, dx, dy2);
+        const float s = fminf(f.zs * (r2 * rsqrtf(r2 + 1e-30f)), f.u_nf);
+        const int i = (int)s;
+        const float t = s - (float)i;
+        ld_if(i != piece, f.u_tab + i, cf);
+        piece = i;
+        const float uf = fminf(fmaxf(fmaf(fmaf(fmaf(cf.w, t, cf.z), t, cf.y), t, cf.x), 0.0f), f.cmax);
+        const int c0 = (int)uf;
+        const float wu = uf - (float)c0;
+        ld_if(c0 != c0_held, f.col_pair + c0, cp);
+        c0_held = c0;
+        const float frac = angle_fraction(dy, dx);
+        int i0, i2;
+        float w0, w1;
+        column_index(cp.x, cp.y, frac, i0, w0);
+        column_index(cp.z, cp.w, frac, i2, w1);
+        const bool l0 = i0 != k0, l1 = i2 != k1;
+        ld_texel_if<LPF>(l0, f.lp, i0, a0);
+        ld_texel_if<LPF>(l0, f.lp, i0 + 1, b0);
+        ld_texel_if<LPF>(l1, f.lp, i2, a1);
+        ld_texel_if<LPF>(l1, f.lp, i2 + 1, b1);
+        k0 = i0;
+        k1 = i2;
+        store_px<DF>(disp, (long long)y * W + x, lerp2(lerp2(a0, b0, w0), lerp2(a1, b1, w1), wu));
+    }
+}
+
+// Tile of TW x R pixels, TW threads.  The LP and display formats are uniform
+// over a block, so the format branch is taken once per block.
+template <int TW, int R, int MINB, class B>
+__global__ void __launch_bounds__(TW, MINB)
+k_reconstruct_runs(const __grid_constant__ B b) {
+    __shared__ ReconShared sh;
+    const int tile = (int)blockIdx.x;
+    if (threadIdx.x == 0) stage_frame(b, tile, sh);
+    __syncthreads();
+    const ReconRegs f = sh.r;
+    const int W = sh.W, H = sh.H;
+    const int local = tile - sh.tile_begin;
+    const int tiles_x = (W + TW - 1) / TW;
+    const int ty = local / tiles_x;
+    const int x = (local - ty * tiles_x) * TW + (int)threadIdx.x;
+    const int y0 = ty * R;
+    if (x >= W) return;
+    const int nrows = min(R, H - y0);
+    const float dx = (float)(x - sh.gxi) + sh.gxf;
+    const int gyi = sh.gyi;
+    const float gyf = sh.gyf;
+    void* const disp = sh.disp;
+    if (f.lp_fmt == VAFR_FMT_RGBA16F) {
+        if (sh.disp_fmt == VAFR_FMT_RGBA16F)
+            recon_run<R, VAFR_FMT_RGBA16F, VAFR_FMT_RGBA16F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
+        else
+            recon_run<R, VAFR_FMT_RGBA16F, VAFR_FMT_RGBA32F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
+    } else {
+        if (sh.disp_fmt == VAFR_FMT_RGBA16F)
+            recon_run<R, VAFR_FMT_RGBA32F, VAFR_FMT_RGBA16F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
+        else
+            recon_run<R, VAFR_FMT_RGBA32F, VAFR_FMT_RGBA32F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
+    }
+}
+
+template <int TW, int R, int MINB, class B>
+cudaError_t launch_runs(const B& b, cudaStream_t s) {
+    if (b.total_tiles <= 0) return cudaSuccess;
+    k_reconstruct_runs<TW, R, MINB, B><<<(unsigned)b.total_tiles, TW, 0, s>>>(b);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
 template <int TW, int TH, int PX, class B>
 cudaError_t launch_shape(const B& b, cudaStream_t s) {
     if (b.total_tiles <= 0) return cudaSuccess;
@@ -225,13 +392,18 @@ cudaError_t launch_shape(const B& b, cudaStream_t s) {
 
 }  // namespace
 
-// Tile shapes the autotuner chooses between (pixels wide, rows, pixels per
-// thread).
+// Tile shapes the autotuner chooses between: column runs (0-3; pixels wide,
+// rows per thread; 1 with a register cap for 10 blocks per SM) and row tiles
+// (4-7; pixels wide, rows, pixels per thread).
 ReconShape recon_shape(int variant) {
     switch (variant) {
-        case 0: return {256, 4, 8};
-        case 1: return {128, 8, 4};
-        case 2: return {64, 8, 2};
+        case 0: return {128, 8, 0};
+        case 1: return {64, 8, 0};
+        case 2: return {128, 4, 0};
+        case 3: return {256, 8, 0};
+        case 4: return {256, 4, 8};
+        case 5: return {128, 8, 4};
+        case 6: return {64, 8, 2};
         default: return {128, 4, 4};
     }
 }
@@ -239,9 +411,13 @@ ReconShape recon_shape(int variant) {
 template <class B>
 cudaError_t launch_reconstruct(const B& batch, int variant, cudaStream_t s) {
     switch (variant) {
-        case 0: return launch_shape<256, 4, 8>(batch, s);
-        case 1: return launch_shape<128, 8, 4>(batch, s);
-        case 2: return launch_shape<64, 8, 2>(batch, s);
+        case 0: return launch_runs<128, 8, 10>(batch, s);
+        case 1: return launch_runs<64, 8, 20>(batch, s);
+        case 2: return launch_runs<128, 4, 10>(batch, s);
+        case 3: return launch_runs<256, 8, 5>(batch, s);
+        case 4: return launch_shape<256, 4, 8>(batch, s);
+        case 5: return launch_shape<128, 8, 4>(batch, s);
+        case 6: return launch_shape<64, 8, 2>(batch, s);
         default: return launch_shape<128, 4, 4>(batch, s);
     }
 }

@@ -402,8 +402,10 @@ __device__ __forceinline__ int find_frame(const B& b, long long w, bool tiles) {
 // texels in screen-space Morton order; texel t = (c, j) sits at distance
 // r = tan(e_c)/c_r from the gaze at angle phi = (j + 0.5) 360/n_c, so its
 // camera direction is (tan(e_c) cos(phi) + gx, -tan(e_c) sin(phi) + gy, 1).
-// Returns the texel index.
-__device__ __forceinline__ int lp_ray(const FrameDesc& f, int k, Ray& r) {
+// Returns the texel's slot; `guard_lo` / `guard_hi` get the guard slots that
+// copy it (texel n_c - 1 -> slot before the column, texel 0 -> slot after),
+// or -1.
+__device__ __forceinline__ int lp_ray(const FrameDesc& f, int k, Ray& r, int& guard_lo, int& guard_hi) {
     const int2 tc = __ldg(f.work + k);
     const int2 cc = __ldg(&f.col[tc.y]);
     const int j = tc.x - cc.x;
@@ -411,7 +413,21 @@ __device__ __forceinline__ int lp_ray(const FrameDesc& f, int k, Ray& r) {
     float sp, cp;
     sincospif(__fdiv_rn((float)(2 * j + 1), (float)cc.y), &sp, &cp);
     world_ray(f, fmaf(te, cp, f.gx), fmaf(-te, sp, f.gy), r);
+    guard_lo = j == cc.y - 1 ? tc.x - cc.y : -1;
+    guard_hi = j == 0 ? tc.x + cc.y : -1;
     return tc.x;
+}
+
+// Shaded LP texel (and hit id) into its slot and the guard slots that copy it.
+__device__ __forceinline__ void store_lp(const FrameDesc& f, int t, int glo, int ghi, float4 c, int id) {
+    store_px(f.lp, t, f.lp_fmt, c);
+    if (glo >= 0) store_px(f.lp, glo, f.lp_fmt, c);
+    if (ghi >= 0) store_px(f.lp, ghi, f.lp_fmt, c);
+    if (f.hit_ids) {
+        f.hit_ids[t] = id;
+        if (glo >= 0) f.hit_ids[glo] = id;
+        if (ghi >= 0) f.hit_ids[ghi] = id;
+    }
 }
 
 template <int TPB, int FETCH, int WIDE, int ORDER, int MINB, class B>
@@ -430,13 +446,13 @@ k_render_lp(const SceneDev sc, const __grid_constant__ B b) {
             const int fi = find_frame(b, w, false);
             const FrameDesc& f = b.d[fi];
             Ray r;
-            const int t = lp_ray(f, (int)(w - f.work_begin), r);
+            int glo, ghi;
+            const int t = lp_ray(f, (int)(w - f.work_begin), r, glo, ghi);
             ray_setup(r);
             Hit h;
             const unsigned fault = traverse<WIDE, false, ORDER>(sc, r, h, nullptr, nullptr, nullptr);
             if (fault) { atomicOr(f.status, fault); h.leaf = -1; h.id = -1; }
-            store_px(f.lp, t, f.lp_fmt, shade(sc, r, h));
-            if (f.hit_ids) f.hit_ids[t] = h.leaf >= 0 ? h.id : -1;
+            store_lp(f, t, glo, ghi, shade(sc, r, h), h.leaf >= 0 ? h.id : -1);
         }
     }
 }
@@ -487,7 +503,8 @@ k_render_stats(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned
          w += (long long)gridDim.x * blockDim.x) {
         const FrameDesc& f = b.d[find_frame(b, w, false)];
         Ray r;
-        lp_ray(f, (int)(w - f.work_begin), r);
+        int glo, ghi;
+        lp_ray(f, (int)(w - f.work_begin), r, glo, ghi);
         ray_setup(r);
         Hit h;
         unsigned long long n0 = nodes;

@@ -95,10 +95,12 @@ static_assert(sizeof(BigBatch) + sizeof(SceneDev) <= 32764, "batch too large for
 // ---- launch interfaces ---------------------------------------------------------
 // Render variants: threads per block, tree width, child order, register cap.
 constexpr int kNumRenderVariants = 6;
-// Reconstruct variants: tile shapes.
-constexpr int kNumReconVariants = 4;
+// Reconstruct variants: column-run tiles (0-3) and row tiles (4-7).
+constexpr int kNumReconVariants = 8;
 
-struct ReconShape { int tw, th; int px; };   // tile width/height in pixels, pixels per thread
+// tile width/height in pixels; pixels per thread along a row (row tiles), or 0
+// for a column-run tile (one thread per display column, `th` rows)
+struct ReconShape { int tw, th; int px; };
 ReconShape recon_shape(int variant);
 
 template <class B>

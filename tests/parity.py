@@ -25,6 +25,35 @@ def device_scene(V, scene, torch):
     return h, (tris, alb)
 
 
+def lp_slots(V, sess):
+    """The library's LP layout: slot of every texel (c, j) in the oracle's
+    column order, slots per eye, counts and column offsets.  Column c is framed
+    by guard slots offs[c] - 1 (a copy of texel n_c - 1) and offs[c] + n_c (a
+    copy of texel 0)."""
+    counts, offs, _, n_tex = V.vafr_lp_layout(sess)
+    counts = counts.astype(np.int64)
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    slot = np.repeat(offs - starts, counts) + np.arange(n_tex)
+    return slot, int(offs[-1] + counts[-1] + 1), counts, offs
+
+
+def check_guards(buf, counts, offs):
+    """Guard slots equal the texels across the angular wrap."""
+    assert np.array_equal(buf[offs - 1], buf[offs + counts - 1])
+    assert np.array_equal(buf[offs + counts], buf[offs])
+
+
+def to_device_lp(lp, V, sess):
+    """Oracle-ordered LP texels -> the library's slot layout, guards filled."""
+    slot, n_slots, counts, offs = lp_slots(V, sess)
+    out = np.zeros((n_slots,) + lp.shape[1:], lp.dtype)
+    out[slot] = lp
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    out[offs - 1] = lp[starts + counts - 1]
+    out[offs + counts] = lp[starts]
+    return out
+
+
 def _plane_t(tri, o, d):
     v0, v1, v2 = tri.astype(np.float64)
     n = np.cross(v1 - v0, v2 - v0)

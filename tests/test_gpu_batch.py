@@ -67,7 +67,7 @@ def test_batch_equals_single(V, torch_mod, setup):
     h, sessions, _ = setup
     ref = _single(V, torch_mod, h, sessions)
     b = V.vafr_batch_create(h, 16)
-    for cfg in [(0, 0), (1, 2), (2, 3), (3, 1), (4, 0), (5, 1)]:
+    for cfg in [(0, 0), (1, 2), (2, 3), (3, 1), (4, 0), (5, 1), (0, 4), (1, 5), (2, 6), (3, 7)]:
         V.vafr_batch_tuning(b, cfg)
         V.vafr_batch_render(b, _frames(sessions))
         torch_mod.cuda.synchronize()

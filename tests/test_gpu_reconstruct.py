@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import device_scene
+from parity import device_scene, lp_slots, to_device_lp
 from workloads import workload
 from workloads.views import look_at_pose
 
@@ -25,7 +25,7 @@ def _recon(V, torch, W, H, fov, gaze, lp_np, lp_fmt=0, disp_fmt=0, variant=None)
     s = V.vafr_session_create(V.make_session_desc(W, H, fov, [POSE], lp_fmt, disp_fmt))
     V.vafr_set_gaze(s, 0, *gaze)
     dt = torch.float16 if lp_fmt else torch.float32
-    lp = torch.from_numpy(np.ascontiguousarray(lp_np)).to(dt).cuda()
+    lp = torch.from_numpy(np.ascontiguousarray(to_device_lp(lp_np, V, s))).to(dt).cuda()
     out = torch.empty((H, W, 4), dtype=torch.float16 if disp_fmt else torch.float32, device="cuda")
     if variant is not None:
         V.vafr_session_tuning(s, (0, variant))
@@ -78,10 +78,15 @@ def test_fp16_formats(V, torch_mod, lay):
     assert np.abs(got - ref).max() < 1e-3 + 2.0 ** -11
 
 
-def test_tile_variants_identical(V, torch_mod, lay):
+@pytest.mark.parametrize("fmts", [(0, 0), (1, 1), (1, 0), (0, 1)])
+def test_tile_variants_identical(V, torch_mod, lay, fmts):
+    """Row tiles and column-run tiles of every shape give the same bits, for
+    every LP / display format pair, on a ragged display (odd width and height)."""
     rng = np.random.default_rng(4)
     lp = rng.uniform(0, 1, (lay.total, 4)).astype(np.float32)
-    outs = [_recon(V, torch_mod, 803, 451, 100.0, (400.0, 225.0), lp, variant=v) for v in range(4)]
+    n_variants = V.vafr_tuning_space()[1]
+    outs = [_recon(V, torch_mod, 803, 451, 100.0, (400.0, 225.0), lp, lp_fmt=fmts[0],
+                   disp_fmt=fmts[1], variant=v) for v in range(n_variants)]
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
 
@@ -108,14 +113,15 @@ def test_whole_frame_random1k(V, torch_mod, lay):
     V.vafr_set_gaze(s, 0, *gaze)
     host = np.zeros((d.height, d.width, 4), np.float32)
     V.vafr_render_frame(h, s, host)                        # host output: D2H inside the call
-    lp = torch_mod.empty((lay.total, 4), device="cuda")
-    ids = torch_mod.empty(lay.total, dtype=torch_mod.int32, device="cuda")
+    slot, n_slots, _, _ = lp_slots(V, s)
+    lp = torch_mod.empty((n_slots, 4), device="cuda")
+    ids = torch_mod.empty(n_slots, dtype=torch_mod.int32, device="cuda")
     V.vafr_render_lp(h, s, 1, lp, ids)
     torch_mod.cuda.synchronize()
     rgba, oid, _, _, _ = oracle.render_lp(sc.tris, sc.albedo, sc.light_dir, lay, d.width,
                                           d.height, d.fov_v_deg, gaze, d.poses[0])
     ref = oracle.reconstruct(rgba, lay, d.width, d.height, d.fov_v_deg, gaze)
-    bad = (ids.cpu().numpy() != oid).astype(np.float64)[:, None]
+    bad = (ids.cpu().numpy()[slot] != oid).astype(np.float64)[:, None]
     touch = oracle.reconstruct(bad, lay, d.width, d.height, d.fov_v_deg, gaze)[:, 0] > 0
     got = host.reshape(-1, 4)
     assert touch.mean() < 0.01

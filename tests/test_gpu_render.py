@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import compare_hits_and_colours, device_scene
+from parity import check_guards, compare_hits_and_colours, device_scene, lp_slots
 from workloads import random_triangles_scene, tiny_scene, workload
 from workloads.views import look_at_pose
 
@@ -25,14 +25,23 @@ def _session(V, W, H, fov, poses, lp_fmt=0, disp_fmt=0, acuity=None):
 
 
 def _render_lp(V, torch, scene_h, sess, n_tex, eye_mask=1, fp16=False):
+    """LP render of the eyes in `eye_mask`; returns the texels (and hit ids) in
+    the oracle's order, eye after eye, after checking every guard slot."""
     eyes = bin(eye_mask).count("1")
+    slot, n_slots, counts, offs = lp_slots(V, sess)
+    assert len(slot) == n_tex
     dt = torch.float16 if fp16 else torch.float32
-    lp = torch.empty((eyes * n_tex, 4), dtype=dt, device="cuda")
-    ids = torch.empty(eyes * n_tex, dtype=torch.int32, device="cuda")
+    lp = torch.empty((eyes * n_slots, 4), dtype=dt, device="cuda")
+    ids = torch.empty(eyes * n_slots, dtype=torch.int32, device="cuda")
     V.vafr_render_lp(scene_h, sess, eye_mask, lp, ids)
     torch.cuda.synchronize()
     assert V.vafr_session_check(sess) == 0
-    return lp.float().cpu().numpy(), ids.cpu().numpy()
+    lp = lp.float().cpu().numpy().reshape(eyes, n_slots, 4)
+    ids = ids.cpu().numpy().reshape(eyes, n_slots)
+    for e in range(eyes):
+        check_guards(lp[e], counts, offs)
+        check_guards(ids[e], counts, offs)
+    return lp[:, slot].reshape(-1, 4), ids[:, slot].reshape(-1)
 
 
 def test_layout_matches_oracle(V, lay):
@@ -42,7 +51,10 @@ def test_layout_matches_oracle(V, lay):
         counts, offs, ecc, n_tex = V.vafr_lp_layout(s)
         assert n_tex == lay.total
         assert np.array_equal(counts, lay.n_col)
-        assert np.array_equal(offs, lay.off_col)
+        # the oracle's offsets plus a guard slot on each side of every column
+        assert np.array_equal(offs, np.asarray(lay.off_col) + 2 * np.arange(len(counts)) + 1)
+        lpb, _ = V.vafr_session_sizes(s)
+        assert lpb == 16 * (lay.total + 2 * len(counts))
         np.testing.assert_allclose(ecc, lay.e_col, rtol=1e-6)
         V.vafr_session_destroy(s)
 
