@@ -181,7 +181,7 @@ void fill_static(vafr_session* s, int eye) {
     const LayoutTables& L = *s->lay;
     f.tan_e = L.d_tan_e;
     f.col = L.d_col;
-    f.col_pair = L.d_col_pair;
+    f.col_pair = L.d_col_pair + 1;   // valid for c = -1 .. C - 1
     f.u_tab = L.d_u_tab;
     f.work = L.d_work;
     f.u_n = kUTable;

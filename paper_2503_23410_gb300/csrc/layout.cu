@@ -182,15 +182,18 @@ int build(const vafr_acuity& acuity, LayoutTables& L, std::string* err) {
     }
     std::vector<float> tan_e(L.n_cols);
     std::vector<int2> col(L.n_cols);
-    std::vector<int4> col_pair(L.n_cols);
+    // entry 0 pairs column 0 with itself (for u - 1/2 < 0), entry c + 1 pairs c
+    // with min(c + 1, C - 1); the device pointer handed to kernels is entry 1
+    std::vector<int4> col_pair(L.n_cols + 1);
     for (int c = 0; c < L.n_cols; ++c) {
         tan_e[c] = (float)std::tan(L.e_col[c] * M_PI / 180.0);
         col[c] = make_int2((int)L.off_col[c], L.n_col[c]);
     }
     for (int c = 0; c < L.n_cols; ++c) {
         const int c1 = c + 1 < L.n_cols ? c + 1 : c;
-        col_pair[c] = make_int4(col[c].x, col[c].y, col[c1].x, col[c1].y);
+        col_pair[c + 1] = make_int4(col[c].x, col[c].y, col[c1].x, col[c1].y);
     }
+    col_pair[0] = make_int4(col[0].x, col[0].y, col[0].x, col[0].y);
     std::vector<float4> u_tab;
     build_u_table(L.map, u_tab, L.u_inv_h);
     std::vector<int2> work;

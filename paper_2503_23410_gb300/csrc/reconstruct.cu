@@ -4,20 +4,24 @@
 // Per pixel centre p = (x + 0.5, y + 0.5):
 //   d = p - gaze, computed as (x - floor(x0)) + (0.5 - frac(x0)) so the FP32
 //       offset is exact near the gaze even at 16K;
-//   z = c_r |d| = tan(e) (Eq. 3; |d| = d.d rsqrt(d.d)), clamped to tan(e_max);
+//   z = c_r |d| = tan(e) (Eq. 3; |d| by the hardware square-root
+//       approximation), clamped to tan(e_max);
 //   u(e(z)) - 1/2 (Eq. 12) from a per-acuity table of cubic Hermite pieces on
 //       2,048 uniform intervals of z, built in FP64 on the host from the exact
 //       u(e) and du/dz (interpolation error < 1e-5 texel, below FP32 rounding);
 //   angle fraction = atan2(dy, dx) / 2pi in [0, 1), by octant reduction and an
 //       odd degree-15 polynomial for atan(t)/2pi on [0, 1] (near-minimax fit by
 //       Lawson's reweighted least squares, csrc/fit_atan.py; |err| < 3e-8);
-//   columns c0 = floor(u - 0.5), c1 = c0 + 1 clamped to [0, C-1] (one 16-byte
-//   load of the column-pair table); in each column rows floor(frac n_c - 0.5)
-//   and +1 wrapped modulo n_c -- two adjacent slots thanks to the column's
-//   guard slots; bilinear blend in FP32.
-// One block per display tile; a thread computes `PX` horizontally adjacent
-// pixels and writes them with 16-byte streaming stores.  The LP buffer (8-17 MB
-// per eye) and the tables stay cache-resident; display writes go to HBM.
+//   columns c0 = floor(u - 0.5) and c0 + 1 (one 16-byte load of the
+//       column-pair table, whose entries -1 and C - 1 pair a column with
+//       itself, so u below the first or past the last column centre clamps
+//       without arithmetic); in each column rows floor(frac n_c - 0.5) and +1
+//       wrapped modulo n_c -- two adjacent slots thanks to the column's guard
+//       slots; bilinear blend in FP32.
+// Two kernel families compute exactly these operations: row tiles (a thread
+// takes PX pixels of a row) and column runs (a thread takes R pixels of a
+// column and reuses table entries and LP texels between them).  The LP buffer
+// (8-17 MB per eye) and the tables stay cache-resident; display writes go to HBM.
 #include "vafr_internal.cuh"
 
 namespace vafr {
@@ -72,12 +76,13 @@ __device__ __forceinline__ float rcp_approx(float x) {
         -0.05304612219333649f, 0.15915483236312866f
 
 // atan2(dy, dx) / 2pi wrapped to [0, 1); (0, 0) -> 0.  Octant reduction
-// t = min(|dx|, |dy|) / max(|dx|, |dy|), then the polynomial, then the octant
-// is undone as 0.25 - a, 0.5 - a, 1 - a.
-__device__ __forceinline__ float angle_fraction(float dy, float dx) {
+// t = min(ax, |dy|) / max(ax, |dy|) with ax = max(|dx|, 1e-30) (a pixel offset
+// is 0 or far above 1e-30, so this only keeps the quotient finite at d = 0),
+// then the polynomial, then the octant is undone as 0.25 - a, 0.5 - a, 1 - a.
+__device__ __forceinline__ float angle_fraction(float dy, float dx, float ax) {
     constexpr float c[8] = {VAFR_ATAN_COEFS};
-    const float ax = fabsf(dx), ay = fabsf(dy);
-    const float mx = fmaxf(fmaxf(ax, ay), 1e-30f), mn = fminf(ax, ay);
+    const float ay = fabsf(dy);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
     const float t = mn * rcp_approx(mx);
     const float s = t * t;
     float p = c[0];
@@ -114,7 +119,6 @@ __device__ __forceinline__ px2 column_sample(const void* lp, int fmt, int off, i
 struct ReconRegs {
     float zs;        // c_r * u_n / tan(e_max): radius in pixels -> table coordinate
     float u_nf;      // u_n (the clamp entry)
-    float cmax;      // C - 1
     const float4* u_tab;
     const int4* col_pair;
     const void* lp;
@@ -141,7 +145,6 @@ __device__ __forceinline__ void stage_frame(const B& b, int tile, ReconShared& s
     const FrameDesc& fd = b.d[lo];
     sh.r.zs = fd.cr * fd.u_inv_h;
     sh.r.u_nf = (float)fd.u_n;
-    sh.r.cmax = (float)(fd.n_cols - 1);
     sh.r.u_tab = fd.u_tab;
     sh.r.col_pair = fd.col_pair;
     sh.r.lp = fd.lp;
@@ -157,19 +160,33 @@ __device__ __forceinline__ void stage_frame(const B& b, int tile, ReconShared& s
     sh.disp = fd.disp;
 }
 
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Table coordinate of a pixel: s = z u_n / tan(e_max) in [0, u_n]; the piece
+// is floor(s), t the position inside it.
+__device__ __forceinline__ float table_coord(const ReconRegs& f, float dx, float dy2) {
+    return fminf(f.zs * sqrt_approx(fmaf(dx, dx, dy2)), f.u_nf);
+}
+
+// u - 1/2 from the piece's cubic (Horner in FP32).
+__device__ __forceinline__ float piece_eval(float4 c, float t) {
+    return fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
+}
+
 // One pixel of a row: dx is its gaze offset, dy2 the row's squared offset.
 __device__ __forceinline__ px2 recon_pixel(const ReconRegs& f, float dx, float dy, float dy2) {
-    const float r2 = fmaf(dx, dx, dy2);
-    // c_r |d| = tan(e) scaled to the table; the 1e-30 bias keeps rsqrt finite at d = 0
-    const float s = fminf(f.zs * (r2 * rsqrtf(r2 + 1e-30f)), f.u_nf);
+    const float s = table_coord(f, dx, dy2);
     const int i = (int)s;
     const float t = s - (float)i;
-    const float4 c = __ldg(f.u_tab + i);
-    const float uf = fminf(fmaxf(fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x), 0.0f), f.cmax);  // u - 0.5
-    const float frac = angle_fraction(dy, dx);
-    const int c0 = (int)uf;
+    const float uf = piece_eval(__ldg(f.u_tab + i), t);
+    const int c0 = __float2int_rd(uf);
     const float wu = uf - (float)c0;
-    const int4 cp = __ldg(f.col_pair + c0);  // (offset, count) of c0 and of min(c0 + 1, C - 1)
+    const float frac = angle_fraction(dy, dx, fmaxf(fabsf(dx), 1e-30f));
+    const int4 cp = __ldg(f.col_pair + c0);  // (slot, count) of c0 and of c0 + 1 (clamped)
     const px2 v0 = column_sample(f.lp, f.lp_fmt, cp.x, cp.y, frac);
     const px2 v1 = column_sample(f.lp, f.lp_fmt, cp.z, cp.w, frac);
     return lerp2(v0, v1, wu);
@@ -299,31 +316,51 @@ __device__ __forceinline__ void ld_texel_if(bool p, const void* lp, int idx, px2
     }
 }
 
-template <int R, int LPF, int DF>
-__device__ __forceinline__ void recon_run(const ReconRegs& f, void* disp, long long W, int x, int y0,
-                                          int nrows, float dx, int gyi, float gyf) {
-    int piece = -1, c0_held = -1, k0 = -1, k1 = -1;
+// R rows (FULL) or the first `nrows` of them, of display column x.  The
+// column's dx is fixed, so angle_fraction's dx < 0 reflection becomes the
+// per-thread FMA a * sx + ox (0.5 - a rounded once, or a exactly).
+template <int R, bool FULL, bool REUSE_U, int LPF, int DF>
+__device__ __forceinline__ void recon_run(const ReconRegs& f, void* disp, int W, int x, int y0, int nrows,
+                                          float dx, int gyi, float gyf) {
+    constexpr float c[8] = {VAFR_ATAN_COEFS};
+    constexpr int BPP = DF == VAFR_FMT_RGBA16F ? 8 : 16;
+    int piece = -1, c0_held = -2, k0 = -1, k1 = -1;
     float4 cf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     int4 cp = make_int4(0, 1, 0, 1);
     px2 a0{}, b0{}, a1{}, b1{};
+    const float ax = fmaxf(fabsf(dx), 1e-30f);
+    const float sx = dx < 0.0f ? -1.0f : 1.0f, ox = dx < 0.0f ? 0.5f : 0.0f;
+    char* out = static_cast<char*>(disp) + ((long long)y0 * W + x) * BPP;
+    const long long row_bytes = (long long)W * BPP;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-        if (k >= nrows) break;
-        const int y = y0 + k;
-        const float dy = (float)(y - gyi) + gyf;
-        const float dy2 = dy * dy;
-        const float r2 = fmaf(dx, dx, dy2);
-        const float s = fminf(f.zs * (r2 * rsqrtf(r2 + 1e-30f)), f.u_nf);
+        if (!FULL && k >= nrows) break;
+        const float dy = (float)(y0 + k - gyi) + gyf;
+        const float s = table_coord(f, dx, dy * dy);
         const int i = (int)s;
         const float t = s - (float)i;
-        ld_if(i != piece, f.u_tab + i, cf);
-        piece = i;
-        const float uf = fminf(fmaxf(fmaf(fmaf(fmaf(cf.w, t, cf.z), t, cf.y), t, cf.x), 0.0f), f.cmax);
-        const int c0 = (int)uf;
+        if (REUSE_U) {
+            ld_if(i != piece, f.u_tab + i, cf);
+            piece = i;
+        } else {
+            cf = __ldg(f.u_tab + i);
+        }
+        const float uf = piece_eval(cf, t);
+        const int c0 = __float2int_rd(uf);
         const float wu = uf - (float)c0;
         ld_if(c0 != c0_held, f.col_pair + c0, cp);
         c0_held = c0;
-        const float frac = angle_fraction(dy, dx);
+        // angle_fraction(dy, dx, ax) with the dx reflection as one FMA
+        const float ay = fabsf(dy);
+        const float tt = fminf(ax, ay) * rcp_approx(fmaxf(ax, ay));
+        const float ss = tt * tt;
+        float p = c[0];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) p = fmaf(p, ss, c[q]);
+        float a = p * tt;
+        a = ay > ax ? 0.25f - a : a;
+        a = fmaf(a, sx, ox);
+        const float frac = dy < 0.0f ? 1.0f - a : a;
         int i0, i2;
         float w0, w1;
         column_index(cp.x, cp.y, frac, i0, w0);
@@ -335,13 +372,23 @@ __device__ __forceinline__ void recon_run(const ReconRegs& f, void* disp, long l
         ld_texel_if<LPF>(l1, f.lp, i2 + 1, b1);
         k0 = i0;
         k1 = i2;
-        store_px<DF>(disp, (long long)y * W + x, lerp2(lerp2(a0, b0, w0), lerp2(a1, b1, w1), wu));
+        store_px<DF>(out, 0, lerp2(lerp2(a0, b0, w0), lerp2(a1, b1, w1), wu));
+        out += row_bytes;
     }
+}
+
+template <int R, bool REUSE_U, int LPF, int DF>
+__device__ __forceinline__ void recon_run_any(const ReconRegs& f, void* disp, int W, int x, int y0, int nrows,
+                                              float dx, int gyi, float gyf) {
+    if (nrows == R)
+        recon_run<R, true, REUSE_U, LPF, DF>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
+    else
+        recon_run<R, false, REUSE_U, LPF, DF>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
 }
 
 // Tile of TW x R pixels, TW threads.  The LP and display formats are uniform
 // over a block, so the format branch is taken once per block.
-template <int TW, int R, int MINB, class B>
+template <int TW, int R, int MINB, bool REUSE_U, class B>
 __global__ void __launch_bounds__(TW, MINB)
 k_reconstruct_runs(const __grid_constant__ B b) {
     __shared__ ReconShared sh;
@@ -363,21 +410,21 @@ k_reconstruct_runs(const __grid_constant__ B b) {
     void* const disp = sh.disp;
     if (f.lp_fmt == VAFR_FMT_RGBA16F) {
         if (sh.disp_fmt == VAFR_FMT_RGBA16F)
-            recon_run<R, VAFR_FMT_RGBA16F, VAFR_FMT_RGBA16F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
+            recon_run_any<R, REUSE_U, VAFR_FMT_RGBA16F, VAFR_FMT_RGBA16F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
         else
-            recon_run<R, VAFR_FMT_RGBA16F, VAFR_FMT_RGBA32F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
+            recon_run_any<R, REUSE_U, VAFR_FMT_RGBA16F, VAFR_FMT_RGBA32F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
     } else {
         if (sh.disp_fmt == VAFR_FMT_RGBA16F)
-            recon_run<R, VAFR_FMT_RGBA32F, VAFR_FMT_RGBA16F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
+            recon_run_any<R, REUSE_U, VAFR_FMT_RGBA32F, VAFR_FMT_RGBA16F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
         else
-            recon_run<R, VAFR_FMT_RGBA32F, VAFR_FMT_RGBA32F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
+            recon_run_any<R, REUSE_U, VAFR_FMT_RGBA32F, VAFR_FMT_RGBA32F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
     }
 }
 
-template <int TW, int R, int MINB, class B>
+template <int TW, int R, int MINB, bool REUSE_U, class B>
 cudaError_t launch_runs(const B& b, cudaStream_t s) {
     if (b.total_tiles <= 0) return cudaSuccess;
-    k_reconstruct_runs<TW, R, MINB, B><<<(unsigned)b.total_tiles, TW, 0, s>>>(b);
+    k_reconstruct_runs<TW, R, MINB, REUSE_U, B><<<(unsigned)b.total_tiles, TW, 0, s>>>(b);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -398,9 +445,9 @@ cudaError_t launch_shape(const B& b, cudaStream_t s) {
 ReconShape recon_shape(int variant) {
     switch (variant) {
         case 0: return {128, 8, 0};
-        case 1: return {64, 8, 0};
-        case 2: return {128, 4, 0};
-        case 3: return {256, 8, 0};
+        case 1: return {128, 8, 0};
+        case 2: return {128, 8, 0};
+        case 3: return {128, 8, 0};
         case 4: return {256, 4, 8};
         case 5: return {128, 8, 4};
         case 6: return {64, 8, 2};
@@ -411,10 +458,10 @@ ReconShape recon_shape(int variant) {
 template <class B>
 cudaError_t launch_reconstruct(const B& batch, int variant, cudaStream_t s) {
     switch (variant) {
-        case 0: return launch_runs<128, 8, 10>(batch, s);
-        case 1: return launch_runs<64, 8, 20>(batch, s);
-        case 2: return launch_runs<128, 4, 10>(batch, s);
-        case 3: return launch_runs<256, 8, 5>(batch, s);
+        case 0: return launch_runs<128, 8, 10, true>(batch, s);
+        case 1: return launch_runs<128, 8, 8, true>(batch, s);
+        case 2: return launch_runs<128, 8, 10, false>(batch, s);
+        case 3: return launch_runs<128, 8, 12, false>(batch, s);
         case 4: return launch_shape<256, 4, 8>(batch, s);
         case 5: return launch_shape<128, 8, 4>(batch, s);
         case 6: return launch_shape<64, 8, 2>(batch, s);
