@@ -174,11 +174,13 @@ VAFR_API int vafr_session_sizes(const vafr_session* session, int64_t* lp_bytes_p
  * Errors: INVALID_ARG (NULL, variant out of range). */
 VAFR_API int vafr_session_tuning(vafr_session* session, int32_t set, int32_t cfg[2]);
 /* Sets the gaze point (x0, y0) in display pixels of one eye (Eq. 3).  Any
- * finite value is accepted (gaze outside the display is legal).  The FP64
+ * finite value with |x0|, |y0| <= 1e7 is accepted (gaze outside the display
+ * is legal; with displays of at most 32768 pixels a side every pixel offset
+ * from the gaze is then an exact FP32 integer plus fraction).  The FP64
  * per-frame set-up (c_r, gaze tangent offsets, the integer/fraction split of
  * the gaze used by reconstruction) is done here on the host; the next render
  * or reconstruct call on the session uses it.  Errors: INVALID_ARG (eye out
- * of range, NaN/inf). */
+ * of range, NaN/inf, |gaze| > 1e7). */
 VAFR_API int vafr_set_gaze(vafr_session* session, int32_t eye, double x0, double y0);
 /* Synchronises `stream` and reads + clears the session's device status word. */
 VAFR_API int vafr_session_check(vafr_session* session, void* stream);

@@ -113,6 +113,13 @@ void build_u_table(const Mapping& mp, std::vector<float4>& tab, double& inv_h) {
     inv_h = N / z_max;
 }
 
+int32_t float_bits(int32_t n) {
+    const float f = (float)n;
+    int32_t b;
+    std::memcpy(&b, &f, sizeof(b));
+    return b;
+}
+
 uint32_t spread16(uint32_t x) {
     x &= 0xffffu;
     x = (x | (x << 8)) & 0x00ff00ffu;
@@ -183,7 +190,8 @@ int build(const vafr_acuity& acuity, LayoutTables& L, std::string* err) {
     std::vector<float> tan_e(L.n_cols);
     std::vector<int2> col(L.n_cols);
     // entry 0 pairs column 0 with itself (for u - 1/2 < 0), entry c + 1 pairs c
-    // with min(c + 1, C - 1); the device pointer handed to kernels is entry 1
+    // with min(c + 1, C - 1); the device pointer handed to kernels is entry 1.
+    // Counts are stored as FP32 bit patterns: the filter only uses n_c as a float.
     std::vector<int4> col_pair(L.n_cols + 1);
     for (int c = 0; c < L.n_cols; ++c) {
         tan_e[c] = (float)std::tan(L.e_col[c] * M_PI / 180.0);
@@ -191,9 +199,9 @@ int build(const vafr_acuity& acuity, LayoutTables& L, std::string* err) {
     }
     for (int c = 0; c < L.n_cols; ++c) {
         const int c1 = c + 1 < L.n_cols ? c + 1 : c;
-        col_pair[c + 1] = make_int4(col[c].x, col[c].y, col[c1].x, col[c1].y);
+        col_pair[c + 1] = make_int4(col[c].x, float_bits(col[c].y), col[c1].x, float_bits(col[c1].y));
     }
-    col_pair[0] = make_int4(col[0].x, col[0].y, col[0].x, col[0].y);
+    col_pair[0] = make_int4(col[0].x, float_bits(col[0].y), col[0].x, float_bits(col[0].y));
     std::vector<float4> u_tab;
     build_u_table(L.map, u_tab, L.u_inv_h);
     std::vector<int2> work;

@@ -46,8 +46,8 @@ struct LayoutTables {
     std::vector<int64_t> off_col;   // slot of texel (c, 0); slots off - 1 and off + n_c are guards
     float* d_tan_e = nullptr;       // [C]
     int2* d_col = nullptr;          // [C] (slot of texel 0, count)
-    int4* d_col_pair = nullptr;     // [C + 1]: entry c + 1 = (slot of texel 0, count) of c and of
-                                    // min(c + 1, C - 1); entry 0 = column 0 twice
+    int4* d_col_pair = nullptr;     // [C + 1]: entry c + 1 = (slot of texel 0, FP32 bits of the
+                                    // count) of c and of min(c + 1, C - 1); entry 0 = column 0 twice
     float4* d_u_tab = nullptr;      // cubic pieces of u(z), z = tan(e)
     double u_inv_h = 0.0;
     int2* d_work = nullptr;         // [n_texels] (slot, column) in screen-space Morton order

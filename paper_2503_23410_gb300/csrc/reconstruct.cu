@@ -99,14 +99,14 @@ __device__ __forceinline__ float angle_fraction(float dy, float dx, float ax) {
 // - 1/2, rows floor(v) in [-1, n_c - 1] and floor(v) + 1.  The column's guard
 // slots (off - 1 holds row n_c - 1, off + n_c holds row 0) make the pair the
 // two adjacent slots i0, i0 + 1 for every v; w is the weight of i0 + 1.
-__device__ __forceinline__ void column_index(int off, int n, float frac, int& i0, float& w) {
-    const float v = fmaf(frac, (float)n, -0.5f);
+__device__ __forceinline__ void column_index(int off, float n, float frac, int& i0, float& w) {
+    const float v = fmaf(frac, n, -0.5f);
     const float j0f = floorf(v);
     w = v - j0f;
     i0 = off + (int)j0f;
 }
 
-__device__ __forceinline__ px2 column_sample(const void* lp, int fmt, int off, int n, float frac) {
+__device__ __forceinline__ px2 column_sample(const void* lp, int fmt, int off, float n, float frac) {
     int i0;
     float w;
     column_index(off, n, frac, i0, w);
@@ -187,8 +187,8 @@ __device__ __forceinline__ px2 recon_pixel(const ReconRegs& f, float dx, float d
     const float wu = uf - (float)c0;
     const float frac = angle_fraction(dy, dx, fmaxf(fabsf(dx), 1e-30f));
     const int4 cp = __ldg(f.col_pair + c0);  // (slot, count) of c0 and of c0 + 1 (clamped)
-    const px2 v0 = column_sample(f.lp, f.lp_fmt, cp.x, cp.y, frac);
-    const px2 v1 = column_sample(f.lp, f.lp_fmt, cp.z, cp.w, frac);
+    const px2 v0 = column_sample(f.lp, f.lp_fmt, cp.x, __int_as_float(cp.y), frac);
+    const px2 v1 = column_sample(f.lp, f.lp_fmt, cp.z, __int_as_float(cp.w), frac);
     return lerp2(v0, v1, wu);
 }
 
@@ -319,23 +319,24 @@ __device__ __forceinline__ void ld_texel_if(bool p, const void* lp, int idx, px2
 // R rows (FULL) or the first `nrows` of them, of display column x.  The
 // column's dx is fixed, so angle_fraction's dx < 0 reflection becomes the
 // per-thread FMA a * sx + ox (0.5 - a rounded once, or a exactly).
-template <int R, bool FULL, bool REUSE_U, int LPF, int DF>
+template <int R, int LH, bool FULL, bool REUSE_U, int LPF, int DF>
 __device__ __forceinline__ void recon_run(const ReconRegs& f, void* disp, int W, int x, int y0, int nrows,
                                           float dx, int gyi, float gyf) {
     constexpr float c[8] = {VAFR_ATAN_COEFS};
     constexpr int BPP = DF == VAFR_FMT_RGBA16F ? 8 : 16;
     int piece = -1, c0_held = -2, k0 = -1, k1 = -1;
     float4 cf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    int4 cp = make_int4(0, 1, 0, 1);
+    int4 cp = make_int4(0, 0x3f800000, 0, 0x3f800000);
     px2 a0{}, b0{}, a1{}, b1{};
     const float ax = fmaxf(fabsf(dx), 1e-30f);
     const float sx = dx < 0.0f ? -1.0f : 1.0f, ox = dx < 0.0f ? 0.5f : 0.0f;
+    const float dy0 = (float)(y0 - gyi);
     char* out = static_cast<char*>(disp) + ((long long)y0 * W + x) * BPP;
-    const long long row_bytes = (long long)W * BPP;
+    const long long row_bytes = (long long)W * BPP * LH;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         if (!FULL && k >= nrows) break;
-        const float dy = (float)(y0 + k - gyi) + gyf;
+        const float dy = (dy0 + (float)(LH * k)) + gyf;   // (float)(y - floor(y0)) exactly: |y - floor(y0)| < 2^24
         const float s = table_coord(f, dx, dy * dy);
         const int i = (int)s;
         const float t = s - (float)i;
@@ -363,8 +364,8 @@ __device__ __forceinline__ void recon_run(const ReconRegs& f, void* disp, int W,
         const float frac = dy < 0.0f ? 1.0f - a : a;
         int i0, i2;
         float w0, w1;
-        column_index(cp.x, cp.y, frac, i0, w0);
-        column_index(cp.z, cp.w, frac, i2, w1);
+        column_index(cp.x, __int_as_float(cp.y), frac, i0, w0);
+        column_index(cp.z, __int_as_float(cp.w), frac, i2, w1);
         const bool l0 = i0 != k0, l1 = i2 != k1;
         ld_texel_if<LPF>(l0, f.lp, i0, a0);
         ld_texel_if<LPF>(l0, f.lp, i0 + 1, b0);
@@ -377,20 +378,27 @@ __device__ __forceinline__ void recon_run(const ReconRegs& f, void* disp, int W,
     }
 }
 
-template <int R, bool REUSE_U, int LPF, int DF>
+template <int R, int LH, bool REUSE_U, int LPF, int DF>
 __device__ __forceinline__ void recon_run_any(const ReconRegs& f, void* disp, int W, int x, int y0, int nrows,
                                               float dx, int gyi, float gyf) {
     if (nrows == R)
-        recon_run<R, true, REUSE_U, LPF, DF>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
+        recon_run<R, LH, true, REUSE_U, LPF, DF>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
     else
-        recon_run<R, false, REUSE_U, LPF, DF>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
+        recon_run<R, LH, false, REUSE_U, LPF, DF>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
 }
 
-// Tile of TW x R pixels, TW threads.  The LP and display formats are uniform
-// over a block, so the format branch is taken once per block.
-template <int TW, int R, int MINB, bool REUSE_U, class B>
+// Block of TW threads (TW / 32 warps side by side).  A warp covers LW columns
+// and LH = 32 / LW interleaved runs: lane (lx, ly) owns column lx and rows
+// ly, ly + LH, ..., ly + (R - 1) LH of the warp's LW x (LH R) window, so at each
+// step the warp touches an LW x LH block of pixels (its stores are LH
+// contiguous row segments of LW pixels).  Tile: (TW / 32) LW x LH R pixels.
+// The LP and display formats are uniform over a block, so the format branch
+// is taken once per block.
+template <int TW, int R, int LW, int MINB, bool REUSE_U, class B>
 __global__ void __launch_bounds__(TW, MINB)
 k_reconstruct_runs(const __grid_constant__ B b) {
+    constexpr int LH = 32 / LW;
+    constexpr int TX = (TW / 32) * LW, TY = LH * R;
     __shared__ ReconShared sh;
     const int tile = (int)blockIdx.x;
     if (threadIdx.x == 0) stage_frame(b, tile, sh);
@@ -398,33 +406,34 @@ k_reconstruct_runs(const __grid_constant__ B b) {
     const ReconRegs f = sh.r;
     const int W = sh.W, H = sh.H;
     const int local = tile - sh.tile_begin;
-    const int tiles_x = (W + TW - 1) / TW;
+    const int tiles_x = (W + TX - 1) / TX;
     const int ty = local / tiles_x;
-    const int x = (local - ty * tiles_x) * TW + (int)threadIdx.x;
-    const int y0 = ty * R;
-    if (x >= W) return;
-    const int nrows = min(R, H - y0);
+    const int lane = (int)(threadIdx.x & 31), warp = (int)(threadIdx.x >> 5);
+    const int x = (local - ty * tiles_x) * TX + warp * LW + lane % LW;
+    const int y0 = ty * TY + lane / LW;
+    if (x >= W || y0 >= H) return;
+    const int nrows = min(R, (H - y0 + LH - 1) / LH);
     const float dx = (float)(x - sh.gxi) + sh.gxf;
     const int gyi = sh.gyi;
     const float gyf = sh.gyf;
     void* const disp = sh.disp;
     if (f.lp_fmt == VAFR_FMT_RGBA16F) {
         if (sh.disp_fmt == VAFR_FMT_RGBA16F)
-            recon_run_any<R, REUSE_U, VAFR_FMT_RGBA16F, VAFR_FMT_RGBA16F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
+            recon_run_any<R, LH, REUSE_U, VAFR_FMT_RGBA16F, VAFR_FMT_RGBA16F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
         else
-            recon_run_any<R, REUSE_U, VAFR_FMT_RGBA16F, VAFR_FMT_RGBA32F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
+            recon_run_any<R, LH, REUSE_U, VAFR_FMT_RGBA16F, VAFR_FMT_RGBA32F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
     } else {
         if (sh.disp_fmt == VAFR_FMT_RGBA16F)
-            recon_run_any<R, REUSE_U, VAFR_FMT_RGBA32F, VAFR_FMT_RGBA16F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
+            recon_run_any<R, LH, REUSE_U, VAFR_FMT_RGBA32F, VAFR_FMT_RGBA16F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
         else
-            recon_run_any<R, REUSE_U, VAFR_FMT_RGBA32F, VAFR_FMT_RGBA32F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
+            recon_run_any<R, LH, REUSE_U, VAFR_FMT_RGBA32F, VAFR_FMT_RGBA32F>(f, disp, W, x, y0, nrows, dx, gyi, gyf);
     }
 }
 
-template <int TW, int R, int MINB, bool REUSE_U, class B>
+template <int TW, int R, int LW, int MINB, bool REUSE_U, class B>
 cudaError_t launch_runs(const B& b, cudaStream_t s) {
     if (b.total_tiles <= 0) return cudaSuccess;
-    k_reconstruct_runs<TW, R, MINB, REUSE_U, B><<<(unsigned)b.total_tiles, TW, 0, s>>>(b);
+    k_reconstruct_runs<TW, R, LW, MINB, REUSE_U, B><<<(unsigned)b.total_tiles, TW, 0, s>>>(b);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -439,15 +448,15 @@ cudaError_t launch_shape(const B& b, cudaStream_t s) {
 
 }  // namespace
 
-// Tile shapes the autotuner chooses between: column runs (0-3; pixels wide,
-// rows per thread; 1 with a register cap for 10 blocks per SM) and row tiles
-// (4-7; pixels wide, rows, pixels per thread).
+// Tile shapes the autotuner chooses between: column runs (0-3: rows per
+// thread, lanes per warp row, minimum blocks per SM, u-table piece reuse) and
+// row tiles (4-7: pixels wide, rows, pixels per thread).
 ReconShape recon_shape(int variant) {
     switch (variant) {
         case 0: return {128, 8, 0};
         case 1: return {128, 8, 0};
-        case 2: return {128, 8, 0};
-        case 3: return {128, 8, 0};
+        case 2: return {128, 16, 0};
+        case 3: return {64, 16, 0};
         case 4: return {256, 4, 8};
         case 5: return {128, 8, 4};
         case 6: return {64, 8, 2};
@@ -458,10 +467,10 @@ ReconShape recon_shape(int variant) {
 template <class B>
 cudaError_t launch_reconstruct(const B& batch, int variant, cudaStream_t s) {
     switch (variant) {
-        case 0: return launch_runs<128, 8, 10, true>(batch, s);
-        case 1: return launch_runs<128, 8, 8, true>(batch, s);
-        case 2: return launch_runs<128, 8, 10, false>(batch, s);
-        case 3: return launch_runs<128, 8, 12, false>(batch, s);
+        case 0: return launch_runs<128, 8, 32, 10, false>(batch, s);
+        case 1: return launch_runs<128, 8, 32, 8, true>(batch, s);
+        case 2: return launch_runs<128, 16, 32, 10, false>(batch, s);
+        case 3: return launch_runs<128, 8, 16, 10, false>(batch, s);
         case 4: return launch_shape<256, 4, 8>(batch, s);
         case 5: return launch_shape<128, 8, 4>(batch, s);
         case 6: return launch_shape<64, 8, 2>(batch, s);

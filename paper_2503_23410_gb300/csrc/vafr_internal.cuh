@@ -63,7 +63,7 @@ struct FrameDesc {
     int lp_fmt, disp_fmt;
     const float* tan_e;     // device [C] tan(e_c) of the column centres
     const int2* col;        // device [C] (first texel, texel count)
-    const int4* col_pair;   // device [-1 .. C-1] (slot, count) of c and of min(c + 1, C - 1); [-1] = column 0 twice
+    const int4* col_pair;   // device [-1 .. C-1] (slot, FP32 bits of count) of c and of min(c + 1, C - 1); [-1] = column 0 twice
     const float4* u_tab;    // device [u_n + 1] cubic pieces of u(z)
     const int2* work;       // device [n_texels] (texel, column) in processing order
     int u_n;                // number of pieces
