@@ -69,17 +69,35 @@ typedef struct vafr_batch vafr_batch;
 /* Acuity pivots of the segmented mapping (Sec. 3.3, Eq. 12): MAR = 1/f is
  * piecewise linear through (pivot_ecc_deg[k], 1/pivot_cpd[k]);
  * pivot_ecc_deg[0] must be 0 and strictly increasing; e_max_deg is the
- * maximum perceivable eccentricity (Sec. 3.2.2). */
+ * maximum perceivable eccentricity (Sec. 3.2.2).
+ * Anisotropic acuity (Sec. 9, Eq. 19): with anisotropic != 0 the tangential
+ * shading rate is Delta(e) times the radial one, Delta piecewise linear in e
+ * through (pivot_ecc_deg[k], pivot_delta[k]) and constant past the last
+ * pivot (every pivot_delta[k] > 0); column c then holds
+ * max(1, round(Delta(e_c) l(e_c))) texels.  anisotropic = 0 ignores
+ * pivot_delta (Delta = 1, the paper's default mapping). */
 typedef struct {
     int32_t n_pivots;
     double  pivot_ecc_deg[VAFR_MAX_PIVOTS];
     double  pivot_cpd[VAFR_MAX_PIVOTS];
     double  e_max_deg;
+    int32_t anisotropic;
+    double  pivot_delta[VAFR_MAX_PIVOTS];
 } vafr_acuity;
 
 /* Fills the paper's pivots: f = 40, 10, 6, 5, 4 cpd at 0, 10, 20, 30, 60 deg
- * and e_max = 60 deg (Sec. 3.3 and Sec. 3.2.2). */
+ * and e_max = 60 deg (Sec. 3.3 and Sec. 3.2.2); isotropic. */
 VAFR_API void vafr_acuity_default(vafr_acuity* a);
+/* The paper's pivots with the anisotropy of Sec. 9: tangential acuity equal
+ * to radial at the fovea and half of it from 30 deg on (the factor of two at
+ * 30 deg the paper takes from the literature), linear in between:
+ * Delta = 1, 5/6, 2/3, 1/2, 1/2 at the five pivots. */
+VAFR_API void vafr_acuity_anisotropic(vafr_acuity* a);
+/* A curve for a display that resolves at most max_cpd cycles/deg (the
+ * head-mounted-display curves of Sec. 3.3): the paper's pivots with every
+ * pivot acuity capped at max_cpd, so the fovea is shaded at the display's
+ * own density.  Errors: INVALID_ARG (NULL, max_cpd <= 0). */
+VAFR_API int vafr_acuity_display_limited(vafr_acuity* a, double max_cpd);
 
 /* A display + viewer.  n_eyes 1 (mono) or 2 (binocular, VaFR_Dup of Sec. 5.1:
  * each eye rendered independently).  fov_v_deg is the vertical field of view;

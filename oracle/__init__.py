@@ -56,6 +56,8 @@ def lib():
         i64 = ctypes.c_int64
         L.or_acuity_init.argtypes = [P, P, P, ctypes.c_int]
         L.or_acuity_init.restype = ctypes.c_int
+        L.or_acuity_set_delta.argtypes = [P, P]
+        L.or_acuity_set_delta.restype = ctypes.c_int
         L.or_sizeof_acuity.restype = i64
         L.or_eval.argtypes = [P, ctypes.c_int, P, P, i64]
         L.or_acuity_get.argtypes = [P, P, P, P]
@@ -103,13 +105,21 @@ class Acuity:
     """Segmented acuity model (Eq. 12) built from pivots (E_k deg, f_k cpd)."""
 
     def __init__(self, pivots_deg: Sequence[float] = PAPER_PIVOTS_DEG,
-                 pivots_cpd: Sequence[float] = PAPER_PIVOTS_CPD):
+                 pivots_cpd: Sequence[float] = PAPER_PIVOTS_CPD,
+                 delta: Optional[Sequence[float]] = None):
+        """`delta`: tangential/radial shading-rate ratio at the pivots (Sec. 9,
+        Eq. 19), or None for the isotropic mapping."""
         self.E = _c(pivots_deg, np.float64)
         self.f = _c(pivots_cpd, np.float64)
         self._buf = ctypes.create_string_buffer(int(lib().or_sizeof_acuity()))
         rc = lib().or_acuity_init(self._buf, _p(self.E), _p(self.f), len(self.E))
         if rc != 0:
             raise ValueError("bad pivots")
+        self.delta = None
+        if delta is not None:
+            self.delta = _c(delta, np.float64)
+            if self.delta.size != self.E.size or lib().or_acuity_set_delta(self._buf, _p(self.delta)) != 0:
+                raise ValueError("bad delta")
         n = len(self.E) - 1
         self.m = np.zeros(n)
         self.w0 = np.zeros(n)
@@ -137,6 +147,9 @@ class Acuity:
 
     def f_of_e(self, e):
         return self._eval(3, e)
+
+    def delta_of_e(self, e):
+        return self._eval(4, e)
 
 
 @dataclass

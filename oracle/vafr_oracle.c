@@ -62,6 +62,8 @@ typedef struct {
     double m[OR_MAX_PIVOTS];      /* MAR slope of segment i (Eq. 2)           */
     double w0[OR_MAX_PIVOTS];     /* MAR intercept omega_i of segment i       */
     double c[OR_MAX_PIVOTS];      /* integration constant c_i (Eq. 12)        */
+    int    aniso;                 /* 0: Delta(e) = 1 (isotropic, Eq. 8)       */
+    double delta[OR_MAX_PIVOTS];  /* Delta at the pivots (Eq. 19)             */
 } or_acuity;
 
 /* u on segment i in the paper's literal form 2 ln(m_i e + w_i)/m_i + c_i,
@@ -139,6 +141,31 @@ double or_v_of_e_theta(const or_acuity* a, double e, double theta_deg) {
 /* Shading height l(e) = v(e, 360 deg), Eq. 9. */
 double or_l_of_e(const or_acuity* a, double e) { return or_v_of_e_theta(a, e, 360.0); }
 
+/* Anisotropic acuity (Sec. 9, Eq. 19): the tangential shading rate is Delta(e)
+ * times the radial one, v(e, theta) = Delta(e) theta sin(2e)/(m e + omega).
+ * The paper leaves Delta's form open; here it is piecewise linear in e
+ * through (E_k, delta_k) and constant past the last pivot.  Returns -1 unless
+ * every delta_k > 0. */
+int or_acuity_set_delta(or_acuity* a, const double* delta) {
+    for (int k = 0; k <= a->n_seg; ++k)
+        if (!(delta[k] > 0.0)) return -1;
+    for (int k = 0; k <= a->n_seg; ++k) a->delta[k] = delta[k];
+    a->aniso = 1;
+    return 0;
+}
+
+double or_delta(const or_acuity* a, double e) {
+    if (!a->aniso) return 1.0;
+    if (e >= a->E[a->n_seg]) return a->delta[a->n_seg];
+    int i = 0;
+    while (i + 1 < a->n_seg && e >= a->E[i + 1]) ++i;
+    double s = (e - a->E[i]) / (a->E[i + 1] - a->E[i]);
+    return a->delta[i] + s * (a->delta[i + 1] - a->delta[i]);
+}
+
+/* Texels per column before rounding: Delta(e) l(e) (Eq. 19 at theta = 360). */
+double or_l_delta_of_e(const or_acuity* a, double e) { return or_delta(a, e) * or_l_of_e(a, e); }
+
 /* Vectorised helpers for the Python side. */
 void or_eval(const or_acuity* a, int what, const double* in, double* out, int64_t n) {
     for (int64_t k = 0; k < n; ++k) {
@@ -147,6 +174,7 @@ void or_eval(const or_acuity* a, int what, const double* in, double* out, int64_
             case 1: out[k] = or_e_of_u(a, in[k]); break;
             case 2: out[k] = or_l_of_e(a, in[k]); break;
             case 3: out[k] = or_acuity_f(a, in[k]); break;
+            case 4: out[k] = or_delta(a, in[k]); break;
             default: out[k] = NAN;
         }
     }
@@ -160,7 +188,8 @@ void or_acuity_get(const or_acuity* a, double* m, double* w0, double* c) {
 
 /* ------------------------------------------------------------------------- */
 /* Discrete LP layout (Sec. 3.2.2): columns at u = c + 0.5 for c + 0.5 < u(e_max);
- * column c holds n_c = max(1, round(l(e_c))) texels at angles (j+0.5) 360/n_c.
+ * column c holds n_c = max(1, round(Delta(e_c) l(e_c))) texels at angles
+ * (j+0.5) 360/n_c (Delta = 1 unless the acuity is anisotropic, Sec. 9).
  * Texels are stored column after column: texel (c, j) at offset_c + j.
  * Returns the column count, or -1 if it would exceed cap. */
 int or_lp_layout(const or_acuity* a, double e_max, int cap,
@@ -172,7 +201,7 @@ int or_lp_layout(const or_acuity* a, double e_max, int cap,
     int64_t acc = 0;
     for (int c = 0; c < C; ++c) {
         double e = or_e_of_u(a, (double)c + 0.5);
-        double l = or_l_of_e(a, e);
+        double l = or_l_delta_of_e(a, e);
         int32_t n = (int32_t)floor(l + 0.5);
         if (n < 1) n = 1;
         e_col[c] = e;

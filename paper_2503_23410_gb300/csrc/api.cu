@@ -235,8 +235,28 @@ void vafr_acuity_default(vafr_acuity* a) {
     std::memset(a, 0, sizeof(*a));
     const double E[5] = {0, 10, 20, 30, 60}, f[5] = {40, 10, 6, 5, 4};
     a->n_pivots = 5;
-    for (int k = 0; k < 5; ++k) { a->pivot_ecc_deg[k] = E[k]; a->pivot_cpd[k] = f[k]; }
+    for (int k = 0; k < 5; ++k) {
+        a->pivot_ecc_deg[k] = E[k];
+        a->pivot_cpd[k] = f[k];
+        a->pivot_delta[k] = 1.0;
+    }
     a->e_max_deg = 60.0;
+}
+
+void vafr_acuity_anisotropic(vafr_acuity* a) {
+    if (!a) return;
+    vafr_acuity_default(a);
+    const double d[5] = {1.0, 5.0 / 6.0, 2.0 / 3.0, 0.5, 0.5};
+    for (int k = 0; k < 5; ++k) a->pivot_delta[k] = d[k];
+    a->anisotropic = 1;
+}
+
+int vafr_acuity_display_limited(vafr_acuity* a, double max_cpd) {
+    if (!a || !(max_cpd > 0.0) || !std::isfinite(max_cpd))
+        return fail(VAFR_ERR_INVALID_ARG, "max_cpd must be finite and > 0");
+    vafr_acuity_default(a);
+    for (int k = 0; k < a->n_pivots; ++k) a->pivot_cpd[k] = std::min(a->pivot_cpd[k], max_cpd);
+    return VAFR_OK;
 }
 
 // ---- scene ---------------------------------------------------------------------------

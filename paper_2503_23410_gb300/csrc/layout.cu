@@ -20,6 +20,11 @@ int Mapping::init(const vafr_acuity& a) {
         if (k > 0 && !(a.pivot_ecc_deg[k] > a.pivot_ecc_deg[k - 1])) return -1;
     }
     if (!(a.e_max_deg > 0.0) || !(a.e_max_deg < 90.0)) return -1;
+    aniso = a.anisotropic != 0;
+    for (int k = 0; k < a.n_pivots; ++k) {
+        if (aniso && !(a.pivot_delta[k] > 0.0 && std::isfinite(a.pivot_delta[k]))) return -1;
+        delta[k] = aniso ? a.pivot_delta[k] : 1.0;
+    }
     n_seg = a.n_pivots - 1;
     e_max = a.e_max_deg;
     U[0] = 0.0;
@@ -67,6 +72,13 @@ double Mapping::e_of_u(double u) const {
 double Mapping::l_of_e(double e) const {
     const int i = seg_e(e);
     return 360.0 * std::sin(2.0 * e * M_PI / 180.0) / (m[i] * e + w[i]);
+}
+
+double Mapping::delta_of_e(double e) const {
+    if (!aniso) return 1.0;
+    if (e >= E[n_seg]) return delta[n_seg];
+    const int i = seg_e(e);
+    return delta[i] + (e - E[i]) / (E[i + 1] - E[i]) * (delta[i + 1] - delta[i]);
 }
 
 double Mapping::du_de(double e) const {
@@ -157,7 +169,8 @@ void build_work_order(const LayoutTables& L, std::vector<int2>& work) {
 
 int build(const vafr_acuity& acuity, LayoutTables& L, std::string* err) {
     if (L.map.init(acuity) != 0) {
-        *err = "bad acuity pivots (need E_0 = 0, increasing pivots, f > 0, 0 < e_max < 90, MAR > 0)";
+        *err = "bad acuity pivots (need E_0 = 0, increasing pivots, f > 0, 0 < e_max < 90, MAR > 0, "
+               "delta > 0 when anisotropic)";
         return VAFR_ERR_INVALID_ARG;
     }
     // Column c occupies slots [off_c - 1, off_c + n_c]: its n_c texels plus a
@@ -168,7 +181,7 @@ int build(const vafr_acuity& acuity, LayoutTables& L, std::string* err) {
     int64_t acc = 0, slots = 0;
     for (int c = 0; (double)c + 0.5 < u_max; ++c) {
         const double e = L.map.e_of_u((double)c + 0.5);
-        int32_t nc = (int32_t)std::floor(L.map.l_of_e(e) + 0.5);
+        int32_t nc = (int32_t)std::floor(L.map.delta_of_e(e) * L.map.l_of_e(e) + 0.5);
         if (nc < 1) nc = 1;
         L.e_col.push_back(e);
         L.n_col.push_back(nc);
@@ -243,6 +256,9 @@ int get_layout(const vafr_acuity& acuity, std::shared_ptr<const LayoutTables>* o
     key.append(reinterpret_cast<const char*>(acuity.pivot_ecc_deg), sizeof(double) * np);
     key.append(reinterpret_cast<const char*>(acuity.pivot_cpd), sizeof(double) * np);
     key.append(reinterpret_cast<const char*>(&acuity.e_max_deg), sizeof(double));
+    const int32_t aniso = acuity.anisotropic != 0;
+    key.append(reinterpret_cast<const char*>(&aniso), sizeof(aniso));
+    if (aniso) key.append(reinterpret_cast<const char*>(acuity.pivot_delta), sizeof(double) * np);
     std::lock_guard<std::mutex> lock(g_mu);
     auto it = g_cache.find(key);
     if (it != g_cache.end()) {

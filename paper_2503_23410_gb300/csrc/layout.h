@@ -19,10 +19,14 @@ namespace vafr {
 // with U_0 = 0 and U_i making u continuous (the integration constants),
 //   e(u) its inverse (Eq. 10), l(e) = 360 sin(2e) / omega(e) (Eqs. 8-9),
 //   du/de = 2 / omega(e) (Eq. 4).  Flat segments (m_i = 0) use the limit.
+// Anisotropy (Sec. 9, Eq. 19): Delta(e) piecewise linear through the pivots'
+// deltas, constant past the last pivot; 1 for an isotropic model.
 struct Mapping {
     int n_seg = 0;
     double E[VAFR_MAX_PIVOTS], m[VAFR_MAX_PIVOTS], w[VAFR_MAX_PIVOTS], U[VAFR_MAX_PIVOTS + 1];
     double e_max = 60.0;
+    bool aniso = false;
+    double delta[VAFR_MAX_PIVOTS];
 
     int init(const vafr_acuity& a);
     double du(int i, double de) const;
@@ -30,6 +34,7 @@ struct Mapping {
     double u_of_e(double e) const;
     double e_of_u(double u) const;
     double l_of_e(double e) const;
+    double delta_of_e(double e) const;
     double du_de(double e) const;
 };
 

@@ -43,7 +43,9 @@ class vafr_acuity(ctypes.Structure):
     _fields_ = [("n_pivots", ctypes.c_int32),
                 ("pivot_ecc_deg", ctypes.c_double * MAX_PIVOTS),
                 ("pivot_cpd", ctypes.c_double * MAX_PIVOTS),
-                ("e_max_deg", ctypes.c_double)]
+                ("e_max_deg", ctypes.c_double),
+                ("anisotropic", ctypes.c_int32),
+                ("pivot_delta", ctypes.c_double * MAX_PIVOTS)]
 
 
 class vafr_session_desc(ctypes.Structure):
@@ -68,6 +70,8 @@ _PROTOS = {
     "vafr_version": (_I32, []),
     "vafr_kernel_launch_count": (_I64, []),
     "vafr_acuity_default": (None, [_P]),
+    "vafr_acuity_anisotropic": (None, [_P]),
+    "vafr_acuity_display_limited": (ctypes.c_int, [_P, ctypes.c_double]),
     "vafr_build_scene": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P]),
     "vafr_scene_destroy": (ctypes.c_int, [_P]),
     "vafr_scene_info": (ctypes.c_int, [_P, _P, _P]),
@@ -176,14 +180,31 @@ def vafr_acuity_default() -> vafr_acuity:
     return a
 
 
+def vafr_acuity_anisotropic() -> vafr_acuity:
+    a = vafr_acuity()
+    load().vafr_acuity_anisotropic(ctypes.byref(a))
+    return a
+
+
+def vafr_acuity_display_limited(max_cpd: float) -> vafr_acuity:
+    a = vafr_acuity()
+    _check(load().vafr_acuity_display_limited(ctypes.byref(a), float(max_cpd)))
+    return a
+
+
 def make_acuity(pivots_deg: Sequence[float], pivots_cpd: Sequence[float],
-                e_max_deg: float = 60.0) -> vafr_acuity:
+                e_max_deg: float = 60.0, delta: Optional[Sequence[float]] = None) -> vafr_acuity:
     a = vafr_acuity()
     a.n_pivots = len(pivots_deg)
     for k, (e, f) in enumerate(zip(pivots_deg, pivots_cpd)):
         a.pivot_ecc_deg[k] = float(e)
         a.pivot_cpd[k] = float(f)
+        a.pivot_delta[k] = 1.0
     a.e_max_deg = float(e_max_deg)
+    if delta is not None:
+        a.anisotropic = 1
+        for k, d in enumerate(delta):
+            a.pivot_delta[k] = float(d)
     return a
 
 

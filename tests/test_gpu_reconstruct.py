@@ -21,8 +21,8 @@ def lay():
     return oracle.lp_layout()
 
 
-def _recon(V, torch, W, H, fov, gaze, lp_np, lp_fmt=0, disp_fmt=0, variant=None):
-    s = V.vafr_session_create(V.make_session_desc(W, H, fov, [POSE], lp_fmt, disp_fmt))
+def _recon(V, torch, W, H, fov, gaze, lp_np, lp_fmt=0, disp_fmt=0, variant=None, acuity=None):
+    s = V.vafr_session_create(V.make_session_desc(W, H, fov, [POSE], lp_fmt, disp_fmt, acuity))
     V.vafr_set_gaze(s, 0, *gaze)
     dt = torch.float16 if lp_fmt else torch.float32
     lp = torch.from_numpy(np.ascontiguousarray(to_device_lp(lp_np, V, s))).to(dt).cuda()
@@ -47,6 +47,24 @@ def test_random_lp_all_pixels(V, torch_mod, lay, W, H, gaze):
     err = np.abs(got - ref).max()
     print(f"recon {W}x{H} gaze {gaze}: max err {err:.2e}")
     assert err < 1e-3
+
+
+@pytest.mark.parametrize("which", ["anisotropic", "display9"])
+def test_other_acuity_layouts(V, torch_mod, which):
+    """Reconstruction over the anisotropic (Sec. 9) and display-limited (Sec. 3.3)
+    layouts against the oracle, every pixel."""
+    P, F = oracle.PAPER_PIVOTS_DEG, oracle.PAPER_PIVOTS_CPD
+    if which == "anisotropic":
+        acu, ora = V.vafr_acuity_anisotropic(), oracle.Acuity(P, F, delta=(1, 5 / 6, 2 / 3, 0.5, 0.5))
+    else:
+        acu, ora = V.vafr_acuity_display_limited(9.0), oracle.Acuity(P, np.minimum(F, 9.0))
+    lay_a = oracle.lp_layout(ora)
+    rng = np.random.default_rng(17)
+    lp = rng.uniform(0, 1, (lay_a.total, 4)).astype(np.float32)
+    W, H, gaze = 801, 449, (300.5, 260.25)
+    got = _recon(V, torch_mod, W, H, 100.0, gaze, lp, acuity=acu)
+    ref = oracle.reconstruct(lp.astype(np.float64), lay_a, W, H, 100.0, gaze, acuity=ora)
+    assert np.abs(got - ref).max() < 1e-3
 
 
 def test_constant_lp_is_exact(V, torch_mod, lay):

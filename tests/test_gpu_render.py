@@ -59,6 +59,47 @@ def test_layout_matches_oracle(V, lay):
         V.vafr_session_destroy(s)
 
 
+ANISO = (1.0, 5.0 / 6.0, 2.0 / 3.0, 0.5, 0.5)
+
+
+def _acuities(V):
+    """(library acuity, oracle acuity) pairs: Sec. 9 anisotropy, Sec. 3.3 display-limited curves."""
+    P, F = oracle.PAPER_PIVOTS_DEG, oracle.PAPER_PIVOTS_CPD
+    return [(V.vafr_acuity_anisotropic(), oracle.Acuity(P, F, delta=ANISO)),
+            (V.vafr_acuity_display_limited(9.0), oracle.Acuity(P, np.minimum(F, 9.0))),
+            (V.vafr_acuity_display_limited(18.0), oracle.Acuity(P, np.minimum(F, 18.0)))]
+
+
+def test_layouts_of_other_acuities_match_oracle(V):
+    pose = look_at_pose((0, 0, -3), (0, 0, 0))
+    for acu, ora in _acuities(V):
+        ref = oracle.lp_layout(ora)
+        s = _session(V, 1920, 1080, 100.0, [pose], acuity=acu)
+        counts, offs, ecc, n_tex = V.vafr_lp_layout(s)
+        assert n_tex == ref.total
+        assert np.array_equal(counts, ref.n_col)
+        np.testing.assert_allclose(ecc, ref.e_col, rtol=1e-6)
+        V.vafr_session_destroy(s)
+
+
+def test_lp_frame_anisotropic_full(V, torch_mod):
+    """Every LP ray of an anisotropic layout (Sec. 9) against the oracle."""
+    w = workload("random1k")
+    d, sc = w.displays[0], w.scene
+    h, keep = device_scene(V, sc, torch_mod)
+    acu, ora = _acuities(V)[0]
+    lay_a = oracle.lp_layout(ora)
+    s = _session(V, d.width, d.height, d.fov_v_deg, d.poses, acuity=acu)
+    gaze = (d.width * 0.4, d.height * 0.55)
+    V.vafr_set_gaze(s, 0, *gaze)
+    lp, ids = _render_lp(V, torch_mod, h, s, lay_a.total)
+    rgba, oid, ot, o, dd = oracle.render_lp(sc.tris, sc.albedo, sc.light_dir, lay_a, d.width,
+                                            d.height, d.fov_v_deg, gaze, d.poses[0])
+    compare_hits_and_colours(sc.tris, o, dd, ids, lp, oid, ot, rgba, 1e-3)
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)
+
+
 def test_lp_frame_random1k_full(V, torch_mod, lay):
     w = workload("random1k")
     d, sc = w.displays[0], w.scene
