@@ -78,6 +78,8 @@ def lib():
         L.or_reconstruct_points.argtypes = [P, ctypes.c_double, P, P, P, ctypes.c_int,
                                             P, ctypes.c_int, P, i64, P]
         L.or_morton.argtypes = [P, i64, P]
+        L.or_fxaa_lp.argtypes = [P, P, ctypes.c_int, P, ctypes.c_int, P]
+        L.or_lp_neighbor.argtypes = [P, P, ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, i64, P]
         L.or_lbvh.argtypes = [P, i64, P, P, P, P, P, P]
         L.or_lbvh.restype = ctypes.c_int
         L.or_num_threads.restype = ctypes.c_int
@@ -313,6 +315,33 @@ def pixel_centres(width, height, pixels=None):
 def reconstruct(lp, layout, width, height, fov_v_deg, gaze, pixels=None, **kw):
     return reconstruct_points(lp, layout, width, height, fov_v_deg, gaze,
                               pixel_centres(width, height, pixels), **kw)
+
+
+def fxaa_lp(lp, layout: Layout) -> np.ndarray:
+    """FXAA inside the LP buffer (Sec. 3.4, Sec. 7) on texels in layout order;
+    `layout` may be any (n_col, off_col) grid."""
+    lpa = _c(lp, np.float64)
+    nch = lpa.shape[1] if lpa.ndim == 2 else 1
+    out = np.empty_like(lpa)
+    n = _c(layout.n_col, np.int32)
+    off = _c(layout.off_col, np.int64)
+    lib().or_fxaa_lp(_p(n), _p(off), int(n.size), _p(lpa), nch, _p(out))
+    return out
+
+
+def lp_neighbor(layout: Layout, c: int, j: int, c2: int, dj: int) -> int:
+    """Index of the texel of column c2 at the angle of (c, j), moved dj rows."""
+    out = np.zeros(1, np.int64)
+    n = _c(layout.n_col, np.int32)
+    off = _c(layout.off_col, np.int64)
+    lib().or_lp_neighbor(_p(n), _p(off), int(n.size), int(c), int(j), int(c2), int(dj), _p(out))
+    return int(out[0])
+
+
+def uniform_layout(n_cols: int, n_rows: int) -> Layout:
+    """A rectangular LP grid (every column n_rows texels) for closed-form tests."""
+    return Layout(np.zeros(n_cols), np.full(n_cols, n_rows, np.int32),
+                  np.arange(n_cols, dtype=np.int64) * n_rows, n_cols * n_rows)
 
 
 def morton(tris):

@@ -822,3 +822,148 @@ int or_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------- */
+/* Anti-aliasing inside the LP buffer (Sec. 3.4 "internal anti-aliasing";
+ * Sec. 7 ablation).  The paper runs FXAA (Lottes 2009) on the LP buffer and
+ * gives no parameters.  This is that method on the LP grid, in its steps:
+ *
+ *  grid      texel (c, j); along the angle its neighbours are (c, j -+ 1)
+ *            modulo n_c; across the radius, column c' = c -+ 1 (clamped to
+ *            [0, C-1]) contributes the texel whose angular interval holds the
+ *            angle of (c, j): j' = floor((2j + 1) n_c' / (2 n_c)).
+ *  luma      0.299 R + 0.587 G + 0.114 B.
+ *  1 skip    contrast range of {M, N, S, E, W} below max(1/12, max / 6): the
+ *            texel is copied (N/S = j +- 1, E/W = c +- 1).
+ *  2 axis    second differences across the angle (kA) and across the radius
+ *            (kR) from the 3 x 3 neighbourhood; kR >= kA means the luma
+ *            changes across columns: the edge runs along the angle and the
+ *            blend steps one column, otherwise the reverse.
+ *  3 side    the blend neighbour is the one with the larger luma step
+ *            (positive side on a tie); the edge's mid-line luma is their
+ *            mean, its threshold a quarter of the step.
+ *  4 search  walk along the edge both ways, up to 12 unit steps, averaging
+ *            the luma of the texel on the walk and of its partner across the
+ *            edge; an end is where that mean leaves the mid-line by the
+ *            threshold (a walk that finds none ends at 12).
+ *  5 offset  from the nearer end d and both ends' sum D: 1/2 - d/D, applied
+ *            only when the luma at that end lies on the other side of the
+ *            mid-line than the texel (ties: the positive end).
+ *  6 subpix  a = |mean of the 3 x 3 (edges weight 2, corners 1) - M| / range,
+ *            (3 - 2a) a^2 squared, times 3/4.
+ *  7 blend   texel + max(offset, subpix) (neighbour - texel), all channels.
+ * Luma and every comparison are in FP32 with the operation order written
+ * here, so a kernel that rounds the same way takes the same branches; the
+ * offsets and the blend are FP64. */
+
+#define OR_FXAA_STEPS 12
+
+typedef struct {
+    const int32_t* n;
+    const int64_t* off;
+    int C;
+    const double* lp;
+    int nch;
+} or_lpgrid;
+
+/* Texel of column c2 (clamped to [0, C-1]) at the angle of texel (c, j),
+ * then moved dj rows within that column (modulo its count). */
+static int64_t lp_at(const or_lpgrid* g, int c, int64_t j, int c2, int64_t dj) {
+    if (c2 < 0) c2 = 0;
+    if (c2 > g->C - 1) c2 = g->C - 1;
+    int64_t n = g->n[c], n2 = g->n[c2];
+    int64_t j2 = c2 == c ? j : ((2 * j + 1) * n2) / (2 * n);
+    j2 = ((j2 + dj) % n2 + n2) % n2;
+    return g->off[c2] + j2;
+}
+
+static float lp_luma(const or_lpgrid* g, int64_t t) {
+    const double* p = g->lp + t * g->nch;
+    float y = 0.299f * (float)p[0];
+    y = y + 0.587f * (float)p[1];
+    y = y + 0.114f * (float)p[2];
+    return y;
+}
+
+void or_lp_neighbor(const int32_t* n_col, const int64_t* off_col, int C, int c, int64_t j, int c2,
+                    int64_t dj, int64_t* out) {
+    or_lpgrid g = {n_col, off_col, C, NULL, 0};
+    *out = lp_at(&g, c, j, c2, dj);
+}
+
+void or_fxaa_lp(const int32_t* n_col, const int64_t* off_col, int C, const double* lp, int nch,
+                double* out) {
+    const or_lpgrid g = {n_col, off_col, C, lp, nch};
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int c = 0; c < C; ++c) {
+        for (int64_t j = 0; j < n_col[c]; ++j) {
+            const int64_t tM = off_col[c] + j;
+            for (int ch = 0; ch < nch; ++ch) out[tM * nch + ch] = lp[tM * nch + ch];
+            const float M = lp_luma(&g, tM);
+            const float N = lp_luma(&g, lp_at(&g, c, j, c, 1)), S = lp_luma(&g, lp_at(&g, c, j, c, -1));
+            const float E = lp_luma(&g, lp_at(&g, c, j, c + 1, 0)), W = lp_luma(&g, lp_at(&g, c, j, c - 1, 0));
+            /* 1 skip */
+            const float lo = fminf(M, fminf(fminf(N, S), fminf(E, W)));
+            const float hi = fmaxf(M, fmaxf(fmaxf(N, S), fmaxf(E, W)));
+            const float range = hi - lo;
+            if (range < fmaxf(1.0f / 12.0f, hi * (1.0f / 6.0f))) continue;
+            const float NE = lp_luma(&g, lp_at(&g, c, j, c + 1, 1)), SE = lp_luma(&g, lp_at(&g, c, j, c + 1, -1));
+            const float NW = lp_luma(&g, lp_at(&g, c, j, c - 1, 1)), SW = lp_luma(&g, lp_at(&g, c, j, c - 1, -1));
+            /* 2 axis */
+            const float kA = 2.0f * fabsf((N + S) - 2.0f * M) + fabsf((NE + SE) - 2.0f * E) + fabsf((NW + SW) - 2.0f * W);
+            const float kR = 2.0f * fabsf((E + W) - 2.0f * M) + fabsf((NE + NW) - 2.0f * N) + fabsf((SE + SW) - 2.0f * S);
+            const int across_cols = kR >= kA;
+            /* 3 side */
+            const float Ln = across_cols ? W : S, Lp = across_cols ? E : N;
+            const float gn = fabsf(Ln - M), gp = fabsf(Lp - M);
+            const int pos = gp >= gn;
+            const float avg = 0.5f * (M + (pos ? Lp : Ln));
+            const float thr = 0.25f * fmaxf(gn, gp);
+            const int side = pos ? 1 : -1;
+            /* 4 search */
+            int dist[2];
+            float end[2];
+            for (int d = 0; d < 2; ++d) {
+                const int sgn = d ? 1 : -1;
+                dist[d] = OR_FXAA_STEPS;
+                end[d] = 0.0f;
+                for (int k = 1; k <= OR_FXAA_STEPS; ++k) {
+                    int64_t ta, tb;
+                    if (across_cols) {               /* walk rows of column c */
+                        ta = lp_at(&g, c, j, c, sgn * k);
+                        tb = lp_at(&g, c, ta - off_col[c], c + side, 0);
+                    } else {                         /* walk columns at the angle of (c, j) */
+                        int ck = c + sgn * k;
+                        if (ck < 0) ck = 0;
+                        if (ck > C - 1) ck = C - 1;
+                        ta = lp_at(&g, c, j, ck, 0);
+                        tb = lp_at(&g, ck, ta - off_col[ck], ck, side);
+                    }
+                    const float s = 0.5f * (lp_luma(&g, ta) + lp_luma(&g, tb));
+                    end[d] = s;
+                    if (fabsf(s - avg) >= thr) { dist[d] = k; break; }
+                }
+            }
+            /* 5 offset */
+            const int near_neg = dist[0] < dist[1];
+            const int dn = near_neg ? dist[0] : dist[1];
+            const float lend = near_neg ? end[0] : end[1];
+            const int good = ((lend - avg) < 0.0f) != ((M - avg) < 0.0f);
+            const double off_edge = good ? 0.5 - (double)dn / (double)(dist[0] + dist[1]) : 0.0;
+            /* 6 subpix */
+            const double l3 = (2.0 * ((double)N + (double)S + (double)E + (double)W) +
+                               ((double)NE + (double)NW + (double)SE + (double)SW)) / 12.0;
+            double a = fabs(l3 - (double)M) / (double)range;
+            if (a > 1.0) a = 1.0;
+            const double b = (3.0 - 2.0 * a) * a * a;
+            const double sub = b * b * 0.75;
+            /* 7 blend */
+            const double w = off_edge > sub ? off_edge : sub;
+            const int64_t tS = across_cols ? lp_at(&g, c, j, c + side, 0) : lp_at(&g, c, j, c, side);
+            for (int ch = 0; ch < nch; ++ch) {
+                const double m = lp[tM * nch + ch], q = lp[tS * nch + ch];
+                out[tM * nch + ch] = m + w * (q - m);
+            }
+        }
+    }
+}
