@@ -110,6 +110,9 @@ typedef struct {
     int32_t     lp_format;       /* VAFR_FMT_* of the LP buffer             */
     int32_t     display_format;  /* VAFR_FMT_* of the reconstructed display */
     vafr_acuity acuity;
+    int32_t     lp_fxaa;         /* 1: FXAA inside the LP buffer before the
+                                    inverse mapping (Sec. 3.4), see
+                                    vafr_fxaa_lp; 0: none                  */
 } vafr_session_desc;
 
 /* One frame-eye of a batched launch. */
@@ -118,6 +121,8 @@ typedef struct {
     int32_t       eye;
     void*         lp;        /* device, LP buffer of that eye (see vafr_render_lp) */
     void*         display;   /* device, height x width pixels of display_format     */
+    void*         lp_aa;     /* device, second LP buffer receiving the FXAA pass;
+                                required when the session has lp_fxaa, else ignored */
 } vafr_frame_desc;
 
 /* ---- errors -------------------------------------------------------------- */
@@ -230,6 +235,21 @@ VAFR_API int vafr_render_lp(const vafr_scene* scene, vafr_session* session, int3
  * Errors: INVALID_ARG, CUDA. */
 VAFR_API int vafr_reconstruct(vafr_session* session, int32_t eye, const void* lp, void* display_out,
                      void* stream);
+/* vafr_fxaa_lp: FXAA inside one eye's LP buffer (Sec. 3.4: the paper
+ * anti-aliases the LP buffer with FXAA before the inverse mapping; Sec. 7
+ * ablates it).  FXAA (Lottes 2009) on the LP grid: angular neighbours are
+ * the rows j -+ 1 of a column (wrapping), radial neighbours the texel of
+ * column c -+ 1 (clamped) whose angular interval holds the same angle; luma
+ * 0.299 R + 0.587 G + 0.114 B; texels whose 5-neighbourhood luma range is
+ * below max(1/12, max/6) are copied; the others are blended towards one
+ * neighbour by the larger of the edge offset (from a 12-step search along
+ * the edge) and the subpixel term (weight 3/4).  FP32.
+ *   lp      device, the eye's LP buffer as vafr_render_lp writes it.
+ *   lp_out  device, another buffer of the same size (not overlapping lp);
+ *           receives every texel and its guard copies.
+ * Errors: INVALID_ARG (NULL, bad eye, unaligned, lp == lp_out), CUDA. */
+VAFR_API int vafr_fxaa_lp(vafr_session* session, int32_t eye, const void* lp, void* lp_out,
+                          void* stream);
 /* vafr_render_full_gt: the paper's GT (Sec. 5.2.1, Table 1): one ray per
  * display pixel centre, same traversal and shading, written straight to the
  * display (display_format).  hit_ids_out: device or NULL, height x width int32.
@@ -237,7 +257,8 @@ VAFR_API int vafr_reconstruct(vafr_session* session, int32_t eye, const void* lp
 VAFR_API int vafr_render_full_gt(const vafr_scene* scene, vafr_session* session, int32_t eye,
                         void* display_out, int32_t* hit_ids_out, void* stream);
 /* vafr_render_frame: one whole frame of the session (render_lp of every eye
- * into a session-owned LP buffer, then reconstruct every eye).
+ * into a session-owned LP buffer, the FXAA pass when the session has
+ * lp_fxaa, then reconstruct every eye).
  *   display_out  host or device, [n_eyes][height][width] of display_format,
  *                16-byte aligned.  Pinned host memory (page-locked or
  *                registered) is written directly by the reconstruction kernel

@@ -5,6 +5,7 @@
 #include "layout.h"
 #include "vafr_internal.cuh"
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -111,6 +112,7 @@ struct vafr_session {
     bool gaze_set[2] = {false, false};
     FrameDesc fd[2]{};
     void* lp_internal = nullptr;       // render_frame's LP buffer
+    void* lp_aa_internal = nullptr;    // render_frame's FXAA output
     void* disp_internal = nullptr;     // render_frame's device display for host output
     int recon_variant = 0;
     int render_variant = 0;
@@ -120,6 +122,7 @@ struct vafr_session {
         cudaFree(d_counter);
         cudaFree(d_stats);
         cudaFree(lp_internal);
+        cudaFree(lp_aa_internal);
         cudaFree(disp_internal);
     }
 };
@@ -133,8 +136,10 @@ struct vafr_batch {
     // captured graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t render_node = nullptr, recon_node = nullptr;
-    cudaKernelNodeParams render_params{}, recon_params{};
+    // kernel nodes in launch order: render (scene + batch), then the FXAA pass
+    // if any and reconstruct (batch only)
+    std::vector<cudaGraphNode_t> kernel_nodes;
+    std::vector<cudaKernelNodeParams> kernel_params;
     std::vector<vafr_frame_desc> captured;
     BigBatch* host_batch = nullptr;  // parameters of the captured launches
 
@@ -190,6 +195,7 @@ void fill_static(vafr_session* s, int eye) {
     f.n_texels = (int)s->n_texels;
     f.status = s->d_status;
     f.lp = nullptr;
+    f.lp_aa = nullptr;
     f.disp = nullptr;
     f.hit_ids = nullptr;
 }
@@ -531,12 +537,30 @@ int vafr_reconstruct(vafr_session* s, int32_t eye, const void* lp, void* display
     SmallBatch b{};
     FrameDesc f = s->fd[eye];
     f.lp = const_cast<void*>(lp);
+    f.lp_aa = nullptr;
     f.disp = display_out;
     f.tile_begin = 0;
     b.d[0] = f;
     b.n = 1;
     b.total_tiles = recon_tiles(f, s->recon_variant);
     CUDA_TRY(launch_reconstruct(b, s->recon_variant, as_stream(stream)));
+    return VAFR_OK;
+}
+
+int vafr_fxaa_lp(vafr_session* s, int32_t eye, const void* lp, void* lp_out, void* stream) {
+    if (!s || !lp || !lp_out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    if (eye < 0 || eye >= s->desc.n_eyes) return fail(VAFR_ERR_INVALID_ARG, "eye %d out of range", eye);
+    if (!aligned(lp, 16) || !aligned(lp_out, 16)) return fail(VAFR_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    if (lp == lp_out) return fail(VAFR_ERR_INVALID_ARG, "lp_out must not be lp");
+    SmallBatch b{};
+    FrameDesc f = s->fd[eye];   // the layout tables only: no gaze needed
+    f.lp = const_cast<void*>(lp);
+    f.lp_aa = lp_out;
+    f.aa_begin = 0;
+    b.d[0] = f;
+    b.n = 1;
+    b.total_aa = s->n_texels;
+    CUDA_TRY(launch_fxaa(b, as_stream(stream), s->sms));
     return VAFR_OK;
 }
 
@@ -587,8 +611,18 @@ int vafr_render_frame(const vafr_scene* scene, vafr_session* s, void* display_ou
     if (!aligned(target, 16)) return fail(VAFR_ERR_INVALID_ARG, "display must be 16-byte aligned");
     int rc = vafr_render_lp(scene, s, (1 << eyes) - 1, s->lp_internal, nullptr, stream);
     if (rc) return rc;
+    void* lp_final = s->lp_internal;
+    if (s->desc.lp_fxaa) {
+        if (!s->lp_aa_internal) CUDA_TRY(cudaMalloc(&s->lp_aa_internal, (size_t)lpb * eyes));
+        for (int e = 0; e < eyes; ++e) {
+            rc = vafr_fxaa_lp(s, e, static_cast<char*>(s->lp_internal) + (size_t)e * lpb,
+                              static_cast<char*>(s->lp_aa_internal) + (size_t)e * lpb, stream);
+            if (rc) return rc;
+        }
+        lp_final = s->lp_aa_internal;
+    }
     for (int e = 0; e < eyes; ++e) {
-        rc = vafr_reconstruct(s, e, static_cast<char*>(s->lp_internal) + (size_t)e * lpb,
+        rc = vafr_reconstruct(s, e, static_cast<char*>(lp_final) + (size_t)e * lpb,
                               static_cast<char*>(target) + (size_t)e * dpb, stream);
         if (rc) return rc;
     }
@@ -635,12 +669,20 @@ static int build_batch(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n,
         if (!aligned(fr.lp, 16) || !aligned(fr.display, 16)) return fail(VAFR_ERR_INVALID_ARG, "frame %d: unaligned buffer", i);
         FrameDesc f = s->fd[fr.eye];
         f.lp = fr.lp;
+        f.lp_aa = nullptr;
+        if (s->desc.lp_fxaa) {
+            if (!fr.lp_aa || !aligned(fr.lp_aa, 16) || fr.lp_aa == fr.lp)
+                return fail(VAFR_ERR_INVALID_ARG, "frame %d: FXAA session needs a separate aligned lp_aa", i);
+            f.lp_aa = fr.lp_aa;
+        }
         f.disp = fr.display;
         f.hit_ids = nullptr;
         f.work_begin = b->total_work;
         f.tile_begin = b->total_tiles;
+        f.aa_begin = b->total_aa;
         b->total_work += s->n_texels;
         b->total_tiles += recon_tiles(f, bt->recon_variant);
+        if (f.lp_aa) b->total_aa += s->n_texels;
         b->d[i] = f;
     }
     b->n = n;
@@ -649,6 +691,7 @@ static int build_batch(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n,
 
 static int launch_batch(vafr_batch* bt, const BigBatch& b, cudaStream_t st) {
     CUDA_TRY(launch_render_lp(bt->scene->dev, b, bt->render_variant, st, bt->scene->sms));
+    CUDA_TRY(launch_fxaa(b, st, bt->scene->sms));
     CUDA_TRY(launch_reconstruct(b, bt->recon_variant, st));
     return VAFR_OK;
 }
@@ -702,32 +745,50 @@ int vafr_batch_capture(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n,
     if (rc) return rc;
     CUDA_TRY(e);
     CUDA_TRY(cudaGraphInstantiate(&bt->exec, bt->graph, 0));
-    // locate the two kernel nodes (capture order: memset -> render -> reconstruct)
+    // the kernel nodes, ordered along the captured chain (memset -> render ->
+    // [FXAA ->] reconstruct): a node's rank is its number of kernel ancestors
     size_t nn = 0;
     CUDA_TRY(cudaGraphGetNodes(bt->graph, nullptr, &nn));
     std::vector<cudaGraphNode_t> nodes(nn);
     CUDA_TRY(cudaGraphGetNodes(bt->graph, nodes.data(), &nn));
-    bt->render_node = bt->recon_node = nullptr;
+    auto kernel_ancestors = [&](cudaGraphNode_t nd, auto&& self) -> int {
+        size_t ndep = 0;
+        if (cudaGraphNodeGetDependencies(nd, nullptr, nullptr, &ndep) != cudaSuccess) return -1;
+        std::vector<cudaGraphNode_t> deps(ndep);
+        if (ndep && cudaGraphNodeGetDependencies(nd, deps.data(), nullptr, &ndep) != cudaSuccess) return -1;
+        int k = 0;
+        for (cudaGraphNode_t dn : deps) {
+            cudaGraphNodeType dt;
+            if (cudaGraphNodeGetType(dn, &dt) != cudaSuccess) return -1;
+            const int up = self(dn, self);
+            if (up < 0) return -1;
+            k = std::max(k, up + (dt == cudaGraphNodeTypeKernel ? 1 : 0));
+        }
+        return k;
+    };
+    std::vector<std::pair<int, cudaGraphNode_t>> ranked;
     for (cudaGraphNode_t nd : nodes) {
         cudaGraphNodeType ty;
         CUDA_TRY(cudaGraphNodeGetType(nd, &ty));
         if (ty != cudaGraphNodeTypeKernel) continue;
-        cudaKernelNodeParams p{};
-        CUDA_TRY(cudaGraphKernelNodeGetParams(nd, &p));
-        size_t ndep = 0;
-        CUDA_TRY(cudaGraphNodeGetDependencies(nd, nullptr, nullptr, &ndep));
-        std::vector<cudaGraphNode_t> deps(ndep);
-        if (ndep) CUDA_TRY(cudaGraphNodeGetDependencies(nd, deps.data(), nullptr, &ndep));
-        bool after_kernel = false;
-        for (cudaGraphNode_t dn : deps) {
-            cudaGraphNodeType dt;
-            CUDA_TRY(cudaGraphNodeGetType(dn, &dt));
-            if (dt == cudaGraphNodeTypeKernel) after_kernel = true;
-        }
-        if (after_kernel) { bt->recon_node = nd; bt->recon_params = p; }
-        else { bt->render_node = nd; bt->render_params = p; }
+        const int r = kernel_ancestors(nd, kernel_ancestors);
+        if (r < 0) return fail(VAFR_ERR_CUDA, "graph: dependency query failed");
+        ranked.push_back({r, nd});
     }
-    if (!bt->render_node || !bt->recon_node) return fail(VAFR_ERR_CUDA, "graph: kernel nodes not found");
+    std::sort(ranked.begin(), ranked.end(),
+              [](const std::pair<int, cudaGraphNode_t>& a, const std::pair<int, cudaGraphNode_t>& b) {
+                  return a.first < b.first;
+              });
+    bt->kernel_nodes.clear();
+    bt->kernel_params.clear();
+    for (size_t k = 0; k < ranked.size(); ++k) {
+        if (ranked[k].first != (int)k) return fail(VAFR_ERR_CUDA, "graph: kernel nodes are not a chain");
+        cudaKernelNodeParams p{};
+        CUDA_TRY(cudaGraphKernelNodeGetParams(ranked[k].second, &p));
+        bt->kernel_nodes.push_back(ranked[k].second);
+        bt->kernel_params.push_back(p);
+    }
+    if (bt->kernel_nodes.size() < 2) return fail(VAFR_ERR_CUDA, "graph: kernel nodes not found");
     bt->captured.assign(frames, frames + n);
     return VAFR_OK;
 }
@@ -746,16 +807,15 @@ int vafr_batch_replay(vafr_batch* bt, void* stream) {
     }
     SceneDev sc = bt->scene->dev;
     void* rargs[2] = {&sc, b};
-    void* cargs[1] = {b};
-    cudaKernelNodeParams rp = bt->render_params, cp = bt->recon_params;
-    rp.kernelParams = rargs;
-    rp.extra = nullptr;
-    cp.kernelParams = cargs;
-    cp.extra = nullptr;
-    CUDA_TRY(cudaGraphExecKernelNodeSetParams(bt->exec, bt->render_node, &rp));
-    CUDA_TRY(cudaGraphExecKernelNodeSetParams(bt->exec, bt->recon_node, &cp));
+    void* bargs[1] = {b};
+    for (size_t k = 0; k < bt->kernel_nodes.size(); ++k) {
+        cudaKernelNodeParams p = bt->kernel_params[k];
+        p.kernelParams = k == 0 ? rargs : bargs;   // render takes (scene, batch), the rest (batch)
+        p.extra = nullptr;
+        CUDA_TRY(cudaGraphExecKernelNodeSetParams(bt->exec, bt->kernel_nodes[k], &p));
+    }
     CUDA_TRY(cudaGraphLaunch(bt->exec, as_stream(stream)));
-    count_launch(2);
+    count_launch((int)bt->kernel_nodes.size());
     return VAFR_OK;
 }
 

@@ -147,7 +147,7 @@ __device__ __forceinline__ void stage_frame(const B& b, int tile, ReconShared& s
     sh.r.u_nf = (float)fd.u_n;
     sh.r.u_tab = fd.u_tab;
     sh.r.col_pair = fd.col_pair;
-    sh.r.lp = fd.lp;
+    sh.r.lp = fd.lp_aa ? fd.lp_aa : fd.lp;   // the FXAA output when the pass ran
     sh.r.lp_fmt = fd.lp_fmt;
     sh.gxi = fd.gxi;
     sh.gyi = fd.gyi;

@@ -71,11 +71,13 @@ struct FrameDesc {
     int n_cols;
     int n_texels;
     void* lp;
+    void* lp_aa;            // FXAA output (read by reconstruct) or nullptr: no FXAA
     void* disp;
     int* hit_ids;
     unsigned* status;
     long long work_begin;   // first global work item (render) of this frame
     long long tile_begin;   // first global tile (reconstruct) of this frame
+    long long aa_begin;     // first global FXAA texel of this frame
 };
 
 template <int MAXD>
@@ -83,6 +85,7 @@ struct Batch {
     int n;
     long long total_work;   // sum of render work items
     long long total_tiles;  // sum of reconstruct tiles
+    long long total_aa;     // sum of FXAA texels (frames with lp_aa)
     unsigned long long* work_counter;  // device counter (persistent fetch)
     FrameDesc d[MAXD];
 };
@@ -111,6 +114,9 @@ cudaError_t launch_render_gt(const SceneDev& scene, const B& batch, int variant,
                              cudaStream_t s, int num_sms);
 template <class B>
 cudaError_t launch_reconstruct(const B& batch, int variant, cudaStream_t s);
+// FXAA inside the LP buffer of every frame with lp_aa set (fxaa.cu).
+template <class B>
+cudaError_t launch_fxaa(const B& batch, cudaStream_t s, int num_sms);
 cudaError_t launch_render_stats(const SceneDev& scene, const SmallBatch& batch,
                                 unsigned long long* counters, cudaStream_t s, int num_sms);
 

@@ -53,12 +53,13 @@ class vafr_session_desc(ctypes.Structure):
                 ("fov_v_deg", ctypes.c_double), ("n_eyes", ctypes.c_int32),
                 ("eye_pose", (ctypes.c_double * 12) * 2),
                 ("lp_format", ctypes.c_int32), ("display_format", ctypes.c_int32),
-                ("acuity", vafr_acuity)]
+                ("acuity", vafr_acuity), ("lp_fxaa", ctypes.c_int32)]
 
 
 class vafr_frame_desc(ctypes.Structure):
     _fields_ = [("session", ctypes.c_void_p), ("eye", ctypes.c_int32),
-                ("lp", ctypes.c_void_p), ("display", ctypes.c_void_p)]
+                ("lp", ctypes.c_void_p), ("display", ctypes.c_void_p),
+                ("lp_aa", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p
@@ -86,6 +87,7 @@ _PROTOS = {
     "vafr_session_check": (ctypes.c_int, [_P, _P]),
     "vafr_render_lp": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P]),
     "vafr_reconstruct": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
+    "vafr_fxaa_lp": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     "vafr_render_full_gt": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P]),
     "vafr_render_frame": (ctypes.c_int, [_P, _P, _P, _P]),
     "vafr_traversal_stats": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
@@ -261,7 +263,8 @@ def vafr_session_create(desc: vafr_session_desc) -> int:
 
 
 def make_session_desc(width, height, fov_v_deg, poses, lp_format=FMT_RGBA32F,
-                      display_format=FMT_RGBA32F, acuity: Optional[vafr_acuity] = None):
+                      display_format=FMT_RGBA32F, acuity: Optional[vafr_acuity] = None,
+                      lp_fxaa: bool = False):
     d = vafr_session_desc()
     d.width, d.height, d.fov_v_deg = int(width), int(height), float(fov_v_deg)
     d.n_eyes = len(poses)
@@ -271,6 +274,7 @@ def make_session_desc(width, height, fov_v_deg, poses, lp_format=FMT_RGBA32F,
             d.eye_pose[e][k] = float(flat[k])
     d.lp_format, d.display_format = int(lp_format), int(display_format)
     d.acuity = acuity if acuity is not None else vafr_acuity_default()
+    d.lp_fxaa = 1 if lp_fxaa else 0
     return d
 
 
@@ -319,6 +323,10 @@ def vafr_reconstruct(session: int, eye: int, lp, display_out, stream=None) -> No
     _check(load().vafr_reconstruct(session, int(eye), ptr(lp), ptr(display_out), stream_ptr(stream)))
 
 
+def vafr_fxaa_lp(session: int, eye: int, lp, lp_out, stream=None) -> None:
+    _check(load().vafr_fxaa_lp(session, int(eye), ptr(lp), ptr(lp_out), stream_ptr(stream)))
+
+
 def vafr_render_full_gt(scene: int, session: int, eye: int, display_out, hit_ids_out=None,
                         stream=None) -> None:
     _check(load().vafr_render_full_gt(scene, session, int(eye), ptr(display_out),
@@ -337,12 +345,15 @@ def vafr_traversal_stats(scene: int, session: int, eye: int = 0, stream=None):
 
 
 def _frames(frames):
+    """frames: (session, eye, lp, display) or (session, eye, lp, display, lp_aa)."""
     arr = (vafr_frame_desc * len(frames))()
-    for i, (sess, eye, lp, disp) in enumerate(frames):
+    for i, fr in enumerate(frames):
+        sess, eye, lp, disp = fr[:4]
         arr[i].session = sess
         arr[i].eye = int(eye)
         arr[i].lp = ptr(lp)
         arr[i].display = ptr(disp)
+        arr[i].lp_aa = ptr(fr[4]) if len(fr) > 4 else None
     return arr
 
 
