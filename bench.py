@@ -244,9 +244,15 @@ def run_gpu(args, w):
     scene = V.vafr_build_scene(tris, alb, w.scene.light_dir)
     lp_fmt = V.FMT_RGBA16F if w.lp_fp16 else V.FMT_RGBA32F
     dp_fmt = V.FMT_RGBA16F if w.display_fp16 else V.FMT_RGBA32F
-    sess = V.vafr_session_create(V.make_session_desc(W_, H_, d.fov_v_deg, d.poses, lp_fmt, dp_fmt))
+    fxaa = bool(args.fxaa)
+    acuity = {"paper": None, "anisotropic": V.vafr_acuity_anisotropic,
+              "display9": lambda: V.vafr_acuity_display_limited(9.0),
+              "display18": lambda: V.vafr_acuity_display_limited(18.0)}[args.acuity]
+    sess = V.vafr_session_create(V.make_session_desc(W_, H_, d.fov_v_deg, d.poses, lp_fmt, dp_fmt,
+                                                     acuity() if acuity else None, lp_fxaa=fxaa))
     lp_b, dp_b = V.vafr_session_sizes(sess)
     lp = torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda")
+    lp_aa = torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda") if fxaa else lp
     disp = torch.empty(eyes * dp_b, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
@@ -262,10 +268,15 @@ def run_gpu(args, w):
         V.vafr_render_lp(scene, sess, mask, lp)
         if evs:
             evs[1].record()
+        if fxaa:                                   # FXAA inside the LP buffer (Sec. 3.4)
+            for e in range(eyes):
+                V.vafr_fxaa_lp(sess, e, lp[e * lp_b:], lp_aa[e * lp_b:])
+            if evs:
+                evs[2].record()
         for e in range(eyes):
-            V.vafr_reconstruct(sess, e, lp[e * lp_b:], disp[e * dp_b:])
+            V.vafr_reconstruct(sess, e, lp_aa[e * lp_b:], disp[e * dp_b:])
         if evs:
-            evs[2].record()
+            evs[-1].record()
 
     def gt_frame(k, evs=None):
         if evs:
@@ -302,7 +313,7 @@ def run_gpu(args, w):
     assert V.vafr_session_check(sess) == 0
 
     with ClockSampler(local) as clk:
-        per, wall, launches = timed(frame, args.steps, 3)
+        per, wall, launches = timed(frame, args.steps, 4 if fxaa else 3)
         gt_steps = max(3, min(args.steps, args.gt_steps))
         gper, gwall, _ = timed(gt_frame, gt_steps, 2)
         # end to end through the C ABI with HOST buffers, two ways:
@@ -326,10 +337,14 @@ def run_gpu(args, w):
             V.vafr_render_frame(scene, sess, host[0])
         e2e_sync_s = time.perf_counter() - te
         lps = [torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda") for _ in range(2)]
+        aas = [torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda") for _ in range(2)] if fxaa else None
         streams = [torch.cuda.Stream() for _ in range(2)]
         batches = [V.vafr_batch_create(scene, 2 * eyes) for _ in range(2)]
 
         def frames_for(slot):
+            if fxaa:
+                return [(sess, e, lps[slot][e * lp_b:], host[slot][e * dp_b:], aas[slot][e * lp_b:])
+                        for e in range(eyes)]
             return [(sess, e, lps[slot][e * lp_b:], host[slot][e * dp_b:]) for e in range(eyes)]
         for k in range(4):
             V.vafr_batch_render(batches[k % 2], frames_for(k % 2), stream=streams[k % 2])
@@ -350,7 +365,7 @@ def run_gpu(args, w):
     assert V.vafr_session_check(sess) == 0
 
     step_ms = per.sum(1)
-    render_ms, recon_ms = per[:, 0], per[:, 1]
+    render_ms, recon_ms = per[:, 0], per[:, -1]
     gt_ms = gper[:, 0]
     total_s = step_ms.sum() / 1e3
     from paper_2503_23410_gb300.dist import max_over_ranks
@@ -401,6 +416,7 @@ def run_gpu(args, w):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": _workload_desc(w),
                    "l2": "flushed between steps (256 MiB write outside the per-step events)",
+                   "acuity": args.acuity, "lp_fxaa": fxaa,
                    "parallelism": f"replicas x{ws} (independent sessions, no collective)"},
         "fps": 1e3 / float(step_ms.mean()),
         "p50_frame_ms": float(np.percentile(step_ms, 50)),
@@ -409,7 +425,8 @@ def run_gpu(args, w):
                "mpix_per_s": mpix_frame * 1e3 / gt_mean, "rays_per_frame": W_ * H_ * eyes,
                "steps": gt_steps},
         "speedup_vs_gt": gt_mean / float(step_ms.mean()),
-        "stage_ms": {"render_lp": float(render_ms.mean()), "reconstruct": float(recon_ms.mean())},
+        "stage_ms": dict({"render_lp": float(render_ms.mean()), "reconstruct": float(recon_ms.mean())},
+                         **({"fxaa_lp": float(per[:, 1].mean())} if fxaa else {})),
         "roofline": dominant,
         "roofline_other": roof_recon if dominant is roof_render else roof_render,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * eyes,
@@ -611,6 +628,11 @@ def main():
     ap.add_argument("--ref-pixels", type=int, default=524288)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--acuity", default="paper", choices=["paper", "anisotropic", "display9", "display18"],
+                    help="acuity model: the paper's pivots, the Sec. 9 anisotropy, or the Sec. 3.3 "
+                         "display-limited curves at 9 / 18 cpd")
+    ap.add_argument("--fxaa", action="store_true",
+                    help="run the LP-space FXAA pass (Sec. 3.4) inside each timed frame")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

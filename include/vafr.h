@@ -247,7 +247,10 @@ VAFR_API int vafr_reconstruct(vafr_session* session, int32_t eye, const void* lp
  *   lp      device, the eye's LP buffer as vafr_render_lp writes it.
  *   lp_out  device, another buffer of the same size (not overlapping lp);
  *           receives every texel and its guard copies.
- * Errors: INVALID_ARG (NULL, bad eye, unaligned, lp == lp_out), CUDA. */
+ * The pass keeps the lumas of the eye's texels in session-owned scratch
+ * (allocated by vafr_session_create when lp_fxaa is set, else by the first
+ * call), so FXAA calls for one session and eye must not overlap in time.
+ * Errors: INVALID_ARG (NULL, bad eye, unaligned, lp == lp_out), OOM, CUDA. */
 VAFR_API int vafr_fxaa_lp(vafr_session* session, int32_t eye, const void* lp, void* lp_out,
                           void* stream);
 /* vafr_render_full_gt: the paper's GT (Sec. 5.2.1, Table 1): one ray per

@@ -113,6 +113,7 @@ struct vafr_session {
     FrameDesc fd[2]{};
     void* lp_internal = nullptr;       // render_frame's LP buffer
     void* lp_aa_internal = nullptr;    // render_frame's FXAA output
+    float* d_luma = nullptr;           // FXAA scratch: [n_eyes][n_slots] lumas
     void* disp_internal = nullptr;     // render_frame's device display for host output
     int recon_variant = 0;
     int render_variant = 0;
@@ -123,6 +124,7 @@ struct vafr_session {
         cudaFree(d_stats);
         cudaFree(lp_internal);
         cudaFree(lp_aa_internal);
+        cudaFree(d_luma);
         cudaFree(disp_internal);
     }
 };
@@ -196,6 +198,7 @@ void fill_static(vafr_session* s, int eye) {
     f.status = s->d_status;
     f.lp = nullptr;
     f.lp_aa = nullptr;
+    f.luma = nullptr;
     f.disp = nullptr;
     f.hit_ids = nullptr;
 }
@@ -438,6 +441,8 @@ int vafr_session_create(const vafr_session_desc* desc, vafr_session** out) {
     if ((e = cudaMalloc(&s->d_counter, sizeof(unsigned long long))) != cudaSuccess) return bail(e);
     if ((e = cudaMalloc(&s->d_stats, 6 * sizeof(unsigned long long))) != cudaSuccess) return bail(e);
     if ((e = cudaMemset(s->d_status, 0, sizeof(unsigned))) != cudaSuccess) return bail(e);
+    if (d.lp_fxaa && (e = cudaMalloc(&s->d_luma, sizeof(float) * s->n_slots * d.n_eyes)) != cudaSuccess)
+        return bail(e);
     for (int eye = 0; eye < d.n_eyes; ++eye) fill_static(s, eye);
     *out = s;
     return VAFR_OK;
@@ -552,10 +557,13 @@ int vafr_fxaa_lp(vafr_session* s, int32_t eye, const void* lp, void* lp_out, voi
     if (eye < 0 || eye >= s->desc.n_eyes) return fail(VAFR_ERR_INVALID_ARG, "eye %d out of range", eye);
     if (!aligned(lp, 16) || !aligned(lp_out, 16)) return fail(VAFR_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
     if (lp == lp_out) return fail(VAFR_ERR_INVALID_ARG, "lp_out must not be lp");
+    // luma scratch: allocated with the session when it has lp_fxaa, else on first use
+    if (!s->d_luma) CUDA_TRY(cudaMalloc(&s->d_luma, sizeof(float) * s->n_slots * s->desc.n_eyes));
     SmallBatch b{};
     FrameDesc f = s->fd[eye];   // the layout tables only: no gaze needed
     f.lp = const_cast<void*>(lp);
     f.lp_aa = lp_out;
+    f.luma = s->d_luma + (size_t)eye * s->n_slots;
     f.aa_begin = 0;
     b.d[0] = f;
     b.n = 1;
@@ -674,6 +682,7 @@ static int build_batch(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n,
             if (!fr.lp_aa || !aligned(fr.lp_aa, 16) || fr.lp_aa == fr.lp)
                 return fail(VAFR_ERR_INVALID_ARG, "frame %d: FXAA session needs a separate aligned lp_aa", i);
             f.lp_aa = fr.lp_aa;
+            f.luma = s->d_luma + (size_t)fr.eye * s->n_slots;
         }
         f.disp = fr.display;
         f.hit_ids = nullptr;

@@ -24,9 +24,11 @@
 //             ((3 - 2a) a^2)^2 x 3/4.
 //   7 blend   texel + max(offset, subpix) (neighbour - texel), every channel.
 // Luma and every branch decision use FP32 in one fixed order (no contraction),
-// offsets and the blend FP32.  One thread per texel, texels in the frame's
-// screen-space Morton order; the output (a second LP buffer) gets the guard
-// copies too.
+// offsets and the blend FP32.  Two passes, one thread per texel in the
+// frame's screen-space Morton order: the luma of every slot into a scratch
+// array, then the filter, which reads lumas (4 bytes) for its neighbourhood
+// and search and colours only for the texel and its blend partner.  The
+// output (a second LP buffer) gets the guard copies too.
 #include "vafr_internal.cuh"
 
 namespace vafr {
@@ -62,21 +64,43 @@ __device__ __forceinline__ float luma_of(float4 c) {
     return __fadd_rn(y, __fmul_rn(0.114f, c.z));
 }
 
+// floor(num / D) for a divisor D = 2 n_c fixed per texel: with num < 2^24 the
+// FP32 product num * (1/D) is within one of the quotient (relative error
+// <= 2^-23 and quotients < 2^16), fixed by one step each way; larger
+// numerators divide in integers.
+struct RowDiv {
+    unsigned D;
+    float rD;
+    __device__ __forceinline__ explicit RowDiv(int n) : D(2u * (unsigned)n), rD(1.0f / (float)(2 * n)) {}
+    __device__ __forceinline__ int operator()(unsigned num) const {
+        if (num >= (1u << 24)) return (int)(num / D);
+        unsigned q = (unsigned)((float)num * rD);
+        q += (q + 1u) * D <= num ? 1u : 0u;
+        q -= q * D > num ? 1u : 0u;
+        return (int)q;
+    }
+};
+
 struct Grid {
     const int2* col;   // (slot of row 0, count)
     int C;
     const void* lp;
     int fmt;
+    const float* lum;  // luma of every slot (guards included)
 
     // slot of the texel of column c2 (clamped) at the angle of row j of column
-    // c (count n), moved dj rows; |dj| <= 1 may land on a guard slot
-    __device__ __forceinline__ int at(int c, int j, int n, int c2, int dj) const {
+    // c, moved dj rows; |dj| <= 1 may land on a guard slot.  The row is
+    // floor((2j + 1) n_c2 / (2 n_c)): the one whose angular interval holds the
+    // centre of row j.
+    __device__ __forceinline__ int at(int c, int j, const RowDiv& div, int c2, int dj) const {
         c2 = min(max(c2, 0), C - 1);
         const int2 cc = __ldg(col + c2);
-        const int j2 = c2 == c ? j : (int)(((long long)(2 * j + 1) * cc.y) / (2ll * n));
+        const unsigned long long num = (unsigned long long)(2 * j + 1) * (unsigned)cc.y;
+        const int j2 = c2 == c ? j
+                               : (num < (1ull << 32) ? div((unsigned)num) : (int)(num / div.D));
         return cc.x + j2 + dj;
     }
-    __device__ __forceinline__ float luma(int slot) const { return luma_of(ld_texel(lp, fmt, slot)); }
+    __device__ __forceinline__ float luma(int slot) const { return __ldg(lum + slot); }
 };
 
 __device__ __forceinline__ float abs_second_diff(float a, float b, float m) {
@@ -85,17 +109,20 @@ __device__ __forceinline__ float abs_second_diff(float a, float b, float m) {
 
 // The filtered colour of texel (c, j) (slot t, count n).
 __device__ float4 fxaa_texel(const Grid& g, int c, int j, int n, int t) {
-    const float4 cM = ld_texel(g.lp, g.fmt, t);
-    const float M = luma_of(cM);
+    const RowDiv div(n);
+    const float M = g.luma(t);
+    // radial neighbours; their angular neighbours are the adjacent slots
+    const int sE = g.at(c, j, div, c + 1, 0), sW = g.at(c, j, div, c - 1, 0);
     const float N = g.luma(t + 1), S = g.luma(t - 1);
-    const float E = g.luma(g.at(c, j, n, c + 1, 0)), W = g.luma(g.at(c, j, n, c - 1, 0));
+    const float E = g.luma(sE), W = g.luma(sW);
     // 1 skip
     const float lo = fminf(M, fminf(fminf(N, S), fminf(E, W)));
     const float hi = fmaxf(M, fmaxf(fmaxf(N, S), fmaxf(E, W)));
     const float range = __fsub_rn(hi, lo);
+    const float4 cM = ld_texel(g.lp, g.fmt, t);
     if (range < fmaxf(1.0f / 12.0f, __fmul_rn(hi, 1.0f / 6.0f))) return cM;
-    const float NE = g.luma(g.at(c, j, n, c + 1, 1)), SE = g.luma(g.at(c, j, n, c + 1, -1));
-    const float NW = g.luma(g.at(c, j, n, c - 1, 1)), SW = g.luma(g.at(c, j, n, c - 1, -1));
+    const float NE = g.luma(sE + 1), SE = g.luma(sE - 1);
+    const float NW = g.luma(sW + 1), SW = g.luma(sW - 1);
     // 2 axis
     const float kA = __fadd_rn(__fadd_rn(__fmul_rn(2.0f, abs_second_diff(N, S, M)), abs_second_diff(NE, SE, E)),
                                abs_second_diff(NW, SW, W));
@@ -122,12 +149,17 @@ __device__ float4 fxaa_texel(const Grid& g, int c, int j, int n, int t) {
         for (int k = 1; k <= kFxaaSteps; ++k) {
             int ta, tb;
             if (across_cols) {   // walk the rows of column c
-                int jk = (j + sgn * k) % n;
-                jk = jk < 0 ? jk + n : jk;
+                int jk = j + sgn * k;
+                if (n > kFxaaSteps) {            // at most one wrap
+                    jk = jk < 0 ? jk + n : (jk >= n ? jk - n : jk);
+                } else {
+                    jk %= n;
+                    jk = jk < 0 ? jk + n : jk;
+                }
                 ta = cc.x + jk;
-                tb = g.at(c, jk, n, c + side, 0);
+                tb = g.at(c, jk, div, c + side, 0);
             } else {             // walk the columns at the angle of (c, j)
-                ta = g.at(c, j, n, c + sgn * k, 0);
+                ta = g.at(c, j, div, c + sgn * k, 0);
                 tb = ta + side;
             }
             const float s = __fmul_rn(0.5f, __fadd_rn(g.luma(ta), g.luma(tb)));
@@ -150,7 +182,7 @@ __device__ float4 fxaa_texel(const Grid& g, int c, int j, int n, int t) {
     const float bsub = (3.0f - 2.0f * a) * a * a;
     const float w = fmaxf(off_edge, bsub * bsub * 0.75f);
     // 7 blend
-    const float4 q = ld_texel(g.lp, g.fmt, across_cols ? g.at(c, j, n, c + side, 0) : t + side);
+    const float4 q = ld_texel(g.lp, g.fmt, across_cols ? (pos ? sE : sW) : t + side);
     return make_float4(fmaf(w, q.x - cM.x, cM.x), fmaf(w, q.y - cM.y, cM.y), fmaf(w, q.z - cM.z, cM.z),
                        fmaf(w, q.w - cM.w, cM.w));
 }
@@ -165,15 +197,32 @@ __device__ __forceinline__ int find_aa_frame(const B& b, long long w) {
     return lo;
 }
 
+// Pass 1: the luma of every texel into the frame's scratch, guard slots too.
 template <class B>
-__global__ void __launch_bounds__(256) k_fxaa_lp(const __grid_constant__ B b) {
+__global__ void __launch_bounds__(256) k_lp_luma(const __grid_constant__ B b) {
     for (long long w = (long long)blockIdx.x * 256 + threadIdx.x; w < b.total_aa;
          w += (long long)gridDim.x * 256) {
         const FrameDesc& f = b.d[find_aa_frame(b, w)];
         const int2 tc = __ldg(f.work + (w - f.aa_begin));   // (slot, column)
         const int2 cc = __ldg(f.col + tc.y);
         const int j = tc.x - cc.x, n = cc.y;
-        const Grid g{f.col, f.n_cols, f.lp, f.lp_fmt};
+        const float y = luma_of(ld_texel(f.lp, f.lp_fmt, tc.x));
+        f.luma[tc.x] = y;
+        if (j == 0) f.luma[tc.x + n] = y;
+        if (j == n - 1) f.luma[tc.x - n] = y;
+    }
+}
+
+// Pass 2: the filter.
+template <class B>
+__global__ void __launch_bounds__(256, 6) k_fxaa_lp(const __grid_constant__ B b) {
+    for (long long w = (long long)blockIdx.x * 256 + threadIdx.x; w < b.total_aa;
+         w += (long long)gridDim.x * 256) {
+        const FrameDesc& f = b.d[find_aa_frame(b, w)];
+        const int2 tc = __ldg(f.work + (w - f.aa_begin));   // (slot, column)
+        const int2 cc = __ldg(f.col + tc.y);
+        const int j = tc.x - cc.x, n = cc.y;
+        const Grid g{f.col, f.n_cols, f.lp, f.lp_fmt, f.luma};
         const float4 v = fxaa_texel(g, tc.y, j, n, tc.x);
         st_texel(f.lp_aa, f.lp_fmt, tc.x, v);
         if (j == 0) st_texel(f.lp_aa, f.lp_fmt, tc.x + n, v);       // guard after the column
@@ -186,10 +235,12 @@ __global__ void __launch_bounds__(256) k_fxaa_lp(const __grid_constant__ B b) {
 template <class B>
 cudaError_t launch_fxaa(const B& b, cudaStream_t s, int num_sms) {
     if (b.total_aa <= 0) return cudaSuccess;
-    const long long want = (b.total_aa + 255) / 256;
-    const long long cap = (long long)num_sms * 8;
-    k_fxaa_lp<B><<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(b);
-    count_launch(1);
+    const long long want = (b.total_aa + 255) / 256;   // one thread per texel
+    const long long cap = (long long)num_sms * 64;
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    k_lp_luma<B><<<grid, 256, 0, s>>>(b);
+    k_fxaa_lp<B><<<grid, 256, 0, s>>>(b);
+    count_launch(2);
     return cudaGetLastError();
 }
 

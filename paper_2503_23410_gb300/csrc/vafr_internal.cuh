@@ -72,6 +72,7 @@ struct FrameDesc {
     int n_texels;
     void* lp;
     void* lp_aa;            // FXAA output (read by reconstruct) or nullptr: no FXAA
+    float* luma;            // FXAA scratch: luma of every LP slot
     void* disp;
     int* hit_ids;
     unsigned* status;
