@@ -402,7 +402,7 @@ def run_gpu(args, w):
                    "box_tests_per_ray": stats["box_tests"] / max(stats["rays"], 1),
                    "tri_tests_per_ray": stats["tri_tests"] / max(stats["rays"], 1),
                    "mrays_per_s": rays / render_s / 1e6, "avg_ms": render_s * 1e3}
-    roof_recon = {"kernel": "k_reconstruct", "bound": "hbm",
+    roof_recon = {"kernel": "k_reconstruct_runs", "bound": "hbm",
                   "achieved": recon_bytes / recon_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
                   "frac": recon_bytes / recon_s / 1e9 / hbm_peak, "traffic": tr_recon,
                   "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured"
