@@ -79,6 +79,9 @@ def lib():
                                             P, ctypes.c_int, P, i64, P]
         L.or_morton.argtypes = [P, i64, P]
         L.or_fxaa_lp.argtypes = [P, P, ctypes.c_int, P, ctypes.c_int, P]
+        L.or_path_trace.argtypes = [P, P, P, P, P, P, i64, ctypes.c_uint64, ctypes.c_int, P, P, P]
+        L.or_pt_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int]
+        L.or_pt_uniform.restype = ctypes.c_double
         L.or_lp_neighbor.argtypes = [P, P, ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, i64, P]
         L.or_lbvh.argtypes = [P, i64, P, P, P, P, P, P]
         L.or_lbvh.restype = ctypes.c_int
@@ -391,6 +394,32 @@ def render_lp(scene_tris, albedo, light_dir, layout, width, height, fov_v_deg, g
         ids, t = cast_brute(scene_tris, o, d)
     rgba = shade(scene_tris, albedo, light_dir, d, ids)
     return rgba, ids, t, o, d
+
+
+def pt_uniform(seed: int, texel: int, k: int, dim: int) -> float:
+    """The path tracer's counter-based uniform for (seed, texel, bounce k, dim)."""
+    return float(lib().or_pt_uniform(int(seed), int(texel), int(k), int(dim)))
+
+
+def path_trace_lp(scene_tris, albedo, light_dir, layout, width, height, fov_v_deg, gaze, pose,
+                  seed: int, max_diffuse: int = 3, texels=None, bvh: Optional[CpuBVH] = None,
+                  segments: bool = False):
+    """Path-traced LP texels (Sec. 8).  Returns (rgba (n, 4), signature (n, D + 2)
+    [, segment rays (n, D + 1, 6)]): signature = hit id per segment (-1 miss,
+    -2 not traced) then the mask of segments whose shadow ray saw the light."""
+    if texels is None:
+        texels = np.arange(layout.total, dtype=np.int64)
+    tex = _c(texels, np.int64)
+    o, d, _ = lp_rays(layout, width, height, fov_v_deg, gaze, pose, tex)
+    b = bvh or CpuBVH(scene_tris)
+    n = tex.size
+    rgba = np.empty((n, 4))
+    sig = np.empty((n, max_diffuse + 2), np.int32)
+    seg = np.empty((n, max_diffuse + 1, 6)) if segments else None
+    lib().or_path_trace(b.h, _p(_c(albedo, np.float32)), _p(_c(light_dir, np.float64)), _p(o), _p(d),
+                        _p(tex), n, int(seed) & (2**64 - 1), int(max_diffuse), _p(rgba), _p(sig),
+                        _p(seg) if seg is not None else None)
+    return (rgba, sig, seg) if segments else (rgba, sig)
 
 
 def render_gt(scene_tris, albedo, light_dir, width, height, fov_v_deg, pose, pixels=None,

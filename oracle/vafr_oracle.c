@@ -518,42 +518,46 @@ static int box_enter(const or_bnode* nd, const double o[3], const double inv[3],
     return t0 <= t1 * (1.0 + 1e-12);
 }
 
+/* Closest hit of one ray through the CPU BVH, ignoring triangle `skip` (-1:
+ * none); returns the id or -1 and the distance in *t_out. */
+static int32_t bvh_closest(const or_bvh* b, const double o[3], const double d[3], int32_t skip,
+                           double* t_out) {
+    or_wray r;
+    wray_init(&r, o, d);
+    double inv[3] = {1.0 / d[0], 1.0 / d[1], 1.0 / d[2]};
+    int32_t best = -1;
+    double bt = INFINITY;
+    int32_t stack[128];
+    int sp = 0;
+    if (b->n_tris > 0) stack[sp++] = 0;
+    while (sp > 0) {
+        const or_bnode* nd = &b->nodes[stack[--sp]];
+        if (!box_enter(nd, o, inv, bt)) continue;
+        if (nd->left < 0) {
+            for (int32_t i = nd->first; i < nd->first + nd->count; ++i) {
+                int32_t tid = b->order[i];
+                double t;
+                if (tid != skip && wray_hit(&r, b->tris + 9 * (int64_t)tid, &t) &&
+                    (t < bt || (t == bt && tid < best))) {
+                    bt = t;
+                    best = tid;
+                }
+            }
+        } else if (sp + 2 <= 128) {
+            stack[sp++] = nd->right;
+            stack[sp++] = nd->left;
+        }
+    }
+    *t_out = best >= 0 ? bt : INFINITY;
+    return best;
+}
+
 void or_cast_bvh(void* p, const double* orig, const double* dir, int64_t n_rays,
                  int32_t* hit_id, double* hit_t) {
     const or_bvh* b = (const or_bvh*)p;
 #pragma omp parallel for schedule(dynamic, 64)
-    for (int64_t k = 0; k < n_rays; ++k) {
-        or_wray r;
-        const double* o = orig + 3 * k;
-        const double* d = dir + 3 * k;
-        wray_init(&r, o, d);
-        double inv[3] = {1.0 / d[0], 1.0 / d[1], 1.0 / d[2]};
-        int32_t best = -1;
-        double bt = INFINITY;
-        int32_t stack[128];
-        int sp = 0;
-        if (b->n_tris > 0) stack[sp++] = 0;
-        while (sp > 0) {
-            const or_bnode* nd = &b->nodes[stack[--sp]];
-            if (!box_enter(nd, o, inv, bt)) continue;
-            if (nd->left < 0) {
-                for (int32_t i = nd->first; i < nd->first + nd->count; ++i) {
-                    int32_t tid = b->order[i];
-                    double t;
-                    if (wray_hit(&r, b->tris + 9 * (int64_t)tid, &t) &&
-                        (t < bt || (t == bt && tid < best))) {
-                        bt = t;
-                        best = tid;
-                    }
-                }
-            } else if (sp + 2 <= 128) {
-                stack[sp++] = nd->right;
-                stack[sp++] = nd->left;
-            }
-        }
-        hit_id[k] = best;
-        hit_t[k] = best >= 0 ? bt : INFINITY;
-    }
+    for (int64_t k = 0; k < n_rays; ++k)
+        hit_id[k] = bvh_closest(b, orig + 3 * k, dir + 3 * k, -1, hit_t + k);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -965,5 +969,129 @@ void or_fxaa_lp(const int32_t* n_col, const int64_t* off_col, int C, const doubl
                 out[tM * nch + ch] = m + w * (q - m);
             }
         }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Path tracing into the LP buffer (Sec. 8): the paper renders the LP texels
+ * with the Path Tracing SDK at 1 sample per texel with next-event estimation,
+ * Russian roulette off, up to 3 diffuse bounces.  Here every surface is
+ * Lambertian (the scene's albedo) and the lights are the scene's directional
+ * light (radiance scale 1, as the ray-casting shading) and the sky gradient
+ * (what an escaping ray sees).  Per LP texel, with throughput beta = 1:
+ *   segment k = 0 .. D: closest hit of the ray, ignoring the triangle it
+ *     leaves (-1 for the primary ray; a planar triangle cannot be hit again);
+ *     a miss adds beta * sky(d) and ends the path;
+ *     rays leaving a surface start at p + delta n with delta = 1e-5 max(1,
+ *     max_i |p_i|) (so coplanar neighbours of the hit triangle lie behind
+ *     them) and also ignore the hit triangle;
+ *     at a hit with albedo rho and normal n facing the ray: when
+ *     cos = n . (-L) > 0 a shadow ray (p, -L), again ignoring the hit
+ *     triangle, decides visibility and a visible light adds beta rho cos;
+ *     unless k = D, the next direction is cosine-distributed about n
+ *     (r = sqrt(u1), phi = 2 pi u2, z = sqrt(1 - u1), in the orthonormal
+ *     basis of Duff et al. 2017), and beta *= rho (BRDF rho/pi times cos
+ *     over the pdf cos/pi).
+ * Random numbers: u = top 24 bits of a counter hash / 2^24, the hash being
+ * SplitMix64's output function (Steele, Lea, Flood 2014) applied to seed,
+ * texel index, and 2 k + dim in turn.
+ * Outputs: rgba per texel and a signature per texel: the hit id of each
+ * segment (-1 miss, -2 not traced) and a bit mask of the segments whose
+ * shadow ray saw the light. */
+
+static uint64_t sm64_mix(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+double or_pt_uniform(uint64_t seed, uint64_t texel, int k, int dim) {
+    uint64_t h = sm64_mix(sm64_mix(sm64_mix(seed) ^ texel) ^ (uint64_t)(2 * k + dim));
+    return (double)(h >> 40) * (1.0 / 16777216.0);
+}
+
+static void sky_rgb(const double d[3], double out[3]) {
+    double dl = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double s = 0.5 * (d[1] / dl + 1.0);
+    out[0] = (1.0 - s) * 1.0 + s * 0.5;
+    out[1] = (1.0 - s) * 1.0 + s * 0.7;
+    out[2] = (1.0 - s) * 1.0 + s * 1.0;
+}
+
+void or_path_trace(void* bvh, const float* albedo, const double* light_dir, const double* orig,
+                   const double* dir, const int64_t* texel_ids, int64_t n, uint64_t seed, int D,
+                   double* rgba, int32_t* sig, double* seg) {
+    const or_bvh* b = (const or_bvh*)bvh;
+    double L[3] = {light_dir[0], light_dir[1], light_dir[2]};
+    double ln = sqrt(L[0] * L[0] + L[1] * L[1] + L[2] * L[2]);
+    for (int k = 0; k < 3; ++k) L[k] /= ln;
+    const double toL[3] = {-L[0], -L[1], -L[2]};
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < n; ++q) {
+        int32_t* sg = sig + q * (D + 2);
+        for (int k = 0; k <= D; ++k) sg[k] = -2;
+        sg[D + 1] = 0;
+        double o[3] = {orig[3 * q], orig[3 * q + 1], orig[3 * q + 2]};
+        double d[3] = {dir[3 * q], dir[3 * q + 1], dir[3 * q + 2]};
+        double beta[3] = {1.0, 1.0, 1.0}, acc[3] = {0.0, 0.0, 0.0};
+        int32_t skip = -1;
+        for (int k = 0; k <= D; ++k) {
+            if (seg) for (int a = 0; a < 3; ++a) { seg[(q * (D + 1) + k) * 6 + a] = o[a]; seg[(q * (D + 1) + k) * 6 + 3 + a] = d[a]; }
+            double t;
+            const int32_t id = bvh_closest(b, o, d, skip, &t);
+            sg[k] = id;
+            if (id < 0) {
+                double sky[3];
+                sky_rgb(d, sky);
+                for (int a = 0; a < 3; ++a) acc[a] += beta[a] * sky[a];
+                break;
+            }
+            const float* tr = b->tris + 9 * (int64_t)id;
+            double e1[3], e2[3], nrm[3], p[3];
+            for (int a = 0; a < 3; ++a) {
+                e1[a] = (double)tr[3 + a] - tr[a];
+                e2[a] = (double)tr[6 + a] - tr[a];
+                p[a] = o[a] + t * d[a];
+            }
+            nrm[0] = e1[1] * e2[2] - e1[2] * e2[1];
+            nrm[1] = e1[2] * e2[0] - e1[0] * e2[2];
+            nrm[2] = e1[0] * e2[1] - e1[1] * e2[0];
+            double nl = sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+            for (int a = 0; a < 3; ++a) nrm[a] /= nl;
+            if (nrm[0] * d[0] + nrm[1] * d[1] + nrm[2] * d[2] > 0.0)
+                for (int a = 0; a < 3; ++a) nrm[a] = -nrm[a];
+            const float* rho = albedo + 3 * (int64_t)id;
+            const double pm = fmax(1.0, fmax(fabs(p[0]), fmax(fabs(p[1]), fabs(p[2]))));
+            for (int a = 0; a < 3; ++a) p[a] += 1e-5 * pm * nrm[a];
+            const double cosl = nrm[0] * toL[0] + nrm[1] * toL[1] + nrm[2] * toL[2];
+            if (cosl > 0.0) {
+                double ts;
+                if (bvh_closest(b, p, toL, id, &ts) < 0) {
+                    sg[D + 1] |= 1 << k;
+                    for (int a = 0; a < 3; ++a) acc[a] += beta[a] * rho[a] * cosl;
+                }
+            }
+            if (k == D) break;
+            const double u1 = or_pt_uniform(seed, (uint64_t)texel_ids[q], k, 0);
+            const double u2 = or_pt_uniform(seed, (uint64_t)texel_ids[q], k, 1);
+            const double r = sqrt(u1), phi = 2.0 * M_PI * u2;
+            const double lx = r * cos(phi), ly = r * sin(phi), lz = sqrt(fmax(0.0, 1.0 - u1));
+            const double sgn = copysign(1.0, nrm[2]);
+            const double aa = -1.0 / (sgn + nrm[2]);
+            const double bb = nrm[0] * nrm[1] * aa;
+            const double t1[3] = {1.0 + sgn * nrm[0] * nrm[0] * aa, sgn * bb, -sgn * nrm[0]};
+            const double t2[3] = {bb, sgn + nrm[1] * nrm[1] * aa, -nrm[1]};
+            for (int a = 0; a < 3; ++a) {
+                d[a] = lx * t1[a] + ly * t2[a] + lz * nrm[a];
+                o[a] = p[a];
+                beta[a] *= rho[a];
+            }
+            skip = id;
+        }
+        rgba[4 * q] = acc[0];
+        rgba[4 * q + 1] = acc[1];
+        rgba[4 * q + 2] = acc[2];
+        rgba[4 * q + 3] = 1.0;
     }
 }
