@@ -223,6 +223,27 @@ VAFR_API int vafr_session_check(vafr_session* session, void* stream);
  * eyes or empty, gaze never set), CUDA. */
 VAFR_API int vafr_render_lp(const vafr_scene* scene, vafr_session* session, int32_t eye_mask,
                    void* lp_out, int32_t* hit_ids_out, void* stream);
+/* vafr_render_lp_pt: the path-traced LP buffer (Sec. 8: the LP texels are
+ * rendered by a path tracer at one sample each, next-event estimation on, no
+ * Russian roulette, at most max_diffuse diffuse bounces; 3 is the paper's
+ * setting).  Every surface is Lambertian with the scene's albedo; lights are
+ * the scene's directional light (radiance scale 1, through shadow rays) and
+ * the sky gradient of vafr_render_lp's miss shading (seen by escaping rays).
+ * Rays leaving a surface start 1e-5 max(1, |p|_inf) off it along the normal
+ * facing the incoming ray and ignore the triangle they leave; bounce
+ * directions are cosine-distributed (basis of Duff et al. 2017).  Random
+ * numbers: uniform = top 24 bits of SplitMix64's output function applied to
+ * seed, the texel's index in column order (texels only, no guard slots) and
+ * 2 k + dim (k = bounce, dim 0/1) in turn, / 2^24.
+ *   lp_out        as vafr_render_lp; alpha 1.
+ *   path_sig_out  device or NULL, [popcount(eye_mask)][slots][max_diffuse + 2]
+ *                 int32: hit triangle id of each segment (-1 miss, -2 not
+ *                 traced), then the mask of segments whose shadow ray reached
+ *                 the light; written for texel slots only.
+ * Errors: INVALID_ARG (as vafr_render_lp, max_diffuse outside [0, 15]), CUDA. */
+VAFR_API int vafr_render_lp_pt(const vafr_scene* scene, vafr_session* session, int32_t eye_mask,
+                               void* lp_out, uint64_t seed, int32_t max_diffuse,
+                               int32_t* path_sig_out, void* stream);
 /* vafr_reconstruct: inverse-mapping pass (Sec. 3.4): every display pixel
  * (x + 0.5, y + 0.5) maps forward to (u, angle) with r = |p - gaze|,
  * e = atan(c_r r) clamped to e_max (Eq. 3), u = u(e) (Eq. 12), angle =

@@ -534,6 +534,30 @@ int vafr_render_lp(const vafr_scene* scene, vafr_session* s, int32_t eye_mask, v
     return VAFR_OK;
 }
 
+int vafr_render_lp_pt(const vafr_scene* scene, vafr_session* s, int32_t eye_mask, void* lp_out,
+                      uint64_t seed, int32_t max_diffuse, int32_t* path_sig_out, void* stream) {
+    if (!scene || !s || !lp_out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    const int all = (1 << s->desc.n_eyes) - 1;
+    if (eye_mask <= 0 || (eye_mask & ~all)) return fail(VAFR_ERR_INVALID_ARG, "bad eye_mask %d", eye_mask);
+    if (max_diffuse < 0 || max_diffuse > 15) return fail(VAFR_ERR_INVALID_ARG, "max_diffuse %d out of [0, 15]", max_diffuse);
+    if (!aligned(lp_out, 16) || !aligned(path_sig_out, 4)) return fail(VAFR_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    SmallBatch b{};
+    b.work_counter = s->d_counter;
+    const int bpp = bytes_per_px(s->desc.lp_format);
+    for (int eye = 0; eye < s->desc.n_eyes; ++eye) {
+        if (!(eye_mask & (1 << eye))) continue;
+        if (!s->gaze_set[eye]) return fail(VAFR_ERR_INVALID_ARG, "gaze of eye %d never set", eye);
+        FrameDesc f = s->fd[eye];
+        f.lp = static_cast<char*>(lp_out) + (size_t)b.n * s->n_slots * bpp;
+        f.hit_ids = path_sig_out ? path_sig_out + (size_t)b.n * s->n_slots * (max_diffuse + 2) : nullptr;
+        f.work_begin = b.total_work;
+        b.total_work += s->n_texels;
+        b.d[b.n++] = f;
+    }
+    CUDA_TRY(launch_path_lp(scene->dev, b, (unsigned long long)seed, max_diffuse, as_stream(stream), s->sms));
+    return VAFR_OK;
+}
+
 int vafr_reconstruct(vafr_session* s, int32_t eye, const void* lp, void* display_out, void* stream) {
     if (!s || !lp || !display_out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
     if (eye < 0 || eye >= s->desc.n_eyes) return fail(VAFR_ERR_INVALID_ARG, "eye %d out of range", eye);

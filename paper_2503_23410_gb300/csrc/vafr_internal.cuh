@@ -115,6 +115,11 @@ cudaError_t launch_render_gt(const SceneDev& scene, const B& batch, int variant,
                              cudaStream_t s, int num_sms);
 template <class B>
 cudaError_t launch_reconstruct(const B& batch, int variant, cudaStream_t s);
+// Path-traced LP buffers (render.cu): one path per texel, `depth` diffuse
+// bounces; FrameDesc.hit_ids, when set, receives depth + 2 ints per slot.
+template <class B>
+cudaError_t launch_path_lp(const SceneDev& scene, const B& batch, unsigned long long seed, int depth,
+                           cudaStream_t s, int num_sms);
 // FXAA inside the LP buffer of every frame with lp_aa set (fxaa.cu).
 template <class B>
 cudaError_t launch_fxaa(const B& batch, cudaStream_t s, int num_sms);

@@ -88,6 +88,7 @@ _PROTOS = {
     "vafr_render_lp": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P]),
     "vafr_reconstruct": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     "vafr_fxaa_lp": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
+    "vafr_render_lp_pt": (ctypes.c_int, [_P, _P, _I32, _P, ctypes.c_uint64, _I32, _P, _P]),
     "vafr_render_full_gt": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P]),
     "vafr_render_frame": (ctypes.c_int, [_P, _P, _P, _P]),
     "vafr_traversal_stats": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
@@ -321,6 +322,13 @@ def vafr_render_lp(scene: int, session: int, eye_mask: int, lp_out, hit_ids_out=
 
 def vafr_reconstruct(session: int, eye: int, lp, display_out, stream=None) -> None:
     _check(load().vafr_reconstruct(session, int(eye), ptr(lp), ptr(display_out), stream_ptr(stream)))
+
+
+def vafr_render_lp_pt(scene: int, session: int, eye_mask: int, lp_out, seed: int,
+                      max_diffuse: int = 3, path_sig_out=None, stream=None) -> None:
+    _check(load().vafr_render_lp_pt(scene, session, int(eye_mask), ptr(lp_out),
+                                    int(seed) & (2 ** 64 - 1), int(max_diffuse),
+                                    ptr(path_sig_out), stream_ptr(stream)))
 
 
 def vafr_fxaa_lp(session: int, eye: int, lp, lp_out, stream=None) -> None:
