@@ -47,6 +47,7 @@ FP32_LANES_PER_SM = 128
 OPS_PER_BOX = 18
 OPS_PER_TRI = 58
 OPS_PER_RAY = 60
+PT_DIFFUSE = 3        # the paper's maximum diffuse bounces (Sec. 8.1)
 
 
 def _dist():
@@ -245,6 +246,7 @@ def run_gpu(args, w):
     lp_fmt = V.FMT_RGBA16F if w.lp_fp16 else V.FMT_RGBA32F
     dp_fmt = V.FMT_RGBA16F if w.display_fp16 else V.FMT_RGBA32F
     fxaa = bool(args.fxaa)
+    pt = bool(args.pt)
     acuity = {"paper": None, "anisotropic": V.vafr_acuity_anisotropic,
               "display9": lambda: V.vafr_acuity_display_limited(9.0),
               "display18": lambda: V.vafr_acuity_display_limited(18.0)}[args.acuity]
@@ -265,7 +267,10 @@ def run_gpu(args, w):
             V.vafr_set_gaze(sess, e, g[e, 0], g[e, 1])
         if evs:
             evs[0].record()
-        V.vafr_render_lp(scene, sess, mask, lp)
+        if pt:                                     # path-traced LP buffer (Sec. 8)
+            V.vafr_render_lp_pt(scene, sess, mask, lp, seed=k, max_diffuse=PT_DIFFUSE)
+        else:
+            V.vafr_render_lp(scene, sess, mask, lp)
         if evs:
             evs[1].record()
         if fxaa:                                   # FXAA inside the LP buffer (Sec. 3.4)
@@ -282,7 +287,10 @@ def run_gpu(args, w):
         if evs:
             evs[0].record()
         for e in range(eyes):
-            V.vafr_render_full_gt(scene, sess, e, disp[e * dp_b:])
+            if pt:
+                V.vafr_render_full_gt_pt(scene, sess, e, disp[e * dp_b:], seed=k, max_diffuse=PT_DIFFUSE)
+            else:
+                V.vafr_render_full_gt(scene, sess, e, disp[e * dp_b:])
         if evs:
             evs[1].record()
 
@@ -326,42 +334,59 @@ def run_gpu(args, w):
         #      computes while frame k crosses the CPU-GPU link.
         e2e_steps = max(3, min(args.steps, args.e2e_steps))
         host = [torch.empty(eyes * dp_b, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
-        for k in range(2):
-            V.vafr_render_frame(scene, sess, host[0])
-        torch.cuda.synchronize()
-        te = time.perf_counter()
-        for k in range(e2e_steps):
-            g = d.gaze[k % nf]
-            for e in range(eyes):
-                V.vafr_set_gaze(sess, e, g[e, 0], g[e, 1])
-            V.vafr_render_frame(scene, sess, host[0])
-        e2e_sync_s = time.perf_counter() - te
-        lps = [torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda") for _ in range(2)]
-        aas = [torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda") for _ in range(2)] if fxaa else None
-        streams = [torch.cuda.Stream() for _ in range(2)]
-        batches = [V.vafr_batch_create(scene, 2 * eyes) for _ in range(2)]
+        if pt:
+            # (a) only: the path-traced frame, then one device-to-host copy
+            def pt_e2e(k):
+                g = d.gaze[k % nf]
+                for e in range(eyes):
+                    V.vafr_set_gaze(sess, e, g[e, 0], g[e, 1])
+                frame(k)
+                host[0].copy_(disp)
+                torch.cuda.synchronize()
+            for k in range(2):
+                pt_e2e(k)
+            te = time.perf_counter()
+            for k in range(e2e_steps):
+                pt_e2e(k)
+            e2e_sync_s = e2e_s = time.perf_counter() - te
+        else:
+            for k in range(2):
+                V.vafr_render_frame(scene, sess, host[0])
+            torch.cuda.synchronize()
+            te = time.perf_counter()
+            for k in range(e2e_steps):
+                g = d.gaze[k % nf]
+                for e in range(eyes):
+                    V.vafr_set_gaze(sess, e, g[e, 0], g[e, 1])
+                V.vafr_render_frame(scene, sess, host[0])
+            e2e_sync_s = time.perf_counter() - te
+        if not pt:
+            lps = [torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda") for _ in range(2)]
+            aas = [torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda") for _ in range(2)] if fxaa else None
+            streams = [torch.cuda.Stream() for _ in range(2)]
+            batches = [V.vafr_batch_create(scene, 2 * eyes) for _ in range(2)]
 
-        def frames_for(slot):
-            if fxaa:
-                return [(sess, e, lps[slot][e * lp_b:], host[slot][e * dp_b:], aas[slot][e * lp_b:])
-                        for e in range(eyes)]
-            return [(sess, e, lps[slot][e * lp_b:], host[slot][e * dp_b:]) for e in range(eyes)]
-        for k in range(4):
-            V.vafr_batch_render(batches[k % 2], frames_for(k % 2), stream=streams[k % 2])
-        torch.cuda.synchronize()
-        te = time.perf_counter()
-        for k in range(e2e_steps):
-            slot = k % 2
-            streams[slot].synchronize()          # frame k - 2 has landed in host[slot]
-            g = d.gaze[k % nf]
-            for e in range(eyes):
-                V.vafr_set_gaze(sess, e, g[e, 0], g[e, 1])
-            V.vafr_batch_render(batches[slot], frames_for(slot), stream=streams[slot])
-        for st_ in streams:
-            st_.synchronize()
-        e2e_s = time.perf_counter() - te
-        for bt in batches:
-            V.vafr_batch_destroy(bt)
+            def frames_for(slot):
+                if fxaa:
+                    return [(sess, e, lps[slot][e * lp_b:], host[slot][e * dp_b:], aas[slot][e * lp_b:])
+                            for e in range(eyes)]
+                return [(sess, e, lps[slot][e * lp_b:], host[slot][e * dp_b:]) for e in range(eyes)]
+            for k in range(4):
+                V.vafr_batch_render(batches[k % 2], frames_for(k % 2), stream=streams[k % 2])
+            torch.cuda.synchronize()
+            te = time.perf_counter()
+            for k in range(e2e_steps):
+                slot = k % 2
+                streams[slot].synchronize()          # frame k - 2 has landed in host[slot]
+                g = d.gaze[k % nf]
+                for e in range(eyes):
+                    V.vafr_set_gaze(sess, e, g[e, 0], g[e, 1])
+                V.vafr_batch_render(batches[slot], frames_for(slot), stream=streams[slot])
+            for st_ in streams:
+                st_.synchronize()
+            e2e_s = time.perf_counter() - te
+            for bt in batches:
+                V.vafr_batch_destroy(bt)
     assert V.vafr_session_check(sess) == 0
 
     step_ms = per.sum(1)
@@ -381,6 +406,21 @@ def run_gpu(args, w):
     rays = stats["rays"] * eyes
     ops = (stats["box_tests"] * OPS_PER_BOX + stats["tri_tests"] * OPS_PER_TRI
            + stats["rays"] * OPS_PER_RAY) * eyes
+    pt_rays = None
+    if pt:
+        # rays per path from one signature run (segments traced + shadow rays
+        # cast); the ops estimate scales the primary rays' per-ray cost
+        sig = torch.empty((eyes * (lp_b // (8 if w.lp_fp16 else 16)), PT_DIFFUSE + 2), dtype=torch.int32,
+                          device="cuda")
+        sig.fill_(-2)
+        V.vafr_render_lp_pt(scene, sess, mask, lp, seed=0, max_diffuse=PT_DIFFUSE, path_sig_out=sig)
+        sg = sig.cpu().numpy()
+        sg = sg[sg[:, 0] >= -1]                      # texel slots (guard slots stay -2)
+        seg = int((sg[:, :PT_DIFFUSE + 1] >= -1).sum())
+        shadow = int(np.unpackbits(((sg[:, -1] >> 16) & 0xff).astype(np.uint8)).sum())
+        pt_rays = seg + shadow
+        ops = ops / max(rays, 1) * pt_rays
+        rays = pt_rays
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = n_sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12      # T FP32 ops/s
@@ -392,7 +432,8 @@ def run_gpu(args, w):
     csrc = os.path.join(ROOT, "paper_2503_23410_gb300", "csrc")
     tr_render, _ = _traffic("render_lp", os.path.join(csrc, "render.cu"))
     tr_recon, _ = _traffic("reconstruct", os.path.join(csrc, "reconstruct.cu"))
-    roof_render = {"kernel": "k_render_lp", "bound": "alu", "achieved": ops / render_s / 1e12,
+    roof_render = {"kernel": "k_path_lp" if pt else "k_render_lp", "bound": "alu",
+                   "achieved": ops / render_s / 1e12,
                    "peak": alu_peak, "unit": "TFLOP/s", "frac": ops / render_s / 1e12 / alu_peak,
                    "traffic": tr_render,
                    "peak_kind": f"derived: {n_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
@@ -417,6 +458,8 @@ def run_gpu(args, w):
         "config": {"workload": _workload_desc(w),
                    "l2": "flushed between steps (256 MiB write outside the per-step events)",
                    "acuity": args.acuity, "lp_fxaa": fxaa,
+                   "shading": f"path traced, 1 path/texel, NEE, {PT_DIFFUSE} diffuse bounces" if pt
+                   else "ray cast, Lambert + ambient",
                    "parallelism": f"replicas x{ws} (independent sessions, no collective)"},
         "fps": 1e3 / float(step_ms.mean()),
         "p50_frame_ms": float(np.percentile(step_ms, 50)),
@@ -431,8 +474,10 @@ def run_gpu(args, w):
         "roofline_other": roof_recon if dominant is roof_render else roof_render,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * eyes,
                 "d2h_bytes_per_step": dp_b * eyes, "steps": e2e_steps,
-                "path": "vafr_batch_render into pinned host frames, 2 frames in flight on 2 "
-                        "streams (C ABI); gaze passed by value each step",
+                "path": ("vafr_render_lp_pt + vafr_reconstruct, then one device-to-host copy into "
+                         "pinned memory, synchronous per frame") if pt else
+                        ("vafr_batch_render into pinned host frames, 2 frames in flight on 2 "
+                         "streams (C ABI); gaze passed by value each step"),
                 "sync_per_frame_value": e2e_sync_value,
                 "sync_per_frame_path": "vafr_render_frame into pinned host memory, one "
                                        "synchronous call per frame"},
@@ -631,6 +676,9 @@ def main():
     ap.add_argument("--acuity", default="paper", choices=["paper", "anisotropic", "display9", "display18"],
                     help="acuity model: the paper's pivots, the Sec. 9 anisotropy, or the Sec. 3.3 "
                          "display-limited curves at 9 / 18 cpd")
+    ap.add_argument("--pt", action="store_true",
+                    help="path-trace the LP buffer (Sec. 8: 1 path per texel, NEE, 3 diffuse bounces) "
+                         "and compare with the path-traced full-resolution GT")
     ap.add_argument("--fxaa", action="store_true",
                     help="run the LP-space FXAA pass (Sec. 3.4) inside each timed frame")
     args = ap.parse_args()

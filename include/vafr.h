@@ -238,12 +238,20 @@ VAFR_API int vafr_render_lp(const vafr_scene* scene, vafr_session* session, int3
  *   lp_out        as vafr_render_lp; alpha 1.
  *   path_sig_out  device or NULL, [popcount(eye_mask)][slots][max_diffuse + 2]
  *                 int32: hit triangle id of each segment (-1 miss, -2 not
- *                 traced), then the mask of segments whose shadow ray reached
- *                 the light; written for texel slots only.
+ *                 traced), then a mask: bit k = segment k's shadow ray
+ *                 reached the light, bit 16 + k = a shadow ray was cast there
+ *                 (n . -L > 0); written for texel slots only.
  * Errors: INVALID_ARG (as vafr_render_lp, max_diffuse outside [0, 15]), CUDA. */
 VAFR_API int vafr_render_lp_pt(const vafr_scene* scene, vafr_session* session, int32_t eye_mask,
                                void* lp_out, uint64_t seed, int32_t max_diffuse,
                                int32_t* path_sig_out, void* stream);
+/* vafr_render_full_gt_pt: the path-traced GT: one path per display pixel
+ * centre with vafr_render_lp_pt's estimator (random numbers keyed by the
+ * pixel index y width + x), written to display_out (display_format).
+ * Errors: INVALID_ARG, CUDA. */
+VAFR_API int vafr_render_full_gt_pt(const vafr_scene* scene, vafr_session* session, int32_t eye,
+                                    void* display_out, uint64_t seed, int32_t max_diffuse,
+                                    void* stream);
 /* vafr_reconstruct: inverse-mapping pass (Sec. 3.4): every display pixel
  * (x + 0.5, y + 0.5) maps forward to (u, angle) with r = |p - gaze|,
  * e = atan(c_r r) clamped to e_max (Eq. 3), u = u(e) (Eq. 12), angle =

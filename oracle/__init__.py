@@ -406,7 +406,8 @@ def path_trace_lp(scene_tris, albedo, light_dir, layout, width, height, fov_v_de
                   segments: bool = False):
     """Path-traced LP texels (Sec. 8).  Returns (rgba (n, 4), signature (n, D + 2)
     [, segment rays (n, D + 1, 6)]): signature = hit id per segment (-1 miss,
-    -2 not traced) then the mask of segments whose shadow ray saw the light."""
+    -2 not traced) then a mask: bit k = segment k's shadow ray saw the light,
+    bit 16 + k = a shadow ray was cast."""
     if texels is None:
         texels = np.arange(layout.total, dtype=np.int64)
     tex = _c(texels, np.int64)

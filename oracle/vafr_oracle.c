@@ -996,8 +996,8 @@ void or_fxaa_lp(const int32_t* n_col, const int64_t* off_col, int C, const doubl
  * SplitMix64's output function (Steele, Lea, Flood 2014) applied to seed,
  * texel index, and 2 k + dim in turn.
  * Outputs: rgba per texel and a signature per texel: the hit id of each
- * segment (-1 miss, -2 not traced) and a bit mask of the segments whose
- * shadow ray saw the light. */
+ * segment (-1 miss, -2 not traced) and a mask: bit k = segment k's shadow
+ * ray saw the light, bit 16 + k = a shadow ray was cast there. */
 
 static uint64_t sm64_mix(uint64_t z) {
     z += 0x9E3779B97F4A7C15ull;
@@ -1067,6 +1067,7 @@ void or_path_trace(void* bvh, const float* albedo, const double* light_dir, cons
             const double cosl = nrm[0] * toL[0] + nrm[1] * toL[1] + nrm[2] * toL[2];
             if (cosl > 0.0) {
                 double ts;
+                sg[D + 1] |= 1 << (16 + k);
                 if (bvh_closest(b, p, toL, id, &ts) < 0) {
                     sg[D + 1] |= 1 << k;
                     for (int a = 0; a < 3; ++a) acc[a] += beta[a] * rho[a] * cosl;

@@ -614,6 +614,25 @@ int vafr_render_full_gt(const vafr_scene* scene, vafr_session* s, int32_t eye, v
     return VAFR_OK;
 }
 
+int vafr_render_full_gt_pt(const vafr_scene* scene, vafr_session* s, int32_t eye, void* display_out,
+                           uint64_t seed, int32_t max_diffuse, void* stream) {
+    if (!scene || !s || !display_out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    if (eye < 0 || eye >= s->desc.n_eyes) return fail(VAFR_ERR_INVALID_ARG, "eye %d out of range", eye);
+    if (max_diffuse < 0 || max_diffuse > 15) return fail(VAFR_ERR_INVALID_ARG, "max_diffuse %d out of [0, 15]", max_diffuse);
+    if (!aligned(display_out, 16)) return fail(VAFR_ERR_INVALID_ARG, "display must be 16-byte aligned");
+    SmallBatch b{};
+    b.work_counter = s->d_counter;
+    FrameDesc f = s->fd[eye];
+    f.disp = display_out;
+    f.hit_ids = nullptr;
+    f.work_begin = 0;
+    b.d[0] = f;
+    b.n = 1;
+    b.total_work = gt_items(f);
+    CUDA_TRY(launch_path_gt(scene->dev, b, (unsigned long long)seed, max_diffuse, as_stream(stream), s->sms));
+    return VAFR_OK;
+}
+
 int vafr_render_frame(const vafr_scene* scene, vafr_session* s, void* display_out, void* stream) {
     if (!scene || !s || !display_out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
     const int eyes = s->desc.n_eyes;

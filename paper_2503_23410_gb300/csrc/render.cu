@@ -510,7 +510,8 @@ __device__ __forceinline__ float3 face_normal(const SceneDev& sc, const Ray& r, 
 }
 
 // One path from the primary ray r; returns the radiance, fills sig (depth + 2
-// ints: hit id per segment, -1 miss, -2 not traced; then the shadow mask).
+// ints: hit id per segment, -1 miss, -2 not traced; then the shadow mask: bit k
+// = segment k's shadow ray reached the light, bit 16 + k = it was cast).
 template <int ORDER>
 __device__ float3 trace_path(const SceneDev& sc, Ray r, unsigned long long seed_h, unsigned long long texel,
                              int depth, int* sig, unsigned* fault) {
@@ -540,6 +541,7 @@ __device__ float3 trace_path(const SceneDev& sc, Ray r, unsigned long long seed_
         const float4 rho = __ldg(sc.albedo + h.id);
         const float cosl = fmaf(n.x, tlx, fmaf(n.y, tly, n.z * tlz));
         if (cosl > 0.0f) {
+            mask |= 1u << (16 + k);   // a shadow ray was cast
             Ray s;
             s.ox = px; s.oy = py; s.oz = pz;
             s.dx = tlx; s.dy = tly; s.dz = tlz;
@@ -608,6 +610,42 @@ k_path_lp(const SceneDev sc, const __grid_constant__ B b, unsigned long long see
             store_px(f.lp, t, f.lp_fmt, v);
             if (glo >= 0) store_px(f.lp, glo, f.lp_fmt, v);
             if (ghi >= 0) store_px(f.lp, ghi, f.lp_fmt, v);
+        }
+    }
+}
+
+// Full-resolution path-traced GT: one path per display pixel centre (random
+// numbers keyed by the pixel index y W + x), written straight to the display.
+template <int TPB, int FETCH, int ORDER, class B>
+__global__ void __launch_bounds__(TPB)
+k_path_gt(const SceneDev sc, const __grid_constant__ B b, unsigned long long seed, int depth) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long seed_h = sm64_mix(seed);
+    while (true) {
+        unsigned long long base = 0ull;
+        if (lane == 0) base = atomicAdd(b.work_counter, (unsigned long long)FETCH);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((long long)base >= b.total_work) break;
+#pragma unroll 1
+        for (int k = 0; k < FETCH; k += 32) {
+            const long long w = (long long)base + k + lane;
+            if (w >= b.total_work) break;
+            const FrameDesc& f = b.d[find_frame(b, w, false)];
+            const long long local = w - f.work_begin;
+            const long long tile = local >> 5;
+            const int tiles_x = (f.W + 7) >> 3;
+            const int x = (int)(tile % tiles_x) * 8 + (lane & 7);
+            const int y = (int)(tile / tiles_x) * 4 + (lane >> 3);
+            if (x >= f.W || y >= f.H) continue;
+            const float cx = f.cr * ((float)x + 0.5f - 0.5f * (float)f.W);
+            const float cy = f.cr * (0.5f * (float)f.H - ((float)y + 0.5f));
+            Ray r;
+            world_ray(f, cx, cy, r);
+            const long long p = (long long)y * f.W + x;
+            unsigned fault = 0u;
+            const float3 c = trace_path<ORDER>(sc, r, seed_h, (unsigned long long)p, depth, nullptr, &fault);
+            if (fault) atomicOr(f.status, fault);
+            store_px(f.disp, p, f.disp_fmt, make_float4(c.x, c.y, c.z, 1.0f));
         }
     }
 }
@@ -695,12 +733,12 @@ cudaError_t launch_one(const SceneDev& sc, const B& b, cudaStream_t s, int num_s
     return cudaGetLastError();
 }
 
-template <class B>
+template <bool GT, class B>
 cudaError_t launch_path_one(const SceneDev& sc, const B& b, unsigned long long seed, int depth, cudaStream_t s,
                             int num_sms) {
     if (b.total_work <= 0) return cudaSuccess;
     constexpr int TPB = 128, FETCH = 32;
-    auto kern = k_path_lp<TPB, FETCH, 1, B>;
+    auto kern = GT ? k_path_gt<TPB, FETCH, 1, B> : k_path_lp<TPB, FETCH, 1, B>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB, 0);
     if (e != cudaSuccess) return e;
@@ -746,8 +784,15 @@ cudaError_t launch_render_gt(const SceneDev& scene, const B& batch, int variant,
 template <class B>
 cudaError_t launch_path_lp(const SceneDev& scene, const B& batch, unsigned long long seed, int depth,
                            cudaStream_t s, int num_sms) {
-    return launch_path_one(scene, batch, seed, depth, s, num_sms);
+    return launch_path_one<false>(scene, batch, seed, depth, s, num_sms);
 }
+template <class B>
+cudaError_t launch_path_gt(const SceneDev& scene, const B& batch, unsigned long long seed, int depth,
+                           cudaStream_t s, int num_sms) {
+    return launch_path_one<true>(scene, batch, seed, depth, s, num_sms);
+}
+template cudaError_t launch_path_gt<SmallBatch>(const SceneDev&, const SmallBatch&, unsigned long long, int,
+                                                cudaStream_t, int);
 template cudaError_t launch_path_lp<SmallBatch>(const SceneDev&, const SmallBatch&, unsigned long long, int,
                                                 cudaStream_t, int);
 template cudaError_t launch_path_lp<BigBatch>(const SceneDev&, const BigBatch&, unsigned long long, int,

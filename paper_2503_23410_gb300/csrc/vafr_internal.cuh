@@ -120,6 +120,9 @@ cudaError_t launch_reconstruct(const B& batch, int variant, cudaStream_t s);
 template <class B>
 cudaError_t launch_path_lp(const SceneDev& scene, const B& batch, unsigned long long seed, int depth,
                            cudaStream_t s, int num_sms);
+template <class B>
+cudaError_t launch_path_gt(const SceneDev& scene, const B& batch, unsigned long long seed, int depth,
+                           cudaStream_t s, int num_sms);
 // FXAA inside the LP buffer of every frame with lp_aa set (fxaa.cu).
 template <class B>
 cudaError_t launch_fxaa(const B& batch, cudaStream_t s, int num_sms);

@@ -89,6 +89,7 @@ _PROTOS = {
     "vafr_reconstruct": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     "vafr_fxaa_lp": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     "vafr_render_lp_pt": (ctypes.c_int, [_P, _P, _I32, _P, ctypes.c_uint64, _I32, _P, _P]),
+    "vafr_render_full_gt_pt": (ctypes.c_int, [_P, _P, _I32, _P, ctypes.c_uint64, _I32, _P]),
     "vafr_render_full_gt": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P]),
     "vafr_render_frame": (ctypes.c_int, [_P, _P, _P, _P]),
     "vafr_traversal_stats": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
@@ -329,6 +330,12 @@ def vafr_render_lp_pt(scene: int, session: int, eye_mask: int, lp_out, seed: int
     _check(load().vafr_render_lp_pt(scene, session, int(eye_mask), ptr(lp_out),
                                     int(seed) & (2 ** 64 - 1), int(max_diffuse),
                                     ptr(path_sig_out), stream_ptr(stream)))
+
+
+def vafr_render_full_gt_pt(scene: int, session: int, eye: int, display_out, seed: int,
+                           max_diffuse: int = 3, stream=None) -> None:
+    _check(load().vafr_render_full_gt_pt(scene, session, int(eye), ptr(display_out),
+                                         int(seed) & (2 ** 64 - 1), int(max_diffuse), stream_ptr(stream)))
 
 
 def vafr_fxaa_lp(session: int, eye: int, lp, lp_out, stream=None) -> None:

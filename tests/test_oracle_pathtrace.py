@@ -60,7 +60,7 @@ def test_plane_direct_light_only(layout):
     cos = -(np.array([0.0, 0.0, -1.0]) @ LIGHT)                     # plane faces the camera (-z)
     np.testing.assert_allclose(rgba[hit, :3], np.broadcast_to(RHO.astype(float) * cos, (hit.sum(), 3)),
                                rtol=1e-12)
-    assert np.all(sig[hit, -1] == 1)
+    assert np.all(sig[hit, -1] == 1 | (1 << 16))        # cast and visible at segment 0
 
 
 def test_plane_one_bounce_expectation(layout):
@@ -122,5 +122,6 @@ def test_occluder_shadows_direct_light(layout):
     shadowed = ids >= 0
     assert 0.001 < shadowed.mean() < 0.5
     lit = (sig[on_plane, -1] & 1) == 1
+    assert np.all(sig[on_plane, -1] & (1 << 16))
     assert np.array_equal(lit, ~shadowed)
     assert np.all(rgba[on_plane][shadowed, :3] == 0.0)
