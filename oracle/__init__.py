@@ -79,6 +79,7 @@ def lib():
                                             P, ctypes.c_int, P, i64, P]
         L.or_morton.argtypes = [P, i64, P]
         L.or_fxaa_lp.argtypes = [P, P, ctypes.c_int, P, ctypes.c_int, P]
+        L.or_reproject_lp.argtypes = [P, ctypes.c_double, P, P, P, ctypes.c_int, i64, P, P, P, P, P, P]
         L.or_path_trace.argtypes = [P, P, P, P, P, P, i64, ctypes.c_uint64, ctypes.c_int, P, P, P]
         L.or_pt_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int]
         L.or_pt_uniform.restype = ctypes.c_double
@@ -421,6 +422,43 @@ def path_trace_lp(scene_tris, albedo, light_dir, layout, width, height, fov_v_de
                         _p(tex), n, int(seed) & (2**64 - 1), int(max_diffuse), _p(rgba), _p(sig),
                         _p(seg) if seg is not None else None)
     return (rgba, sig, seg) if segments else (rgba, sig)
+
+
+def reproject_lp(layout: Layout, width, height, fov_v_deg, gaze_left, pose_left, gaze_right,
+                 pose_right, left_t, left_rgba, acuity: Optional[Acuity] = None,
+                 e_max: float = PAPER_E_MAX):
+    """VaFR_Rep's forward grid warp of a left LP buffer (hit distances `left_t`,
+    inf on a miss, and colours) to the right eye.  Returns (right rgba (n, 4),
+    winning left triangle per right texel, -1 for a hole)."""
+    a = acuity or Acuity()
+    vl = _view(width, height, fov_v_deg, gaze_left, pose_left)
+    vr = _view(width, height, fov_v_deg, gaze_right, pose_right)
+    lt = _c(left_t, np.float64)
+    lc = _c(left_rgba, np.float64)
+    out = np.empty((layout.total, 4))
+    tri = np.empty(layout.total, np.int32)
+    lib().or_reproject_lp(a.ptr, float(e_max), _p(_c(layout.e_col, np.float64)), _p(layout.n_col),
+                          _p(layout.off_col), layout.n_cols, layout.total, ctypes.byref(vl),
+                          ctypes.byref(vr), _p(lt), _p(lc), _p(out), _p(tri))
+    return out, tri
+
+
+def render_lp_rep(scene_tris, albedo, light_dir, layout, width, height, fov_v_deg, gazes, poses,
+                  bvh: Optional[CpuBVH] = None):
+    """VaFR_Rep (Sec. 5.1): the left eye cast, the right eye warped from it with
+    its holes cast.  Returns (left rgba, right rgba, right triangle / -1)."""
+    b = bvh or CpuBVH(scene_tris)
+    rgba_l, ids_l, t_l, _, _ = render_lp(scene_tris, albedo, light_dir, layout, width, height,
+                                         fov_v_deg, gazes[0], poses[0], bvh=b)
+    t_l = np.where(ids_l >= 0, t_l, np.inf)
+    right, tri = reproject_lp(layout, width, height, fov_v_deg, gazes[0], poses[0], gazes[1],
+                              poses[1], t_l, rgba_l)
+    holes = np.flatnonzero(tri < 0)
+    if holes.size:
+        rgba_h, _, _, _, _ = render_lp(scene_tris, albedo, light_dir, layout, width, height,
+                                       fov_v_deg, gazes[1], poses[1], texels=holes, bvh=b)
+        right[holes] = rgba_h
+    return rgba_l, right, tri
 
 
 def render_gt(scene_tris, albedo, light_dir, width, height, fov_v_deg, pose, pixels=None,

@@ -1096,3 +1096,210 @@ void or_path_trace(void* bvh, const float* albedo, const double* light_dir, cons
         rgba[4 * q + 3] = 1.0;
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* VaFR_Rep (Sec. 5.1): the right eye's LP buffer by forward grid warping of
+ * the left eye's LP buffer (after Wissmann et al. 2020, but directly from the
+ * LP buffer), disocclusions re-rendered.  The paper names the method only;
+ * the steps here:
+ *  vertices  every left texel's hit point P = o + t d (t from the left cast;
+ *            a miss is a point at infinity in direction d), seen from the
+ *            right eye: camera coordinates, then the right eye's forward map
+ *            (Eq. 3 with its own gaze, e clamped to e_max, Eq. 12):
+ *            U = u(e) - 1/2 (texel column c sits at U = c), F = angle / 360
+ *            (texel j of column c sits at F = (j + 1/2)/n_c); depth =
+ *            distance to the right eye (1e30 for points at infinity).
+ *  mesh      the strip between columns c and c+1 (rings of n and n' texels
+ *            at angles (j + 1/2)/n) is zipped: walking both rings by angle
+ *            (ring c first on equal angles), each step of ring c from a_j to
+ *            a_j+1 makes the triangle (a_j, a_j+1, b_k) with b_k the last
+ *            ring-(c+1) vertex before a_j+1, k = max{k : (2k+1) n <
+ *            (2j+3) n'}, and each step of ring c+1 from b_k to b_k+1 makes
+ *            (b_k, b_k+1, a_j), j = max{j : (2j+1) n' <= (2k+3) n} (indices
+ *            modulo the ring sizes); the triangles tile the strip.  Texel t
+ *            owns triangle 2 t (its step towards column c+1) and 2 t + 1 (its
+ *            step as the outer ring of the strip towards c-1).
+ *  reject    a triangle with a vertex behind the right eye, mixing hits and
+ *            misses, or whose largest finite depth exceeds 1.1 x its
+ *            smallest (it would stretch over a depth discontinuity).
+ *  raster    in the (U, F) plane; a triangle spanning more than half a turn
+ *            in F is unwrapped (+1 on its low vertices) and drawn at F and
+ *            F - 1.  Column c covers [min, max] of the triangle's edge
+ *            crossings of U = c; its rows j with (j + 1/2)/n_c inside are
+ *            covered (boundaries included).  Depth and colour are
+ *            interpolated barycentrically in (U, F); the nearest depth wins,
+ *            ties to the lower triangle id.
+ *  holes     right texels no triangle covers are ray cast like any texel.
+ * Here: right rgba and winning triangle (-1 = hole) per right texel. */
+
+#define OR_REP_DEPTH_RATIO 1.1
+
+typedef struct { double U, F, z; int ok, inf; } or_rvert;
+
+static void rep_vertex(const or_acuity* a, double e_max, const or_view* vl, const or_view* vr,
+                       double e_c, int32_t n_c, int64_t j, double t, or_rvert* out) {
+    double x, y, o[3], d[3];
+    texel_screen_point(vl, e_c, n_c, j, &x, &y);
+    view_ray(vl, x, y, o, d);
+    double P[3];
+    out->inf = !(t < INFINITY);
+    for (int k = 0; k < 3; ++k) P[k] = out->inf ? d[k] : o[k] + t * d[k] - vr->pose[4 * k + 3];
+    /* camera coordinates of the right eye: R^T P (pose columns are the camera axes) */
+    double pc[3];
+    for (int k = 0; k < 3; ++k)
+        pc[k] = vr->pose[k] * P[0] + vr->pose[4 + k] * P[1] + vr->pose[8 + k] * P[2];
+    out->ok = pc[2] > 0.0;
+    if (!out->ok) return;
+    double cr = view_cr(vr);
+    double sx = 0.5 * vr->width + pc[0] / pc[2] / cr, sy = 0.5 * vr->height - pc[1] / pc[2] / cr;
+    double dx = sx - vr->x0, dy = sy - vr->y0;
+    double e = atan(cr * sqrt(dx * dx + dy * dy)) / OR_DEG;
+    if (e > e_max) e = e_max;
+    out->U = or_u_of_e(a, e) - 0.5;
+    double ang = atan2(dy, dx) / OR_DEG;
+    if (ang < 0.0) ang += 360.0;
+    out->F = ang / 360.0;
+    out->z = out->inf ? 1e30 : sqrt(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+}
+
+/* barycentric weights of (u, f) in triangle v; returns 0 if degenerate */
+static int rep_bary(const or_rvert* v[3], const double F3[3], double u, double f, double w[3]) {
+    double x1 = v[1]->U - v[0]->U, y1 = F3[1] - F3[0];
+    double x2 = v[2]->U - v[0]->U, y2 = F3[2] - F3[0];
+    double det = x1 * y2 - x2 * y1;
+    if (det == 0.0) return 0;
+    double px = u - v[0]->U, py = f - F3[0];
+    w[1] = (px * y2 - x2 * py) / det;
+    w[2] = (x1 * py - px * y1) / det;
+    w[0] = 1.0 - w[1] - w[2];
+    return 1;
+}
+
+/* Triangle s of texel (c, j): s = 0 its segment's fan triangle towards
+ * column c+1, s = 1 towards column c-1.  Returns 0 if it does not exist. */
+static int rep_triangle(const int32_t* n_col, const int64_t* off_col, int C, int c, int64_t j, int s,
+                        int64_t tv[3]) {
+    const int c2 = s == 0 ? c + 1 : c - 1;
+    if (c2 < 0 || c2 >= C) return 0;
+    const int64_t n = n_col[c], n2 = n_col[c2];
+    int64_t k;
+    if (s == 0) {          /* ring c is the inner ring: k = max{k : (2k+1) n < (2j+3) n2} */
+        const int64_t w = ((2 * j + 3) * n2 + n - 1) / n - 2;
+        k = w >= 0 ? w / 2 : -1;
+    } else {               /* ring c is the outer ring: k = max{k : (2k+1) n <= (2j+3) n2} */
+        const int64_t q = ((2 * j + 3) * n2) / n;
+        k = q >= 1 ? (q - 1) / 2 : -1;
+    }
+    k = ((k % n2) + n2) % n2;
+    tv[0] = off_col[c] + j;
+    tv[1] = off_col[c] + (j + 1) % n;
+    tv[2] = off_col[c2] + k;
+    return 1;
+}
+
+static void rep_raster(const or_rvert* V, const int64_t tv[3], int32_t tid, const int32_t* n_col,
+                       const int64_t* off_col, int C, double* zbest, int32_t* right_tri) {
+    const or_rvert* v[3] = {&V[tv[0]], &V[tv[1]], &V[tv[2]]};
+    if (!v[0]->ok || !v[1]->ok || !v[2]->ok) return;
+    int ninf = v[0]->inf + v[1]->inf + v[2]->inf;
+    if (ninf != 0 && ninf != 3) return;
+    double zlo = fmin(v[0]->z, fmin(v[1]->z, v[2]->z)), zhi = fmax(v[0]->z, fmax(v[1]->z, v[2]->z));
+    if (ninf == 0 && zhi > OR_REP_DEPTH_RATIO * zlo) return;
+    double F3[3] = {v[0]->F, v[1]->F, v[2]->F};
+    double flo = fmin(F3[0], fmin(F3[1], F3[2])), fhi = fmax(F3[0], fmax(F3[1], F3[2]));
+    int copies = 1;
+    if (fhi - flo > 0.5) {
+        for (int q = 0; q < 3; ++q) if (F3[q] < 0.5) F3[q] += 1.0;
+        copies = 2;
+    }
+    double ulo = fmin(v[0]->U, fmin(v[1]->U, v[2]->U)), uhi = fmax(v[0]->U, fmax(v[1]->U, v[2]->U));
+    int c0 = (int)ceil(ulo), c1 = (int)floor(uhi);
+    if (c0 < 0) c0 = 0;
+    if (c1 > C - 1) c1 = C - 1;
+    for (int cr = c0; cr <= c1; ++cr) {
+        double lo = INFINITY, hi = -INFINITY;
+        for (int e = 0; e < 3; ++e) {
+            int p = e, q = (e + 1) % 3;
+            double up = v[p]->U - cr, uq = v[q]->U - cr;
+            if (up * uq > 0.0) continue;
+            if (v[p]->U == v[q]->U) {
+                lo = fmin(lo, fmin(F3[p], F3[q]));
+                hi = fmax(hi, fmax(F3[p], F3[q]));
+                continue;
+            }
+            double f = F3[p] + (cr - v[p]->U) / (v[q]->U - v[p]->U) * (F3[q] - F3[p]);
+            lo = fmin(lo, f);
+            hi = fmax(hi, f);
+        }
+        if (!(lo <= hi)) continue;
+        for (int cp = 0; cp < copies; ++cp) {
+            double sh = cp ? -1.0 : 0.0;
+            int64_t n = n_col[cr];
+            int64_t j0 = (int64_t)ceil((lo + sh) * n - 0.5), j1 = (int64_t)floor((hi + sh) * n - 0.5);
+            if (j0 < 0) j0 = 0;
+            if (j1 > n - 1) j1 = n - 1;
+            for (int64_t jj = j0; jj <= j1; ++jj) {
+                double f = ((double)jj + 0.5) / (double)n - sh, w[3];
+                if (!rep_bary(v, F3, (double)cr, f, w)) continue;
+                double z = w[0] * v[0]->z + w[1] * v[1]->z + w[2] * v[2]->z;
+                int64_t k = off_col[cr] + jj;
+                if (z < zbest[k] || (z == zbest[k] && tid < right_tri[k])) {
+                    zbest[k] = z;
+                    right_tri[k] = tid;
+                }
+            }
+        }
+    }
+}
+
+void or_reproject_lp(const or_acuity* a, double e_max, const double* e_col, const int32_t* n_col,
+                     const int64_t* off_col, int C, int64_t n_tex, const or_view* vl, const or_view* vr,
+                     const double* left_t, const double* left_rgba, double* right_rgba,
+                     int32_t* right_tri) {
+    or_rvert* V = (or_rvert*)malloc(sizeof(or_rvert) * (size_t)n_tex);
+    double* zbest = (double*)malloc(sizeof(double) * (size_t)n_tex);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int c = 0; c < C; ++c)
+        for (int64_t j = 0; j < n_col[c]; ++j)
+            rep_vertex(a, e_max, vl, vr, e_col[c], n_col[c], j, left_t[off_col[c] + j], &V[off_col[c] + j]);
+    for (int64_t k = 0; k < n_tex; ++k) { zbest[k] = INFINITY; right_tri[k] = -1; }
+    /* serial raster: the z-test with its id tie rule is order-independent */
+    for (int c = 0; c < C; ++c) {
+        for (int64_t j = 0; j < n_col[c]; ++j) {
+            for (int s = 0; s < 2; ++s) {
+                int64_t tv[3];
+                if (!rep_triangle(n_col, off_col, C, c, j, s, tv)) continue;
+                const int32_t tid = (int32_t)(2 * (off_col[c] + j) + s);
+                rep_raster(V, tv, tid, n_col, off_col, C, zbest, right_tri);
+            }
+        }
+    }
+    /* resolve: colours of the winning triangles */
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int cr = 0; cr < C; ++cr) {
+        for (int64_t jj = 0; jj < n_col[cr]; ++jj) {
+            int64_t k = off_col[cr] + jj;
+            for (int ch = 0; ch < 4; ++ch) right_rgba[4 * k + ch] = 0.0;
+            int32_t tid = right_tri[k];
+            if (tid < 0) continue;
+            int64_t ia = tid / 2;
+            int s = tid % 2;
+            int c = 0;
+            { int lo = 0, hi = C - 1; while (lo < hi) { int mid = (lo + hi + 1) / 2; if (off_col[mid] <= ia) lo = mid; else hi = mid - 1; } c = lo; }
+            int64_t tv[3];
+            rep_triangle(n_col, off_col, C, c, ia - off_col[c], s, tv);
+            const or_rvert* v[3] = {&V[tv[0]], &V[tv[1]], &V[tv[2]]};
+            double F3[3] = {v[0]->F, v[1]->F, v[2]->F};
+            double flo = fmin(F3[0], fmin(F3[1], F3[2])), fhi = fmax(F3[0], fmax(F3[1], F3[2]));
+            if (fhi - flo > 0.5) for (int q = 0; q < 3; ++q) if (F3[q] < 0.5) F3[q] += 1.0;
+            double f = ((double)jj + 0.5) / (double)n_col[cr], w[3];
+            if (!rep_bary(v, F3, (double)cr, f, w) || w[0] < -1e-6 || w[1] < -1e-6 || w[2] < -1e-6)
+                rep_bary(v, F3, (double)cr, f + 1.0, w);
+            for (int ch = 0; ch < 4; ++ch)
+                right_rgba[4 * k + ch] = w[0] * left_rgba[4 * tv[0] + ch] + w[1] * left_rgba[4 * tv[1] + ch] +
+                                         w[2] * left_rgba[4 * tv[2] + ch];
+        }
+    }
+    free(V);
+    free(zbest);
+}

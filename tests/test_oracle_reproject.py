@@ -1,0 +1,81 @@
+"""Pins of the oracle's VaFR_Rep reprojection (Sec. 5.1: the right eye's LP
+buffer warped from the left eye's): the identity warp, exactness on flat
+colour, and where holes may appear."""
+
+import numpy as np
+
+import oracle
+from workloads.views import eye_pair_poses, look_at_pose
+
+W, H, FOV = 1280, 720, 100.0
+HEAD = look_at_pose((0.0, 0.2, -3.0), (0, 0, 0))
+
+
+def _plane_scene(albedo=(0.6, 0.4, 0.2), half=50.0, z=2.0):
+    a, b, c, d = [-half, -half, z], [half, -half, z], [half, half, z], [-half, half, z]
+    tris = np.array([[a, b, c], [a, c, d]], np.float32)
+    alb = np.float32([albedo, albedo])
+    return tris, alb, np.float32([-0.4, -1.0, 0.6]) / np.linalg.norm([-0.4, -1.0, 0.6])
+
+
+def _left(tris, alb, L, lay, gaze, pose):
+    rgba, ids, t, _, _ = oracle.render_lp(tris, alb, L, lay, W, H, FOV, gaze, pose)
+    return rgba, np.where(ids >= 0, t, np.inf)
+
+
+def test_identity_warp_reproduces_the_buffer(layout):
+    # right view == left view: every right texel centre is a left vertex
+    rng = np.random.default_rng(0)
+    tris = rng.uniform(-1, 1, (64, 3, 3)).astype(np.float32)
+    alb = rng.uniform(0.2, 1, (64, 3)).astype(np.float32)
+    L = np.float32([0, -1, 0])
+    gaze = (600.5, 300.25)
+    rgba, t = _left(tris, alb, L, layout, gaze, HEAD)
+    right, tri = oracle.reproject_lp(layout, W, H, FOV, gaze, HEAD, gaze, HEAD, t, rgba)
+    ok = tri >= 0
+    assert ok.mean() > 0.95
+    np.testing.assert_allclose(right[ok], rgba[ok], atol=1e-9)
+
+
+def test_flat_colour_plane_is_exact_and_holes_stay_at_the_rim(layout):
+    tris, alb, L = _plane_scene()
+    poses = eye_pair_poses(HEAD, 0.063)
+    gaze = (640.0, 360.0)
+    rgba, t = _left(tris, alb, L, layout, gaze, poses[0])
+    right, tri = oracle.reproject_lp(layout, W, H, FOV, gaze, poses[0], gaze, poses[1], t, rgba)
+    direct, ids, _, _, _ = oracle.render_lp(tris, alb, L, layout, W, H, FOV, gaze, poses[1])
+    ok = (tri >= 0) & (ids >= 0)
+    # one flat-lit colour: the interpolation of equal colours is exact
+    np.testing.assert_allclose(right[ok], direct[ok], atol=1e-12)
+    holes = np.flatnonzero(tri < 0)
+    assert holes.size < 0.02 * layout.total
+    col = np.repeat(np.arange(layout.n_cols), layout.n_col)
+    # holes only where the left view ends (outer rim) and at the two polar
+    # centres, which no ring triangle covers: the right eye's own innermost
+    # ring and the image of the left eye's centre
+    assert np.sum(col[holes] < layout.n_cols - 8) <= 8
+
+
+def test_occluder_opens_holes_beside_it(layout):
+    # a box-like occluder in front of the plane: the right eye sees plane
+    # texels the left eye does not (disocclusion) -> holes next to the object
+    tris, alb, L = _plane_scene()
+    q = np.array([[-0.3, -0.3, 0.5], [0.3, -0.3, 0.5], [0.3, 0.3, 0.5], [-0.3, 0.3, 0.5]], np.float32)
+    occ = np.array([[q[0], q[1], q[2]], [q[0], q[2], q[3]]], np.float32)
+    tris = np.concatenate([tris, occ])
+    alb = np.concatenate([alb, np.float32([[0.9, 0.9, 0.9]] * 2)])
+    poses = eye_pair_poses(HEAD, 0.063)
+    gaze = (640.0, 380.0)
+    rgba, t = _left(tris, alb, L, layout, gaze, poses[0])
+    right, tri = oracle.reproject_lp(layout, W, H, FOV, gaze, poses[0], gaze, poses[1], t, rgba)
+    direct, ids, _, _, _ = oracle.render_lp(tris, alb, L, layout, W, H, FOV, gaze, poses[1])
+    inner = np.repeat(np.arange(layout.n_cols), layout.n_col) < layout.n_cols - 8
+    holes = (tri < 0) & inner
+    assert holes.sum() > 50
+    # most holes are background the left eye could not see (disocclusion);
+    # the rest are the object's rim, whose triangles span the depth jump
+    assert np.mean(ids[holes] <= 1) > 0.5
+    # elsewhere the warp agrees with the direct render, edges of the object aside
+    ok = (tri >= 0) & inner
+    agree = np.all(np.abs(right[ok] - direct[ok]) < 1e-9, axis=1)
+    assert agree.mean() > 0.99
