@@ -252,6 +252,36 @@ VAFR_API int vafr_render_lp_pt(const vafr_scene* scene, vafr_session* session, i
 VAFR_API int vafr_render_full_gt_pt(const vafr_scene* scene, vafr_session* session, int32_t eye,
                                     void* display_out, uint64_t seed, int32_t max_diffuse,
                                     void* stream);
+/* VaFR_Rep (Sec. 5.1): the right eye's LP buffer by forward grid warping of
+ * the left eye's (the reprojection of Wissmann et al. 2020, directly from the
+ * LP buffer), disocclusions ray cast.  Each left texel's hit point (a miss:
+ * the point at infinity along its ray) is mapped through the right eye's
+ * forward map to (U, F) = (u - 1/2, angle fraction); each pair of
+ * neighbouring LP rings is zipped by angle into triangles; triangles with a
+ * vertex behind the right eye, mixing hits and misses, spread over more than
+ * 1.1x in depth, or spanning more than 64 columns or a quarter turn are
+ * dropped; the rest are rasterised at the right texel centres with a
+ * nearest-depth test (ties: lower triangle id) and their three left colours
+ * interpolated.  Needs a binocular session with both gazes set; session-owned
+ * scratch (~62 MB at the default acuity) is allocated on first use, so calls
+ * on one session must not overlap.
+ * vafr_render_lp_rep: the whole mode: casts the left eye (eye 0) into
+ *   lp_out[0], warps it into lp_out[1] and casts the right eye's holes.
+ *   lp_out as vafr_render_lp with both eyes.
+ * vafr_reproject_lp: the warp alone, from a caller's left LP buffer and hit
+ *   distances (left_depth: device, one float per slot, +inf on a miss; only
+ *   texel slots are read); holes are left unwritten in right_lp_out and
+ *   marked -1 in right_tri_out (device or NULL, one int32 per slot: the
+ *   winning left triangle, 2 t + {0: towards the next column, 1: towards the
+ *   previous one} for left texel t in column order).
+ * vafr_rep_hole_count: holes of the last warp on this session (synchronises
+ *   `stream`).
+ * Errors: INVALID_ARG (NULL, unaligned, not binocular, gaze not set), OOM, CUDA. */
+VAFR_API int vafr_render_lp_rep(const vafr_scene* scene, vafr_session* session, void* lp_out,
+                                void* stream);
+VAFR_API int vafr_reproject_lp(vafr_session* session, const void* left_lp, const float* left_depth,
+                               void* right_lp_out, int32_t* right_tri_out, void* stream);
+VAFR_API int vafr_rep_hole_count(vafr_session* session, int64_t* holes, void* stream);
 /* vafr_reconstruct: inverse-mapping pass (Sec. 3.4): every display pixel
  * (x + 0.5, y + 0.5) maps forward to (u, angle) with r = |p - gaze|,
  * e = atan(c_r r) clamped to e_max (Eq. 3), u = u(e) (Eq. 12), angle =

@@ -1120,8 +1120,11 @@ void or_path_trace(void* bvh, const float* albedo, const double* light_dir, cons
  *            owns triangle 2 t (its step towards column c+1) and 2 t + 1 (its
  *            step as the outer ring of the strip towards c-1).
  *  reject    a triangle with a vertex behind the right eye, mixing hits and
- *            misses, or whose largest finite depth exceeds 1.1 x its
- *            smallest (it would stretch over a depth discontinuity).
+ *            misses, whose largest finite depth exceeds 1.1 x its smallest
+ *            (it would stretch over a depth discontinuity), or spanning more
+ *            than 64 columns or (after unwrapping) a quarter turn: such
+ *            slivers only arise around a polar centre and are left to the
+ *            hole pass.
  *  raster    in the (U, F) plane; a triangle spanning more than half a turn
  *            in F is unwrapped (+1 on its low vertices) and drawn at F and
  *            F - 1.  Column c covers [min, max] of the triangle's edge
@@ -1133,6 +1136,8 @@ void or_path_trace(void* bvh, const float* albedo, const double* light_dir, cons
  * Here: right rgba and winning triangle (-1 = hole) per right texel. */
 
 #define OR_REP_DEPTH_RATIO 1.1
+#define OR_REP_MAX_U_SPAN 64.0
+#define OR_REP_MAX_F_SPAN 0.25
 
 typedef struct { double U, F, z; int ok, inf; } or_rvert;
 
@@ -1205,14 +1210,18 @@ static void rep_raster(const or_rvert* V, const int64_t tv[3], int32_t tid, cons
     if (ninf != 0 && ninf != 3) return;
     double zlo = fmin(v[0]->z, fmin(v[1]->z, v[2]->z)), zhi = fmax(v[0]->z, fmax(v[1]->z, v[2]->z));
     if (ninf == 0 && zhi > OR_REP_DEPTH_RATIO * zlo) return;
+    double ulo = fmin(v[0]->U, fmin(v[1]->U, v[2]->U)), uhi = fmax(v[0]->U, fmax(v[1]->U, v[2]->U));
+    if (uhi - ulo > OR_REP_MAX_U_SPAN) return;
     double F3[3] = {v[0]->F, v[1]->F, v[2]->F};
     double flo = fmin(F3[0], fmin(F3[1], F3[2])), fhi = fmax(F3[0], fmax(F3[1], F3[2]));
     int copies = 1;
     if (fhi - flo > 0.5) {
         for (int q = 0; q < 3; ++q) if (F3[q] < 0.5) F3[q] += 1.0;
         copies = 2;
+        flo = fmin(F3[0], fmin(F3[1], F3[2]));
+        fhi = fmax(F3[0], fmax(F3[1], F3[2]));
     }
-    double ulo = fmin(v[0]->U, fmin(v[1]->U, v[2]->U)), uhi = fmax(v[0]->U, fmax(v[1]->U, v[2]->U));
+    if (fhi - flo > OR_REP_MAX_F_SPAN) return;
     int c0 = (int)ceil(ulo), c1 = (int)floor(uhi);
     if (c0 < 0) c0 = 0;
     if (c1 > C - 1) c1 = C - 1;
@@ -1293,7 +1302,7 @@ void or_reproject_lp(const or_acuity* a, double e_max, const double* e_col, cons
             double flo = fmin(F3[0], fmin(F3[1], F3[2])), fhi = fmax(F3[0], fmax(F3[1], F3[2]));
             if (fhi - flo > 0.5) for (int q = 0; q < 3; ++q) if (F3[q] < 0.5) F3[q] += 1.0;
             double f = ((double)jj + 0.5) / (double)n_col[cr], w[3];
-            if (!rep_bary(v, F3, (double)cr, f, w) || w[0] < -1e-6 || w[1] < -1e-6 || w[2] < -1e-6)
+            if (!rep_bary(v, F3, (double)cr, f, w) || w[0] < -0.25 || w[1] < -0.25 || w[2] < -0.25)
                 rep_bary(v, F3, (double)cr, f + 1.0, w);
             for (int ch = 0; ch < 4; ++ch)
                 right_rgba[4 * k + ch] = w[0] * left_rgba[4 * tv[0] + ch] + w[1] * left_rgba[4 * tv[1] + ch] +

@@ -114,6 +114,12 @@ struct vafr_session {
     void* lp_internal = nullptr;       // render_frame's LP buffer
     void* lp_aa_internal = nullptr;    // render_frame's FXAA output
     float* d_luma = nullptr;           // FXAA scratch: [n_eyes][n_slots] lumas
+    // VaFR_Rep scratch (first use): left depth, warped vertices, right z-buffer, holes
+    float* d_rep_depth = nullptr;
+    float4* d_rep_vert = nullptr;
+    unsigned long long* d_rep_zbuf = nullptr;
+    int2* d_rep_holes = nullptr;
+    unsigned* d_rep_count = nullptr;
     void* disp_internal = nullptr;     // render_frame's device display for host output
     int recon_variant = 0;
     int render_variant = 0;
@@ -125,6 +131,11 @@ struct vafr_session {
         cudaFree(lp_internal);
         cudaFree(lp_aa_internal);
         cudaFree(d_luma);
+        cudaFree(d_rep_depth);
+        cudaFree(d_rep_vert);
+        cudaFree(d_rep_zbuf);
+        cudaFree(d_rep_holes);
+        cudaFree(d_rep_count);
         cudaFree(disp_internal);
     }
 };
@@ -199,6 +210,7 @@ void fill_static(vafr_session* s, int eye) {
     f.lp = nullptr;
     f.lp_aa = nullptr;
     f.luma = nullptr;
+    f.depth = nullptr;
     f.disp = nullptr;
     f.hit_ids = nullptr;
 }
@@ -555,6 +567,96 @@ int vafr_render_lp_pt(const vafr_scene* scene, vafr_session* s, int32_t eye_mask
         b.d[b.n++] = f;
     }
     CUDA_TRY(launch_path_lp(scene->dev, b, (unsigned long long)seed, max_diffuse, as_stream(stream), s->sms));
+    return VAFR_OK;
+}
+
+// ---- VaFR_Rep ------------------------------------------------------------------------
+static int rep_scratch(vafr_session* s) {
+    if (s->d_rep_vert) return VAFR_OK;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_rep_depth, sizeof(float) * s->n_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_rep_vert, sizeof(float4) * s->n_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_rep_zbuf, sizeof(unsigned long long) * s->n_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_rep_holes, sizeof(int2) * s->n_texels);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_rep_count, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        cudaFree(s->d_rep_depth); cudaFree(s->d_rep_vert); cudaFree(s->d_rep_zbuf);
+        cudaFree(s->d_rep_holes); cudaFree(s->d_rep_count);
+        s->d_rep_depth = nullptr; s->d_rep_vert = nullptr; s->d_rep_zbuf = nullptr;
+        s->d_rep_holes = nullptr; s->d_rep_count = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? VAFR_ERR_OOM : VAFR_ERR_CUDA, "reprojection scratch: %s",
+                    cudaGetErrorString(e));
+    }
+    return VAFR_OK;
+}
+
+static int rep_check(vafr_session* s) {
+    if (s->desc.n_eyes != 2) return fail(VAFR_ERR_INVALID_ARG, "reprojection needs a binocular session");
+    if (!s->gaze_set[0] || !s->gaze_set[1]) return fail(VAFR_ERR_INVALID_ARG, "gaze of both eyes must be set");
+    return rep_scratch(s);
+}
+
+int vafr_reproject_lp(vafr_session* s, const void* left_lp, const float* left_depth, void* right_lp_out,
+                      int32_t* right_tri_out, void* stream) {
+    if (!s || !left_lp || !left_depth || !right_lp_out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    if (!aligned(left_lp, 16) || !aligned(right_lp_out, 16) || !aligned(left_depth, 4) || !aligned(right_tri_out, 4))
+        return fail(VAFR_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    if (int rc = rep_check(s)) return rc;
+    SmallBatch b{};
+    b.d[0] = s->fd[0];
+    b.d[0].lp = const_cast<void*>(left_lp);
+    b.d[0].depth = const_cast<float*>(left_depth);
+    b.d[1] = s->fd[1];
+    b.d[1].lp = right_lp_out;
+    b.n = 2;
+    RepScratch r{s->d_rep_vert, s->d_rep_zbuf, s->d_rep_holes, s->d_rep_count, right_tri_out};
+    CUDA_TRY(launch_reproject(b, r, as_stream(stream), s->sms));
+    return VAFR_OK;
+}
+
+int vafr_render_lp_rep(const vafr_scene* scene, vafr_session* s, void* lp_out, void* stream) {
+    if (!scene || !s || !lp_out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    if (!aligned(lp_out, 16)) return fail(VAFR_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    if (int rc = rep_check(s)) return rc;
+    cudaStream_t st = as_stream(stream);
+    const size_t eye_bytes = (size_t)s->n_slots * bytes_per_px(s->desc.lp_format);
+    void* right = static_cast<char*>(lp_out) + eye_bytes;
+    // 1. the left eye cast, with hit distances
+    SmallBatch b{};
+    b.work_counter = s->d_counter;
+    b.d[0] = s->fd[0];
+    b.d[0].lp = lp_out;
+    b.d[0].depth = s->d_rep_depth;
+    b.d[0].work_begin = 0;
+    b.n = 1;
+    b.total_work = s->n_texels;
+    CUDA_TRY(launch_render_lp(scene->dev, b, s->render_variant, st, s->sms));
+    // 2. warp into the right eye
+    SmallBatch w{};
+    w.d[0] = b.d[0];
+    w.d[1] = s->fd[1];
+    w.d[1].lp = right;
+    w.n = 2;
+    RepScratch r{s->d_rep_vert, s->d_rep_zbuf, s->d_rep_holes, s->d_rep_count, nullptr};
+    CUDA_TRY(launch_reproject(w, r, st, s->sms));
+    // 3. cast the right eye's holes
+    SmallBatch h{};
+    h.work_counter = s->d_counter;
+    h.d[0] = s->fd[1];
+    h.d[0].lp = right;
+    h.d[0].work = s->d_rep_holes;
+    h.n = 1;
+    CUDA_TRY(launch_render_list(scene->dev, h, s->d_rep_count, st, s->sms));
+    return VAFR_OK;
+}
+
+int vafr_rep_hole_count(vafr_session* s, int64_t* holes, void* stream) {
+    if (!s || !holes) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    if (!s->d_rep_count) { *holes = 0; return VAFR_OK; }
+    unsigned h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, s->d_rep_count, sizeof(h), cudaMemcpyDeviceToHost, as_stream(stream)));
+    CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    *holes = h;
     return VAFR_OK;
 }
 

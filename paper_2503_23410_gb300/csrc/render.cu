@@ -457,6 +457,33 @@ k_render_lp(const SceneDev sc, const __grid_constant__ B b) {
             const unsigned fault = traverse<WIDE, false, ORDER>(sc, r, h, nullptr, nullptr, nullptr);
             if (fault) { atomicOr(f.status, fault); h.leaf = -1; h.id = -1; }
             store_lp(f, t, glo, ghi, shade(sc, r, h), h.leaf >= 0 ? h.id : -1);
+            if (f.depth) f.depth[t] = h.leaf >= 0 ? h.t : INFINITY;
+        }
+    }
+}
+
+// Ray casting of the work items listed in frame 0's work table, as many as
+// *count says (a device-side count: the reprojection's holes).
+__global__ void __launch_bounds__(128)
+k_render_list(const SceneDev sc, const __grid_constant__ SmallBatch b, const unsigned* count) {
+    const int lane = threadIdx.x & 31;
+    const long long total = (long long)*count;
+    const FrameDesc& f = b.d[0];
+    while (true) {
+        unsigned long long base = 0ull;
+        if (lane == 0) base = atomicAdd(b.work_counter, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((long long)base >= total) break;
+        const long long w = (long long)base + lane;
+        if (w < total) {
+            Ray r;
+            int glo, ghi;
+            const int t = lp_ray(f, (int)w, r, glo, ghi);
+            ray_setup(r);
+            Hit h;
+            const unsigned fault = traverse<4, false, 1>(sc, r, h, nullptr, nullptr, nullptr);
+            if (fault) { atomicOr(f.status, fault); h.leaf = -1; h.id = -1; }
+            store_lp(f, t, glo, ghi, shade(sc, r, h), h.leaf >= 0 ? h.id : -1);
         }
     }
 }
@@ -802,6 +829,19 @@ template cudaError_t launch_render_lp<SmallBatch>(const SceneDev&, const SmallBa
 template cudaError_t launch_render_lp<BigBatch>(const SceneDev&, const BigBatch&, int, cudaStream_t, int);
 template cudaError_t launch_render_gt<SmallBatch>(const SceneDev&, const SmallBatch&, int, cudaStream_t, int);
 template cudaError_t launch_render_gt<BigBatch>(const SceneDev&, const BigBatch&, int, cudaStream_t, int);
+
+cudaError_t launch_render_list(const SceneDev& scene, const SmallBatch& batch, const unsigned* count,
+                               cudaStream_t s, int num_sms) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_list, 128, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    e = cudaMemsetAsync(batch.work_counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_render_list<<<(unsigned)(per_sm * num_sms), 128, 0, s>>>(scene, batch, count);
+    count_launch(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_render_stats(const SceneDev& scene, const SmallBatch& batch,
                                 unsigned long long* counters, cudaStream_t s, int num_sms) {

@@ -73,6 +73,7 @@ struct FrameDesc {
     void* lp;
     void* lp_aa;            // FXAA output (read by reconstruct) or nullptr: no FXAA
     float* luma;            // FXAA scratch: luma of every LP slot
+    float* depth;           // hit distance per LP slot (inf on a miss) or nullptr
     void* disp;
     int* hit_ids;
     unsigned* status;
@@ -123,6 +124,20 @@ cudaError_t launch_path_lp(const SceneDev& scene, const B& batch, unsigned long 
 template <class B>
 cudaError_t launch_path_gt(const SceneDev& scene, const B& batch, unsigned long long seed, int depth,
                            cudaStream_t s, int num_sms);
+// Ray casting of an explicit list of (slot, column) work items whose count
+// is read from device memory (render.cu): the reprojection's holes.
+cudaError_t launch_render_list(const SceneDev& scene, const SmallBatch& batch, const unsigned* count,
+                               cudaStream_t s, int num_sms);
+// VaFR_Rep reprojection (reproject.cu): left frame d[0] (lp, depth) warped into
+// right frame d[1] (lp written, holes appended to `holes` / `count`).
+struct RepScratch {
+    float4* vert;                 // [left slots] (U, F, depth, flags) seen from the right eye
+    unsigned long long* zbuf;     // [right slots] (depth bits << 32) | triangle id
+    int2* holes;                  // [right texels] (slot, column) left uncovered
+    unsigned* count;              // number of holes
+    int* tri_out;                 // [right slots] winning triangle id / -1, or nullptr
+};
+cudaError_t launch_reproject(const SmallBatch& batch, const RepScratch& r, cudaStream_t s, int num_sms);
 // FXAA inside the LP buffer of every frame with lp_aa set (fxaa.cu).
 template <class B>
 cudaError_t launch_fxaa(const B& batch, cudaStream_t s, int num_sms);

@@ -90,6 +90,9 @@ _PROTOS = {
     "vafr_fxaa_lp": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     "vafr_render_lp_pt": (ctypes.c_int, [_P, _P, _I32, _P, ctypes.c_uint64, _I32, _P, _P]),
     "vafr_render_full_gt_pt": (ctypes.c_int, [_P, _P, _I32, _P, ctypes.c_uint64, _I32, _P]),
+    "vafr_render_lp_rep": (ctypes.c_int, [_P, _P, _P, _P]),
+    "vafr_reproject_lp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "vafr_rep_hole_count": (ctypes.c_int, [_P, _P, _P]),
     "vafr_render_full_gt": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P]),
     "vafr_render_frame": (ctypes.c_int, [_P, _P, _P, _P]),
     "vafr_traversal_stats": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
@@ -336,6 +339,22 @@ def vafr_render_full_gt_pt(scene: int, session: int, eye: int, display_out, seed
                            max_diffuse: int = 3, stream=None) -> None:
     _check(load().vafr_render_full_gt_pt(scene, session, int(eye), ptr(display_out),
                                          int(seed) & (2 ** 64 - 1), int(max_diffuse), stream_ptr(stream)))
+
+
+def vafr_render_lp_rep(scene: int, session: int, lp_out, stream=None) -> None:
+    _check(load().vafr_render_lp_rep(scene, session, ptr(lp_out), stream_ptr(stream)))
+
+
+def vafr_reproject_lp(session: int, left_lp, left_depth, right_lp_out, right_tri_out=None,
+                      stream=None) -> None:
+    _check(load().vafr_reproject_lp(session, ptr(left_lp), ptr(left_depth), ptr(right_lp_out),
+                                    ptr(right_tri_out), stream_ptr(stream)))
+
+
+def vafr_rep_hole_count(session: int, stream=None) -> int:
+    out = ctypes.c_int64()
+    _check(load().vafr_rep_hole_count(session, ctypes.byref(out), stream_ptr(stream)))
+    return int(out.value)
 
 
 def vafr_fxaa_lp(session: int, eye: int, lp, lp_out, stream=None) -> None:
