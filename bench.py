@@ -247,6 +247,9 @@ def run_gpu(args, w):
     dp_fmt = V.FMT_RGBA16F if w.display_fp16 else V.FMT_RGBA32F
     fxaa = bool(args.fxaa)
     pt = bool(args.pt)
+    rep = bool(args.rep)
+    if rep and (pt or len(w.displays[0].poses) != 2):
+        raise SystemExit("--rep needs a binocular workload and ray casting")
     acuity = {"paper": None, "anisotropic": V.vafr_acuity_anisotropic,
               "display9": lambda: V.vafr_acuity_display_limited(9.0),
               "display18": lambda: V.vafr_acuity_display_limited(18.0)}[args.acuity]
@@ -269,6 +272,8 @@ def run_gpu(args, w):
             evs[0].record()
         if pt:                                     # path-traced LP buffer (Sec. 8)
             V.vafr_render_lp_pt(scene, sess, mask, lp, seed=k, max_diffuse=PT_DIFFUSE)
+        elif rep:                                  # VaFR_Rep: left cast, right warped (Sec. 5.1)
+            V.vafr_render_lp_rep(scene, sess, lp)
         else:
             V.vafr_render_lp(scene, sess, mask, lp)
         if evs:
@@ -334,8 +339,8 @@ def run_gpu(args, w):
         #      computes while frame k crosses the CPU-GPU link.
         e2e_steps = max(3, min(args.steps, args.e2e_steps))
         host = [torch.empty(eyes * dp_b, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
-        if pt:
-            # (a) only: the path-traced frame, then one device-to-host copy
+        if pt or rep:
+            # (a) only: the frame as timed above, then one device-to-host copy
             def pt_e2e(k):
                 g = d.gaze[k % nf]
                 for e in range(eyes):
@@ -360,7 +365,7 @@ def run_gpu(args, w):
                     V.vafr_set_gaze(sess, e, g[e, 0], g[e, 1])
                 V.vafr_render_frame(scene, sess, host[0])
             e2e_sync_s = time.perf_counter() - te
-        if not pt:
+        if not (pt or rep):
             lps = [torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda") for _ in range(2)]
             aas = [torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda") for _ in range(2)] if fxaa else None
             streams = [torch.cuda.Stream() for _ in range(2)]
@@ -460,6 +465,7 @@ def run_gpu(args, w):
                    "acuity": args.acuity, "lp_fxaa": fxaa,
                    "shading": f"path traced, 1 path/texel, NEE, {PT_DIFFUSE} diffuse bounces" if pt
                    else "ray cast, Lambert + ambient",
+                   "binocular_mode": "VaFR_Rep (right eye warped)" if rep else "VaFR_Dup",
                    "parallelism": f"replicas x{ws} (independent sessions, no collective)"},
         "fps": 1e3 / float(step_ms.mean()),
         "p50_frame_ms": float(np.percentile(step_ms, 50)),
@@ -474,8 +480,9 @@ def run_gpu(args, w):
         "roofline_other": roof_recon if dominant is roof_render else roof_render,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * eyes,
                 "d2h_bytes_per_step": dp_b * eyes, "steps": e2e_steps,
-                "path": ("vafr_render_lp_pt + vafr_reconstruct, then one device-to-host copy into "
-                         "pinned memory, synchronous per frame") if pt else
+                "path": ("the timed frame (vafr_render_lp_pt or vafr_render_lp_rep, then "
+                         "vafr_reconstruct), then one device-to-host copy into pinned memory, "
+                         "synchronous per frame") if (pt or rep) else
                         ("vafr_batch_render into pinned host frames, 2 frames in flight on 2 "
                          "streams (C ABI); gaze passed by value each step"),
                 "sync_per_frame_value": e2e_sync_value,
@@ -679,6 +686,9 @@ def main():
     ap.add_argument("--pt", action="store_true",
                     help="path-trace the LP buffer (Sec. 8: 1 path per texel, NEE, 3 diffuse bounces) "
                          "and compare with the path-traced full-resolution GT")
+    ap.add_argument("--rep", action="store_true",
+                    help="VaFR_Rep (Sec. 5.1): the right eye's LP buffer warped from the left eye's, "
+                         "holes ray cast (binocular workloads)")
     ap.add_argument("--fxaa", action="store_true",
                     help="run the LP-space FXAA pass (Sec. 3.4) inside each timed frame")
     args = ap.parse_args()
