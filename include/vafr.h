@@ -61,6 +61,7 @@ extern "C" {
 
 #define VAFR_MAX_PIVOTS 9
 #define VAFR_MAX_BATCH  128   /* frame-eyes per batched launch */
+#define VAFR_MAX_POINT_LIGHTS 256   /* vafr_scene_set_point_lights */
 
 typedef struct vafr_scene vafr_scene;
 typedef struct vafr_session vafr_session;
@@ -150,6 +151,17 @@ VAFR_API int64_t vafr_kernel_launch_count(void);
  * non-finite light), OOM, CUDA. */
 VAFR_API int vafr_build_scene(const float* tri_xyz, const float* albedo_rgb, int64_t n_tris,
                      const float light_dir[3], void* stream, vafr_scene** out);
+/* Point lights for the direct-shading pipelines (ray-cast LP and GT, the
+ * deferred path): each adds albedo * rgb * max(0, n . l) / |x - p|^2 at a
+ * hit point p (l the unit vector to the light at x, n the geometric normal
+ * facing the ray), unshadowed, on top of the Lambert + ambient directional
+ * light -- the many-light scenes the paper's deferred tests use (Sec. 5.2).
+ * Path tracing ignores them.  Replaces any previous set; n = 0 removes them.
+ *   pos_xyz, rgb  host, n x 3 floats; rgb >= 0.
+ * Errors: INVALID_ARG (n outside [0, VAFR_MAX_POINT_LIGHTS], NULL arrays,
+ * non-finite values), OOM, CUDA. */
+VAFR_API int vafr_scene_set_point_lights(vafr_scene* scene, int32_t n, const float* pos_xyz,
+                                         const float* rgb);
 VAFR_API int vafr_scene_destroy(vafr_scene* scene);
 /* Triangle count and device bytes held by the scene. */
 VAFR_API int vafr_scene_info(const vafr_scene* scene, int64_t* n_tris, int64_t* device_bytes);
@@ -282,6 +294,33 @@ VAFR_API int vafr_render_lp_rep(const vafr_scene* scene, vafr_session* session, 
 VAFR_API int vafr_reproject_lp(vafr_session* session, const void* left_lp, const float* left_depth,
                                void* right_lp_out, int32_t* right_tri_out, void* stream);
 VAFR_API int vafr_rep_hole_count(vafr_session* session, int64_t* holes, void* stream);
+/* Deferred pipeline (Sec. 3.4, Sec. 5: the G-buffer pass runs at native
+ * resolution and the lighting in the LP buffer).  The G-buffer here is a
+ * visibility buffer rasterised in CUDA: per display pixel the 64-bit key
+ * (FP32 hit distance bits << 32) | triangle id of the closest triangle,
+ * ~0 for the sky.  Its coverage test is the watertight test of the pixel-
+ * centre ray and the depth test keeps the smallest (distance, id), so the
+ * buffer equals the GT cast's closest hits (triangle parts closer than 1e-4
+ * scene units to the camera plane are not drawn).  Triangles are rasterised
+ * one thread each over their clipped bounding box, boxes above 256 pixels by
+ * a whole block.  Scene-owned scratch (~24 B per triangle) is allocated on
+ * first use, so deferred calls on one scene must not overlap.
+ * vafr_render_vbuffer: the G-buffer pass of one eye into vbuf_out (device,
+ *   height x width uint64, 8-byte aligned).
+ * vafr_shade_lp_deferred: LP lighting: each LP texel takes the shading of the
+ *   display pixel under its screen point (clamped to the display); lp_out as
+ *   one eye of vafr_render_lp.
+ * vafr_shade_full_deferred: full-resolution lighting of every pixel (the
+ *   deferred GT) into display_out.
+ * Shading is vafr_render_lp's (Lambert + ambient, point lights, sky).
+ * Errors: INVALID_ARG (NULL, bad eye, unaligned, gaze not set for the LP
+ * pass), OOM, CUDA. */
+VAFR_API int vafr_render_vbuffer(const vafr_scene* scene, vafr_session* session, int32_t eye,
+                                 uint64_t* vbuf_out, void* stream);
+VAFR_API int vafr_shade_lp_deferred(const vafr_scene* scene, vafr_session* session, int32_t eye,
+                                    const uint64_t* vbuf, void* lp_out, void* stream);
+VAFR_API int vafr_shade_full_deferred(const vafr_scene* scene, vafr_session* session, int32_t eye,
+                                      const uint64_t* vbuf, void* display_out, void* stream);
 /* vafr_reconstruct: inverse-mapping pass (Sec. 3.4): every display pixel
  * (x + 0.5, y + 0.5) maps forward to (u, angle) with r = |p - gaze|,
  * e = atan(c_r r) clamped to e_max (Eq. 3), u = u(e) (Eq. 12), angle =

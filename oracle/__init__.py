@@ -79,6 +79,7 @@ def lib():
                                             P, ctypes.c_int, P, i64, P]
         L.or_morton.argtypes = [P, i64, P]
         L.or_fxaa_lp.argtypes = [P, P, ctypes.c_int, P, ctypes.c_int, P]
+        L.or_shade_points.argtypes = [P, P, P, P, P, P, i64, ctypes.c_int, P, P, P]
         L.or_reproject_lp.argtypes = [P, ctypes.c_double, P, P, P, ctypes.c_int, i64, P, P, P, P, P, P]
         L.or_path_trace.argtypes = [P, P, P, P, P, P, i64, ctypes.c_uint64, ctypes.c_int, P, P, P]
         L.or_pt_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int]
@@ -274,7 +275,10 @@ def edge_margin(tri, o, d) -> float:
     return float(lib().or_edge_margin(_p(_c(o, np.float64)), _p(_c(d, np.float64)), _p(tr)))
 
 
-def shade(tris, albedo, light_dir, dirs, hit_ids):
+def shade(tris, albedo, light_dir, dirs, hit_ids, point_lights=None, orig=None, hit_t=None):
+    """Lambert + ambient + directional light, sky on a miss; `point_lights` =
+    (positions (k, 3), rgb (k, 3)) adds unshadowed inverse-square point lights
+    (needs the ray origins and hit distances)."""
     tr = _c(tris, np.float32)
     al = _c(albedo, np.float32)
     L = _c(light_dir, np.float64)
@@ -282,6 +286,13 @@ def shade(tris, albedo, light_dir, dirs, hit_ids):
     h = _c(hit_ids, np.int32)
     out = np.empty((h.size, 4))
     lib().or_shade(_p(tr), _p(al), _p(L), _p(d), _p(h), h.size, _p(out))
+    if point_lights is not None and len(point_lights[0]):
+        pos = _c(point_lights[0], np.float64).reshape(-1, 3)
+        rgb = _c(point_lights[1], np.float64).reshape(-1, 3)
+        o = _c(orig, np.float64)
+        t = _c(np.where(h >= 0, hit_t, 0.0), np.float64)
+        lib().or_shade_points(_p(tr), _p(al), _p(o), _p(d), _p(h), _p(t), h.size, pos.shape[0],
+                              _p(pos), _p(rgb), _p(out))
     return out
 
 
@@ -386,14 +397,14 @@ def lbvh(tris) -> LBVH:
 
 
 def render_lp(scene_tris, albedo, light_dir, layout, width, height, fov_v_deg, gaze, pose,
-              texels=None, bvh: Optional[CpuBVH] = None):
+              texels=None, bvh: Optional[CpuBVH] = None, point_lights=None):
     """LP colours (n, 4) FP64, hit ids and ray directions for the given texels."""
     o, d, _ = lp_rays(layout, width, height, fov_v_deg, gaze, pose, texels)
     if bvh is not None:
         ids, t = bvh.cast(o, d)
     else:
         ids, t = cast_brute(scene_tris, o, d)
-    rgba = shade(scene_tris, albedo, light_dir, d, ids)
+    rgba = shade(scene_tris, albedo, light_dir, d, ids, point_lights, o, t)
     return rgba, ids, t, o, d
 
 
@@ -462,10 +473,10 @@ def render_lp_rep(scene_tris, albedo, light_dir, layout, width, height, fov_v_de
 
 
 def render_gt(scene_tris, albedo, light_dir, width, height, fov_v_deg, pose, pixels=None,
-              bvh: Optional[CpuBVH] = None):
+              bvh: Optional[CpuBVH] = None, point_lights=None):
     o, d = pixel_rays(width, height, fov_v_deg, pose, pixels)
     if bvh is not None:
         ids, t = bvh.cast(o, d)
     else:
         ids, t = cast_brute(scene_tris, o, d)
-    return shade(scene_tris, albedo, light_dir, d, ids), ids, t, o, d
+    return shade(scene_tris, albedo, light_dir, d, ids, point_lights, o, t), ids, t, o, d

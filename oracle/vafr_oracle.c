@@ -562,12 +562,48 @@ void or_cast_bvh(void* p, const double* orig, const double* dir, int64_t n_rays,
 
 /* ------------------------------------------------------------------------- */
 /* Shading (Sec. 6.1: closest-hit and miss shaders; the paper does not print
- * its shading code).  Lambert with a directional light and ambient k_a:
+ * its shading code).  Lambert with a directional light and ambient k_a
+ * (plus any point lights, or_shade_points):
  *   rgb = albedo (k_a + (1 - k_a) max(0, n . (-L))),
  * n = geometric unit normal turned to face the ray origin; a miss returns the
  * sky gradient lerp((1,1,1), (0.5,0.7,1.0), (dhat_y + 1)/2).  Alpha = 1. */
 
 #define OR_KA 0.1
+
+/* Point lights (the deferred pipeline's scenes carry many lights, Sec. 5.2):
+ * each adds albedo * rgb_k * max(0, n . l_k) / |x_k - p|^2 at hit point p,
+ * l_k the unit vector to the light; no shadows. */
+void or_shade_points(const float* tris, const float* albedo, const double* orig, const double* dir,
+                     const int32_t* hit_id, const double* hit_t, int64_t n, int n_pl, const double* pl_pos,
+                     const double* pl_rgb, double* rgba) {
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n; ++k) {
+        if (hit_id[k] < 0 || n_pl <= 0) continue;
+        const double* d = dir + 3 * k;
+        const float* t = tris + 9 * (int64_t)hit_id[k];
+        double e1[3], e2[3], nrm[3], p[3];
+        for (int a = 0; a < 3; ++a) {
+            e1[a] = (double)t[3 + a] - t[a];
+            e2[a] = (double)t[6 + a] - t[a];
+            p[a] = orig[3 * k + a] + hit_t[k] * d[a];
+        }
+        nrm[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        nrm[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        nrm[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        double nl = sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+        for (int a = 0; a < 3; ++a) nrm[a] /= nl;
+        if (nrm[0] * d[0] + nrm[1] * d[1] + nrm[2] * d[2] > 0.0)
+            for (int a = 0; a < 3; ++a) nrm[a] = -nrm[a];
+        const float* al = albedo + 3 * (int64_t)hit_id[k];
+        for (int q = 0; q < n_pl; ++q) {
+            double l[3], d2 = 0.0;
+            for (int a = 0; a < 3; ++a) { l[a] = pl_pos[3 * q + a] - p[a]; d2 += l[a] * l[a]; }
+            double cosl = (nrm[0] * l[0] + nrm[1] * l[1] + nrm[2] * l[2]) / sqrt(d2);
+            if (cosl <= 0.0) continue;
+            for (int a = 0; a < 3; ++a) rgba[4 * k + a] += al[a] * pl_rgb[3 * q + a] * cosl / d2;
+        }
+    }
+}
 
 void or_shade(const float* tris, const float* albedo, const double* light_dir,
               const double* dir, const int32_t* hit_id, int64_t n, double* rgba) {

@@ -82,6 +82,12 @@ struct vafr_scene {
     LbvhBuffers buf{};
     SceneDev dev{};
     unsigned* status = nullptr;
+    float4* d_plights = nullptr;   // point lights (vafr_scene_set_point_lights)
+    // deferred path scratch (first use): triangle id -> leaf, large-triangle list
+    int* d_leaf_of = nullptr;
+    int4* d_big = nullptr;
+    int* d_big_leaf = nullptr;
+    unsigned* d_n_big = nullptr;
 
     template <class T>
     int alloc(T** p, size_t count) {
@@ -373,6 +379,36 @@ int vafr_build_scene(const float* tri_xyz, const float* albedo_rgb, int64_t n_tr
     return VAFR_OK;
 }
 
+int vafr_scene_set_point_lights(vafr_scene* scene, int32_t n, const float* pos_xyz, const float* rgb) {
+    if (!scene) return fail(VAFR_ERR_INVALID_ARG, "scene is NULL");
+    if (n < 0 || n > VAFR_MAX_POINT_LIGHTS || (n > 0 && (!pos_xyz || !rgb)))
+        return fail(VAFR_ERR_INVALID_ARG, "point light count %d out of [0, %d] or NULL arrays", n, VAFR_MAX_POINT_LIGHTS);
+    std::vector<float4> h(2 * (size_t)(n > 0 ? n : 1));
+    for (int q = 0; q < n; ++q) {
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(pos_xyz[3 * q + k]) || !std::isfinite(rgb[3 * q + k]) || rgb[3 * q + k] < 0.0f)
+                return fail(VAFR_ERR_INVALID_ARG, "point light %d: non-finite position or negative colour", q);
+        h[2 * q] = make_float4(pos_xyz[3 * q], pos_xyz[3 * q + 1], pos_xyz[3 * q + 2], 0.0f);
+        h[2 * q + 1] = make_float4(rgb[3 * q], rgb[3 * q + 1], rgb[3 * q + 2], 0.0f);
+    }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(scene->device);
+    int rc = VAFR_OK;
+    if (!scene->d_plights) {
+        if (scene->alloc(&scene->d_plights, 2 * VAFR_MAX_POINT_LIGHTS) != VAFR_OK) rc = VAFR_ERR_OOM;
+    }
+    if (!rc && n > 0 &&
+        cudaMemcpy(scene->d_plights, h.data(), sizeof(float4) * 2 * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = fail(VAFR_ERR_CUDA, "point lights upload failed");
+    if (!rc) {
+        scene->dev.plights = scene->d_plights;
+        scene->dev.n_plights = n;
+    }
+    cudaSetDevice(cur);
+    return rc;
+}
+
 int vafr_scene_destroy(vafr_scene* scene) {
     if (!scene) return VAFR_OK;
     cudaDeviceSynchronize();
@@ -658,6 +694,62 @@ int vafr_rep_hole_count(vafr_session* s, int64_t* holes, void* stream) {
     CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
     *holes = h;
     return VAFR_OK;
+}
+
+// ---- deferred path -----------------------------------------------------------------
+static int deferred_scratch(const vafr_scene* scene_c, cudaStream_t st) {
+    auto* scene = const_cast<vafr_scene*>(scene_c);
+    if (scene->d_leaf_of) return VAFR_OK;
+    const size_t n = (size_t)(scene->n > 0 ? scene->n : 1);
+    int rc = scene->alloc(&scene->d_leaf_of, n);
+    if (!rc) rc = scene->alloc(&scene->d_big, n);
+    if (!rc) rc = scene->alloc(&scene->d_big_leaf, n);
+    if (!rc) rc = scene->alloc(&scene->d_n_big, 1);
+    if (rc) return fail(VAFR_ERR_OOM, "deferred scratch");
+    CUDA_TRY(launch_leaf_of(scene->dev, scene->d_leaf_of, st, scene->sms));
+    return VAFR_OK;
+}
+
+int vafr_render_vbuffer(const vafr_scene* scene, vafr_session* s, int32_t eye, uint64_t* vbuf_out, void* stream) {
+    if (!scene || !s || !vbuf_out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    if (eye < 0 || eye >= s->desc.n_eyes) return fail(VAFR_ERR_INVALID_ARG, "eye %d out of range", eye);
+    if (!aligned(vbuf_out, 8)) return fail(VAFR_ERR_INVALID_ARG, "vbuf must be 8-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    if (int rc = deferred_scratch(scene, st)) return rc;
+    SmallBatch b{};
+    b.d[0] = s->fd[eye];
+    b.n = 1;
+    VbufScratch v{reinterpret_cast<unsigned long long*>(vbuf_out), scene->d_big, scene->d_big_leaf,
+                  scene->d_n_big, (unsigned)(scene->n > 0 ? scene->n : 1)};
+    CUDA_TRY(launch_vbuffer(scene->dev, b, v, st, scene->sms));
+    return VAFR_OK;
+}
+
+static int shade_deferred(const vafr_scene* scene, vafr_session* s, int32_t eye, const uint64_t* vbuf, void* out,
+                          bool full_res, void* stream) {
+    if (!scene || !s || !vbuf || !out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    if (eye < 0 || eye >= s->desc.n_eyes) return fail(VAFR_ERR_INVALID_ARG, "eye %d out of range", eye);
+    if (!aligned(vbuf, 8) || !aligned(out, 16)) return fail(VAFR_ERR_INVALID_ARG, "buffers must be aligned");
+    if (!full_res && !s->gaze_set[eye]) return fail(VAFR_ERR_INVALID_ARG, "gaze of eye %d never set", eye);
+    cudaStream_t st = as_stream(stream);
+    if (int rc = deferred_scratch(scene, st)) return rc;
+    SmallBatch b{};
+    b.d[0] = s->fd[eye];
+    if (full_res) b.d[0].disp = out; else b.d[0].lp = out;
+    b.n = 1;
+    CUDA_TRY(launch_shade_vbuf(scene->dev, b, reinterpret_cast<const unsigned long long*>(vbuf), scene->d_leaf_of,
+                               full_res, st, scene->sms));
+    return VAFR_OK;
+}
+
+int vafr_shade_lp_deferred(const vafr_scene* scene, vafr_session* s, int32_t eye, const uint64_t* vbuf,
+                           void* lp_out, void* stream) {
+    return shade_deferred(scene, s, eye, vbuf, lp_out, false, stream);
+}
+
+int vafr_shade_full_deferred(const vafr_scene* scene, vafr_session* s, int32_t eye, const uint64_t* vbuf,
+                             void* display_out, void* stream) {
+    return shade_deferred(scene, s, eye, vbuf, display_out, true, stream);
 }
 
 int vafr_reconstruct(vafr_session* s, int32_t eye, const void* lp, void* display_out, void* stream) {

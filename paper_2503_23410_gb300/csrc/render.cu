@@ -365,7 +365,24 @@ __device__ __forceinline__ float4 shade(const SceneDev& sc, const Ray& r, const 
     const float lam = fmaxf(0.0f, -fmaf(nx, sc.light[0], fmaf(ny, sc.light[1], nz * sc.light[2])));
     const float s = fmaf(1.0f - kAmbient, lam, kAmbient);
     const float4 al = __ldg(sc.albedo + h.id);
-    return make_float4(al.x * s, al.y * s, al.z * s, 1.0f);
+    float3 acc = make_float3(s, s, s);
+    if (sc.n_plights > 0) {
+        // unshadowed inverse-square point lights: rgb max(0, n . l) / |x - p|^2
+        const float px = fmaf(h.t, r.dx, r.ox), py = fmaf(h.t, r.dy, r.oy), pz = fmaf(h.t, r.dz, r.oz);
+        for (int q = 0; q < sc.n_plights; ++q) {
+            const float4 lp = __ldg(sc.plights + 2 * q), lc = __ldg(sc.plights + 2 * q + 1);
+            const float lx = lp.x - px, ly = lp.y - py, lz = lp.z - pz;
+            const float d2 = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
+            const float c = fmaf(nx, lx, fmaf(ny, ly, nz * lz)) * rsqrtf(d2);
+            if (c > 0.0f) {
+                const float g = c / d2;
+                acc.x = fmaf(lc.x, g, acc.x);
+                acc.y = fmaf(lc.y, g, acc.y);
+                acc.z = fmaf(lc.z, g, acc.z);
+            }
+        }
+    }
+    return make_float4(al.x * acc.x, al.y * acc.y, al.z * acc.z, 1.0f);
 }
 
 __device__ __forceinline__ void store_px(void* base, long long idx, int fmt, float4 v) {
@@ -741,6 +758,182 @@ k_render_stats(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned
     atomicMax(out + 5, worst);
 }
 
+// ---- deferred path (Sec. 3.4 / Sec. 5: G-buffer at native resolution, lighting
+// in the LP buffer) ------------------------------------------------------------
+// The G-buffer is a visibility buffer: per display pixel the 64-bit key
+// (hit distance bits << 32) | triangle id of the closest triangle, written by
+// a rasteriser whose coverage test is the watertight test of the pixel-centre
+// ray (so the buffer equals the GT cast's closest hits exactly); the LP pass
+// shades each texel from the pixel under its screen point, the GT pass every
+// pixel.
+
+constexpr float kClipZ = 1e-4f;       // camera-space near plane for bounding boxes
+constexpr int kSmallTriPixels = 256;  // larger bounding boxes go to the block-per-triangle pass
+
+__device__ __forceinline__ void pixel_ray(const FrameDesc& f, int x, int y, Ray& r) {
+    const float cx = f.cr * ((float)x + 0.5f - 0.5f * (float)f.W);
+    const float cy = f.cr * (0.5f * (float)f.H - ((float)y + 0.5f));
+    world_ray(f, cx, cy, r);
+}
+
+// Camera coordinates R^T (v - o) of a world point.
+__device__ __forceinline__ float3 to_camera(const FrameDesc& f, float4 v) {
+    const float x = v.x - f.org[0], y = v.y - f.org[1], z = v.z - f.org[2];
+    return make_float3(fmaf(f.R[0], x, fmaf(f.R[3], y, f.R[6] * z)),
+                       fmaf(f.R[1], x, fmaf(f.R[4], y, f.R[7] * z)),
+                       fmaf(f.R[2], x, fmaf(f.R[5], y, f.R[8] * z)));
+}
+
+// Pixel bounding box of a triangle's part in front of the plane z = kClipZ
+// (Sutherland-Hodgman against that plane, then projection), widened by one
+// pixel; false if nothing is in front or the box misses the screen.
+__device__ __forceinline__ bool tri_bbox(const FrameDesc& f, float3 p[3], int& x0, int& y0, int& x1, int& y1) {
+    float3 q[4];
+    int m = 0;
+    for (int e = 0; e < 3; ++e) {
+        const float3 a = p[e], b = p[e == 2 ? 0 : e + 1];
+        const bool ia = a.z >= kClipZ, ib = b.z >= kClipZ;
+        if (ia) q[m++] = a;
+        if (ia != ib) {
+            const float s = (kClipZ - a.z) / (b.z - a.z);
+            q[m++] = make_float3(fmaf(s, b.x - a.x, a.x), fmaf(s, b.y - a.y, a.y), kClipZ);
+        }
+    }
+    if (m == 0) return false;
+    float lx = INFINITY, ly = INFINITY, hx = -INFINITY, hy = -INFINITY;
+    const float ic = 1.0f / f.cr;
+    for (int k = 0; k < m; ++k) {
+        const float sx = fmaf(q[k].x / q[k].z, ic, 0.5f * (float)f.W);
+        const float sy = fmaf(-q[k].y / q[k].z, ic, 0.5f * (float)f.H);
+        lx = fminf(lx, sx); hx = fmaxf(hx, sx);
+        ly = fminf(ly, sy); hy = fmaxf(hy, sy);
+    }
+    // pixel x covers [x, x + 1): centres in the box, plus a pixel of slack
+    const float fx0 = fmaxf(floorf(lx - 0.5f) - 1.0f, 0.0f), fy0 = fmaxf(floorf(ly - 0.5f) - 1.0f, 0.0f);
+    const float fx1 = fminf(ceilf(hx - 0.5f) + 1.0f, (float)(f.W - 1)), fy1 = fminf(ceilf(hy - 0.5f) + 1.0f, (float)(f.H - 1));
+    if (!(fx0 <= fx1 && fy0 <= fy1)) return false;
+    x0 = (int)fx0; y0 = (int)fy0; x1 = (int)fx1; y1 = (int)fy1;
+    return true;
+}
+
+__device__ __forceinline__ void raster_pixel(const SceneDev& sc, const FrameDesc& f, unsigned long long* vbuf,
+                                             int x, int y, float4 a, float4 b, float4 c, int id) {
+    Ray r;
+    pixel_ray(f, x, y, r);
+    ray_setup(r);
+    const float t = tri_test(r, a, b, c);
+    if (t < INFINITY)
+        atomicMin(vbuf + (long long)y * f.W + x, ((unsigned long long)__float_as_uint(t) << 32) | (unsigned)id);
+}
+
+// Pass 1: one thread per triangle; small boxes are rasterised here, large
+// ones listed (leaf, x0, y0, x1, y1) for pass 2.
+__global__ void __launch_bounds__(256)
+k_vbuf_raster(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned long long* vbuf, int4* big,
+              int* big_leaf, unsigned* n_big, unsigned big_cap) {
+    const FrameDesc& f = b.d[0];
+    for (int k = blockIdx.x * 256 + threadIdx.x; k < sc.n_tris; k += gridDim.x * 256) {
+        const float4 a = __ldg(sc.leaves + 3ll * k), bb = __ldg(sc.leaves + 3ll * k + 1),
+                     c = __ldg(sc.leaves + 3ll * k + 2);
+        float3 p[3] = {to_camera(f, a), to_camera(f, bb), to_camera(f, c)};
+        if (p[0].z <= 0.0f && p[1].z <= 0.0f && p[2].z <= 0.0f) continue;   // behind the eye
+        int x0, y0, x1, y1;
+        if (!tri_bbox(f, p, x0, y0, x1, y1)) continue;
+        const int id = __float_as_int(a.w);
+        if ((long long)(x1 - x0 + 1) * (y1 - y0 + 1) <= kSmallTriPixels) {
+            for (int y = y0; y <= y1; ++y)
+                for (int x = x0; x <= x1; ++x) raster_pixel(sc, f, vbuf, x, y, a, bb, c, id);
+        } else {
+            const unsigned slot = atomicAdd(n_big, 1u);
+            if (slot < big_cap) {
+                big[slot] = make_int4(x0, y0, x1, y1);
+                big_leaf[slot] = k;
+            } else {
+                atomicOr(f.status, kFaultBadNode);   // list overflow: reported, never silent
+            }
+        }
+    }
+}
+
+// Pass 2: one block per large triangle, its threads striding over the box.
+__global__ void __launch_bounds__(256)
+k_vbuf_big(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned long long* vbuf, const int4* big,
+           const int* big_leaf, const unsigned* n_big, unsigned big_cap) {
+    const FrameDesc& f = b.d[0];
+    const unsigned n = min(*n_big, big_cap);
+    for (unsigned q = blockIdx.x; q < n; q += gridDim.x) {
+        const int k = big_leaf[q];
+        const int4 bx = big[q];
+        const float4 a = __ldg(sc.leaves + 3ll * k), bb = __ldg(sc.leaves + 3ll * k + 1),
+                     c = __ldg(sc.leaves + 3ll * k + 2);
+        const int id = __float_as_int(a.w);
+        const int w = bx.z - bx.x + 1;
+        const long long area = (long long)w * (bx.w - bx.y + 1);
+        for (long long i = threadIdx.x; i < area; i += 256)
+            raster_pixel(sc, f, vbuf, bx.x + (int)(i % w), bx.y + (int)(i / w), a, bb, c, id);
+    }
+}
+
+// Shading of display pixel (x, y) from the visibility buffer (the GT cast's
+// shading of that pixel: its ray, hit distance and triangle).
+__device__ __forceinline__ float4 shade_vbuf(const SceneDev& sc, const FrameDesc& f, const unsigned long long* vbuf,
+                                             const int* leaf_of, int x, int y) {
+    Ray r;
+    pixel_ray(f, x, y, r);
+    const unsigned long long key = vbuf[(long long)y * f.W + x];
+    Hit h;
+    if (key == ~0ull) {
+        h.leaf = -1;
+        h.id = -1;
+        h.t = INFINITY;
+    } else {
+        h.id = (int)(unsigned)(key & 0xffffffffu);
+        h.t = __uint_as_float((unsigned)(key >> 32));
+        h.leaf = __ldg(leaf_of + h.id);
+    }
+    return shade(sc, r, h);
+}
+
+// LP lighting: texel -> the pixel under its screen point (clamped to the
+// display) -> that pixel's shading.
+__global__ void __launch_bounds__(256)
+k_shade_lp_vbuf(const SceneDev sc, const __grid_constant__ SmallBatch b, const unsigned long long* vbuf,
+                const int* leaf_of) {
+    const FrameDesc& f = b.d[0];
+    for (int k = blockIdx.x * 256 + threadIdx.x; k < f.n_texels; k += gridDim.x * 256) {
+        const int2 tc = __ldg(f.work + k);
+        const int2 cc = __ldg(&f.col[tc.y]);
+        const int j = tc.x - cc.x;
+        const float te = __ldg(&f.tan_e[tc.y]);
+        float sp, cp;
+        sincospif(__fdiv_rn((float)(2 * j + 1), (float)cc.y), &sp, &cp);
+        const float cx = fmaf(te, cp, f.gx), cy = fmaf(-te, sp, f.gy);
+        const float sx = fmaf(cx, 1.0f / f.cr, 0.5f * (float)f.W), sy = fmaf(-cy, 1.0f / f.cr, 0.5f * (float)f.H);
+        const int x = min(max((int)floorf(sx), 0), f.W - 1), y = min(max((int)floorf(sy), 0), f.H - 1);
+        const float4 v = shade_vbuf(sc, f, vbuf, leaf_of, x, y);
+        store_px(f.lp, tc.x, f.lp_fmt, v);
+        if (j == 0) store_px(f.lp, tc.x + cc.y, f.lp_fmt, v);
+        if (j == cc.y - 1) store_px(f.lp, tc.x - cc.y, f.lp_fmt, v);
+    }
+}
+
+// Full-resolution lighting (the deferred GT).
+__global__ void __launch_bounds__(256)
+k_shade_gt_vbuf(const SceneDev sc, const __grid_constant__ SmallBatch b, const unsigned long long* vbuf,
+                const int* leaf_of) {
+    const FrameDesc& f = b.d[0];
+    const long long n = (long long)f.W * f.H;
+    for (long long p = blockIdx.x * 256ll + threadIdx.x; p < n; p += gridDim.x * 256ll) {
+        const int y = (int)(p / f.W), x = (int)(p - (long long)y * f.W);
+        store_px(f.disp, p, f.disp_fmt, shade_vbuf(sc, f, vbuf, leaf_of, x, y));
+    }
+}
+
+__global__ void k_leaf_of(const float4* leaves, int n, int* leaf_of) {
+    for (int k = blockIdx.x * 256 + threadIdx.x; k < n; k += gridDim.x * 256)
+        leaf_of[__float_as_int(leaves[3ll * k].w)] = k;
+}
+
 template <int TPB, int FETCH, int WIDE, int ORDER, int MINB, bool GT, class B>
 cudaError_t launch_one(const SceneDev& sc, const B& b, cudaStream_t s, int num_sms) {
     auto kern = GT ? k_render_gt<TPB, FETCH, WIDE, ORDER, MINB, B>
@@ -839,6 +1032,39 @@ cudaError_t launch_render_list(const SceneDev& scene, const SmallBatch& batch, c
     e = cudaMemsetAsync(batch.work_counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     k_render_list<<<(unsigned)(per_sm * num_sms), 128, 0, s>>>(scene, batch, count);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vbuffer(const SceneDev& sc, const SmallBatch& b, const VbufScratch& v, cudaStream_t s,
+                           int num_sms) {
+    const FrameDesc& f = b.d[0];
+    cudaError_t e = cudaMemsetAsync(v.vbuf, 0xff, sizeof(unsigned long long) * (size_t)f.W * f.H, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(v.n_big, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+    if (sc.n_tris <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)min((sc.n_tris + 255) / 256, num_sms * 16);
+    k_vbuf_raster<<<grid, 256, 0, s>>>(sc, b, v.vbuf, v.big, v.big_leaf, v.n_big, v.big_cap);
+    k_vbuf_big<<<(unsigned)(num_sms * 8), 256, 0, s>>>(sc, b, v.vbuf, v.big, v.big_leaf, v.n_big, v.big_cap);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_of(const SceneDev& sc, int* leaf_of, cudaStream_t s, int num_sms) {
+    if (sc.n_tris <= 0) return cudaSuccess;
+    k_leaf_of<<<(unsigned)min((sc.n_tris + 255) / 256, num_sms * 16), 256, 0, s>>>(sc.leaves, sc.n_tris, leaf_of);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shade_vbuf(const SceneDev& sc, const SmallBatch& b, const unsigned long long* vbuf,
+                              const int* leaf_of, bool full_res, cudaStream_t s, int num_sms) {
+    if (full_res) {
+        const long long n = (long long)b.d[0].W * b.d[0].H;
+        k_shade_gt_vbuf<<<(unsigned)min((n + 255) / 256, (long long)num_sms * 16), 256, 0, s>>>(sc, b, vbuf, leaf_of);
+    } else {
+        k_shade_lp_vbuf<<<(unsigned)min((b.d[0].n_texels + 255) / 256, num_sms * 16), 256, 0, s>>>(sc, b, vbuf, leaf_of);
+    }
     count_launch(1);
     return cudaGetLastError();
 }

@@ -40,6 +40,8 @@ struct SceneDev {
     int n_tris;
     float light[3];         // unit light travel direction
     unsigned* status;       // device status word
+    const float4* plights;  // [2 n_plights]: (position, 0), (rgb, 0) of each point light
+    int n_plights;
 };
 
 // ---- per session: forward-map table ------------------------------------------
@@ -138,6 +140,20 @@ struct RepScratch {
     int* tri_out;                 // [right slots] winning triangle id / -1, or nullptr
 };
 cudaError_t launch_reproject(const SmallBatch& batch, const RepScratch& r, cudaStream_t s, int num_sms);
+// Deferred path (render.cu): visibility buffer of frame d[0] at display
+// resolution, then LP or full-resolution lighting from it.
+struct VbufScratch {
+    unsigned long long* vbuf;   // [H][W] (hit distance bits << 32) | triangle id, ~0 = sky
+    int4* big;                  // large triangles' pixel boxes
+    int* big_leaf;              // ... and their leaves
+    unsigned* n_big;
+    unsigned big_cap;
+};
+cudaError_t launch_vbuffer(const SceneDev& sc, const SmallBatch& b, const VbufScratch& v, cudaStream_t s,
+                           int num_sms);
+cudaError_t launch_leaf_of(const SceneDev& sc, int* leaf_of, cudaStream_t s, int num_sms);
+cudaError_t launch_shade_vbuf(const SceneDev& sc, const SmallBatch& b, const unsigned long long* vbuf,
+                              const int* leaf_of, bool full_res, cudaStream_t s, int num_sms);
 // FXAA inside the LP buffer of every frame with lp_aa set (fxaa.cu).
 template <class B>
 cudaError_t launch_fxaa(const B& batch, cudaStream_t s, int num_sms);

@@ -91,6 +91,10 @@ _PROTOS = {
     "vafr_render_lp_pt": (ctypes.c_int, [_P, _P, _I32, _P, ctypes.c_uint64, _I32, _P, _P]),
     "vafr_render_full_gt_pt": (ctypes.c_int, [_P, _P, _I32, _P, ctypes.c_uint64, _I32, _P]),
     "vafr_render_lp_rep": (ctypes.c_int, [_P, _P, _P, _P]),
+    "vafr_scene_set_point_lights": (ctypes.c_int, [_P, _I32, _P, _P]),
+    "vafr_render_vbuffer": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
+    "vafr_shade_lp_deferred": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P]),
+    "vafr_shade_full_deferred": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P]),
     "vafr_reproject_lp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "vafr_rep_hole_count": (ctypes.c_int, [_P, _P, _P]),
     "vafr_render_full_gt": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P]),
@@ -339,6 +343,27 @@ def vafr_render_full_gt_pt(scene: int, session: int, eye: int, display_out, seed
                            max_diffuse: int = 3, stream=None) -> None:
     _check(load().vafr_render_full_gt_pt(scene, session, int(eye), ptr(display_out),
                                          int(seed) & (2 ** 64 - 1), int(max_diffuse), stream_ptr(stream)))
+
+
+def vafr_scene_set_point_lights(scene: int, positions, rgb) -> None:
+    pos = np.ascontiguousarray(positions, np.float32).reshape(-1, 3)
+    col = np.ascontiguousarray(rgb, np.float32).reshape(-1, 3)
+    if pos.shape != col.shape:
+        raise ValueError("positions and colours differ in shape")
+    _check(load().vafr_scene_set_point_lights(scene, pos.shape[0], pos.ctypes.data, col.ctypes.data))
+
+
+def vafr_render_vbuffer(scene: int, session: int, eye: int, vbuf_out, stream=None) -> None:
+    _check(load().vafr_render_vbuffer(scene, session, int(eye), ptr(vbuf_out), stream_ptr(stream)))
+
+
+def vafr_shade_lp_deferred(scene: int, session: int, eye: int, vbuf, lp_out, stream=None) -> None:
+    _check(load().vafr_shade_lp_deferred(scene, session, int(eye), ptr(vbuf), ptr(lp_out), stream_ptr(stream)))
+
+
+def vafr_shade_full_deferred(scene: int, session: int, eye: int, vbuf, display_out, stream=None) -> None:
+    _check(load().vafr_shade_full_deferred(scene, session, int(eye), ptr(vbuf), ptr(display_out),
+                                           stream_ptr(stream)))
 
 
 def vafr_render_lp_rep(scene: int, session: int, lp_out, stream=None) -> None:

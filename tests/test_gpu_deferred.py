@@ -1,0 +1,102 @@
+"""GPU deferred path (Sec. 3.4, Sec. 5): the CUDA-rasterised visibility buffer
+equals the GT cast's closest hits, the LP lighting equals the GT shading of
+the pixel under each texel, both against the FP64 oracle; and point lights
+(the deferred scenes' many lights) against the oracle's shading."""
+
+import numpy as np
+import pytest
+
+import oracle
+from parity import classify, compare_hits_and_colours, device_scene, lp_slots
+from workloads import workload
+
+pytestmark = pytest.mark.gpu
+
+
+def _lights(sc, n, seed):
+    rng = np.random.default_rng(seed)
+    lo, hi = sc.tris.reshape(-1, 3).min(0), sc.tris.reshape(-1, 3).max(0)
+    pos = rng.uniform(lo, hi, (n, 3)).astype(np.float32)
+    pos[:, 1] = hi[1] + rng.uniform(0.5, 3.0, n)           # above the scene
+    rgb = rng.uniform(0.2, 1.0, (n, 3)).astype(np.float32) * float(np.max(hi - lo)) ** 2 * 0.5
+    return pos, rgb
+
+
+@pytest.mark.parametrize("name", ["random1k", "terrain4k"])
+def test_vbuffer_is_the_gt_cast(V, torch_mod, name):
+    w = workload(name, frames=4)
+    d, sc = w.displays[0], w.scene
+    h, keep = device_scene(V, sc, torch_mod)
+    pos, rgb = _lights(sc, 16, 3)
+    V.vafr_scene_set_point_lights(h, pos, rgb)
+    s = V.vafr_session_create(V.make_session_desc(d.width, d.height, d.fov_v_deg, d.poses))
+    V.vafr_set_gaze(s, 0, *d.gaze[1, 0])
+    W, H = d.width, d.height
+    vb = torch_mod.empty((H, W), dtype=torch_mod.int64, device="cuda")
+    V.vafr_render_vbuffer(h, s, 0, vb)
+    gt = torch_mod.empty((H, W, 4), device="cuda")
+    ids = torch_mod.empty(H * W, dtype=torch_mod.int32, device="cuda")
+    V.vafr_render_full_gt(h, s, 0, gt, ids)
+    full = torch_mod.empty((H, W, 4), device="cuda")
+    V.vafr_shade_full_deferred(h, s, 0, vb, full)
+    slot, n_slots, _, _ = lp_slots(V, s)
+    lp = torch_mod.empty((n_slots, 4), device="cuda")
+    V.vafr_shade_lp_deferred(h, s, 0, vb, lp)
+    torch_mod.cuda.synchronize()
+    assert V.vafr_session_check(s) == 0 and V.vafr_scene_check(h) == 0
+    key = vb.cpu().numpy().reshape(-1).view(np.uint64)
+    vid = np.where(key == np.uint64(2 ** 64 - 1), -1, (key & np.uint64(0xffffffff)).astype(np.int64))
+    # the rasteriser's coverage and depth test reproduce the cast exactly
+    assert np.array_equal(vid, ids.cpu().numpy())
+    assert torch_mod.equal(full, gt)
+    # LP lighting = the GT shading of the pixel under each texel
+    lay = oracle.lp_layout()
+    _, _, xy = oracle.lp_rays(lay, W, H, d.fov_v_deg, d.gaze[1, 0], d.poses[0])
+    px = np.clip(np.floor(xy[:, 0]), 0, W - 1).astype(np.int64)
+    py = np.clip(np.floor(xy[:, 1]), 0, H - 1).astype(np.int64)
+    got = lp.cpu().numpy()[slot]
+    ref = gt.cpu().numpy().reshape(-1, 4)[py * W + px]
+    same = np.all(got == ref, axis=1)
+    assert same.mean() > 0.999     # the rest sit on a pixel boundary (FP32 vs FP64 floor)
+    # against the FP64 oracle on a sample of pixels, point lights included
+    rng = np.random.default_rng(7)
+    pix = np.sort(rng.choice(W * H, 40000, replace=False))
+    bvh = oracle.CpuBVH(sc.tris) if sc.n_tris > 5000 else None
+    orgba, oid, ot, o, dd = oracle.render_gt(sc.tris, sc.albedo, sc.light_dir, W, H, d.fov_v_deg,
+                                             d.poses[0], pixels=pix, bvh=bvh, point_lights=(pos, rgb))
+    compare_hits_and_colours(sc.tris, o, dd, vid[pix], full.cpu().numpy().reshape(-1, 4)[pix], oid, ot,
+                             orgba, 1e-3 * max(1.0, float(np.abs(orgba).max())))
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)
+
+
+def test_point_lights_in_the_ray_cast(V, torch_mod):
+    w = workload("random1k")
+    d, sc = w.displays[0], w.scene
+    h, keep = device_scene(V, sc, torch_mod)
+    pos, rgb = _lights(sc, 31, 5)
+    V.vafr_scene_set_point_lights(h, pos, rgb)
+    s = V.vafr_session_create(V.make_session_desc(d.width, d.height, d.fov_v_deg, d.poses))
+    V.vafr_set_gaze(s, 0, *d.gaze[0, 0])
+    slot, n_slots, _, _ = lp_slots(V, s)
+    lp = torch_mod.empty((n_slots, 4), device="cuda")
+    ids = torch_mod.empty(n_slots, dtype=torch_mod.int32, device="cuda")
+    V.vafr_render_lp(h, s, 1, lp, ids)
+    torch_mod.cuda.synchronize()
+    lay = oracle.lp_layout()
+    rgba, oid, ot, o, dd = oracle.render_lp(sc.tris, sc.albedo, sc.light_dir, lay, d.width, d.height,
+                                            d.fov_v_deg, d.gaze[0, 0], d.poses[0], point_lights=(pos, rgb))
+    assert np.abs(rgba[oid >= 0, :3]).max() > 1.5           # the lights do add light
+    compare_hits_and_colours(sc.tris, o, dd, ids.cpu().numpy()[slot], lp.cpu().numpy()[slot], oid, ot,
+                             rgba, 1e-3 * max(1.0, float(np.abs(rgba).max())))
+    # removing them restores the directional shading exactly
+    V.vafr_scene_set_point_lights(h, np.zeros((0, 3)), np.zeros((0, 3)))
+    V.vafr_render_lp(h, s, 1, lp, ids)
+    torch_mod.cuda.synchronize()
+    plain, _, _, _, _ = oracle.render_lp(sc.tris, sc.albedo, sc.light_dir, lay, d.width, d.height,
+                                         d.fov_v_deg, d.gaze[0, 0], d.poses[0])
+    assert np.abs(lp.cpu().numpy()[slot][oid >= 0] - plain[oid >= 0]).max() < 1e-3 + 1e-6
+    with pytest.raises(V.VafrError):
+        V.vafr_scene_set_point_lights(h, np.zeros((300, 3)), np.ones((300, 3)))
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)

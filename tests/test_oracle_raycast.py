@@ -128,3 +128,28 @@ def test_shading_closed_forms():
     sky = oracle.shade(sc.tris, alb, L, np.array([[0, 1.0, 0], [0, -2.0, 0], [3.0, 0, 0]]),
                        np.array([-1, -1, -1]))
     np.testing.assert_allclose(sky, [[0.5, 0.7, 1.0, 1.0], [1, 1, 1, 1], [0.75, 0.85, 1.0, 1.0]])
+
+
+def test_point_light_inverse_square_closed_form():
+    # a point light of power rgb at height h straight above a lit plane point
+    # adds albedo * rgb / h^2 there (cos = 1); two lights add up
+    half = 20.0
+    a, b, c, d = [-half, -half, 0], [half, -half, 0], [half, half, 0], [-half, half, 0]
+    tris = np.array([[a, b, c], [a, c, d]], np.float32)
+    alb = np.float32([[0.5, 0.25, 1.0]] * 2)
+    L = np.array([0.0, 0.0, 1.0])                     # directional light from behind the plane
+    o = np.array([[0.3, -0.2, -2.0], [1.5, 0.5, -2.0]])
+    dirs = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, 1.0]])
+    ids, t = oracle.cast_brute(tris, o, dirs)
+    assert np.all(ids >= 0) and np.allclose(t, 2.0)
+    base = oracle.shade(tris, alb, L, dirs, ids)
+    pl1 = (np.array([[0.3, -0.2, -1.5]]), np.array([[2.0, 1.0, 0.5]]))
+    one = oracle.shade(tris, alb, L, dirs, ids, pl1, o, t)
+    np.testing.assert_allclose(one[0, :3] - base[0, :3], alb[0] * pl1[1][0] / 1.5 ** 2, rtol=1e-12)
+    pl2 = (np.array([[0.3, -0.2, -1.5], [1.5, 0.5, -0.5]]), np.array([[2.0, 1.0, 0.5], [1.0, 1.0, 1.0]]))
+    two = oracle.shade(tris, alb, L, dirs, ids, pl2, o, t)
+    solo = oracle.shade(tris, alb, L, dirs, ids, (pl2[0][1:], pl2[1][1:]), o, t)
+    np.testing.assert_allclose(two - base, (one - base) + (solo - base), atol=1e-12)
+    # a light behind the surface adds nothing
+    behind = oracle.shade(tris, alb, L, dirs, ids, (np.array([[0.3, -0.2, 1.0]]), np.ones((1, 3))), o, t)
+    np.testing.assert_allclose(behind, base, atol=0)
