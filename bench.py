@@ -248,8 +248,11 @@ def run_gpu(args, w):
     fxaa = bool(args.fxaa)
     pt = bool(args.pt)
     rep = bool(args.rep)
+    deferred = bool(args.deferred)
     if rep and (pt or len(w.displays[0].poses) != 2):
         raise SystemExit("--rep needs a binocular workload and ray casting")
+    if deferred and (pt or rep):
+        raise SystemExit("--deferred excludes --pt and --rep")
     acuity = {"paper": None, "anisotropic": V.vafr_acuity_anisotropic,
               "display9": lambda: V.vafr_acuity_display_limited(9.0),
               "display18": lambda: V.vafr_acuity_display_limited(18.0)}[args.acuity]
@@ -258,6 +261,15 @@ def run_gpu(args, w):
     lp_b, dp_b = V.vafr_session_sizes(sess)
     lp = torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda")
     lp_aa = torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda") if fxaa else lp
+    vbuf = torch.empty((H_, W_), dtype=torch.int64, device="cuda") if deferred else None
+    if args.point_lights:
+        rng_l = np.random.default_rng(1234)
+        pts = w.scene.tris.reshape(-1, 3)
+        lo, hi = pts.min(0), pts.max(0)
+        lpos = rng_l.uniform(lo, hi, (args.point_lights, 3)).astype(np.float32)
+        lpos[:, 1] = hi[1] + rng_l.uniform(1.0, 10.0, args.point_lights)
+        lrgb = (rng_l.uniform(0.2, 1.0, (args.point_lights, 3)) * 400.0).astype(np.float32)
+        V.vafr_scene_set_point_lights(scene, lpos, lrgb)
     disp = torch.empty(eyes * dp_b, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
@@ -274,6 +286,10 @@ def run_gpu(args, w):
             V.vafr_render_lp_pt(scene, sess, mask, lp, seed=k, max_diffuse=PT_DIFFUSE)
         elif rep:                                  # VaFR_Rep: left cast, right warped (Sec. 5.1)
             V.vafr_render_lp_rep(scene, sess, lp)
+        elif deferred:                             # G-buffer at native resolution, LP lighting
+            for e in range(eyes):
+                V.vafr_render_vbuffer(scene, sess, e, vbuf)
+                V.vafr_shade_lp_deferred(scene, sess, e, vbuf, lp[e * lp_b:])
         else:
             V.vafr_render_lp(scene, sess, mask, lp)
         if evs:
@@ -294,6 +310,9 @@ def run_gpu(args, w):
         for e in range(eyes):
             if pt:
                 V.vafr_render_full_gt_pt(scene, sess, e, disp[e * dp_b:], seed=k, max_diffuse=PT_DIFFUSE)
+            elif deferred:
+                V.vafr_render_vbuffer(scene, sess, e, vbuf)
+                V.vafr_shade_full_deferred(scene, sess, e, vbuf, disp[e * dp_b:])
             else:
                 V.vafr_render_full_gt(scene, sess, e, disp[e * dp_b:])
         if evs:
@@ -339,7 +358,7 @@ def run_gpu(args, w):
         #      computes while frame k crosses the CPU-GPU link.
         e2e_steps = max(3, min(args.steps, args.e2e_steps))
         host = [torch.empty(eyes * dp_b, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
-        if pt or rep:
+        if pt or rep or deferred:
             # (a) only: the frame as timed above, then one device-to-host copy
             def pt_e2e(k):
                 g = d.gaze[k % nf]
@@ -365,7 +384,7 @@ def run_gpu(args, w):
                     V.vafr_set_gaze(sess, e, g[e, 0], g[e, 1])
                 V.vafr_render_frame(scene, sess, host[0])
             e2e_sync_s = time.perf_counter() - te
-        if not (pt or rep):
+        if not (pt or rep or deferred):
             lps = [torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda") for _ in range(2)]
             aas = [torch.empty(eyes * lp_b, dtype=torch.uint8, device="cuda") for _ in range(2)] if fxaa else None
             streams = [torch.cuda.Stream() for _ in range(2)]
@@ -466,6 +485,8 @@ def run_gpu(args, w):
                    "shading": f"path traced, 1 path/texel, NEE, {PT_DIFFUSE} diffuse bounces" if pt
                    else "ray cast, Lambert + ambient",
                    "binocular_mode": "VaFR_Rep (right eye warped)" if rep else "VaFR_Dup",
+                   "pipeline": "deferred (visibility buffer + LP lighting)" if deferred else "ray casting",
+                   "point_lights": int(args.point_lights),
                    "parallelism": f"replicas x{ws} (independent sessions, no collective)"},
         "fps": 1e3 / float(step_ms.mean()),
         "p50_frame_ms": float(np.percentile(step_ms, 50)),
@@ -480,9 +501,9 @@ def run_gpu(args, w):
         "roofline_other": roof_recon if dominant is roof_render else roof_render,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * eyes,
                 "d2h_bytes_per_step": dp_b * eyes, "steps": e2e_steps,
-                "path": ("the timed frame (vafr_render_lp_pt or vafr_render_lp_rep, then "
+                "path": ("the timed frame (path-traced, VaFR_Rep or deferred LP buffer, then "
                          "vafr_reconstruct), then one device-to-host copy into pinned memory, "
-                         "synchronous per frame") if (pt or rep) else
+                         "synchronous per frame") if (pt or rep or deferred) else
                         ("vafr_batch_render into pinned host frames, 2 frames in flight on 2 "
                          "streams (C ABI); gaze passed by value each step"),
                 "sync_per_frame_value": e2e_sync_value,
@@ -686,6 +707,12 @@ def main():
     ap.add_argument("--pt", action="store_true",
                     help="path-trace the LP buffer (Sec. 8: 1 path per texel, NEE, 3 diffuse bounces) "
                          "and compare with the path-traced full-resolution GT")
+    ap.add_argument("--deferred", action="store_true",
+                    help="deferred pipeline (Sec. 3.4 / 5): visibility buffer rasterised at display "
+                         "resolution, lighting in the LP buffer; GT lights every pixel")
+    ap.add_argument("--point-lights", type=int, default=0,
+                    help="seeded unshadowed point lights added to the scene (the deferred scenes "
+                         "carry many lights; the Sun Temple has 31)")
     ap.add_argument("--rep", action="store_true",
                     help="VaFR_Rep (Sec. 5.1): the right eye's LP buffer warped from the left eye's, "
                          "holes ray cast (binocular workloads)")

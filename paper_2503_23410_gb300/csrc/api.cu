@@ -87,7 +87,8 @@ struct vafr_scene {
     int* d_leaf_of = nullptr;
     int4* d_big = nullptr;
     int* d_big_leaf = nullptr;
-    unsigned* d_n_big = nullptr;
+    long long* d_big_first = nullptr;
+    unsigned long long* d_n_big = nullptr;
 
     template <class T>
     int alloc(T** p, size_t count) {
@@ -704,6 +705,7 @@ static int deferred_scratch(const vafr_scene* scene_c, cudaStream_t st) {
     int rc = scene->alloc(&scene->d_leaf_of, n);
     if (!rc) rc = scene->alloc(&scene->d_big, n);
     if (!rc) rc = scene->alloc(&scene->d_big_leaf, n);
+    if (!rc) rc = scene->alloc(&scene->d_big_first, n);
     if (!rc) rc = scene->alloc(&scene->d_n_big, 1);
     if (rc) return fail(VAFR_ERR_OOM, "deferred scratch");
     CUDA_TRY(launch_leaf_of(scene->dev, scene->d_leaf_of, st, scene->sms));
@@ -720,7 +722,7 @@ int vafr_render_vbuffer(const vafr_scene* scene, vafr_session* s, int32_t eye, u
     b.d[0] = s->fd[eye];
     b.n = 1;
     VbufScratch v{reinterpret_cast<unsigned long long*>(vbuf_out), scene->d_big, scene->d_big_leaf,
-                  scene->d_n_big, (unsigned)(scene->n > 0 ? scene->n : 1)};
+                  scene->d_big_first, scene->d_n_big, (unsigned)(scene->n > 0 ? scene->n : 1)};
     CUDA_TRY(launch_vbuffer(scene->dev, b, v, st, scene->sms));
     return VAFR_OK;
 }

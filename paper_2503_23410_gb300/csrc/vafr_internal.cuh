@@ -145,8 +145,9 @@ cudaError_t launch_reproject(const SmallBatch& batch, const RepScratch& r, cudaS
 struct VbufScratch {
     unsigned long long* vbuf;   // [H][W] (hit distance bits << 32) | triangle id, ~0 = sky
     int4* big;                  // large triangles' pixel boxes
-    int* big_leaf;              // ... and their leaves
-    unsigned* n_big;
+    int* big_leaf;              // ... their leaves
+    long long* big_first;       // ... and first tiles
+    unsigned long long* counter;  // (records << 34) | tiles
     unsigned big_cap;
 };
 cudaError_t launch_vbuffer(const SceneDev& sc, const SmallBatch& b, const VbufScratch& v, cudaStream_t s,
