@@ -447,7 +447,9 @@ def run_gpu(args, w):
         rays = pt_rays
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
-    alu_peak = n_sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12      # T FP32 ops/s
+    derived_peak = n_sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # T FP32 ops/s
+    ffma, ffma2 = V.vafr_measure_fp32_peak()                        # FMAs/s, measured here
+    alu_peak = ffma / 1e12 if ffma > 0 else derived_peak
     render_s = float(render_ms.mean()) / 1e3
     recon_s = float(recon_ms.mean()) / 1e3
     lp_bytes = lp_b * eyes
@@ -460,7 +462,10 @@ def run_gpu(args, w):
                    "achieved": ops / render_s / 1e12,
                    "peak": alu_peak, "unit": "TFLOP/s", "frac": ops / render_s / 1e12 / alu_peak,
                    "traffic": tr_render,
-                   "peak_kind": f"derived: {n_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                   "peak_kind": (f"measured: scalar FFMA issue rate of this GPU (vafr_measure_fp32_peak; "
+                                 f"paired FFMA2 {ffma2 / 1e12:.1f} T FMA/s; lane count x max clock "
+                                 f"{derived_peak:.1f})") if ffma > 0 else
+                                f"derived: {n_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                 f"{sm_mhz:g} MHz (1 op/lane/clk)",
                    "ops_per_launch": ops, "rays_per_launch": rays,
                    "nodes4_per_ray": stats["nodes"] / max(stats["rays"], 1),
@@ -473,6 +478,12 @@ def run_gpu(args, w):
                   "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured"
                   else "fallback 6.8 TB/s",
                   "bytes_per_launch": recon_bytes, "avg_ms": recon_s * 1e3}
+    if deferred:
+        # the render stage is the V-buffer rasteriser + LP lighting: no op count
+        roof_render = {"kernel": "k_vbuf_raster + k_vbuf_tiles + k_shade_lp_vbuf", "bound": "alu",
+                       "achieved": None, "peak": alu_peak, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                       "peak_kind": roof_render["peak_kind"],
+                       "note": "pixel tests are not counted; stage time only", "avg_ms": render_s * 1e3}
     dominant = roof_render if render_s >= recon_s else roof_recon
 
     line = {

@@ -377,6 +377,15 @@ VAFR_API int vafr_render_frame(const vafr_scene* scene, vafr_session* session, v
 VAFR_API int vafr_traversal_stats(const vafr_scene* scene, vafr_session* session, int32_t eye,
                          int64_t out[6], void* stream);
 
+/* FP32 issue rate of the current device, the denominator of the traversal
+ * kernels' ALU roofline: out[0] = FMAs per second with scalar FFMA, out[1] =
+ * FMAs per second with paired FFMA2 (two FMAs per instruction), each the
+ * best of three timed launches of 8 independent FMA chains per thread,
+ * 2,048 threads per SM, after one warm-up launch.  Synchronises `stream`
+ * (allocates and frees a few KB of device memory).  Errors: INVALID_ARG
+ * (NULL out), CUDA. */
+VAFR_API int vafr_measure_fp32_peak(double out[2], void* stream);
+
 /* ---- batching --------------------------------------------------------------
  * A batch renders many frame-eyes (any mix of sessions, eyes and display
  * sizes, all on one scene) with ONE persistent render launch over all LP

@@ -901,6 +901,22 @@ int vafr_traversal_stats(const vafr_scene* scene, vafr_session* s, int32_t eye, 
     return VAFR_OK;
 }
 
+int vafr_measure_fp32_peak(double out[2], void* stream) {
+    if (!out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    int dev = 0, sms = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    float* sink = nullptr;
+    CUDA_TRY(cudaMalloc(&sink, sizeof(float) * (size_t)sms * 8));
+    double ffma = 0.0, ffma2 = 0.0;
+    const cudaError_t e = measure_fp32_peak(sms, sink, as_stream(stream), &ffma, &ffma2);
+    cudaFree(sink);
+    CUDA_TRY(e);
+    out[0] = ffma;
+    out[1] = ffma2;
+    return VAFR_OK;
+}
+
 // ---- batching ----------------------------------------------------------------------------
 static int build_batch(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, BigBatch* b) {
     if (!frames || n <= 0 || n > bt->max_frames)

@@ -155,7 +155,7 @@ struct Hit {
     int id;     // triangle id
 };
 
-template <bool STATS>
+template <bool STATS, bool SKIP = false>
 __device__ __forceinline__ void test_leaf(const SceneDev& sc, const Ray& r, int k, Hit& h,
                                           unsigned long long* tri_tests) {
     const float4 a = __ldg(sc.leaves + 3ll * k);
@@ -163,7 +163,7 @@ __device__ __forceinline__ void test_leaf(const SceneDev& sc, const Ray& r, int 
     const float4 c = __ldg(sc.leaves + 3ll * k + 2);
     if (STATS) ++*tri_tests;
     const int id = __float_as_int(a.w);
-    if (id == r.skip) return;
+    if (SKIP && id == r.skip) return;
     const float t = tri_test(r, a, b, c);
     if (t < h.t || (t == h.t && t < INFINITY && id < h.id)) {
         h.t = t;
@@ -247,7 +247,7 @@ __device__ __forceinline__ void sort2(float& ta, int& ra, float& tb, int& rb) {
 // Closest hit through the 4-wide tree: test the four child boxes, test leaf
 // children at once, then continue with the nearest internal child and push the
 // others far-to-near.  Returns a fault bit (0 = fine).
-template <bool STATS, int ORDER, bool ANY = false>
+template <bool STATS, int ORDER, bool ANY = false, bool SKIP = false>
 __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
                               unsigned long long* node_visits, unsigned long long* box_tests,
                               unsigned long long* tri_tests) {
@@ -256,7 +256,7 @@ __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
     h.id = INT_MAX;
     if (sc.n_tris <= 0) return 0u;
     if (sc.root < 0) {   // single triangle
-        test_leaf<STATS>(sc, r, 0, h, tri_tests);
+        test_leaf<STATS, SKIP>(sc, r, 0, h, tri_tests);
         return 0u;
     }
     int stack[kStackSize];
@@ -281,7 +281,7 @@ __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
         if (T < INFINITY && C < 0) {                                                      \
             if (C != kEmptyRef) {                                                         \
                 if ((unsigned)~C >= (unsigned)sc.n_tris) return kFaultBadNode;            \
-                test_leaf<STATS>(sc, r, ~C, h, tri_tests);                                \
+                test_leaf<STATS, SKIP>(sc, r, ~C, h, tri_tests);                          \
             }                                                                             \
             T = INFINITY;                                                                 \
         }
@@ -566,7 +566,7 @@ __device__ float3 trace_path(const SceneDev& sc, Ray r, unsigned long long seed_
     for (; k <= depth; ++k) {
         ray_setup(r);
         Hit h;
-        *fault |= traverse4<false, ORDER>(sc, r, h, nullptr, nullptr, nullptr);
+        *fault |= traverse4<false, ORDER, false, true>(sc, r, h, nullptr, nullptr, nullptr);
         if (sig) sig[k] = h.leaf >= 0 ? h.id : -1;
         if (h.leaf < 0) {
             const float3 sky = sky_rgb(r.dx, r.dy, r.dz);
@@ -592,7 +592,7 @@ __device__ float3 trace_path(const SceneDev& sc, Ray r, unsigned long long seed_
             s.skip = h.id;
             ray_setup(s);
             Hit hs;
-            *fault |= traverse4<false, ORDER, true>(sc, s, hs, nullptr, nullptr, nullptr);
+            *fault |= traverse4<false, ORDER, true, true>(sc, s, hs, nullptr, nullptr, nullptr);
             if (hs.leaf < 0) {
                 mask |= 1u << k;
                 acc.x = fmaf(beta.x * rho.x, cosl, acc.x);

@@ -195,6 +195,10 @@ constexpr int kPlocRadius = 8;
 size_t tree4_scratch_bytes(int n);
 cudaError_t tree4_build(const LbvhBuffers& b, void* scratch, int radius, cudaStream_t s);
 
+// FP32 issue rate (peak.cu): FMAs per second of scalar FFMA and of paired
+// FFMA2 (two FMAs each) over the whole device; `sink` holds num_sms * 8 floats.
+cudaError_t measure_fp32_peak(int num_sms, float* sink, cudaStream_t s, double* ffma, double* ffma2);
+
 void count_launch(int k = 1);
 
 }  // namespace vafr

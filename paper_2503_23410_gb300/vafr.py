@@ -100,6 +100,7 @@ _PROTOS = {
     "vafr_render_full_gt": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P]),
     "vafr_render_frame": (ctypes.c_int, [_P, _P, _P, _P]),
     "vafr_traversal_stats": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
+    "vafr_measure_fp32_peak": (ctypes.c_int, [_P, _P]),
     "vafr_batch_create": (ctypes.c_int, [_P, _I32, _P]),
     "vafr_batch_destroy": (ctypes.c_int, [_P]),
     "vafr_batch_render": (ctypes.c_int, [_P, _P, _I32, _P]),
@@ -394,6 +395,13 @@ def vafr_render_full_gt(scene: int, session: int, eye: int, display_out, hit_ids
 
 def vafr_render_frame(scene: int, session: int, display_out, stream=None) -> None:
     _check(load().vafr_render_frame(scene, session, ptr(display_out), stream_ptr(stream)))
+
+
+def vafr_measure_fp32_peak(stream=None):
+    """(scalar FFMA, paired FFMA2) FMAs per second of the current device."""
+    out = np.zeros(2, np.float64)
+    _check(load().vafr_measure_fp32_peak(ptr(out), stream_ptr(stream)))
+    return float(out[0]), float(out[1])
 
 
 def vafr_traversal_stats(scene: int, session: int, eye: int = 0, stream=None):
