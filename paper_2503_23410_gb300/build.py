@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvafr.so")
-SOURCES = ["lbvh.cu", "tree4.cu", "render.cu", "reconstruct.cu", "fxaa.cu", "reproject.cu", "peak.cu", "layout.cu",
+SOURCES = ["lbvh.cu", "tree4.cu", "render.cu", "pathtrace.cu", "raster.cu", "reconstruct.cu", "fxaa.cu", "reproject.cu", "peak.cu", "layout.cu",
            "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -41,7 +41,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     nvcc = _nvcc()
     os.makedirs(OBJ, exist_ok=True)
     headers = [os.path.join(CSRC, "vafr_internal.cuh"), os.path.join(CSRC, "layout.h"),
-               os.path.join(CSRC, "lp_map.cuh"),
+               os.path.join(CSRC, "lp_map.cuh"), os.path.join(CSRC, "trace.cuh"),
                os.path.join(HERE, "..", "include", "vafr.h")]
     jobs = []
     for src in SOURCES:
