@@ -126,12 +126,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _traffic(kernel: str, src: str):
+def _traffic(kernel: str, srcs):
     """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel source changed since the counters were taken."""
+    kernel's sources changed since the counters were taken (the hash covers
+    the concatenated source files)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for src in srcs:
+            h.update(open(src, "rb").read())
+        sha = h.hexdigest()[:16]
         for ln in open(path):
             f = ln.split()
             if len(f) >= 4 and f[0] == kernel and f[1] == sha:
@@ -456,8 +460,11 @@ def run_gpu(args, w):
     recon_bytes = dp_b * eyes + lp_bytes                            # display write + LP read once
     hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     csrc = os.path.join(ROOT, "paper_2503_23410_gb300", "csrc")
-    tr_render, _ = _traffic("render_lp", os.path.join(csrc, "render.cu"))
-    tr_recon, _ = _traffic("reconstruct", os.path.join(csrc, "reconstruct.cu"))
+    if pt:
+        tr_render, _ = _traffic("path_lp", [os.path.join(csrc, f) for f in ("pathtrace.cu", "trace.cuh")])
+    else:
+        tr_render, _ = _traffic("render_lp", [os.path.join(csrc, f) for f in ("render.cu", "trace.cuh")])
+    tr_recon, _ = _traffic("reconstruct", [os.path.join(csrc, f) for f in ("reconstruct.cu", "lp_map.cuh")])
     roof_render = {"kernel": "k_path_lp" if pt else "k_render_lp", "bound": "alu",
                    "achieved": ops / render_s / 1e12,
                    "peak": alu_peak, "unit": "TFLOP/s", "frac": ops / render_s / 1e12 / alu_peak,

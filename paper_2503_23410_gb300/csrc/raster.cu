@@ -101,6 +101,31 @@ __device__ __forceinline__ void ray_setup_tri(Ray& r) {
     r.mz2 = kz == 2 ? Sz : 0.0f;
 }
 
+// The watertight test of trace.cuh's tri_test with the three vertex-minus-
+// origin differences already formed (every pixel ray of a frame starts at the
+// eye, so they are per triangle): the same FP32 operations in the same order,
+// hence the same t bit for bit.
+__device__ __forceinline__ float tri_test_rel(const Ray& r, float3 A, float3 B, float3 C) {
+    const float Ax = fmaf(r.mx0, A.x, fmaf(r.mx1, A.y, __fmul_rn(r.mx2, A.z)));
+    const float Ay = fmaf(r.my0, A.x, fmaf(r.my1, A.y, __fmul_rn(r.my2, A.z)));
+    const float Bx = fmaf(r.mx0, B.x, fmaf(r.mx1, B.y, __fmul_rn(r.mx2, B.z)));
+    const float By = fmaf(r.my0, B.x, fmaf(r.my1, B.y, __fmul_rn(r.my2, B.z)));
+    const float Cx = fmaf(r.mx0, C.x, fmaf(r.mx1, C.y, __fmul_rn(r.mx2, C.z)));
+    const float Cy = fmaf(r.my0, C.x, fmaf(r.my1, C.y, __fmul_rn(r.my2, C.z)));
+    const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return INFINITY;
+    const float det = __fadd_rn(__fadd_rn(U, V), W);
+    if (det == 0.0f) return INFINITY;
+    const float Az = fmaf(r.mz0, A.x, fmaf(r.mz1, A.y, __fmul_rn(r.mz2, A.z)));
+    const float Bz = fmaf(r.mz0, B.x, fmaf(r.mz1, B.y, __fmul_rn(r.mz2, B.z)));
+    const float Cz = fmaf(r.mz0, C.x, fmaf(r.mz1, C.y, __fmul_rn(r.mz2, C.z)));
+    const float T = fmaf(U, Az, fmaf(V, Bz, __fmul_rn(W, Cz)));
+    const float t = __fdiv_rn(T, det);
+    return t > 0.0f ? t : INFINITY;
+}
+
 // Per-triangle raster set-up: world vertices, id, the camera-depth lower
 // bound t_lo of any hit (rays are (cx, cy, 1) in camera space, so a hit's
 // distance t is its camera depth), and the screen-space pre-filter.
@@ -117,7 +142,7 @@ __device__ __forceinline__ void ray_setup_tri(Ray& r) {
 // projections, or a slack above 2^16 pixels use no filter.
 constexpr float kEdgeSlack = 1.0f / 64.0f;
 struct TriSetup {
-    float4 a, b, c;
+    float3 A, B, C;           // vertices minus the eye, as the watertight test forms them
     int id;
     float t_lo;               // every hit of the triangle has t >= t_lo
     float ea[3], eb[3], ec[3];  // e_i(x, y) = ea_i x + eb_i y + ec_i
@@ -131,7 +156,9 @@ __device__ __forceinline__ float max_abs3(float x, float y, float z) {
 
 __device__ __forceinline__ void tri_setup(const FrameDesc& f, const float4& a, const float4& b, const float4& c,
                                           const float3 p[3], TriSetup& T) {
-    T.a = a; T.b = b; T.c = c;
+    T.A = make_float3(__fsub_rn(a.x, f.org[0]), __fsub_rn(a.y, f.org[1]), __fsub_rn(a.z, f.org[2]));
+    T.B = make_float3(__fsub_rn(b.x, f.org[0]), __fsub_rn(b.y, f.org[1]), __fsub_rn(b.z, f.org[2]));
+    T.C = make_float3(__fsub_rn(c.x, f.org[0]), __fsub_rn(c.y, f.org[1]), __fsub_rn(c.z, f.org[2]));
     T.id = __float_as_int(a.w);
     const float zmin = fminf(p[0].z, fminf(p[1].z, p[2].z));
     const float vmax = fmaxf(max_abs3(a.x, a.y, a.z), fmaxf(max_abs3(b.x, b.y, b.z), max_abs3(c.x, c.y, c.z)));
@@ -182,12 +209,12 @@ __device__ __forceinline__ bool maybe_inside(const TriSetup& T, int x, int y) {
 __device__ __forceinline__ void raster_pixel(const FrameDesc& f, unsigned long long* vbuf, int x, int y,
                                              const TriSetup& T) {
     unsigned long long* px = vbuf + (long long)y * f.W + x;
-    const unsigned long long cur = __ldcg(px);
+    const unsigned long long cur = *px;   // may be stale in L1: values only decrease
     if (__uint_as_float((unsigned)(cur >> 32)) < T.t_lo) return;   // sky (~0) reads as NaN: never skipped
     Ray r;
     pixel_ray(f, x, y, r);
     ray_setup_tri(r);
-    const float t = tri_test(r, T.a, T.b, T.c);
+    const float t = tri_test_rel(r, T.A, T.B, T.C);
     if (t < INFINITY) {
         const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | (unsigned)T.id;
         if (key < cur) atomicMin(px, key);
@@ -244,7 +271,7 @@ k_vbuf_raster(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned 
 // pixels are four rows of 16 x 2 lanes.  Records are checked against the
 // display and the scene before use, so a list damaged by an overflow (already
 // reported by pass 1) cannot lead out of bounds.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_vbuf_tiles(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned long long* vbuf, const int4* big,
              const int* big_leaf, const long long* big_first, const unsigned long long* counter, unsigned big_cap) {
     const FrameDesc& f = b.d[0];

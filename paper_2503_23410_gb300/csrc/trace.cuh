@@ -93,6 +93,19 @@ __device__ __forceinline__ float2 slab2(float4 nx, float4 ny, float4 nz, const R
     return make_float2(tnl <= tfl * kFarScale ? tnl : INFINITY, tnr <= tfr * kFarScale ? tnr : INFINITY);
 }
 
+// Three-input FP32 minimum / maximum (one PTX instruction on sm_100 and later;
+// same NaN rule as fminf / fmaxf).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 // The four child boxes of a 4-wide node (two pairs of paired-FP32 slabs), with
 // the same robust evaluation as slab2.  Each axis's near and far planes are
 // chosen per ray by the sign of 1/d (the near plane of every box is then its
@@ -112,8 +125,8 @@ __device__ __forceinline__ float4 slab4(const float4* __restrict__ nd, const Ray
     const float2 zfa = __fmul2_rn(sub2(fzp.x, fzp.y, r.oz), iz), zfb = __fmul2_rn(sub2(fzp.z, fzp.w, r.oz), iz);
 #define VAFR_CHILD(XN, XF, YN, YF, ZN, ZF)                                        \
     ([&]() {                                                                      \
-        const float tn = fmaxf(fmaxf(XN, YN), fmaxf(ZN, 0.0f));                   \
-        const float tf = fminf(fminf(XF, YF), fminf(ZF, tmax));                   \
+        const float tn = max3f(XN, YN, fmaxf(ZN, 0.0f));                          \
+        const float tf = min3f(XF, YF, fminf(ZF, tmax));                          \
         return tn <= tf * kFarScale ? tn : INFINITY;                              \
     }())
     const float t0 = VAFR_CHILD(xna.x, xfa.x, yna.x, yfa.x, zna.x, zfa.x);
