@@ -531,8 +531,37 @@ def run_gpu(args, w):
         "wall_s_timed_loop": wall,
         "clocks": clk.summary(),
     }
+    def gpu_eval(k, e):
+        """One eye of frame k on the GPU (hit ids included), for the precision
+        report: LP colours and ids in the oracle's texel order, display pixels."""
+        g = d.gaze[k % nf]
+        for q in range(eyes):
+            V.vafr_set_gaze(sess, q, g[q, 0], g[q, 1])
+        counts, offs, _, n_tex = V.vafr_lp_layout(sess)
+        counts = counts.astype(np.int64)
+        starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+        slot = np.repeat(offs - starts, counts) + np.arange(n_tex)
+        tdt = torch.float16 if w.lp_fp16 else torch.float32
+        lp1 = torch.empty(lp_b, dtype=torch.uint8, device="cuda")
+        ids1 = torch.empty(lp_b // (8 if w.lp_fp16 else 16), dtype=torch.int32, device="cuda")
+        disp1 = torch.empty(dp_b, dtype=torch.uint8, device="cuda")
+        V.vafr_render_lp(scene, sess, 1 << e, lp1, ids1)
+        V.vafr_reconstruct(sess, e, lp1, disp1)
+        torch.cuda.synchronize()
+        lp_h = lp1.view(tdt).view(-1, 4).float().cpu().numpy()[slot]
+        dd = disp1.view(torch.float16 if w.display_fp16 else torch.float32).view(H_, W_, 4).float().cpu().numpy()
+        return lp_h, ids1.cpu().numpy()[slot], dd
+
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_baseline(args, w)
+        plain = not (pt or rep or deferred or fxaa)
+        line["cpu_baseline"], prec = cpu_baseline(args, w, gpu_eval if plain else None)
+        if prec is not None:
+            prec.update({"lp": "f16" if w.lp_fp16 else "f32", "display": "f16" if w.display_fp16 else "f32",
+                         "accumulate": "f32", "frame": 0,
+                         "note": "GPU frame against the FP64 oracle's frame at the same gaze; ids differ "
+                                 "only at ray-edge ties, and display pixels whose filter footprint holds "
+                                 "such a texel make the max"})
+            line["precision"] = prec
     if rank == 0:
         print(json.dumps(line))
     V.vafr_session_destroy(sess)
@@ -680,28 +709,78 @@ def run_serving(args):
     V.vafr_scene_destroy(scene)
 
 
-def cpu_baseline(args, w):
+def cpu_baseline(args, w, gpu_eval=None):
+    """The FP64 oracle on the host cores: whole LP buffers (every texel through
+    the CPU BVH) and the display reconstructed at up to --cpu-pixels pixels per
+    eye (all of them at 4K), frame after frame along the gaze trajectory until
+    --cpu-seconds of oracle work; Mpix/s extrapolates the pixel sample to whole
+    frames.  With gpu_eval, the first frame is also compared with the GPU's
+    (precision against the FP64 oracle)."""
     import oracle
     oracle.build()
     lay = oracle.lp_layout()
     d = w.displays[0]
     eyes = len(d.poses)
+    npx = d.width * d.height
     bvh = oracle.CpuBVH(w.scene.tris)
     rng = np.random.default_rng(7)
-    cpu_s, frames = 0.0, []
-    t_start = time.perf_counter()
-    k = 0
-    while k < 3 or (time.perf_counter() - t_start < args.cpu_seconds and k < 50):
-        s, f = oracle_frame_sample(w, k, args.ref_texels, args.ref_pixels, bvh, lay, rng)
-        cpu_s += s
-        frames.append(f)
+    cpu_s, frame_s, k = 0.0, [], 0
+    precision = None
+    while k < 1 or (cpu_s < args.cpu_seconds and k < 240):
+        t_lp = t_rec = 0.0
+        n_pix = min(npx, args.cpu_pixels)
+        for e in range(eyes):
+            gaze = d.gaze[k % len(d.gaze), e]
+            t0 = time.perf_counter()
+            rgba, ids, _, _, _ = oracle.render_lp(w.scene.tris, w.scene.albedo, w.scene.light_dir, lay,
+                                                  d.width, d.height, d.fov_v_deg, gaze, d.poses[e], bvh=bvh)
+            t_lp += time.perf_counter() - t0
+            pix = None if n_pix == npx else np.sort(rng.choice(npx, n_pix, replace=False))
+            t0 = time.perf_counter()
+            disp = oracle.reconstruct(rgba, lay, d.width, d.height, d.fov_v_deg, gaze, pix)
+            t_rec += time.perf_counter() - t0
+            if gpu_eval is not None and k == 0:
+                precision = _precision(precision, gpu_eval(k, e), rgba, ids, disp, pix)
+        cpu_s += t_lp + t_rec
+        frame_s.append(t_lp + t_rec * npx / n_pix)
         k += 1
-    ft = float(np.mean(frames))
-    return {"value": d.width * d.height * eyes / 1e6 / ft, "unit": UNIT,
-            "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{k} frames x ({args.ref_texels} LP texels via CPU BVH + {args.ref_pixels} "
-                      f"display pixels) per eye, FP64, extrapolated to whole frames; "
-                      f"{cpu_s:.1f} s of sampled work"}
+    ft = float(np.mean(frame_s))
+    n_pix = min(npx, args.cpu_pixels)
+    out = {"value": npx * eyes / 1e6 / ft, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"{k} frames x (all {lay.total} LP texels via CPU BVH + "
+                     f"{'all' if n_pix == npx else n_pix} of {npx} display pixels) per eye, FP64, "
+                     f"ray-cast pipeline{'' if n_pix == npx else ', pixels extrapolated to whole frames'}; "
+                     f"{cpu_s:.1f} s of oracle work"}
+    return out, precision
+
+
+def _precision(acc, gpu, rgba, ids, disp, pix):
+    """Error of one GPU eye (LP slots in oracle texel order, hit ids, display
+    pixels) against the FP64 oracle's frame: hit-id agreement, the LP colour
+    error where the hits agree, and quantiles of the display error."""
+    g_lp, g_ids, g_disp = gpu
+    same = g_ids == ids
+    lp_err = np.abs(g_lp[same] - rgba[same]).max() if same.any() else 0.0
+    gd = g_disp.reshape(-1, 4)
+    if pix is not None:
+        gd = gd[pix]
+    de = np.abs(gd - disp.reshape(-1, 4)).max(axis=1)
+    cur = {"lp_hit_id_mismatch_frac": float(1.0 - same.mean()),
+           "lp_max_abs_err_where_hits_agree": float(lp_err),
+           "display_abs_err": {"p50": float(np.quantile(de, 0.5)), "p99": float(np.quantile(de, 0.99)),
+                               "p99.9": float(np.quantile(de, 0.999)), "max": float(de.max())},
+           "display_frac_err_above_1e-3": float((de > 1e-3).mean())}
+    if acc is None:
+        return cur
+    # worst over eyes
+    acc["lp_hit_id_mismatch_frac"] = max(acc["lp_hit_id_mismatch_frac"], cur["lp_hit_id_mismatch_frac"])
+    acc["lp_max_abs_err_where_hits_agree"] = max(acc["lp_max_abs_err_where_hits_agree"],
+                                                 cur["lp_max_abs_err_where_hits_agree"])
+    for q in acc["display_abs_err"]:
+        acc["display_abs_err"][q] = max(acc["display_abs_err"][q], cur["display_abs_err"][q])
+    acc["display_frac_err_above_1e-3"] = max(acc["display_frac_err_above_1e-3"],
+                                             cur["display_frac_err_above_1e-3"])
+    return acc
 
 
 def main():
@@ -718,6 +797,8 @@ def main():
     ap.add_argument("--ref-texels", type=int, default=65536)
     ap.add_argument("--ref-pixels", type=int, default=524288)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-pixels", type=int, default=1 << 23,
+                    help="display pixels per eye the oracle reconstructs in each baseline frame")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--acuity", default="paper", choices=["paper", "anisotropic", "display9", "display18"],
                     help="acuity model: the paper's pivots, the Sec. 9 anisotropy, or the Sec. 3.3 "
