@@ -100,3 +100,74 @@ def test_point_lights_in_the_ray_cast(V, torch_mod):
         V.vafr_scene_set_point_lights(h, np.zeros((300, 3)), np.ones((300, 3)))
     V.vafr_session_destroy(s)
     V.vafr_scene_destroy(h)
+
+
+def _edge_scene():
+    """Triangles that exercise every branch of the rasteriser's set-up: one
+    reaching behind the eye (near-plane clip), one wholly behind it, a
+    degenerate one, sub-pixel ones, one filling the view just past the eye,
+    one with far-away vertices, coplanar overlaps (equal-depth ties), and
+    boxes that straddle the display edges."""
+    from workloads.scenes import Scene
+    rng = np.random.default_rng(11)
+    t = []
+    t.append([[-50, -1, -20], [50, -1, -20], [0, -1, 60]])        # ground through the eye plane
+    t.append([[-1, -1, -5], [1, -1, -5], [0, 1, -5]])             # behind the eye
+    t.append([[0, 0, 5], [1, 1, 5], [2, 2, 5]])                   # degenerate (collinear)
+    for k in range(200):                                          # sub-pixel, far away
+        c = rng.uniform([-40, -10, 300], [40, 30, 400])
+        t.append(c + rng.uniform(-0.05, 0.05, (3, 3)))
+    t.append([[-0.3, -0.2, 0.2], [0.3, -0.2, 0.2], [0.0, 0.3, 0.2]])   # fills the view near the eye
+    t.append([[-1e5, 2, 1e5], [1e5, 2, 1e5], [0, 2, -1e5]])            # far-away vertices
+    t.append([[-1, 0, 3], [1, 0, 3], [0, 1.5, 3]])                     # coplanar pair: equal t
+    t.append([[-1, 0, 3], [1, 0, 3], [0, 1.5, 3]])
+    t.append([[-0.5, -0.5, 3], [1.5, -0.5, 3], [0.5, 1.0, 3]])
+    for k in range(300):                                          # mid-size, some off-screen
+        c = rng.uniform([-8, -5, 4], [8, 5, 30])
+        t.append(c + rng.uniform(-1.5, 1.5, (3, 3)))
+    tris = np.asarray(t, np.float32)
+    alb = rng.uniform(0.2, 1.0, (len(tris), 3)).astype(np.float32)
+    return Scene(tris, alb, np.float32([-0.4, -1.0, 0.6]) / np.float32(np.linalg.norm([-0.4, -1.0, 0.6])))
+
+
+@pytest.mark.parametrize("size", [(333, 197), (16, 8), (1, 1), (1031, 777)])
+def test_vbuffer_edge_cases(V, torch_mod, size):
+    """The V-buffer equals the GT cast's hits exactly on awkward geometry and
+    on display sizes that are not multiples of the raster tiles."""
+    from workloads.views import look_at_pose
+    sc = _edge_scene()
+    h, keep = device_scene(V, sc, torch_mod)
+    W, H = size
+    pose = look_at_pose((0.0, 0.5, 0.0), (0.0, 0.3, 10.0))
+    s = V.vafr_session_create(V.make_session_desc(W, H, 90.0, [pose]))
+    V.vafr_set_gaze(s, 0, 0.37 * W, 0.61 * H)
+    vb = torch_mod.empty((H, W), dtype=torch_mod.int64, device="cuda")
+    V.vafr_render_vbuffer(h, s, 0, vb)
+    gt = torch_mod.empty((H, W, 4), device="cuda")
+    ids = torch_mod.empty(H * W, dtype=torch_mod.int32, device="cuda")
+    V.vafr_render_full_gt(h, s, 0, gt, ids)
+    full = torch_mod.empty((H, W, 4), device="cuda")
+    V.vafr_shade_full_deferred(h, s, 0, vb, full)
+    torch_mod.cuda.synchronize()
+    assert V.vafr_session_check(s) == 0 and V.vafr_scene_check(h) == 0
+    key = vb.cpu().numpy().reshape(-1).view(np.uint64)
+    vid = np.where(key == np.uint64(2 ** 64 - 1), -1, (key & np.uint64(0xffffffff)).astype(np.int64))
+    assert np.array_equal(vid, ids.cpu().numpy())
+    assert torch_mod.equal(full, gt)
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)
+
+
+def test_vbuffer_empty_scene(V, torch_mod):
+    from workloads.scenes import Scene
+    from workloads.views import look_at_pose
+    sc = Scene(np.zeros((0, 3, 3), np.float32), np.zeros((0, 3), np.float32), np.float32([0, -1, 0]))
+    h, keep = device_scene(V, sc, torch_mod)
+    s = V.vafr_session_create(V.make_session_desc(64, 48, 60.0, [look_at_pose((0, 0, -3), (0, 0, 0))]))
+    V.vafr_set_gaze(s, 0, 32.0, 24.0)
+    vb = torch_mod.zeros((48, 64), dtype=torch_mod.int64, device="cuda")
+    V.vafr_render_vbuffer(h, s, 0, vb)
+    torch_mod.cuda.synchronize()
+    assert bool((vb == -1).all())      # every pixel is sky (key ~0)
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)
