@@ -48,6 +48,13 @@ OPS_PER_BOX = 18
 OPS_PER_TRI = 58
 OPS_PER_RAY = 60
 PT_DIFFUSE = 3        # the paper's maximum diffuse bounces (Sec. 8.1)
+# Deferred rasteriser, counted the same way from raster.cu: the screen-space
+# pre-filter is 2 conversions + 2 adds + 6 FMAs + 3 compares; an exact test
+# is the pixel ray (15), the shear set-up (3 abs, 5 compares/selects, 2 divides
+# + 1 reciprocal, 9 selects = 20), the watertight test on eye-relative
+# vertices (50) and the key (3).
+OPS_PER_PREFILTER = 13
+OPS_PER_PIXEL_TEST = 88
 
 
 def _dist():
@@ -486,11 +493,23 @@ def run_gpu(args, w):
                   else "fallback 6.8 TB/s",
                   "bytes_per_launch": recon_bytes, "avg_ms": recon_s * 1e3}
     if deferred:
-        # the render stage is the V-buffer rasteriser + LP lighting: no op count
-        roof_render = {"kernel": "k_vbuf_raster + k_vbuf_tiles + k_shade_lp_vbuf", "bound": "alu",
-                       "achieved": None, "peak": alu_peak, "unit": "TFLOP/s", "frac": None, "traffic": None,
-                       "peak_kind": roof_render["peak_kind"],
-                       "note": "pixel tests are not counted; stage time only", "avg_ms": render_s * 1e3}
+        # the render stage is the V-buffer rasteriser (+ the LP lighting pass, a
+        # few % of it): FP32 ops counted from the raster source per pre-filter
+        # evaluation, per pixel past it (depth pre-test) and per exact
+        # pixel-ray test, with the counts of an instrumented launch
+        g = d.gaze[0]
+        for q in range(eyes):
+            V.vafr_set_gaze(sess, q, g[q, 0], g[q, 1])
+        rs = {k: 0 for k in ("prefilter", "filtered", "tests", "atomics")}
+        for q in range(eyes):
+            for k, v in V.vafr_vbuffer_stats(scene, sess, q, vbuf).items():
+                rs[k] += v
+        r_ops = rs["prefilter"] * OPS_PER_PREFILTER + rs["filtered"] * 2 + rs["tests"] * OPS_PER_PIXEL_TEST
+        roof_render = {"kernel": "k_vbuf_raster + k_vbuf_tiles (+ k_shade_lp_vbuf)", "bound": "alu",
+                       "achieved": r_ops / render_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                       "frac": r_ops / render_s / 1e12 / alu_peak, "traffic": None,
+                       "peak_kind": roof_render["peak_kind"], "ops_per_launch": r_ops,
+                       "raster_counts_per_frame": rs, "avg_ms": render_s * 1e3}
     dominant = roof_render if render_s >= recon_s else roof_recon
 
     line = {

@@ -301,10 +301,11 @@ VAFR_API int vafr_rep_hole_count(vafr_session* session, int64_t* holes, void* st
  * ~0 for the sky.  Its coverage test is the watertight test of the pixel-
  * centre ray and the depth test keeps the smallest (distance, id), so the
  * buffer equals the GT cast's closest hits (triangle parts closer than 1e-4
- * scene units to the camera plane are not drawn).  Triangles are rasterised
- * one thread each over their clipped bounding box, boxes above 256 pixels by
- * a whole block.  Scene-owned scratch (~24 B per triangle) is allocated on
- * first use, so deferred calls on one scene must not overlap.
+ * scene units to the camera plane are not drawn).  Triangles are clipped to
+ * the view frustum; boxes of at most 64 pixels are rasterised one thread per
+ * triangle, larger ones as 16 x 8 pixel tiles spread evenly over all warps.
+ * Scene-owned scratch (~32 B per triangle) is allocated on first use, so
+ * deferred calls on one scene must not overlap.
  * vafr_render_vbuffer: the G-buffer pass of one eye into vbuf_out (device,
  *   height x width uint64, 8-byte aligned).
  * vafr_shade_lp_deferred: LP lighting: each LP texel takes the shading of the
@@ -317,6 +318,15 @@ VAFR_API int vafr_rep_hole_count(vafr_session* session, int64_t* holes, void* st
  * pass), OOM, CUDA. */
 VAFR_API int vafr_render_vbuffer(const vafr_scene* scene, vafr_session* session, int32_t eye,
                                  uint64_t* vbuf_out, void* stream);
+/* vafr_vbuffer_stats: vafr_render_vbuffer through an instrumented copy of the
+ * rasteriser (never the timed one), then out[0] = pre-filter evaluations
+ * (pixels of triangle boxes outside culled tiles), out[1] = pixels past the
+ * screen-space pre-filter, out[2] = exact pixel-ray tests run (past the depth
+ * pre-test), out[3] = atomic minima issued.  The counts after the depth
+ * pre-test depend on the order the GPU runs triangles in.  Synchronises
+ * `stream`.  Errors: as vafr_render_vbuffer. */
+VAFR_API int vafr_vbuffer_stats(const vafr_scene* scene, vafr_session* session, int32_t eye,
+                                uint64_t* vbuf_out, int64_t out[4], void* stream);
 VAFR_API int vafr_shade_lp_deferred(const vafr_scene* scene, vafr_session* session, int32_t eye,
                                     const uint64_t* vbuf, void* lp_out, void* stream);
 VAFR_API int vafr_shade_full_deferred(const vafr_scene* scene, vafr_session* session, int32_t eye,

@@ -712,7 +712,8 @@ static int deferred_scratch(const vafr_scene* scene_c, cudaStream_t st) {
     return VAFR_OK;
 }
 
-int vafr_render_vbuffer(const vafr_scene* scene, vafr_session* s, int32_t eye, uint64_t* vbuf_out, void* stream) {
+static int render_vbuffer(const vafr_scene* scene, vafr_session* s, int32_t eye, uint64_t* vbuf_out, void* stream,
+                          unsigned long long* stats) {
     if (!scene || !s || !vbuf_out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
     if (eye < 0 || eye >= s->desc.n_eyes) return fail(VAFR_ERR_INVALID_ARG, "eye %d out of range", eye);
     if (!aligned(vbuf_out, 8)) return fail(VAFR_ERR_INVALID_ARG, "vbuf must be 8-byte aligned");
@@ -723,7 +724,24 @@ int vafr_render_vbuffer(const vafr_scene* scene, vafr_session* s, int32_t eye, u
     b.n = 1;
     VbufScratch v{reinterpret_cast<unsigned long long*>(vbuf_out), scene->d_big, scene->d_big_leaf,
                   scene->d_big_first, scene->d_n_big, (unsigned)(scene->n > 0 ? scene->n : 1)};
-    CUDA_TRY(launch_vbuffer(scene->dev, b, v, st, scene->sms));
+    CUDA_TRY(launch_vbuffer(scene->dev, b, v, st, scene->sms, stats));
+    return VAFR_OK;
+}
+
+int vafr_render_vbuffer(const vafr_scene* scene, vafr_session* s, int32_t eye, uint64_t* vbuf_out, void* stream) {
+    return render_vbuffer(scene, s, eye, vbuf_out, stream, nullptr);
+}
+
+int vafr_vbuffer_stats(const vafr_scene* scene, vafr_session* s, int32_t eye, uint64_t* vbuf_out, int64_t out[4],
+                       void* stream) {
+    if (!s || !out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = as_stream(stream);
+    CUDA_TRY(cudaMemsetAsync(s->d_stats, 0, 4 * sizeof(unsigned long long), st));
+    if (int rc = render_vbuffer(scene, s, eye, vbuf_out, stream, s->d_stats)) return rc;
+    unsigned long long h[4];
+    CUDA_TRY(cudaMemcpyAsync(h, s->d_stats, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int k = 0; k < 4; ++k) out[k] = (int64_t)h[k];
     return VAFR_OK;
 }
 

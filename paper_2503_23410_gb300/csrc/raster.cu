@@ -56,12 +56,31 @@ __device__ __forceinline__ bool tri_bbox(const FrameDesc& f, float3 p[3], int& x
     float3 A[8], Bv[8];
     A[0] = p[0]; A[1] = p[1]; A[2] = p[2];
     const float hx = f.cr * (0.5f * (float)f.W + 2.0f), hy = f.cr * (0.5f * (float)f.H + 2.0f);
-    int m = clip_poly(A, 3, Bv, 0.0f, 0.0f, 1.0f, -kClipZ);
-    if (m) m = clip_poly(Bv, m, A, -1.0f, 0.0f, hx, 0.0f);
-    if (m) m = clip_poly(A, m, Bv, 1.0f, 0.0f, hx, 0.0f);
-    if (m) m = clip_poly(Bv, m, A, 0.0f, -1.0f, hy, 0.0f);
-    if (m) m = clip_poly(A, m, Bv, 0.0f, 1.0f, hy, 0.0f);
-    if (m == 0) return false;
+    // the same five planes on the vertices: all outside one plane -> nothing
+    // to draw; all inside every plane -> the vertices are the polygon
+    unsigned in_all = 0x1fu, out_any = 0u;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float3 v = p[k];
+        const unsigned in = (v.z - kClipZ >= 0.0f ? 1u : 0u) | (fmaf(v.z, hx, -v.x) >= 0.0f ? 2u : 0u) |
+                            (fmaf(v.z, hx, v.x) >= 0.0f ? 4u : 0u) | (fmaf(v.z, hy, -v.y) >= 0.0f ? 8u : 0u) |
+                            (fmaf(v.z, hy, v.y) >= 0.0f ? 16u : 0u);
+        in_all &= in;
+        out_any |= in;
+    }
+    if (out_any != 0x1fu) return false;   // some plane has every vertex outside
+    int m;
+    if (in_all == 0x1fu) {
+        Bv[0] = p[0]; Bv[1] = p[1]; Bv[2] = p[2];
+        m = 3;
+    } else {
+        m = clip_poly(A, 3, Bv, 0.0f, 0.0f, 1.0f, -kClipZ);
+        if (m) m = clip_poly(Bv, m, A, -1.0f, 0.0f, hx, 0.0f);
+        if (m) m = clip_poly(A, m, Bv, 1.0f, 0.0f, hx, 0.0f);
+        if (m) m = clip_poly(Bv, m, A, 0.0f, -1.0f, hy, 0.0f);
+        if (m) m = clip_poly(A, m, Bv, 0.0f, 1.0f, hy, 0.0f);
+        if (m == 0) return false;
+    }
     float lx = INFINITY, ly = INFINITY, hxs = -INFINITY, hys = -INFINITY;
     const float ic = 1.0f / f.cr;
     for (int k = 0; k < m; ++k) {
@@ -206,19 +225,49 @@ __device__ __forceinline__ bool maybe_inside(const TriSetup& T, int x, int y) {
 // Exact coverage of pixel (x, y): skipped when the pixel already holds a hit
 // nearer than any of the triangle's (a stale read only costs a test), else
 // the pixel ray's watertight test and an atomic minimum of the key.
+// Counters of the instrumented (STATS) rasteriser launch: pre-filter
+// evaluations (box pixels outside culled tiles), pixels past the pre-filter,
+// exact tests run (past the depth pre-test), atomic minima issued.
+struct RasterCounts {
+    unsigned long long box_px, filtered, tests, atomics;
+};
+
+template <bool STATS>
 __device__ __forceinline__ void raster_pixel(const FrameDesc& f, unsigned long long* vbuf, int x, int y,
-                                             const TriSetup& T) {
+                                             const TriSetup& T, RasterCounts& n) {
     unsigned long long* px = vbuf + (long long)y * f.W + x;
     const unsigned long long cur = *px;   // may be stale in L1: values only decrease
     if (__uint_as_float((unsigned)(cur >> 32)) < T.t_lo) return;   // sky (~0) reads as NaN: never skipped
+    if (STATS) ++n.tests;
     Ray r;
     pixel_ray(f, x, y, r);
     ray_setup_tri(r);
     const float t = tri_test_rel(r, T.A, T.B, T.C);
     if (t < INFINITY) {
         const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | (unsigned)T.id;
-        if (key < cur) atomicMin(px, key);
+        if (key < cur) {
+            atomicMin(px, key);
+            if (STATS) ++n.atomics;
+        }
     }
+}
+
+template <bool STATS>
+__device__ __forceinline__ void raster_if(const FrameDesc& f, unsigned long long* vbuf, int x, int y,
+                                          const TriSetup& T, RasterCounts& n) {
+    if (STATS) ++n.box_px;
+    if (!maybe_inside(T, x, y)) return;
+    if (STATS) ++n.filtered;
+    raster_pixel<STATS>(f, vbuf, x, y, T, n);
+}
+
+template <bool STATS>
+__device__ __forceinline__ void flush_counts(const RasterCounts& n, unsigned long long* stats) {
+    if (!STATS || stats == nullptr) return;
+    atomicAdd(stats + 0, n.box_px);
+    atomicAdd(stats + 1, n.filtered);
+    atomicAdd(stats + 2, n.tests);
+    atomicAdd(stats + 3, n.atomics);
 }
 
 // Large triangles are split into kTileW x kTileH pixel tiles of their boxes.
@@ -233,10 +282,13 @@ constexpr unsigned long long kTileMask = (1ull << kTileBits) - 1;
 
 // Pass 1: one thread per triangle; small boxes are rasterised here, large
 // ones recorded for pass 2.
+template <bool STATS>
 __global__ void __launch_bounds__(256)
 k_vbuf_raster(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned long long* vbuf, int4* big,
-              int* big_leaf, long long* big_first, unsigned long long* counter, unsigned big_cap) {
+              int* big_leaf, long long* big_first, unsigned long long* counter, unsigned big_cap,
+              unsigned long long* stats) {
     const FrameDesc& f = b.d[0];
+    RasterCounts n{};
     for (int k = blockIdx.x * 256 + threadIdx.x; k < sc.n_tris; k += gridDim.x * 256) {
         const float4 a = __ldg(sc.leaves + 3ll * k), bb = __ldg(sc.leaves + 3ll * k + 1),
                      c = __ldg(sc.leaves + 3ll * k + 2);
@@ -249,8 +301,7 @@ k_vbuf_raster(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned 
             TriSetup T;
             tri_setup(f, a, bb, c, p, T);
             for (int y = y0; y <= y1; ++y)
-                for (int x = x0; x <= x1; ++x)
-                    if (maybe_inside(T, x, y)) raster_pixel(f, vbuf, x, y, T);
+                for (int x = x0; x <= x1; ++x) raster_if<STATS>(f, vbuf, x, y, T, n);
         } else {
             const unsigned long long nt =
                 (unsigned long long)((w + kTileW - 1) / kTileW) * (unsigned long long)((h + kTileH - 1) / kTileH);
@@ -265,16 +316,20 @@ k_vbuf_raster(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned 
             }
         }
     }
+    flush_counts<STATS>(n, stats);
 }
 
 // Pass 2: every warp takes an equal run of consecutive tiles; a tile's 128
 // pixels are four rows of 16 x 2 lanes.  Records are checked against the
 // display and the scene before use, so a list damaged by an overflow (already
 // reported by pass 1) cannot lead out of bounds.
+template <bool STATS>
 __global__ void __launch_bounds__(256, 4)
 k_vbuf_tiles(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned long long* vbuf, const int4* big,
-             const int* big_leaf, const long long* big_first, const unsigned long long* counter, unsigned big_cap) {
+             const int* big_leaf, const long long* big_first, const unsigned long long* counter, unsigned big_cap,
+             unsigned long long* stats) {
     const FrameDesc& f = b.d[0];
+    RasterCounts n{};
     const unsigned long long cnt = *counter;
     const long long total = (long long)(cnt & kTileMask);
     const long long n_rec = min((long long)(cnt >> kTileBits), (long long)big_cap);
@@ -313,7 +368,8 @@ k_vbuf_tiles(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned l
         }
         const long long t = g - first;
         if (t < 0 || t >= nt) continue;
-        const int tx = bx.x + (int)(t % ntx) * kTileW, ty = bx.y + (int)(t / ntx) * kTileH;
+        const int ti = (int)t;   // < nt <= 2^23: 32-bit division
+        const int tx = bx.x + (ti % ntx) * kTileW, ty = bx.y + (ti / ntx) * kTileH;
         const int x = tx + (lane & 15);
         if (T.filt) {
             // whole tile outside one edge (at the tile's pixel-centre corner
@@ -330,9 +386,10 @@ k_vbuf_tiles(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned l
 #pragma unroll
         for (int i = 0; i < kTileH / 2; ++i) {
             const int y = ty + (lane >> 4) + 2 * i;
-            if (y <= bx.w && maybe_inside(T, x, y)) raster_pixel(f, vbuf, x, y, T);
+            if (y <= bx.w) raster_if<STATS>(f, vbuf, x, y, T, n);
         }
     }
+    flush_counts<STATS>(n, stats);
 }
 
 // Shading of display pixel (x, y) from the visibility buffer (the GT cast's
@@ -398,16 +455,25 @@ __global__ void k_leaf_of(const float4* leaves, int n, int* leaf_of) {
 }  // namespace
 
 cudaError_t launch_vbuffer(const SceneDev& sc, const SmallBatch& b, const VbufScratch& v, cudaStream_t s,
-                           int num_sms) {
+                           int num_sms, unsigned long long* stats) {
     const FrameDesc& f = b.d[0];
     cudaError_t e = cudaMemsetAsync(v.vbuf, 0xff, sizeof(unsigned long long) * (size_t)f.W * f.H, s);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(v.counter, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
     if (sc.n_tris <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)min((sc.n_tris + 255) / 256, num_sms * 16);
-    k_vbuf_raster<<<grid, 256, 0, s>>>(sc, b, v.vbuf, v.big, v.big_leaf, v.big_first, v.counter, v.big_cap);
-    k_vbuf_tiles<<<(unsigned)(num_sms * 8), 256, 0, s>>>(sc, b, v.vbuf, v.big, v.big_leaf, v.big_first, v.counter,
-                                                          v.big_cap);
+    const unsigned tgrid = (unsigned)(num_sms * 8);
+    if (stats) {
+        k_vbuf_raster<true><<<grid, 256, 0, s>>>(sc, b, v.vbuf, v.big, v.big_leaf, v.big_first, v.counter,
+                                                  v.big_cap, stats);
+        k_vbuf_tiles<true><<<tgrid, 256, 0, s>>>(sc, b, v.vbuf, v.big, v.big_leaf, v.big_first, v.counter,
+                                                  v.big_cap, stats);
+    } else {
+        k_vbuf_raster<false><<<grid, 256, 0, s>>>(sc, b, v.vbuf, v.big, v.big_leaf, v.big_first, v.counter,
+                                                   v.big_cap, nullptr);
+        k_vbuf_tiles<false><<<tgrid, 256, 0, s>>>(sc, b, v.vbuf, v.big, v.big_leaf, v.big_first, v.counter,
+                                                   v.big_cap, nullptr);
+    }
     count_launch(2);
     return cudaGetLastError();
 }

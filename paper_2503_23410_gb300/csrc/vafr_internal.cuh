@@ -150,8 +150,11 @@ struct VbufScratch {
     unsigned long long* counter;  // (records << 34) | tiles
     unsigned big_cap;
 };
+// stats (device, 4 counters, zeroed by the caller) selects an instrumented
+// copy of the rasteriser that counts pre-filter evaluations, pixels past the
+// pre-filter, exact tests and atomic minima; nullptr = the plain kernels.
 cudaError_t launch_vbuffer(const SceneDev& sc, const SmallBatch& b, const VbufScratch& v, cudaStream_t s,
-                           int num_sms);
+                           int num_sms, unsigned long long* stats = nullptr);
 cudaError_t launch_leaf_of(const SceneDev& sc, int* leaf_of, cudaStream_t s, int num_sms);
 cudaError_t launch_shade_vbuf(const SceneDev& sc, const SmallBatch& b, const unsigned long long* vbuf,
                               const int* leaf_of, bool full_res, cudaStream_t s, int num_sms);

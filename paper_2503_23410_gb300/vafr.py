@@ -93,6 +93,7 @@ _PROTOS = {
     "vafr_render_lp_rep": (ctypes.c_int, [_P, _P, _P, _P]),
     "vafr_scene_set_point_lights": (ctypes.c_int, [_P, _I32, _P, _P]),
     "vafr_render_vbuffer": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
+    "vafr_vbuffer_stats": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P]),
     "vafr_shade_lp_deferred": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P]),
     "vafr_shade_full_deferred": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P]),
     "vafr_reproject_lp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -356,6 +357,12 @@ def vafr_scene_set_point_lights(scene: int, positions, rgb) -> None:
 
 def vafr_render_vbuffer(scene: int, session: int, eye: int, vbuf_out, stream=None) -> None:
     _check(load().vafr_render_vbuffer(scene, session, int(eye), ptr(vbuf_out), stream_ptr(stream)))
+
+
+def vafr_vbuffer_stats(scene: int, session: int, eye: int, vbuf_out, stream=None):
+    out = np.zeros(4, np.int64)
+    _check(load().vafr_vbuffer_stats(scene, session, int(eye), ptr(vbuf_out), ptr(out), stream_ptr(stream)))
+    return {"prefilter": int(out[0]), "filtered": int(out[1]), "tests": int(out[2]), "atomics": int(out[3])}
 
 
 def vafr_shade_lp_deferred(scene: int, session: int, eye: int, vbuf, lp_out, stream=None) -> None:

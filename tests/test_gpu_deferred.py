@@ -171,3 +171,24 @@ def test_vbuffer_empty_scene(V, torch_mod):
     assert bool((vb == -1).all())      # every pixel is sky (key ~0)
     V.vafr_session_destroy(s)
     V.vafr_scene_destroy(h)
+
+
+def test_vbuffer_stats_counts_and_buffer(V, torch_mod):
+    """The instrumented rasteriser writes the same buffer, and its counters
+    nest: pre-filter evaluations >= pixels past it >= exact tests >= atomics."""
+    w = workload("random1k", frames=4)
+    d, sc = w.displays[0], w.scene
+    h, keep = device_scene(V, sc, torch_mod)
+    s = V.vafr_session_create(V.make_session_desc(d.width, d.height, d.fov_v_deg, d.poses))
+    V.vafr_set_gaze(s, 0, *d.gaze[0, 0])
+    vb = torch_mod.empty((d.height, d.width), dtype=torch_mod.int64, device="cuda")
+    vb2 = torch_mod.empty_like(vb)
+    V.vafr_render_vbuffer(h, s, 0, vb)
+    st = V.vafr_vbuffer_stats(h, s, 0, vb2)
+    torch_mod.cuda.synchronize()
+    assert torch_mod.equal(vb, vb2)
+    assert st["prefilter"] >= st["filtered"] >= st["tests"] >= st["atomics"] > 0
+    covered = int((vb != -1).sum())
+    assert st["atomics"] >= covered          # every covered pixel took at least one minimum
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)
