@@ -234,51 +234,94 @@ k_rep_raster(const __grid_constant__ SmallBatch b, const float4* vert, unsigned 
     }
 }
 
-// Pass 3: colours of covered right texels, the rest listed as holes.
+// Pass 3: colours of covered right texels, the rest listed as holes.  A
+// block takes 1,024 consecutive work items (4 per thread, in the LP work
+// order) and appends its holes as one contiguous run in that order, so the
+// warps of the hole cast get spatially coherent rays.
+constexpr int kResolveItems = 4;
+
 __global__ void __launch_bounds__(256)
 k_rep_resolve(const __grid_constant__ SmallBatch b, const float4* vert, const unsigned long long* zbuf,
               int2* holes, unsigned* count, int* tri_out) {
     const FrameDesc& L = b.d[0];
     const FrameDesc& R = b.d[1];
     const int C = L.n_cols;
-    for (int k = blockIdx.x * 256 + threadIdx.x; k < R.n_texels; k += gridDim.x * 256) {
-        const int2 tc = __ldg(R.work + k);
-        const int2 rc = __ldg(R.col + tc.y);
-        const int jr = tc.x - rc.x;
-        const unsigned long long key = zbuf[tc.x];
-        if (key == kEmptyKey) {
-            holes[atomicAdd(count, 1u)] = tc;
-            if (tri_out) tri_out[tc.x] = -1;
-            continue;
+    __shared__ unsigned warp_off[8];
+    __shared__ unsigned block_base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long chunk = 256ll * kResolveItems;
+    for (long long c0 = (long long)blockIdx.x * chunk; c0 < R.n_texels; c0 += (long long)gridDim.x * chunk) {
+        int2 tcq[kResolveItems];
+        unsigned hm = 0u;
+#pragma unroll
+        for (int q = 0; q < kResolveItems; ++q) {
+            const long long k = c0 + (long long)threadIdx.x * kResolveItems + q;
+            tcq[q] = make_int2(0, 0);
+            if (k >= R.n_texels) continue;
+            const int2 tc = __ldg(R.work + k);
+            tcq[q] = tc;
+            const int2 rc = __ldg(R.col + tc.y);
+            const int jr = tc.x - rc.x;
+            const unsigned long long key = zbuf[tc.x];
+            if (key == kEmptyKey) {
+                hm |= 1u << q;
+                if (tri_out) tri_out[tc.x] = -1;
+                continue;
+            }
+            const unsigned tid = (unsigned)(key & 0xffffffffu);
+            const int compact = (int)(tid >> 1), sd = (int)(tid & 1u);
+            int lo = 0, hi = C - 1;   // left column holding compact texel `compact`
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(L.col + mid).x - (2 * mid + 1) <= compact) lo = mid; else hi = mid - 1;
+            }
+            const int jl = compact - (__ldg(L.col + lo).x - (2 * lo + 1));
+            int tv[3];
+            rep_triangle(L.col, C, lo, jl, sd, tv);
+            float U[3], F[3], Z[3];
+            int copies;
+            load_tri(vert, tv, U, F, Z, copies);
+            float w[3];
+            const float f = ((float)jr + 0.5f) / (float)rc.y;
+            if (!bary(U, F, (float)tc.y, f, w) || fminf(w[0], fminf(w[1], w[2])) < -0.25f)
+                bary(U, F, (float)tc.y, f + 1.0f, w);
+            const float4 a = ld_rgba(L.lp, L.lp_fmt, tv[0]);
+            const float4 bb = ld_rgba(L.lp, L.lp_fmt, tv[1]);
+            const float4 cc = ld_rgba(L.lp, L.lp_fmt, tv[2]);
+            const float4 v = make_float4(fmaf(w[0], a.x, fmaf(w[1], bb.x, w[2] * cc.x)),
+                                         fmaf(w[0], a.y, fmaf(w[1], bb.y, w[2] * cc.y)),
+                                         fmaf(w[0], a.z, fmaf(w[1], bb.z, w[2] * cc.z)),
+                                         fmaf(w[0], a.w, fmaf(w[1], bb.w, w[2] * cc.w)));
+            st_rgba(R.lp, R.lp_fmt, tc.x, v);
+            if (jr == 0) st_rgba(R.lp, R.lp_fmt, tc.x + rc.y, v);
+            if (jr == rc.y - 1) st_rgba(R.lp, R.lp_fmt, tc.x - rc.y, v);
+            if (tri_out) tri_out[tc.x] = (int)tid;
         }
-        const unsigned tid = (unsigned)(key & 0xffffffffu);
-        const int compact = (int)(tid >> 1), s = (int)(tid & 1u);
-        int lo = 0, hi = C - 1;   // left column holding compact texel `compact`
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(L.col + mid).x - (2 * mid + 1) <= compact) lo = mid; else hi = mid - 1;
+        // block-wide exclusive scan of the hole counts, one atomic per block
+        const unsigned nh = (unsigned)__popc(hm);
+        unsigned incl = nh;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
-        const int jl = compact - (__ldg(L.col + lo).x - (2 * lo + 1));
-        int tv[3];
-        rep_triangle(L.col, C, lo, jl, s, tv);
-        float U[3], F[3], Z[3];
-        int copies;
-        load_tri(vert, tv, U, F, Z, copies);
-        float w[3];
-        const float f = ((float)jr + 0.5f) / (float)rc.y;
-        if (!bary(U, F, (float)tc.y, f, w) || fminf(w[0], fminf(w[1], w[2])) < -0.25f)
-            bary(U, F, (float)tc.y, f + 1.0f, w);
-        const float4 a = ld_rgba(L.lp, L.lp_fmt, tv[0]);
-        const float4 bb = ld_rgba(L.lp, L.lp_fmt, tv[1]);
-        const float4 cc = ld_rgba(L.lp, L.lp_fmt, tv[2]);
-        const float4 v = make_float4(fmaf(w[0], a.x, fmaf(w[1], bb.x, w[2] * cc.x)),
-                                     fmaf(w[0], a.y, fmaf(w[1], bb.y, w[2] * cc.y)),
-                                     fmaf(w[0], a.z, fmaf(w[1], bb.z, w[2] * cc.z)),
-                                     fmaf(w[0], a.w, fmaf(w[1], bb.w, w[2] * cc.w)));
-        st_rgba(R.lp, R.lp_fmt, tc.x, v);
-        if (jr == 0) st_rgba(R.lp, R.lp_fmt, tc.x + rc.y, v);
-        if (jr == rc.y - 1) st_rgba(R.lp, R.lp_fmt, tc.x - rc.y, v);
-        if (tri_out) tri_out[tc.x] = (int)tid;
+        if (lane == 31) warp_off[wid] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned t = 0u;
+            for (int q = 0; q < 8; ++q) {
+                const unsigned u = warp_off[q];
+                warp_off[q] = t;
+                t += u;
+            }
+            block_base = t ? atomicAdd(count, t) : 0u;
+        }
+        __syncthreads();
+        unsigned pos = block_base + warp_off[wid] + incl - nh;
+#pragma unroll
+        for (int q = 0; q < kResolveItems; ++q)
+            if (hm & (1u << q)) holes[pos++] = tcq[q];
+        __syncthreads();   // warp_off and block_base are rewritten by the next chunk
     }
 }
 
@@ -290,9 +333,11 @@ cudaError_t launch_reproject(const SmallBatch& b, const RepScratch& r, cudaStrea
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(r.count, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
     const unsigned grid = (unsigned)min((b.d[0].n_texels + 255) / 256, num_sms * 16);
+    const unsigned rgrid =
+        (unsigned)max(1, min((R.n_texels + 256 * kResolveItems - 1) / (256 * kResolveItems), num_sms * 8));
     k_rep_vertices<<<grid, 256, 0, s>>>(b, r.vert);
     k_rep_raster<<<grid, 256, 0, s>>>(b, r.vert, r.zbuf);
-    k_rep_resolve<<<grid, 256, 0, s>>>(b, r.vert, r.zbuf, r.holes, r.count, r.tri_out);
+    k_rep_resolve<<<rgrid, 256, 0, s>>>(b, r.vert, r.zbuf, r.holes, r.count, r.tri_out);
     count_launch(3);
     return cudaGetLastError();
 }
