@@ -205,9 +205,25 @@ VAFR_API int vafr_session_sizes(const vafr_session* session, int64_t* lp_bytes_p
                        int64_t* display_bytes_per_eye);
 /* Reads (set = 0) or writes (set = 1) the kernel variants used by this
  * session's single-session calls: cfg[0] render variant, cfg[1] reconstruct
- * tile shape (see vafr_tuning_space).  Results do not depend on the choice.
+ * tile shape (see vafr_tuning_space).  Render variant 6 takes the LP work in
+ * chunks of 32 rays and renders the chunks that were slowest in the session's
+ * previous frame first, so a launch does not end waiting for slow chunks that
+ * happened to come last.  Results do not depend on the choice.
  * Errors: INVALID_ARG (NULL, variant out of range). */
 VAFR_API int vafr_session_tuning(vafr_session* session, int32_t set, int32_t cfg[2]);
+/* Picks the session's kernel variants by timing whole frames at the current
+ * gaze: every render variant renders `warm` untimed frames (variant 6, the
+ * longest-first order, needs two frames of history) and then `iters` timed
+ * frames (render_lp of all eyes + reconstruct of every eye, CUDA events on
+ * `stream`); then every reconstruct variant is timed the same way with the
+ * chosen render variant.  The fastest pair is kept and written to cfg_out
+ * (may be NULL).
+ *   lp       device, n_eyes x vafr_session_sizes lp bytes, 16-byte aligned.
+ *   display  device, n_eyes x display bytes, 16-byte aligned.
+ * Synchronises `stream`.  Errors: INVALID_ARG (NULL, unaligned, gaze not set),
+ * CUDA. */
+VAFR_API int vafr_session_autotune(const vafr_scene* scene, vafr_session* session, void* lp, void* display,
+                                   int32_t warm, int32_t iters, int32_t cfg_out[2], void* stream);
 /* Sets the gaze point (x0, y0) in display pixels of one eye (Eq. 3).  Any
  * finite value with |x0|, |y0| <= 1e7 is accepted (gaze outside the display
  * is legal; with displays of at most 32768 pixels a side every pixel offset

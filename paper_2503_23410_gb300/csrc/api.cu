@@ -130,8 +130,12 @@ struct vafr_session {
     void* disp_internal = nullptr;     // render_frame's device display for host output
     int recon_variant = 0;
     int render_variant = 0;
+    LptState* d_lpt[2] = {nullptr, nullptr};   // longest-first order state per eye
+    unsigned lpt_frames[2] = {0u, 0u};          // frames rendered with it (parity)
 
     ~vafr_session() {
+        cudaFree(d_lpt[0]);
+        cudaFree(d_lpt[1]);
         cudaFree(d_status);
         cudaFree(d_counter);
         cudaFree(d_stats);
@@ -162,8 +166,14 @@ struct vafr_batch {
     std::vector<cudaKernelNodeParams> kernel_params;
     std::vector<vafr_frame_desc> captured;
     BigBatch* host_batch = nullptr;  // parameters of the captured launches
+    // longest-first order state per frame slot (the batch's own, so batches in
+    // flight on different streams never share one)
+    std::vector<LptState*> lpt;
+    std::vector<int> lpt_cap;
+    std::vector<unsigned> lpt_frames;
 
     ~vafr_batch() {
+        for (LptState* q : lpt) cudaFree(q);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         cudaFree(d_counter);
@@ -172,6 +182,39 @@ struct vafr_batch {
 };
 
 namespace {
+
+// One device block: the LptState, then hot[2] and flag[2] for `chunks` chunks.
+cudaError_t lpt_alloc(LptState** out, int chunks) {
+    *out = nullptr;
+    const size_t head = (sizeof(LptState) + 255) & ~(size_t)255;
+    const size_t arr = (size_t)chunks * sizeof(int);
+    char* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, head + 2 * arr + 2 * (size_t)chunks);
+    if (e != cudaSuccess) return e;
+    LptState h{};
+    h.hot[0] = reinterpret_cast<int*>(q + head);
+    h.hot[1] = reinterpret_cast<int*>(q + head + arr);
+    h.flag[0] = reinterpret_cast<unsigned char*>(q + head + 2 * arr);
+    h.flag[1] = reinterpret_cast<unsigned char*>(q + head + 2 * arr + chunks);
+    h.capacity = chunks;
+    e = cudaMemcpy(q, &h, sizeof(h), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(q); return e; }
+    *out = reinterpret_cast<LptState*>(q);
+    return cudaSuccess;
+}
+
+// The state pointer for the next frame of `st` (frame parity in bit 0), after
+// clearing the counters of the half that frame collects into.
+cudaError_t lpt_next(LptState* st, unsigned& frames, cudaStream_t s, LptState** tagged) {
+    const int p = (int)(frames & 1u);
+    cudaError_t e = cudaMemsetAsync(&st->ctr[p ^ 1], 0, sizeof(LptCounters), s);
+    if (e != cudaSuccess) return e;
+    ++frames;
+    *tagged = reinterpret_cast<LptState*>(reinterpret_cast<uintptr_t>(st) | (uintptr_t)p);
+    return cudaSuccess;
+}
+
+int lpt_chunks(int64_t n_texels) { return (int)((n_texels + kLptChunk - 1) / kLptChunk); }
 
 // FP64 per-frame set-up of one eye (Eq. 3): c_r, gaze offsets, gaze split.
 void setup_gaze(vafr_session* s, int eye, double x0, double y0) {
@@ -220,6 +263,7 @@ void fill_static(vafr_session* s, int eye) {
     f.depth = nullptr;
     f.disp = nullptr;
     f.hit_ids = nullptr;
+    f.lpt = nullptr;   // set per render (frame parity) when the longest-first order is used
 }
 
 long long recon_tiles(const FrameDesc& f, int variant) {
@@ -487,7 +531,9 @@ int vafr_session_create(const vafr_session_desc* desc, vafr_session** out) {
     };
     cudaError_t e;
     if ((e = cudaMalloc(&s->d_status, sizeof(unsigned))) != cudaSuccess) return bail(e);
-    if ((e = cudaMalloc(&s->d_counter, sizeof(unsigned long long))) != cudaSuccess) return bail(e);
+    if ((e = cudaMalloc(&s->d_counter, 2 * sizeof(unsigned long long))) != cudaSuccess) return bail(e);
+    for (int eye = 0; eye < d.n_eyes; ++eye)
+        if ((e = lpt_alloc(&s->d_lpt[eye], lpt_chunks(s->n_texels))) != cudaSuccess) return bail(e);
     if ((e = cudaMalloc(&s->d_stats, 6 * sizeof(unsigned long long))) != cudaSuccess) return bail(e);
     if ((e = cudaMemset(s->d_status, 0, sizeof(unsigned))) != cudaSuccess) return bail(e);
     if (d.lp_fxaa && (e = cudaMalloc(&s->d_luma, sizeof(float) * s->n_slots * d.n_eyes)) != cudaSuccess)
@@ -576,6 +622,8 @@ int vafr_render_lp(const vafr_scene* scene, vafr_session* s, int32_t eye_mask, v
         f.lp = static_cast<char*>(lp_out) + (size_t)b.n * s->n_slots * bpp;
         f.hit_ids = hit_ids_out ? hit_ids_out + (size_t)b.n * s->n_slots : nullptr;
         f.work_begin = b.total_work;
+        if (s->render_variant == kLptVariant)
+            CUDA_TRY(lpt_next(s->d_lpt[eye], s->lpt_frames[eye], as_stream(stream), &f.lpt));
         b.total_work += s->n_texels;
         b.d[b.n++] = f;
     }
@@ -936,7 +984,10 @@ int vafr_measure_fp32_peak(double out[2], void* stream) {
 }
 
 // ---- batching ----------------------------------------------------------------------------
-static int build_batch(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, BigBatch* b) {
+// graph = true: for a captured graph, which replays fixed launches, so frames
+// take no longest-first state (its frame parity alternates).
+static int build_batch(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, BigBatch* b,
+                       cudaStream_t st, bool graph) {
     if (!frames || n <= 0 || n > bt->max_frames)
         return fail(VAFR_ERR_INVALID_ARG, "frame count %d out of range (max %d)", n, bt->max_frames);
     std::memset(b, 0, sizeof(*b));
@@ -951,6 +1002,25 @@ static int build_batch(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n,
         FrameDesc f = s->fd[fr.eye];
         f.lp = fr.lp;
         f.lp_aa = nullptr;
+        f.lpt = nullptr;
+        if (bt->render_variant == kLptVariant && !graph) {
+            if ((int)bt->lpt.size() <= i) {
+                bt->lpt.resize(i + 1, nullptr);
+                bt->lpt_cap.resize(i + 1, 0);
+                bt->lpt_frames.resize(i + 1, 0u);
+            }
+            const int need = lpt_chunks(s->n_texels);
+            if (bt->lpt_cap[i] < need) {   // grows only (a state in use is never freed mid-flight)
+                LptState* q = nullptr;
+                CUDA_TRY(lpt_alloc(&q, need));
+                CUDA_TRY(cudaDeviceSynchronize());   // the old state may still be in use
+                cudaFree(bt->lpt[i]);
+                bt->lpt[i] = q;
+                bt->lpt_cap[i] = need;
+                bt->lpt_frames[i] = 0u;
+            }
+            CUDA_TRY(lpt_next(bt->lpt[i], bt->lpt_frames[i], st, &f.lpt));
+        }
         if (s->desc.lp_fxaa) {
             if (!fr.lp_aa || !aligned(fr.lp_aa, 16) || fr.lp_aa == fr.lp)
                 return fail(VAFR_ERR_INVALID_ARG, "frame %d: FXAA session needs a separate aligned lp_aa", i);
@@ -985,7 +1055,7 @@ int vafr_batch_create(const vafr_scene* scene, int32_t max_frames, vafr_batch** 
     auto* bt = new vafr_batch();
     bt->scene = scene;
     bt->max_frames = max_frames;
-    if (cudaMalloc(&bt->d_counter, sizeof(unsigned long long)) != cudaSuccess) {
+    if (cudaMalloc(&bt->d_counter, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         delete bt;
         return fail(VAFR_ERR_OOM, "batch counter");
     }
@@ -1004,7 +1074,7 @@ int vafr_batch_destroy(vafr_batch* batch) {
 int vafr_batch_render(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream) {
     if (!bt) return fail(VAFR_ERR_INVALID_ARG, "batch is NULL");
     BigBatch* b = new BigBatch();
-    int rc = build_batch(bt, frames, n, b);
+    int rc = build_batch(bt, frames, n, b, as_stream(stream), false);
     if (!rc) rc = launch_batch(bt, *b, as_stream(stream));
     delete b;
     return rc;
@@ -1012,7 +1082,7 @@ int vafr_batch_render(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, 
 
 int vafr_batch_capture(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream) {
     if (!bt) return fail(VAFR_ERR_INVALID_ARG, "batch is NULL");
-    int rc = build_batch(bt, frames, n, bt->host_batch);
+    int rc = build_batch(bt, frames, n, bt->host_batch, as_stream(stream), true);
     if (rc) return rc;
     if (bt->exec) { cudaGraphExecDestroy(bt->exec); bt->exec = nullptr; }
     if (bt->graph) { cudaGraphDestroy(bt->graph); bt->graph = nullptr; }
@@ -1121,6 +1191,64 @@ int vafr_batch_tuning(vafr_batch* bt, int32_t set, int32_t cfg[2]) {
     return VAFR_OK;
 }
 
+int vafr_session_autotune(const vafr_scene* scene, vafr_session* s, void* lp, void* display, int32_t warm,
+                          int32_t iters, int32_t cfg_out[2], void* stream) {
+    if (!scene || !s || !lp || !display) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    if (!aligned(lp, 16) || !aligned(display, 16)) return fail(VAFR_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    const int eyes = s->desc.n_eyes;
+    for (int e = 0; e < eyes; ++e)
+        if (!s->gaze_set[e]) return fail(VAFR_ERR_INVALID_ARG, "gaze of eye %d never set", e);
+    if (warm < 0) warm = 0;
+    if (iters <= 0) iters = 3;
+    int64_t lpb = 0, dpb = 0;
+    vafr_session_sizes(s, &lpb, &dpb);
+    cudaStream_t st = as_stream(stream);
+    auto frame = [&]() -> int {
+        int rc = vafr_render_lp(scene, s, (1 << eyes) - 1, lp, nullptr, stream);
+        for (int e = 0; e < eyes && !rc; ++e)
+            rc = vafr_reconstruct(s, e, static_cast<char*>(lp) + (size_t)e * lpb,
+                                  static_cast<char*>(display) + (size_t)e * dpb, stream);
+        return rc;
+    };
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    int rc = VAFR_OK;
+    auto time_frames = [&](float& ms) {
+        for (int i = 0; i < warm && !rc; ++i) rc = frame();
+        cudaEventRecord(e0, st);
+        for (int i = 0; i < iters && !rc; ++i) rc = frame();
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        ms = INFINITY;
+        if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+    };
+    const int keep_recon = s->recon_variant;
+    float best = INFINITY;
+    int best_r = s->render_variant;
+    for (int v = 0; v < kNumRenderVariants && !rc; ++v) {
+        s->render_variant = v;
+        float ms;
+        time_frames(ms);
+        if (ms < best) { best = ms; best_r = v; }
+    }
+    s->render_variant = best_r;
+    best = INFINITY;
+    int best_c = keep_recon;
+    for (int v = 0; v < kNumReconVariants && !rc; ++v) {
+        s->recon_variant = v;
+        float ms;
+        time_frames(ms);
+        if (ms < best) { best = ms; best_c = v; }
+    }
+    s->recon_variant = best_c;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (cfg_out) { cfg_out[0] = best_r; cfg_out[1] = best_c; }
+    return VAFR_OK;
+}
+
 int vafr_batch_autotune(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream,
                         int32_t iters) {
     if (!bt) return fail(VAFR_ERR_INVALID_ARG, "batch is NULL");
@@ -1145,7 +1273,7 @@ int vafr_batch_autotune(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n
     int best_v = 0;
     const int keep_recon = bt->recon_variant;
     for (int v = 0; v < kNumRenderVariants && !rc; ++v) {
-        rc = build_batch(bt, frames, n, b);
+        rc = build_batch(bt, frames, n, b, st, true);
         if (rc) break;
         const float ms = time_it([&] { return launch_render_lp(bt->scene->dev, *b, v, st, bt->scene->sms); });
         if (ms < best) { best = ms; best_v = v; }
@@ -1155,7 +1283,7 @@ int vafr_batch_autotune(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n
     best_v = keep_recon;
     for (int v = 0; v < kNumReconVariants && !rc; ++v) {
         bt->recon_variant = v;
-        rc = build_batch(bt, frames, n, b);
+        rc = build_batch(bt, frames, n, b, st, true);
         if (rc) break;
         const float ms = time_it([&] { return launch_reconstruct(*b, v, st); });
         if (ms < best) { best = ms; best_v = v; }

@@ -65,6 +65,136 @@ k_render_list(const SceneDev sc, const __grid_constant__ SmallBatch b, const uns
     }
 }
 
+// ---- longest-first LP render -----------------------------------------------------
+// FrameDesc.lpt carries the frame parity p in bit 0: half p of the state holds
+// this frame's list (built while the previous frame rendered), half 1 - p
+// collects the next frame's.  A chunk is listed when it took at least twice
+// the previous frame's mean; before any valid mean exists nothing is listed.
+__device__ __forceinline__ LptState* lpt_state(const FrameDesc& f, int& p) {
+    const uintptr_t v = reinterpret_cast<uintptr_t>(f.lpt);
+    p = (int)(v & 1u);
+    return reinterpret_cast<LptState*>(v & ~(uintptr_t)1);
+}
+
+// The LP render in chunks of 32 work items: first the listed chunks of every
+// frame (counter [1]), then all chunks in work order (counter [0]) except the
+// listed ones.
+template <int TPB, int ORDER, class B>
+__global__ void __launch_bounds__(TPB, 7)
+k_render_lp_lpt(const SceneDev sc, const __grid_constant__ B b) {
+    constexpr int MAXD = sizeof(b.d) / sizeof(b.d[0]);
+    __shared__ long long cbeg[MAXD + 1];   // first chunk of each frame
+    __shared__ unsigned hbeg[MAXD + 1];    // first listed chunk of each frame
+    __shared__ unsigned thr[MAXD];         // listing threshold of each frame (~0 = none)
+    // this block's chunk costs per frame, added to the state once at the end
+    // (one global atomic per block instead of one per chunk on a single address)
+    __shared__ unsigned long long bsum[MAXD];
+    __shared__ unsigned bcnt[MAXD];
+    for (int f = threadIdx.x; f < b.n; f += blockDim.x) {
+        bsum[f] = 0ull;
+        bcnt[f] = 0u;
+    }
+    if (threadIdx.x == 0) {
+        long long c = 0;
+        unsigned h = 0;
+        for (int f = 0; f < b.n; ++f) {
+            int p;
+            const LptState* S = lpt_state(b.d[f], p);
+            const int nch = (b.d[f].n_texels + kLptChunk - 1) / kLptChunk;
+            cbeg[f] = c;
+            hbeg[f] = h;
+            thr[f] = 0xffffffffu;
+            // the half is valid when the previous frame costed exactly this
+            // frame's chunks: then its list and flags cover every chunk
+            if (S && nch <= S->capacity && S->ctr[p].chunks_done == (unsigned)nch &&
+                S->ctr[p].hot_count <= (unsigned)nch) {
+                h += S->ctr[p].hot_count;
+                thr[f] = (unsigned)min(2ull * (S->ctr[p].cyc_sum / (unsigned)nch), 0xffffffffull);
+            }
+            c += nch;
+        }
+        cbeg[b.n] = c;
+        hbeg[b.n] = h;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long total_chunks = cbeg[b.n];
+    const unsigned total_hot = hbeg[b.n];
+    bool listed = true;
+    while (true) {
+        unsigned long long idx = 0ull;
+        if (lane == 0) idx = atomicAdd(b.work_counter + (listed ? 1 : 0), 1ull);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        int fi = 0, c = 0;
+        if (listed) {
+            if (idx >= total_hot) {
+                listed = false;
+                continue;
+            }
+            int lo = 0, hi = b.n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (hbeg[mid] <= (unsigned)idx) lo = mid; else hi = mid - 1;
+            }
+            fi = lo;
+            int p;
+            const LptState* S = lpt_state(b.d[fi], p);
+            c = S->hot[p][idx - hbeg[fi]];
+            if (c < 0 || c >= S->capacity) continue;
+        } else {
+            if ((long long)idx >= total_chunks) break;
+            int lo = 0, hi = b.n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (cbeg[mid] <= (long long)idx) lo = mid; else hi = mid - 1;
+            }
+            fi = lo;
+            c = (int)((long long)idx - cbeg[fi]);
+            int p;
+            const LptState* S = lpt_state(b.d[fi], p);
+            if (S && c < S->capacity && thr[fi] != 0xffffffffu && S->flag[p][c]) continue;   // listed
+        }
+        const FrameDesc& f = b.d[fi];
+        const long long t0 = clock64();
+        const int local = c * kLptChunk + lane;
+        if (local < f.n_texels) {
+            Ray r;
+            int glo, ghi;
+            const int t = lp_ray(f, local, r, glo, ghi);
+            ray_setup(r);
+            Hit h;
+            const unsigned fault = traverse<4, false, ORDER>(sc, r, h, nullptr, nullptr, nullptr);
+            if (fault) { atomicOr(f.status, fault); h.leaf = -1; h.id = -1; }
+            store_lp(f, t, glo, ghi, shade(sc, r, h), h.leaf >= 0 ? h.id : -1);
+            if (f.depth) f.depth[t] = h.leaf >= 0 ? h.t : INFINITY;
+        }
+        const unsigned cyc = (unsigned)min(clock64() - t0, 0xffffffffll);
+        const unsigned cmax = __reduce_max_sync(0xffffffffu, cyc);
+        int p;
+        LptState* S = lpt_state(f, p);
+        if (lane == 0 && S && c < S->capacity) {
+            const int q = p ^ 1;
+            const bool hot = cmax >= thr[fi];
+            S->flag[q][c] = (unsigned char)hot;
+            if (hot) {
+                const unsigned pos = atomicAdd(&S->ctr[q].hot_count, 1u);
+                if (pos < (unsigned)S->capacity) S->hot[q][pos] = c;
+            }
+            atomicAdd(&bsum[fi], (unsigned long long)cmax);
+            atomicAdd(&bcnt[fi], 1u);
+        }
+    }
+    __syncthreads();
+    for (int f = threadIdx.x; f < b.n; f += blockDim.x) {
+        int p;
+        LptState* S = lpt_state(b.d[f], p);
+        if (S && bcnt[f]) {
+            atomicAdd(&S->ctr[p ^ 1].cyc_sum, bsum[f]);
+            atomicAdd(&S->ctr[p ^ 1].chunks_done, bcnt[f]);
+        }
+    }
+}
+
 // GT: work item = (tile of 8 x 4 pixels, lane); pixel centre rays.
 template <int TPB, int FETCH, int WIDE, int ORDER, int MINB, class B>
 __global__ void __launch_bounds__(TPB, MINB)
@@ -148,9 +278,33 @@ cudaError_t launch_one(const SceneDev& sc, const B& b, cudaStream_t s, int num_s
     return cudaGetLastError();
 }
 
+template <int TPB, int ORDER, class B>
+cudaError_t launch_lpt(const SceneDev& sc, const B& b, cudaStream_t s, int num_sms) {
+    auto kern = k_render_lp_lpt<TPB, ORDER, B>;
+    // the kernel's few bytes of shared memory must not shrink the L1 the
+    // traversal lives in: ask for the smallest shared-memory carveout
+    static const cudaError_t carve =
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    if (carve != cudaSuccess) return carve;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    e = cudaMemsetAsync(b.work_counter, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    long long grid = (long long)per_sm * num_sms;
+    const long long need = (b.total_work + TPB - 1) / TPB;
+    if (need < grid) grid = need < 1 ? 1 : need;
+    kern<<<(unsigned)grid, TPB, 0, s>>>(sc, b);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
 template <bool GT, class B>
 cudaError_t launch_variant(const SceneDev& sc, const B& b, int variant, cudaStream_t s, int sms) {
     if (b.total_work <= 0) return cudaSuccess;
+    if (variant == kLptVariant)
+        return GT ? launch_one<128, 32, 4, 1, 1, GT>(sc, b, s, sms) : launch_lpt<128, 1>(sc, b, s, sms);
     // (threads per block, rays per warp fetch, tree width, child order, min blocks/SM)
     switch (variant) {
         case 0: return launch_one<128, 32, 4, 1, 1, GT>(sc, b, s, sms);

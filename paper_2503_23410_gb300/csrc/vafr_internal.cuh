@@ -51,6 +51,30 @@ struct SceneDev {
 // u(e_max) - 1/2 used for z >= tan(e_max).
 constexpr int kUTable = 2048;
 
+// ---- longest-first LP render: per frame-eye state kept from frame to frame ----
+// The LP render takes its work in chunks of 32 consecutive work items (one per
+// lane of a warp).  While a frame renders, every chunk whose traversal time
+// (the slowest lane's clock cycles) is at least twice the previous frame's
+// mean is listed, and the next frame renders the listed chunks before all
+// others.  Only the order changes: every chunk is still rendered exactly once,
+// so the results are those of the plain order.  Without it the slowest chunks,
+// wherever they fall in the work order, decide when the launch ends.  The
+// state has two halves used alternately (frame parity): the half being read
+// holds this frame's list, the other collects the next frame's; the host
+// clears the collecting half's counters before each frame.
+struct LptCounters {
+    unsigned long long cyc_sum;   // sum of the chunk costs of the frame
+    unsigned chunks_done;         // chunks costed
+    unsigned hot_count;           // entries of the list
+};
+struct LptState {
+    LptCounters ctr[2];
+    int* hot[2];                  // [capacity] listed chunks
+    unsigned char* flag[2];       // [capacity] 1 = listed
+    int capacity;                 // chunks the arrays hold
+};
+constexpr int kLptChunk = 32;
+
 // ---- one frame-eye of work (kernel parameter; filled on the host in FP64,
 // rounded to FP32) ------------------------------------------------------------
 struct FrameDesc {
@@ -82,6 +106,7 @@ struct FrameDesc {
     long long work_begin;   // first global work item (render) of this frame
     long long tile_begin;   // first global tile (reconstruct) of this frame
     long long aa_begin;     // first global FXAA texel of this frame
+    LptState* lpt;          // longest-first state | frame parity (bit 0), or nullptr
 };
 
 template <int MAXD>
@@ -90,7 +115,7 @@ struct Batch {
     long long total_work;   // sum of render work items
     long long total_tiles;  // sum of reconstruct tiles
     long long total_aa;     // sum of FXAA texels (frames with lp_aa)
-    unsigned long long* work_counter;  // device counter (persistent fetch)
+    unsigned long long* work_counter;  // device counters (persistent fetch; [1]: longest-first list)
     FrameDesc d[MAXD];
 };
 
@@ -100,8 +125,10 @@ using BigBatch = Batch<VAFR_MAX_BATCH>;
 static_assert(sizeof(BigBatch) + sizeof(SceneDev) <= 32764, "batch too large for kernel params");
 
 // ---- launch interfaces ---------------------------------------------------------
-// Render variants: threads per block, tree width, child order, register cap.
-constexpr int kNumRenderVariants = 6;
+// Render variants: threads per block, tree width, child order, register cap;
+// variant 6 is the longest-first LP order (the GT keeps variant 0's kernel).
+constexpr int kNumRenderVariants = 7;
+constexpr int kLptVariant = 6;
 // Reconstruct variants: column-run tiles (0-3) and row tiles (4-7).
 constexpr int kNumReconVariants = 8;
 

@@ -102,6 +102,7 @@ _PROTOS = {
     "vafr_render_frame": (ctypes.c_int, [_P, _P, _P, _P]),
     "vafr_traversal_stats": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
     "vafr_measure_fp32_peak": (ctypes.c_int, [_P, _P]),
+    "vafr_session_autotune": (ctypes.c_int, [_P, _P, _P, _P, _I32, _I32, _P, _P]),
     "vafr_batch_create": (ctypes.c_int, [_P, _I32, _P]),
     "vafr_batch_destroy": (ctypes.c_int, [_P]),
     "vafr_batch_render": (ctypes.c_int, [_P, _P, _I32, _P]),
@@ -313,6 +314,16 @@ def vafr_session_tuning(session: int, cfg: Optional[Sequence[int]] = None):
     c = (ctypes.c_int32 * 2)(*(cfg if cfg is not None else (0, 0)))
     _check(load().vafr_session_tuning(session, 1 if cfg is not None else 0,
                                       ctypes.cast(c, ctypes.c_void_p)))
+    return int(c[0]), int(c[1])
+
+
+def vafr_session_autotune(scene: int, session: int, lp, display, warm: int = 3, iters: int = 5,
+                          stream=None):
+    """Times every render and reconstruct variant on whole frames at the
+    current gaze, keeps the fastest pair and returns it."""
+    c = (ctypes.c_int32 * 2)(0, 0)
+    _check(load().vafr_session_autotune(scene, session, ptr(lp), ptr(display), int(warm), int(iters),
+                                        ctypes.cast(c, ctypes.c_void_p), stream_ptr(stream)))
     return int(c[0]), int(c[1])
 
 

@@ -67,7 +67,7 @@ def test_batch_equals_single(V, torch_mod, setup):
     h, sessions, _ = setup
     ref = _single(V, torch_mod, h, sessions)
     b = V.vafr_batch_create(h, 16)
-    for cfg in [(0, 0), (1, 2), (2, 3), (3, 1), (4, 0), (5, 1), (0, 4), (1, 5), (2, 6), (3, 7)]:
+    for cfg in [(0, 0), (1, 2), (2, 3), (3, 1), (4, 0), (5, 1), (6, 0), (6, 3), (0, 4), (1, 5), (2, 6), (3, 7)]:
         V.vafr_batch_tuning(b, cfg)
         V.vafr_batch_render(b, _frames(sessions))
         torch_mod.cuda.synchronize()
@@ -121,3 +121,60 @@ def test_batch_rejects_bad_frames(V, torch_mod, setup):
     with pytest.raises(V.VafrError):
         V.vafr_batch_replay(b)                            # nothing captured
     V.vafr_batch_destroy(b)
+
+
+def test_longest_first_order_keeps_results(V, torch_mod, setup):
+    """Render variant 6 renders the previous frame's slowest chunks first: the
+    LP buffers and displays stay bitwise those of the plain order, frame after
+    frame (the order is rebuilt from each frame's costs), across gaze changes,
+    in the single-session path and in a replayed graph."""
+    h, sessions, _ = setup
+    for s, *_ in sessions:
+        V.vafr_session_tuning(s, (6, 0))
+    try:
+        for it in range(3):
+            got = _single(V, torch_mod, h, sessions)
+            for s, *_ in sessions:
+                V.vafr_session_tuning(s, (0, 0))
+            ref = _single(V, torch_mod, h, sessions)
+            for s, *_ in sessions:
+                V.vafr_session_tuning(s, (6, 0))
+            for (lp, d), (rlp, rd) in zip(got, ref):
+                assert np.array_equal(lp, rlp)
+                assert np.array_equal(d, rd)
+            if it == 1:
+                for k, (s, *_r) in enumerate(sessions):
+                    V.vafr_set_gaze(s, 0, 20.0 + 7 * k, 30.0)
+    finally:
+        for s, *_ in sessions:
+            V.vafr_session_tuning(s, (0, 0))
+    b = V.vafr_batch_create(h, 16)
+    V.vafr_batch_tuning(b, (6, 0))
+    V.vafr_batch_capture(b, _frames(sessions))
+    for it in range(3):
+        for k, (s, bufs, lpb, dpb) in enumerate(sessions):
+            V.vafr_set_gaze(s, 1, 60.0 + 17 * it + k, 50.0 + 3 * it)
+        V.vafr_batch_replay(b)
+        torch_mod.cuda.synchronize()
+        got = _read(sessions)
+        ref = _single(V, torch_mod, h, sessions)
+        for (lp, d), (rlp, rd) in zip(got, ref):
+            assert np.array_equal(lp, rlp)
+            assert np.array_equal(d, rd)
+    V.vafr_batch_destroy(b)
+
+
+def test_session_autotune_picks_valid_variants(V, torch_mod, setup):
+    h, sessions, _ = setup
+    s, bufs, lpb, dpb = sessions[1]
+    lp = torch_mod.empty(2 * lpb, dtype=torch_mod.uint8, device="cuda")
+    disp = torch_mod.empty(2 * dpb, dtype=torch_mod.uint8, device="cuda")
+    before = _single(V, torch_mod, h, [sessions[1]])
+    r, c = V.vafr_session_autotune(h, s, lp, disp, warm=2, iters=2)
+    nr, nc = V.vafr_tuning_space()
+    assert 0 <= r < nr and 0 <= c < nc
+    assert V.vafr_session_tuning(s) == (r, c)
+    after = _single(V, torch_mod, h, [sessions[1]])
+    for (lp0, d0), (lp1, d1) in zip(before, after):
+        assert np.array_equal(lp0, lp1) and np.array_equal(d0, d1)
+    V.vafr_session_tuning(s, (0, 0))
