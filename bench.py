@@ -286,7 +286,10 @@ def run_gpu(args, w):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     nf = len(d.gaze)
     tuning = None
-    if not (pt or rep or deferred or args.no_tune):
+    if args.tuning:
+        tuning = tuple(int(x) for x in args.tuning.split(","))
+        V.vafr_session_tuning(sess, tuning)
+    elif not (pt or rep or deferred or args.no_tune):
         # kernel variants picked on whole frames at the first gaze (untimed set-up)
         g0 = d.gaze[0]
         for e in range(eyes):
@@ -535,7 +538,8 @@ def run_gpu(args, w):
                    "pipeline": "deferred (visibility buffer + LP lighting)" if deferred else "ray casting",
                    "point_lights": int(args.point_lights),
                    "tuning": ({"render_variant": tuning[0], "reconstruct_variant": tuning[1],
-                               "by": "vafr_session_autotune on whole frames at the first gaze, before warm-up"}
+                               "by": "--tuning" if args.tuning else
+                               "vafr_session_autotune on whole frames at the first gaze, before warm-up"}
                               if tuning else "default variants (0, 0)"),
                    "parallelism": f"replicas x{ws} (independent sessions, no collective)"},
         "fps": 1e3 / float(step_ms.mean()),
@@ -849,6 +853,9 @@ def main():
                          "holes ray cast (binocular workloads)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default kernel variants instead of vafr_session_autotune's choice")
+    ap.add_argument("--tuning", default=None,
+                    help="render,reconstruct variants to use instead of autotuning (e.g. 6,2; for "
+                         "profiling runs, where the tuner's timings are distorted)")
     ap.add_argument("--fxaa", action="store_true",
                     help="run the LP-space FXAA pass (Sec. 3.4) inside each timed frame")
     args = ap.parse_args()
