@@ -145,7 +145,7 @@ cudaError_t launch_render_gt(const SceneDev& scene, const B& batch, int variant,
                              cudaStream_t s, int num_sms);
 template <class B>
 cudaError_t launch_reconstruct(const B& batch, int variant, cudaStream_t s);
-// Path-traced LP buffers (render.cu): one path per texel, `depth` diffuse
+// Path-traced LP buffers (pathtrace.cu): one path per texel, `depth` diffuse
 // bounces; FrameDesc.hit_ids, when set, receives depth + 2 ints per slot.
 template <class B>
 cudaError_t launch_path_lp(const SceneDev& scene, const B& batch, unsigned long long seed, int depth,
@@ -167,7 +167,7 @@ struct RepScratch {
     int* tri_out;                 // [right slots] winning triangle id / -1, or nullptr
 };
 cudaError_t launch_reproject(const SmallBatch& batch, const RepScratch& r, cudaStream_t s, int num_sms);
-// Deferred path (render.cu): visibility buffer of frame d[0] at display
+// Deferred path (raster.cu): visibility buffer of frame d[0] at display
 // resolution, then LP or full-resolution lighting from it.
 struct VbufScratch {
     unsigned long long* vbuf;   // [H][W] (hit distance bits << 32) | triangle id, ~0 = sky
