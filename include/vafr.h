@@ -429,6 +429,11 @@ VAFR_API int vafr_measure_fp32_peak(double out[2], void* stream);
  *                       each, CUDA events) and keeps the fastest.
  *   vafr_batch_tuning   reads (set = 0) or writes (set = 1) the choice:
  *                       cfg[0] render variant, cfg[1] reconstruct variant.
+ * With render variant 6 (longest-first order) vafr_batch_render keeps one
+ * order state per frame position of the batch (the first render at a
+ * position, or one whose session has more LP texels than before, allocates
+ * it and synchronises the device); captured graphs and the autotuner's
+ * timings run variant 6 without an order (chunks in work order).
  * Errors: INVALID_ARG (n out of range, frame with a NULL buffer, eye out of
  * range, session never given a gaze), CUDA. */
 VAFR_API int vafr_batch_create(const vafr_scene* scene, int32_t max_frames, vafr_batch** out);
