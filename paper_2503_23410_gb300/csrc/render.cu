@@ -80,10 +80,13 @@ __device__ __forceinline__ LptState* lpt_state(const FrameDesc& f, int& p) {
 // frame (counter [1]), then all chunks in work order (counter [0]) except the
 // listed ones.
 template <int TPB, int ORDER, class B>
-__global__ void __launch_bounds__(TPB, 7)
+__global__ void __launch_bounds__(TPB)
 k_render_lp_lpt(const SceneDev sc, const __grid_constant__ B b) {
+    // Everything the fetch needs lives in shared memory and is re-read there,
+    // so the traversal keeps the registers of the plain kernel (a register cap
+    // on this kernel costs more than the order gains).
     constexpr int MAXD = sizeof(b.d) / sizeof(b.d[0]);
-    __shared__ long long cbeg[MAXD + 1];   // first chunk of each frame
+    __shared__ int cbeg[MAXD + 1];         // first chunk of each frame
     __shared__ unsigned hbeg[MAXD + 1];    // first listed chunk of each frame
     __shared__ unsigned thr[MAXD];         // listing threshold of each frame (~0 = none)
     // this block's chunk costs per frame, added to the state once at the end
@@ -95,7 +98,7 @@ k_render_lp_lpt(const SceneDev sc, const __grid_constant__ B b) {
         bcnt[f] = 0u;
     }
     if (threadIdx.x == 0) {
-        long long c = 0;
+        int c = 0;
         unsigned h = 0;
         for (int f = 0; f < b.n; ++f) {
             int p;
@@ -118,23 +121,21 @@ k_render_lp_lpt(const SceneDev sc, const __grid_constant__ B b) {
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const long long total_chunks = cbeg[b.n];
-    const unsigned total_hot = hbeg[b.n];
     bool listed = true;
     while (true) {
-        unsigned long long idx = 0ull;
-        if (lane == 0) idx = atomicAdd(b.work_counter + (listed ? 1 : 0), 1ull);
+        unsigned idx = 0u;
+        if (lane == 0) idx = (unsigned)atomicAdd(b.work_counter + (listed ? 1 : 0), 1ull);
         idx = __shfl_sync(0xffffffffu, idx, 0);
-        int fi = 0, c = 0;
+        int fi, c;
         if (listed) {
-            if (idx >= total_hot) {
+            if (idx >= hbeg[b.n]) {
                 listed = false;
                 continue;
             }
             int lo = 0, hi = b.n - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (hbeg[mid] <= (unsigned)idx) lo = mid; else hi = mid - 1;
+                if (hbeg[mid] <= idx) lo = mid; else hi = mid - 1;
             }
             fi = lo;
             int p;
@@ -142,20 +143,20 @@ k_render_lp_lpt(const SceneDev sc, const __grid_constant__ B b) {
             c = S->hot[p][idx - hbeg[fi]];
             if (c < 0 || c >= S->capacity) continue;
         } else {
-            if ((long long)idx >= total_chunks) break;
+            if (idx >= (unsigned)cbeg[b.n]) break;
             int lo = 0, hi = b.n - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (cbeg[mid] <= (long long)idx) lo = mid; else hi = mid - 1;
+                if ((unsigned)cbeg[mid] <= idx) lo = mid; else hi = mid - 1;
             }
             fi = lo;
-            c = (int)((long long)idx - cbeg[fi]);
+            c = (int)idx - cbeg[fi];
             int p;
             const LptState* S = lpt_state(b.d[fi], p);
             if (S && c < S->capacity && thr[fi] != 0xffffffffu && S->flag[p][c]) continue;   // listed
         }
         const FrameDesc& f = b.d[fi];
-        const long long t0 = clock64();
+        const unsigned t0 = (unsigned)clock();
         const int local = c * kLptChunk + lane;
         if (local < f.n_texels) {
             Ray r;
@@ -168,8 +169,7 @@ k_render_lp_lpt(const SceneDev sc, const __grid_constant__ B b) {
             store_lp(f, t, glo, ghi, shade(sc, r, h), h.leaf >= 0 ? h.id : -1);
             if (f.depth) f.depth[t] = h.leaf >= 0 ? h.t : INFINITY;
         }
-        const unsigned cyc = (unsigned)min(clock64() - t0, 0xffffffffll);
-        const unsigned cmax = __reduce_max_sync(0xffffffffu, cyc);
+        const unsigned cmax = __reduce_max_sync(0xffffffffu, (unsigned)clock() - t0);
         int p;
         LptState* S = lpt_state(f, p);
         if (lane == 0 && S && c < S->capacity) {
