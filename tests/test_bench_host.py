@@ -1,0 +1,56 @@
+"""Host-side logic of bench.py (no GPU): the precision summary against the
+oracle and the whole-frame oracle baseline on a small workload."""
+
+import types
+
+import numpy as np
+
+import bench
+import oracle
+from workloads import workload
+
+
+def test_precision_summary():
+    rng = np.random.default_rng(3)
+    n, W, H = 1000, 8, 4
+    ref = rng.uniform(0, 1, (n, 4))
+    ids = np.arange(n)
+    gpu_lp = ref + 1e-6
+    gids = ids.copy()
+    gids[7] = -1                                  # one disagreeing hit
+    gpu_lp[7] = 0.0                               # ... whose colour is not counted
+    disp = rng.uniform(0, 1, (H * W, 4))
+    gdisp = disp.copy()
+    gdisp[5, 2] += 0.5                            # one bad pixel
+    p = bench._precision(None, (gpu_lp, gids, gdisp.reshape(H, W, 4)), ref, ids, disp, None)
+    assert abs(p["lp_hit_id_mismatch_frac"] - 1.0 / n) < 1e-12
+    assert abs(p["lp_max_abs_err_where_hits_agree"] - 1e-6) < 1e-9
+    assert abs(p["display_abs_err"]["max"] - 0.5) < 1e-12
+    assert abs(p["display_frac_err_above_1e-3"] - 1.0 / (H * W)) < 1e-12
+    # a second eye keeps the worst of both
+    q = bench._precision(dict(p, display_abs_err=dict(p["display_abs_err"])),
+                         (ref, ids, disp.reshape(H, W, 4)), ref, ids, disp, None)
+    assert q["display_abs_err"]["max"] == p["display_abs_err"]["max"]
+    # a pixel sample selects the same pixels on both sides
+    pix = np.array([1, 5, 9])
+    r = bench._precision(None, (gpu_lp, gids, gdisp.reshape(H, W, 4)), ref, ids, disp[pix], pix)
+    assert abs(r["display_abs_err"]["max"] - 0.5) < 1e-12
+
+
+def test_cpu_baseline_small_workload():
+    w = workload("random1k", frames=4)
+    args = types.SimpleNamespace(cpu_seconds=0.0, cpu_pixels=1 << 23)
+    lay = oracle.lp_layout()
+    d = w.displays[0]
+
+    def gpu_eval(k, e):     # the oracle standing in for the GPU: zero error
+        rgba, ids, _, _, _ = oracle.render_lp(w.scene.tris, w.scene.albedo, w.scene.light_dir, lay,
+                                              d.width, d.height, d.fov_v_deg, d.gaze[k, e], d.poses[e])
+        out = oracle.reconstruct(rgba, lay, d.width, d.height, d.fov_v_deg, d.gaze[k, e])
+        return rgba, ids, out.reshape(d.height, d.width, 4)
+
+    line, prec = bench.cpu_baseline(args, w, gpu_eval)
+    assert line["kind"] == "oracle" and line["value"] > 0 and line["cores"] >= 1
+    assert "all 1061630 LP texels" in line["sample"]
+    assert prec["lp_hit_id_mismatch_frac"] == 0.0
+    assert prec["display_abs_err"]["max"] == 0.0
