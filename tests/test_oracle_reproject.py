@@ -79,3 +79,45 @@ def test_occluder_opens_holes_beside_it(layout):
     ok = (tri >= 0) & inner
     agree = np.all(np.abs(right[ok] - direct[ok]) < 1e-9, axis=1)
     assert agree.mean() > 0.99
+
+
+def _right_uf(P, pose, gaze, acuity):
+    """(U, F) of world points in the right eye's LP coordinates, from the
+    definitions: camera coordinates, screen point, e = atan(c_r r) (Eq. 3),
+    U = u(e) - 1/2 (Eq. 12), F = angle / 360 with y down."""
+    R, eye = pose[:, :3], pose[:, 3]
+    c = (P - eye) @ R
+    cr = 2.0 * np.tan(np.radians(FOV) / 2) / H
+    px = W / 2 + c[:, 0] / (c[:, 2] * cr)
+    py = H / 2 - c[:, 1] / (c[:, 2] * cr)
+    dx, dy = px - gaze[0], py - gaze[1]
+    e = np.minimum(np.degrees(np.arctan(cr * np.hypot(dx, dy))), 60.0)
+    U = acuity.u_of_e(e) - 0.5
+    F = np.mod(np.arctan2(dy, dx), 2 * np.pi) / (2 * np.pi)
+    return U, F
+
+
+def test_affine_data_in_lp_coordinates_is_reproduced(layout, acuity):
+    # left colours that are an affine function of where each left texel's hit
+    # point lands in the right eye's (U, F) plane: the barycentric
+    # interpolation there must reproduce that function at every covered right
+    # texel centre (U = c, F = (j + 1/2) / n_c), away from the angular seam
+    tris, alb, L = _plane_scene()
+    poses = eye_pair_poses(HEAD, 0.063)
+    gl, gr = (610.0, 350.0), (655.0, 372.0)
+    _, t = _left(tris, alb, L, layout, gl, poses[0])
+    o, d, _ = oracle.lp_rays(layout, W, H, FOV, gl, poses[0])
+    hit = np.isfinite(t)
+    P = o + np.where(hit, t, 0.0)[:, None] * d
+    U, F = _right_uf(P, poses[1], gr, acuity)
+    A = np.array([[0.1, 1e-3, 0.4], [0.7, -5e-4, 0.2], [0.3, 2e-4, -0.3]])
+    left = np.ones((layout.total, 4))
+    left[:, :3] = A[:, 0] + np.outer(U, A[:, 1]) + np.outer(F, A[:, 2])
+    right, tri = oracle.reproject_lp(layout, W, H, FOV, gl, poses[0], gr, poses[1], t, left)
+    col = np.repeat(np.arange(layout.n_cols), layout.n_col)
+    j = np.arange(layout.total) - layout.off_col[col]
+    Fc = (j + 0.5) / layout.n_col[col]
+    want = A[:, 0] + np.outer(col, A[:, 1]) + np.outer(Fc, A[:, 2])
+    sel = (tri >= 0) & (Fc > 0.1) & (Fc < 0.9) & (col >= 4) & (col < layout.n_cols - 8)
+    assert sel.sum() > 0.7 * layout.total
+    np.testing.assert_allclose(right[sel, :3], want[sel], atol=1e-9)
