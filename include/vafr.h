@@ -318,7 +318,7 @@ VAFR_API int vafr_rep_hole_count(vafr_session* session, int64_t* holes, void* st
  * centre ray and the depth test keeps the smallest (distance, id), so the
  * buffer equals the GT cast's closest hits (triangle parts closer than 1e-4
  * scene units to the camera plane are not drawn).  Triangles are clipped to
- * the view frustum; boxes of at most 64 pixels are rasterised one thread per
+ * the view frustum; boxes of at most 128 pixels are rasterised one thread per
  * triangle, larger ones as 16 x 8 pixel tiles spread evenly over all warps.
  * Scene-owned scratch (~32 B per triangle) is allocated on first use, so
  * deferred calls on one scene must not overlap.

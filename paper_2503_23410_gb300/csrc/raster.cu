@@ -275,7 +275,7 @@ __device__ __forceinline__ void flush_counts(const RasterCounts& n, unsigned lon
 // records' first tiles increase with the slot: the tile pass finds a tile's
 // record by binary search.  n_tris < 2^30 bounds the slots; a tile sum that
 // would pass 2^kTileBits is reported as a fault.
-constexpr int kSmallTriPixels = 64;   // larger boxes go to the tile pass
+constexpr int kSmallTriPixels = 128;  // larger boxes go to the tile pass
 constexpr int kTileW = 16, kTileH = 8;
 constexpr int kTileBits = 34;
 constexpr unsigned long long kTileMask = (1ull << kTileBits) - 1;
