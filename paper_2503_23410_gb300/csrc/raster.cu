@@ -277,6 +277,8 @@ __device__ __forceinline__ void flush_counts(const RasterCounts& n, unsigned lon
 // would pass 2^kTileBits is reported as a fault.
 constexpr int kSmallTriPixels = 128;  // larger boxes go to the tile pass
 constexpr int kTileW = 16, kTileH = 8;
+constexpr int kTileRows = 32 / kTileW;   // tile rows a warp covers per pass
+static_assert(32 % kTileW == 0 && kTileH % kTileRows == 0, "tile shape");
 constexpr int kTileBits = 34;
 constexpr unsigned long long kTileMask = (1ull << kTileBits) - 1;
 
@@ -370,7 +372,7 @@ k_vbuf_tiles(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned l
         if (t < 0 || t >= nt) continue;
         const int ti = (int)t;   // < nt <= 2^23: 32-bit division
         const int tx = bx.x + (ti % ntx) * kTileW, ty = bx.y + (ti / ntx) * kTileH;
-        const int x = tx + (lane & 15);
+        const int x = tx + lane % kTileW;
         if (T.filt) {
             // whole tile outside one edge (at the tile's pixel-centre corner
             // that maximises it, with twice the slack): skip
@@ -384,8 +386,8 @@ k_vbuf_tiles(const SceneDev sc, const __grid_constant__ SmallBatch b, unsigned l
         }
         if (x > bx.z) continue;
 #pragma unroll
-        for (int i = 0; i < kTileH / 2; ++i) {
-            const int y = ty + (lane >> 4) + 2 * i;
+        for (int i = 0; i < kTileH / kTileRows; ++i) {
+            const int y = ty + lane / kTileW + kTileRows * i;
             if (y <= bx.w) raster_if<STATS>(f, vbuf, x, y, T, n);
         }
     }
