@@ -558,10 +558,12 @@ def run_gpu(args, w):
                 "path": ("the timed frame (path-traced, VaFR_Rep or deferred LP buffer, then "
                          "vafr_reconstruct), then one device-to-host copy into pinned memory, "
                          "synchronous per frame") if (pt or rep or deferred) else
-                        ("vafr_batch_render into pinned host frames, 2 frames in flight on 2 "
-                         "streams (C ABI); gaze passed by value each step"),
+                        ("vafr_batch_render into pinned host frames (reconstruction into the "
+                         "batch's device staging buffers, copy-engine transfer to the host), 2 "
+                         "frames in flight on 2 streams (C ABI); gaze passed by value each step"),
                 "sync_per_frame_value": e2e_sync_value,
-                "sync_per_frame_path": "vafr_render_frame into pinned host memory, one "
+                "sync_per_frame_path": "vafr_render_frame into pinned host memory (the "
+                                       "reconstruction writes it through its device alias), one "
                                        "synchronous call per frame"},
         "gpu_launches": int(launches),
         "wall_s_timed_loop": wall,

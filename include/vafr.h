@@ -121,7 +121,10 @@ typedef struct {
     vafr_session* session;
     int32_t       eye;
     void*         lp;        /* device, LP buffer of that eye (see vafr_render_lp) */
-    void*         display;   /* device, height x width pixels of display_format     */
+    void*         display;   /* device or page-locked host memory, height x width
+                                pixels of display_format (host displays are written
+                                through a device staging buffer of the batch and a
+                                copy-engine transfer on the same stream)           */
     void*         lp_aa;     /* device, second LP buffer receiving the FXAA pass;
                                 required when the session has lp_fxaa, else ignored */
 } vafr_frame_desc;
@@ -435,7 +438,7 @@ VAFR_API int vafr_measure_fp32_peak(double out[2], void* stream);
  * it and synchronises the device); captured graphs and the autotuner's
  * timings run variant 6 without an order (chunks in work order).
  * Errors: INVALID_ARG (n out of range, frame with a NULL buffer, eye out of
- * range, session never given a gaze), CUDA. */
+ * range, session never given a gaze, display in pageable host memory), CUDA. */
 VAFR_API int vafr_batch_create(const vafr_scene* scene, int32_t max_frames, vafr_batch** out);
 VAFR_API int vafr_batch_destroy(vafr_batch* batch);
 VAFR_API int vafr_batch_render(vafr_batch* batch, const vafr_frame_desc* frames, int32_t n, void* stream);

@@ -171,9 +171,21 @@ struct vafr_batch {
     std::vector<LptState*> lpt;
     std::vector<int> lpt_cap;
     std::vector<unsigned> lpt_frames;
+    // displays in page-locked host memory: the reconstruction writes a device
+    // staging buffer per frame position, which the copy engine then moves to
+    // the host (faster over the CPU-GPU link than the kernel's own stores)
+    struct HostCopy {
+        void* dst;
+        const void* src;
+        size_t bytes;
+    };
+    std::vector<void*> stage;
+    std::vector<size_t> stage_cap;
+    std::vector<HostCopy> copies;   // of the last built batch
 
     ~vafr_batch() {
         for (LptState* q : lpt) cudaFree(q);
+        for (void* q : stage) cudaFree(q);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         cudaFree(d_counter);
@@ -903,8 +915,9 @@ int vafr_render_frame(const vafr_scene* scene, vafr_session* s, void* display_ou
     if (!s->lp_internal) CUDA_TRY(cudaMalloc(&s->lp_internal, (size_t)lpb * eyes));
     // Where the display goes: device memory as is; pinned (page-locked or
     // registered) host memory through its device alias, so the reconstruction
-    // kernel writes it directly over the CPU-GPU link; pageable host memory
-    // through a device buffer and one device-to-host copy.
+    // kernel writes it directly over the CPU-GPU link (for one synchronous
+    // frame this beats a device display plus a copy, which cannot overlap);
+    // pageable host memory through a device buffer and one device-to-host copy.
     cudaPointerAttributes pa;
     void* target = nullptr;
     bool copy_out = false;
@@ -992,6 +1005,7 @@ static int build_batch(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n,
         return fail(VAFR_ERR_INVALID_ARG, "frame count %d out of range (max %d)", n, bt->max_frames);
     std::memset(b, 0, sizeof(*b));
     b->work_counter = bt->d_counter;
+    bt->copies.clear();
     for (int i = 0; i < n; ++i) {
         const vafr_frame_desc& fr = frames[i];
         vafr_session* s = fr.session;
@@ -1028,6 +1042,31 @@ static int build_batch(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n,
             f.luma = s->d_luma + (size_t)fr.eye * s->n_slots;
         }
         f.disp = fr.display;
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, fr.display) != cudaSuccess) {
+            cudaGetLastError();
+            pa.type = cudaMemoryTypeUnregistered;
+        }
+        if (pa.type == cudaMemoryTypeUnregistered)
+            return fail(VAFR_ERR_INVALID_ARG, "frame %d: display must be device or page-locked host memory", i);
+        if (pa.type == cudaMemoryTypeHost) {
+            int64_t lpb = 0, dpb = 0;
+            vafr_session_sizes(s, &lpb, &dpb);
+            if ((int)bt->stage.size() <= i) {
+                bt->stage.resize(i + 1, nullptr);
+                bt->stage_cap.resize(i + 1, 0);
+            }
+            if (bt->stage_cap[i] < (size_t)dpb) {   // grows only
+                void* q = nullptr;
+                CUDA_TRY(cudaMalloc(&q, (size_t)dpb));
+                CUDA_TRY(cudaDeviceSynchronize());   // the old buffer may still be in use
+                cudaFree(bt->stage[i]);
+                bt->stage[i] = q;
+                bt->stage_cap[i] = (size_t)dpb;
+            }
+            f.disp = bt->stage[i];
+            bt->copies.push_back({fr.display, bt->stage[i], (size_t)dpb});
+        }
         f.hit_ids = nullptr;
         f.work_begin = b->total_work;
         f.tile_begin = b->total_tiles;
@@ -1045,6 +1084,8 @@ static int launch_batch(vafr_batch* bt, const BigBatch& b, cudaStream_t st) {
     CUDA_TRY(launch_render_lp(bt->scene->dev, b, bt->render_variant, st, bt->scene->sms));
     CUDA_TRY(launch_fxaa(b, st, bt->scene->sms));
     CUDA_TRY(launch_reconstruct(b, bt->recon_variant, st));
+    for (const auto& c : bt->copies)
+        CUDA_TRY(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, st));
     return VAFR_OK;
 }
 

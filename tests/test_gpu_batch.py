@@ -178,3 +178,36 @@ def test_session_autotune_picks_valid_variants(V, torch_mod, setup):
     for (lp0, d0), (lp1, d1) in zip(before, after):
         assert np.array_equal(lp0, lp1) and np.array_equal(d0, d1)
     V.vafr_session_tuning(s, (0, 0))
+
+
+def test_host_displays_equal_device_displays(V, torch_mod, setup):
+    """Displays in page-locked host memory (staged on the device, copied by
+    the copy engine) hold the same bytes as device displays, for direct
+    launches and replayed graphs."""
+    h, sessions, _ = setup
+    b = V.vafr_batch_create(h, 16)
+    V.vafr_batch_render(b, _frames(sessions))
+    torch_mod.cuda.synchronize()
+    ref = _read(sessions)
+    hosts = []
+    frames = []
+    for s, bufs, lpb, dpb in sessions:
+        for e in range(2):
+            hd = torch_mod.zeros(dpb, dtype=torch_mod.uint8, pin_memory=True)
+            hosts.append(hd)
+            frames.append((s, e, bufs[e][0], hd))
+    V.vafr_batch_render(b, frames)
+    torch_mod.cuda.synchronize()
+    for hd, (lp, d) in zip(hosts, ref):
+        assert np.array_equal(hd.numpy(), d)
+    for hd in hosts:
+        hd.zero_()
+    V.vafr_batch_capture(b, frames)
+    V.vafr_batch_replay(b)
+    torch_mod.cuda.synchronize()
+    for hd, (lp, d) in zip(hosts, ref):
+        assert np.array_equal(hd.numpy(), d)
+    with pytest.raises(V.VafrError):
+        s0, bufs0, _, dpb0 = sessions[0]
+        V.vafr_batch_render(b, [(s0, 0, bufs0[0][0], np.zeros(dpb0, np.uint8))])
+    V.vafr_batch_destroy(b)

@@ -169,3 +169,21 @@ def test_render_frame_host_outputs_match_device(V, torch_mod, lay):
     assert np.array_equal(pageable, ref)
     V.vafr_session_destroy(s)
     V.vafr_scene_destroy(h)
+
+
+def test_render_frame_pinned_host_equals_device(V, torch_mod):
+    """render_frame into page-locked host memory (device display + one copy)
+    holds the bytes of render_frame into device memory."""
+    w = workload("random1k")
+    d, sc = w.displays[0], w.scene
+    h, keep = device_scene(V, sc, torch_mod)
+    s = V.vafr_session_create(V.make_session_desc(d.width, d.height, d.fov_v_deg, d.poses))
+    V.vafr_set_gaze(s, 0, *d.gaze[0, 0])
+    dev = torch_mod.empty((d.height, d.width, 4), device="cuda")
+    pin = torch_mod.zeros((d.height, d.width, 4), pin_memory=True)
+    V.vafr_render_frame(h, s, dev)
+    V.vafr_render_frame(h, s, pin)
+    torch_mod.cuda.synchronize()
+    assert torch_mod.equal(dev.cpu(), pin)
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)
