@@ -134,10 +134,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _traffic(kernel: str, srcs):
+def _traffic(kernel: str, srcs, workload: str):
     """DRAM bytes per launch from the committed ncu summary, or None when the
     kernel's sources changed since the counters were taken (the hash covers
-    the concatenated source files)."""
+    the concatenated source files) or no capture covers this workload."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     try:
         h = hashlib.sha256()
@@ -146,7 +146,7 @@ def _traffic(kernel: str, srcs):
         sha = h.hexdigest()[:16]
         for ln in open(path):
             f = ln.split()
-            if len(f) >= 4 and f[0] == kernel and f[1] == sha:
+            if len(f) >= 4 and f[0] == kernel and f[1] == sha and f[3] == workload:
                 return float(f[2]), f[3]
     except OSError:
         pass
@@ -480,11 +480,13 @@ def run_gpu(args, w):
     csrc = os.path.join(ROOT, "paper_2503_23410_gb300", "csrc")
     lpt = bool(tuning) and tuning[0] == LPT_VARIANT
     if pt:
-        tr_render, _ = _traffic("path_lp", [os.path.join(csrc, f) for f in ("pathtrace.cu", "trace.cuh")])
+        tr_render, _ = _traffic("path_lp", [os.path.join(csrc, f) for f in ("pathtrace.cu", "trace.cuh")],
+                                args.workload)
     else:
         tr_render, _ = _traffic("render_lp_lpt" if lpt else "render_lp",
-                                [os.path.join(csrc, f) for f in ("render.cu", "trace.cuh")])
-    tr_recon, _ = _traffic("reconstruct", [os.path.join(csrc, f) for f in ("reconstruct.cu", "lp_map.cuh")])
+                                [os.path.join(csrc, f) for f in ("render.cu", "trace.cuh")], args.workload)
+    tr_recon, _ = _traffic("reconstruct", [os.path.join(csrc, f) for f in ("reconstruct.cu", "lp_map.cuh")],
+                           args.workload)
     roof_render = {"kernel": "k_path_lp" if pt else ("k_render_lp_lpt" if lpt else "k_render_lp"), "bound": "alu",
                    "achieved": ops / render_s / 1e12,
                    "peak": alu_peak, "unit": "TFLOP/s", "frac": ops / render_s / 1e12 / alu_peak,
