@@ -41,10 +41,12 @@ HERE_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 FP32_LANES_PER_SM = 128
 # FP32 operations per traversal step, counted from the kernel source: a child
-# box test is 6 slab FMAs + 10 min/max + 1 FMA + 1 compare; a triangle test is
-# 9 sub + 18 shear ops + 9 (U,V,W) + 2 (det) + 9 (z) + 3 (T) + 1 div + 7
-# compares; ray set-up + generation + shading ~ 60.
-OPS_PER_BOX = 18
+# box test is 12 slab ops (a subtract and a multiply per plane, the robust
+# form), 6 min/max (two three-input min/max and the clamps to 0 and t_max),
+# the far-bound scale, the compare and the select; a triangle test is 9 sub +
+# 18 shear ops + 9 (U,V,W) + 2 (det) + 9 (z) + 3 (T) + 1 div + 7 compares; ray
+# set-up + generation + shading ~ 60.
+OPS_PER_BOX = 21
 OPS_PER_TRI = 58
 OPS_PER_RAY = 60
 PT_DIFFUSE = 3        # the paper's maximum diffuse bounces (Sec. 8.1)

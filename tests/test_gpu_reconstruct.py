@@ -120,6 +120,30 @@ def test_full_size_sampled(V, torch_mod, lay, W, H):
     assert np.abs(got[pix] - ref).max() < 1e-3
 
 
+@pytest.mark.parametrize("disp_fmt", [0, 1])
+def test_16k_sampled(V, torch_mod, lay, disp_fmt):
+    """15360 x 8640 (the sweep's largest display, 132.7 M pixels in one launch),
+    FP32 or FP16 display: sampled pixels against the oracle."""
+    W, H = 15360, 8640
+    rng = np.random.default_rng(15360 + disp_fmt)
+    lp_np = rng.uniform(0, 1, (lay.total, 4)).astype(np.float32)
+    gaze = (W * 0.58, H * 0.33)
+    s = V.vafr_session_create(V.make_session_desc(W, H, 100.0, [POSE], 0, disp_fmt))
+    V.vafr_set_gaze(s, 0, *gaze)
+    lp = torch_mod.from_numpy(np.ascontiguousarray(to_device_lp(lp_np, V, s))).cuda()
+    dt = torch_mod.float16 if disp_fmt else torch_mod.float32
+    out = torch_mod.empty((H * W, 4), dtype=dt, device="cuda")
+    V.vafr_reconstruct(s, 0, lp, out)
+    torch_mod.cuda.synchronize()
+    pix = np.sort(rng.choice(W * H, 65536, replace=False))
+    got = out[torch_mod.from_numpy(pix).cuda()].float().cpu().numpy()
+    del out
+    V.vafr_session_destroy(s)
+    ref = oracle.reconstruct(lp_np.astype(np.float64), lay, W, H, 100.0, gaze, pix)
+    tol = 1e-3 + (2.0 ** -11 if disp_fmt else 0.0)
+    assert np.abs(got - ref).max() < tol
+
+
 def test_whole_frame_random1k(V, torch_mod, lay):
     """render_frame (LP render + reconstruct) vs the oracle's LP render + reconstruct;
     pixels whose filter footprint touches a tie texel are excluded."""

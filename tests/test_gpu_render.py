@@ -196,6 +196,28 @@ def test_gt_terrain_full_size_sampled(V, torch_mod, terrain):
     V.vafr_session_destroy(s)
 
 
+def test_gt_terrain_16k_sampled(V, torch_mod, terrain):
+    """The largest display of the resolution sweep (15360 x 8640, 132.7 M rays in
+    one launch): sampled pixels against the oracle's CPU-BVH cast."""
+    w, h, bvh = terrain
+    d, sc = w.displays[0], w.scene
+    W, H = 15360, 8640
+    s = _session(V, W, H, d.fov_v_deg, d.poses)
+    out = torch_mod.empty((H * W, 4), dtype=torch_mod.float32, device="cuda")
+    ids = torch_mod.empty(H * W, dtype=torch_mod.int32, device="cuda")
+    V.vafr_render_full_gt(h, s, 0, out, ids)
+    torch_mod.cuda.synchronize()
+    rng = np.random.default_rng(16)
+    pix = np.sort(rng.choice(W * H, 65536, replace=False))
+    sel = torch_mod.from_numpy(pix).cuda()
+    got_ids, got = ids[sel].cpu().numpy(), out[sel].cpu().numpy()
+    del out, ids
+    rgba, oid, ot, o, dd = oracle.render_gt(sc.tris, sc.albedo, sc.light_dir, W, H, d.fov_v_deg,
+                                            d.poses[0], pixels=pix, bvh=bvh)
+    compare_hits_and_colours(sc.tris, o, dd, got_ids, got, oid, ot, rgba, 1e-3)
+    V.vafr_session_destroy(s)
+
+
 def test_lp_fp16_binocular_and_gaze_outside(V, torch_mod, lay):
     sc = random_triangles_scene(1024, seed=1001)
     head = look_at_pose((0.0, 0.2, -3.0), (0, 0, 0))
