@@ -508,7 +508,8 @@ def run_gpu(args, w):
                   "frac": recon_bytes / recon_s / 1e9 / hbm_peak, "traffic": tr_recon,
                   "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured"
                   else "fallback 6.8 TB/s",
-                  "bytes_per_launch": recon_bytes, "avg_ms": recon_s * 1e3}
+                  "bytes_per_launch": recon_bytes / eyes, "avg_ms": recon_s * 1e3 / eyes,
+                  "launches_per_frame": eyes}
     if deferred:
         # the render stage is the V-buffer rasteriser (+ the LP lighting pass, a
         # few % of it): FP32 ops counted from the raster source per pre-filter
