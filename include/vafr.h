@@ -181,6 +181,33 @@ VAFR_API int vafr_scene_export_lbvh(const vafr_scene* scene, uint32_t* codes, in
  * Returns VAFR_OK, VAFR_ERR_DEVICE or VAFR_ERR_TIMEOUT. */
 VAFR_API int vafr_scene_check(const vafr_scene* scene, void* stream);
 
+/* Failure injection for tests of the device status words, made on the host:
+ * rewrites the child references of the root of the scene's 4-wide tree in
+ * device memory (the node boxes stay), so that the traversal's own checks
+ * stop the affected rays and report the fault through the session status word
+ * of the launch (vafr_session_check) instead of touching memory out of range.
+ *   VAFR_INJECT_NONE        restore the references saved by the first injection
+ *   VAFR_INJECT_BAD_CHILD   every used slot names inner node n_tris + 4, past
+ *                           the last one: the node check fails (VAFR_ERR_DEVICE)
+ *   VAFR_INJECT_LOOP        slot 0 names the root itself, the other slots are
+ *                           emptied: a ray entering slot 0's box cycles without
+ *                           growing its stack until the iteration limit of
+ *                           4 n_tris + 64 node visits (VAFR_ERR_TIMEOUT)
+ *   VAFR_INJECT_STACK       every used slot names the root: a ray entering two
+ *                           or more of the root's boxes pushes at every visit
+ *                           until the 96-entry stack would overflow (status
+ *                           bit 1); a ray entering one box cycles as above
+ *                           (bit 2, which takes precedence: VAFR_ERR_TIMEOUT)
+ * The check's error message ("session status 0x..") carries the bits:
+ * 1 stack, 2 iteration limit, 4 child reference out of range.
+ * The scene must have at least two triangles.  Synchronises the device.
+ * Errors: INVALID_ARG (NULL, unknown kind, one triangle), CUDA. */
+#define VAFR_INJECT_NONE      0
+#define VAFR_INJECT_BAD_CHILD 1
+#define VAFR_INJECT_LOOP      2
+#define VAFR_INJECT_STACK     3
+VAFR_API int vafr_scene_inject_fault(vafr_scene* scene, int32_t kind);
+
 /* ---- session --------------------------------------------------------------
  * vafr_session_create: validates the description and builds, in FP64 on the
  * host, the discrete LP layout of the acuity model: columns c at

@@ -82,6 +82,8 @@ struct vafr_scene {
     LbvhBuffers buf{};
     SceneDev dev{};
     unsigned* status = nullptr;
+    bool injected = false;         // vafr_scene_inject_fault: root references saved
+    int4 root_refs{};
     float4* d_plights = nullptr;   // point lights (vafr_scene_set_point_lights)
     // deferred path scratch (first use): triangle id -> leaf, large-triangle list
     int* d_leaf_of = nullptr;
@@ -503,6 +505,31 @@ int vafr_scene_check(const vafr_scene* scene, void* stream) {
     CUDA_TRY(cudaMemset(scene->status, 0, sizeof(unsigned)));
     if (st & kFaultWatchdog) return fail(VAFR_ERR_TIMEOUT, "scene status 0x%x", st);
     if (st) return fail(VAFR_ERR_DEVICE, "scene status 0x%x", st);
+    return VAFR_OK;
+}
+
+int vafr_scene_inject_fault(vafr_scene* scene, int32_t kind) {
+    if (!scene) return fail(VAFR_ERR_INVALID_ARG, "scene is NULL");
+    if (kind < VAFR_INJECT_NONE || kind > VAFR_INJECT_STACK) return fail(VAFR_ERR_INVALID_ARG, "unknown kind %d", kind);
+    if (scene->n < 2) return fail(VAFR_ERR_INVALID_ARG, "a one-triangle scene has no tree");
+    // the root is 4-wide node 0; its child references are the node's 7th float4
+    int4* refs = reinterpret_cast<int4*>(scene->buf.nodes4 + 6);
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (!scene->injected) {
+        if (kind == VAFR_INJECT_NONE) return VAFR_OK;
+        CUDA_TRY(cudaMemcpy(&scene->root_refs, refs, sizeof(int4), cudaMemcpyDeviceToHost));
+        scene->injected = true;
+    }
+    int4 v = scene->root_refs;
+    int* c = &v.x;
+    const int bad = (int)(scene->n + 4);   // inner nodes are 0 .. n - 2
+    for (int k = 0; k < 4; ++k) {
+        if (kind == VAFR_INJECT_BAD_CHILD && c[k] != kEmptyRef) c[k] = bad;
+        if (kind == VAFR_INJECT_LOOP) c[k] = k == 0 ? 0 : kEmptyRef;
+        if (kind == VAFR_INJECT_STACK && c[k] != kEmptyRef) c[k] = 0;
+    }
+    CUDA_TRY(cudaMemcpy(refs, &v, sizeof(int4), cudaMemcpyHostToDevice));
+    if (kind == VAFR_INJECT_NONE) scene->injected = false;
     return VAFR_OK;
 }
 

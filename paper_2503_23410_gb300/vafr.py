@@ -78,6 +78,7 @@ _PROTOS = {
     "vafr_scene_info": (ctypes.c_int, [_P, _P, _P]),
     "vafr_scene_export_lbvh": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "vafr_scene_check": (ctypes.c_int, [_P, _P]),
+    "vafr_scene_inject_fault": (ctypes.c_int, [_P, ctypes.c_int32]),
     "vafr_session_create": (ctypes.c_int, [_P, _P]),
     "vafr_session_destroy": (ctypes.c_int, [_P]),
     "vafr_lp_layout": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -266,6 +267,13 @@ def vafr_scene_export_lbvh(scene: int):
 
 def vafr_scene_check(scene: int, stream=None) -> int:
     return int(load().vafr_scene_check(scene, stream_ptr(stream)))
+
+
+INJECT_NONE, INJECT_BAD_CHILD, INJECT_LOOP, INJECT_STACK = 0, 1, 2, 3
+
+
+def vafr_scene_inject_fault(scene: int, kind: int) -> None:
+    _check(load().vafr_scene_inject_fault(scene, int(kind)))
 
 
 def vafr_session_create(desc: vafr_session_desc) -> int:

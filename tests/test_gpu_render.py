@@ -119,6 +119,41 @@ def test_lp_frame_random1k_full(V, torch_mod, lay):
     V.vafr_scene_destroy(h)
 
 
+# injection kind -> (status code, status bit that must be set: 1 stack, 2 iteration limit, 4 bad node)
+@pytest.mark.parametrize("kind,code,bit", [(1, (-6,), 4), (2, (-4,), 2), (3, (-4, -6), 1)])
+def test_traversal_faults_reach_the_status_word(V, torch_mod, lay, kind, code, bit):
+    """Failure detection without a GPU fault: a tree corrupted on the host (an
+    out-of-range child, a self-loop, a stack-growing self-loop) makes the
+    traversal's own bounds, iteration and stack checks stop the rays; the
+    session status word reports VAFR_ERR_DEVICE / VAFR_ERR_TIMEOUT, and the
+    restored tree renders the same bits as before in the same context.  In the
+    stack-growing loop the rays that enter a single root box push nothing and
+    reach the iteration limit, which takes precedence in the code; the stack
+    bit must still be set."""
+    w = workload("random1k")
+    d, sc = w.displays[0], w.scene
+    h, keep = device_scene(V, sc, torch_mod)
+    s = _session(V, d.width, d.height, d.fov_v_deg, d.poses)
+    V.vafr_set_gaze(s, 0, *d.gaze[0, 0])
+    slot, n_slots, _, _ = lp_slots(V, s)
+    lp_ref, ids_ref = _render_lp(V, torch_mod, h, s, lay.total)
+    lp = torch_mod.empty((n_slots, 4), dtype=torch_mod.float32, device="cuda")
+    ids = torch_mod.empty(n_slots, dtype=torch_mod.int32, device="cuda")
+    V.vafr_scene_inject_fault(h, kind)
+    V.vafr_render_lp(h, s, 1, lp, ids)
+    assert V.vafr_session_check(s) in code
+    status = int(V.load().vafr_last_error_message().decode().split("0x")[-1], 16)
+    assert status & bit
+    assert V.vafr_session_check(s) == 0            # reading clears the word
+    # the stopped rays report no hit
+    assert (ids.cpu().numpy()[slot] == -1).sum() > (ids_ref == -1).sum()
+    V.vafr_scene_inject_fault(h, V.INJECT_NONE)
+    lp2, ids2 = _render_lp(V, torch_mod, h, s, lay.total)
+    assert np.array_equal(ids2, ids_ref) and np.array_equal(lp2, lp_ref)
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)
+
+
 def test_gt_random1k_full(V, torch_mod):
     w = workload("random1k")
     d, sc = w.displays[0], w.scene
@@ -285,6 +320,12 @@ def test_invalid_arguments(V, torch_mod):
     V.vafr_set_gaze(s, 0, 50.0, 50.0)
     with pytest.raises(V.VafrError):   # eye mask outside the session
         V.vafr_render_lp(h, s, 2, lp)
+    with pytest.raises(V.VafrError):   # unknown injection
+        V.vafr_scene_inject_fault(h, 7)
+    one, keep1 = device_scene(V, random_triangles_scene(1, seed=2), torch_mod)
+    with pytest.raises(V.VafrError):   # no tree to corrupt
+        V.vafr_scene_inject_fault(one, V.INJECT_LOOP)
+    V.vafr_scene_destroy(one)
     V.vafr_session_destroy(s)
     V.vafr_scene_destroy(h)
 
