@@ -54,3 +54,25 @@ def test_cpu_baseline_small_workload():
     assert "all 1061630 LP texels" in line["sample"]
     assert prec["lp_hit_id_mismatch_frac"] == 0.0
     assert prec["display_abs_err"]["max"] == 0.0
+
+
+def test_traffic_lines_match_sources_and_workload(tmp_path):
+    """A committed DRAM-traffic line is used only for the kernel, source hash and
+    workload it was captured on."""
+    import hashlib
+    import os
+    csrc = os.path.join(bench.ROOT, "paper_2503_23410_gb300", "csrc")
+    srcs = [os.path.join(csrc, f) for f in ("render.cu", "trace.cuh")]
+    h = hashlib.sha256()
+    for s in srcs:
+        h.update(open(s, "rb").read())
+    sha = h.hexdigest()[:16]
+    lines = [ln.split() for ln in open(os.path.join(bench.ROOT, "profiles", "ncu_traffic.txt"))
+             if ln.strip() and not ln.startswith("#")]
+    want = {(f[0], f[3]): float(f[2]) for f in lines if f[1] == sha}
+    for (kernel, wl), b in want.items():
+        assert bench._traffic(kernel, srcs, wl) == (b, wl)
+    assert bench._traffic("render_lp", srcs, "no-such-workload") == (None, None)
+    other = tmp_path / "edited.cu"
+    other.write_bytes(open(srcs[0], "rb").read() + b"\n")
+    assert bench._traffic("render_lp", [str(other), srcs[1]], "terrain4k") == (None, None)
