@@ -469,6 +469,13 @@ def run_gpu(args, w):
         pt_rays = seg + shadow
         ops = ops / max(rays, 1) * pt_rays
         rays = pt_rays
+    if rep:
+        # the VaFR_Rep render stage casts the left eye's rays and the right
+        # eye's holes (the last timed frame's count); the warp itself is
+        # counted as no FP32 work, so the fraction is a lower bound
+        rep_rays = stats["rays"] + V.vafr_rep_hole_count(sess)
+        ops = ops / max(rays, 1) * rep_rays
+        rays = rep_rays
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     derived_peak = n_sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # T FP32 ops/s
@@ -484,12 +491,17 @@ def run_gpu(args, w):
     if pt:
         tr_render, _ = _traffic("path_lp", [os.path.join(csrc, f) for f in ("pathtrace.cu", "trace.cuh")],
                                 args.workload)
+    elif rep:
+        tr_render = None      # no capture covers the Rep stage's kernels together
     else:
         tr_render, _ = _traffic("render_lp_lpt" if lpt else "render_lp",
                                 [os.path.join(csrc, f) for f in ("render.cu", "trace.cuh")], args.workload)
     tr_recon, _ = _traffic("reconstruct", [os.path.join(csrc, f) for f in ("reconstruct.cu", "lp_map.cuh")],
                            args.workload)
-    roof_render = {"kernel": "k_path_lp" if pt else ("k_render_lp_lpt" if lpt else "k_render_lp"), "bound": "alu",
+    render_kernel = ("k_path_lp" if pt else
+                     "k_render_lp (left eye) + k_rep_* warp + k_render_list (holes)" if rep else
+                     "k_render_lp_lpt" if lpt else "k_render_lp")
+    roof_render = {"kernel": render_kernel, "bound": "alu",
                    "achieved": ops / render_s / 1e12,
                    "peak": alu_peak, "unit": "TFLOP/s", "frac": ops / render_s / 1e12 / alu_peak,
                    "traffic": tr_render,
