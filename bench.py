@@ -487,17 +487,20 @@ def run_gpu(args, w):
     recon_bytes = dp_b * eyes + lp_bytes                            # display write + LP read once
     hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     csrc = os.path.join(ROOT, "paper_2503_23410_gb300", "csrc")
+    # traffic lines were captured with the paper's acuity model; another model
+    # changes the ray count and the LP buffer, so it needs captures of its own
+    traffic_key = args.workload if args.acuity == "paper" else f"{args.workload}+{args.acuity}"
     lpt = bool(tuning) and tuning[0] == LPT_VARIANT
     if pt:
         tr_render, _ = _traffic("path_lp", [os.path.join(csrc, f) for f in ("pathtrace.cu", "trace.cuh")],
-                                args.workload)
+                                traffic_key)
     elif rep:
         tr_render = None      # no capture covers the Rep stage's kernels together
     else:
         tr_render, _ = _traffic("render_lp_lpt" if lpt else "render_lp",
-                                [os.path.join(csrc, f) for f in ("render.cu", "trace.cuh")], args.workload)
+                                [os.path.join(csrc, f) for f in ("render.cu", "trace.cuh")], traffic_key)
     tr_recon, _ = _traffic("reconstruct", [os.path.join(csrc, f) for f in ("reconstruct.cu", "lp_map.cuh")],
-                           args.workload)
+                           traffic_key)
     render_kernel = ("k_path_lp" if pt else
                      "k_render_lp (left eye) + k_rep_* warp + k_render_list (holes)" if rep else
                      "k_render_lp_lpt" if lpt else "k_render_lp")
