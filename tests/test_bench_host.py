@@ -76,3 +76,26 @@ def test_traffic_lines_match_sources_and_workload(tmp_path):
     other = tmp_path / "edited.cu"
     other.write_bytes(open(srcs[0], "rb").read() + b"\n")
     assert bench._traffic("render_lp", [str(other), srcs[1]], "terrain4k") == (None, None)
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` (the FP64 oracle on the host cores) prints one
+    JSON line with the benchmark contract's keys."""
+    import json
+    import os
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "random1k", "--steps", "2", "--warmup", "0",
+                          "--ref-texels", "512", "--ref-pixels", "4096"],
+                         capture_output=True, text=True, timeout=600, cwd=bench.ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
