@@ -464,6 +464,11 @@ VAFR_API int vafr_measure_fp32_peak(double out[2], void* stream);
  * position, or one whose session has more LP texels than before, allocates
  * it and synchronises the device); captured graphs and the autotuner's
  * timings run variant 6 without an order (chunks in work order).
+ * A batch owns device state that its launches use: the render's work
+ * counter, the order states and one staging buffer per host display.  Keep
+ * at most one render or replay of a batch in flight at a time (for frames in
+ * flight on several streams, create one batch per stream); a session may take
+ * part in several batches, but not with the same eye in two batches in flight.
  * Errors: INVALID_ARG (n out of range, frame with a NULL buffer, eye out of
  * range, session never given a gaze, display in pageable host memory), CUDA. */
 VAFR_API int vafr_batch_create(const vafr_scene* scene, int32_t max_frames, vafr_batch** out);
