@@ -144,6 +144,21 @@ def test_16k_sampled(V, torch_mod, lay, disp_fmt):
     assert np.abs(got - ref).max() < tol
 
 
+@pytest.mark.parametrize("variant", [1, 2])
+def test_8k_fp16_sampled(V, torch_mod, lay, variant):
+    """One eye of the 8K binocular configuration (FP16 LP, FP16 display) in the
+    reconstruct variants the autotuner picks (2 at 8K, 1 at 4K): sampled pixels
+    against the oracle fed the same FP16-rounded LP texels."""
+    W, H = 7680, 4320
+    rng = np.random.default_rng(8 + variant)
+    lp = rng.uniform(0, 1, (lay.total, 4)).astype(np.float16).astype(np.float32)
+    gaze = (W * 0.44, H * 0.57)
+    got = _recon(V, torch_mod, W, H, 100.0, gaze, lp, lp_fmt=1, disp_fmt=1, variant=variant)
+    pix = rng.choice(W * H, 65536, replace=False)
+    ref = oracle.reconstruct(lp.astype(np.float64), lay, W, H, 100.0, gaze, pix)
+    assert np.abs(got[pix] - ref).max() < 1e-3 + 2.0 ** -11
+
+
 def test_whole_frame_random1k(V, torch_mod, lay):
     """render_frame (LP render + reconstruct) vs the oracle's LP render + reconstruct;
     pixels whose filter footprint touches a tie texel are excluded."""

@@ -282,6 +282,39 @@ def test_lp_fp16_binocular_and_gaze_outside(V, torch_mod, lay):
     V.vafr_scene_destroy(h)
 
 
+@pytest.fixture(scope="module")
+def objects8k(V, torch_mod):
+    w = workload("objects8k", frames=240)
+    h, keep = device_scene(V, w.scene, torch_mod)
+    bvh = oracle.CpuBVH(w.scene.tris)
+    yield w, h, bvh
+    V.vafr_scene_destroy(h)
+
+
+@pytest.mark.parametrize("frame,variant", [(0, 2), (150, 2), (150, 6)])
+def test_lp_objects8k_binocular_sampled(V, torch_mod, lay, objects8k, frame, variant):
+    """The 8K binocular workload at full size (1,998,088 triangles, FP16 LP, both
+    eyes in one launch, each eye on its own gaze trajectory) in the render
+    variant the autotuner picks for it (2) and in the longest-first order (6):
+    sampled texels of both eyes against the oracle's CPU-BVH cast."""
+    w, h, bvh = objects8k
+    d, sc = w.displays[0], w.scene
+    s = _session(V, d.width, d.height, d.fov_v_deg, d.poses, lp_fmt=1, disp_fmt=1)
+    for e in range(2):
+        V.vafr_set_gaze(s, e, *d.gaze[frame, e])
+    V.vafr_session_tuning(s, (variant, 2))
+    lp, ids = _render_lp(V, torch_mod, h, s, lay.total, eye_mask=3, fp16=True)
+    rng = np.random.default_rng(frame + variant)
+    tex = np.sort(rng.choice(lay.total, 65536, replace=False))
+    for e in range(2):
+        rgba, oid, ot, o, dd = oracle.render_lp(sc.tris, sc.albedo, sc.light_dir, lay, d.width,
+                                                d.height, d.fov_v_deg, d.gaze[frame, e], d.poses[e],
+                                                texels=tex, bvh=bvh)
+        compare_hits_and_colours(sc.tris, o, dd, ids[e * lay.total + tex], lp[e * lay.total + tex],
+                                 oid, ot, rgba, 1e-3 + 2.0 ** -11)
+    V.vafr_session_destroy(s)
+
+
 def test_lp_independent_of_resolution(V, torch_mod, lay):
     # Sec. 3.2.2: same FOV, pose and gaze direction -> same LP buffer at 1080p and 8K
     sc = random_triangles_scene(1024, seed=1001)
