@@ -13,8 +13,10 @@
  *
  * Conventions (every entry point):
  *  - Return value: VAFR_OK (0) or a negative VAFR_ERR_* code.  No C++
- *    exception crosses this boundary.  vafr_last_error_message() gives a
- *    human-readable detail for the calling thread's last failure.
+ *    exception crosses this boundary: a failed host allocation returns
+ *    VAFR_ERR_OOM.  vafr_last_error_message() gives a human-readable detail
+ *    for the calling thread's last failure (a per-thread buffer, valid until
+ *    that thread's next failure).
  *  - Work is asynchronous on the given CUDA stream (passed as void*, a
  *    cudaStream_t; NULL = legacy default stream).  Device-side faults of the
  *    method (traversal stack overflow, watchdog) set a per-object status word

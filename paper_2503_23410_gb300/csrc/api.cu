@@ -13,6 +13,7 @@
 #include <cstring>
 #include <limits.h>
 #include <memory>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -25,16 +26,30 @@ void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 namespace {
 
-thread_local std::string g_msg;
+// the calling thread's last failure, formatted in place (no allocation, so
+// reporting an out-of-memory failure cannot fail itself)
+thread_local char g_msg[512];
 
 int fail(int code, const char* fmt, ...) {
-    char buf[512];
     va_list ap;
     va_start(ap, fmt);
-    vsnprintf(buf, sizeof(buf), fmt, ap);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
     va_end(ap);
-    g_msg = buf;
     return code;
+}
+
+// Entry points that allocate host memory run their body through this, so a
+// failed host allocation returns VAFR_ERR_OOM and no C++ exception leaves the
+// library.
+template <class F>
+int guarded(F&& body) noexcept {
+    try {
+        return body();
+    } catch (const std::bad_alloc&) {
+        return fail(VAFR_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        return fail(VAFR_ERR_CUDA, "unexpected host-side exception");
+    }
 }
 
 #define CUDA_TRY(expr)                                                                   \
@@ -310,7 +325,7 @@ const char* vafr_error_string(int code) {
     }
 }
 
-const char* vafr_last_error_message(void) { return g_msg.c_str(); }
+const char* vafr_last_error_message(void) { return g_msg; }
 
 int32_t vafr_version(void) { return 10000; }
 
@@ -346,7 +361,7 @@ int vafr_acuity_display_limited(vafr_acuity* a, double max_cpd) {
 }
 
 // ---- scene ---------------------------------------------------------------------------
-int vafr_build_scene(const float* tri_xyz, const float* albedo_rgb, int64_t n_tris,
+static int vafr_build_scene_impl(const float* tri_xyz, const float* albedo_rgb, int64_t n_tris,
                      const float light_dir[3], void* stream, vafr_scene** out) {
     if (!out) return fail(VAFR_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -438,7 +453,12 @@ int vafr_build_scene(const float* tri_xyz, const float* albedo_rgb, int64_t n_tr
     return VAFR_OK;
 }
 
-int vafr_scene_set_point_lights(vafr_scene* scene, int32_t n, const float* pos_xyz, const float* rgb) {
+int vafr_build_scene(const float* tri_xyz, const float* albedo_rgb, int64_t n_tris,
+                     const float light_dir[3], void* stream, vafr_scene** out) {
+    return guarded([&] { return vafr_build_scene_impl(tri_xyz, albedo_rgb, n_tris, light_dir, stream, out); });
+}
+
+static int vafr_scene_set_point_lights_impl(vafr_scene* scene, int32_t n, const float* pos_xyz, const float* rgb) {
     if (!scene) return fail(VAFR_ERR_INVALID_ARG, "scene is NULL");
     if (n < 0 || n > VAFR_MAX_POINT_LIGHTS || (n > 0 && (!pos_xyz || !rgb)))
         return fail(VAFR_ERR_INVALID_ARG, "point light count %d out of [0, %d] or NULL arrays", n, VAFR_MAX_POINT_LIGHTS);
@@ -466,6 +486,10 @@ int vafr_scene_set_point_lights(vafr_scene* scene, int32_t n, const float* pos_x
     }
     cudaSetDevice(cur);
     return rc;
+}
+
+int vafr_scene_set_point_lights(vafr_scene* scene, int32_t n, const float* pos_xyz, const float* rgb) {
+    return guarded([&] { return vafr_scene_set_point_lights_impl(scene, n, pos_xyz, rgb); });
 }
 
 int vafr_scene_destroy(vafr_scene* scene) {
@@ -534,7 +558,7 @@ int vafr_scene_inject_fault(vafr_scene* scene, int32_t kind) {
 }
 
 // ---- session -------------------------------------------------------------------------
-int vafr_session_create(const vafr_session_desc* desc, vafr_session** out) {
+static int vafr_session_create_impl(const vafr_session_desc* desc, vafr_session** out) {
     if (!desc || !out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     const vafr_session_desc& d = *desc;
@@ -580,6 +604,10 @@ int vafr_session_create(const vafr_session_desc* desc, vafr_session** out) {
     for (int eye = 0; eye < d.n_eyes; ++eye) fill_static(s, eye);
     *out = s;
     return VAFR_OK;
+}
+
+int vafr_session_create(const vafr_session_desc* desc, vafr_session** out) {
+    return guarded([&] { return vafr_session_create_impl(desc, out); });
 }
 
 int vafr_session_destroy(vafr_session* session) {
@@ -1116,7 +1144,7 @@ static int launch_batch(vafr_batch* bt, const BigBatch& b, cudaStream_t st) {
     return VAFR_OK;
 }
 
-int vafr_batch_create(const vafr_scene* scene, int32_t max_frames, vafr_batch** out) {
+static int vafr_batch_create_impl(const vafr_scene* scene, int32_t max_frames, vafr_batch** out) {
     if (!scene || !out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
     if (max_frames <= 0 || max_frames > VAFR_MAX_BATCH)
         return fail(VAFR_ERR_INVALID_ARG, "max_frames out of range");
@@ -1132,6 +1160,10 @@ int vafr_batch_create(const vafr_scene* scene, int32_t max_frames, vafr_batch** 
     return VAFR_OK;
 }
 
+int vafr_batch_create(const vafr_scene* scene, int32_t max_frames, vafr_batch** out) {
+    return guarded([&] { return vafr_batch_create_impl(scene, max_frames, out); });
+}
+
 int vafr_batch_destroy(vafr_batch* batch) {
     if (!batch) return VAFR_OK;
     cudaDeviceSynchronize();
@@ -1139,7 +1171,7 @@ int vafr_batch_destroy(vafr_batch* batch) {
     return VAFR_OK;
 }
 
-int vafr_batch_render(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream) {
+static int vafr_batch_render_impl(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream) {
     if (!bt) return fail(VAFR_ERR_INVALID_ARG, "batch is NULL");
     BigBatch* b = new BigBatch();
     int rc = build_batch(bt, frames, n, b, as_stream(stream), false);
@@ -1148,7 +1180,11 @@ int vafr_batch_render(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, 
     return rc;
 }
 
-int vafr_batch_capture(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream) {
+int vafr_batch_render(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream) {
+    return guarded([&] { return vafr_batch_render_impl(bt, frames, n, stream); });
+}
+
+static int vafr_batch_capture_impl(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream) {
     if (!bt) return fail(VAFR_ERR_INVALID_ARG, "batch is NULL");
     int rc = build_batch(bt, frames, n, bt->host_batch, as_stream(stream), true);
     if (rc) return rc;
@@ -1211,6 +1247,10 @@ int vafr_batch_capture(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n,
     if (bt->kernel_nodes.size() < 2) return fail(VAFR_ERR_CUDA, "graph: kernel nodes not found");
     bt->captured.assign(frames, frames + n);
     return VAFR_OK;
+}
+
+int vafr_batch_capture(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream) {
+    return guarded([&] { return vafr_batch_capture_impl(bt, frames, n, stream); });
 }
 
 int vafr_batch_replay(vafr_batch* bt, void* stream) {
@@ -1317,7 +1357,7 @@ int vafr_session_autotune(const vafr_scene* scene, vafr_session* s, void* lp, vo
     return VAFR_OK;
 }
 
-int vafr_batch_autotune(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream,
+static int vafr_batch_autotune_impl(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream,
                         int32_t iters) {
     if (!bt) return fail(VAFR_ERR_INVALID_ARG, "batch is NULL");
     if (iters <= 0) iters = 3;
@@ -1365,6 +1405,11 @@ int vafr_batch_autotune(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n
         if (e != cudaSuccess) rc = fail(VAFR_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
     }
     return rc;
+}
+
+int vafr_batch_autotune(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream,
+                        int32_t iters) {
+    return guarded([&] { return vafr_batch_autotune_impl(bt, frames, n, stream, iters); });
 }
 
 }  // extern "C"
