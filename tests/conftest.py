@@ -50,3 +50,16 @@ def V():
 def torch_mod():
     import torch
     return torch
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Widest classified ray-edge / depth tie of the session, per kind."""
+    mod = sys.modules.get("parity")
+    if not mod or not getattr(mod, "TIE_WIDTHS", None):
+        return
+    worst = {}
+    for kind, w in mod.TIE_WIDTHS:
+        n, m = worst.get(kind, (0, 0.0))
+        worst[kind] = (n + 1, max(m, w))
+    terminalreporter.write_line("classified ties (count, widest): " + ", ".join(
+        f"{k} {n} {m:.3e}" for k, (n, m) in sorted(worst.items())))

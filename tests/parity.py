@@ -8,6 +8,11 @@ the GPU's triangle is within that distance of being hit by the FP64 ray and
 its plane lies no farther than the oracle's hit (relative 1e-5).  Anything
 else is a genuine error.  A colour comparison skips rays that graze their
 triangle (|n.d| < 1e-5), where the face-forward flip is ambiguous.
+
+Every classified tie's width (|margin| / (t |d|), and the relative depth
+excess of the GPU's triangle) is recorded in TIE_WIDTHS, and the session
+summary prints the largest, so the window can be checked against the FP32
+rounding bound it stands for.
 """
 
 from __future__ import annotations
@@ -15,6 +20,11 @@ from __future__ import annotations
 import numpy as np
 
 import oracle
+
+# (kind, width) of every classified tie of the session: kind "edge" = |margin| /
+# (t |d|) of the oracle's triangle, "gpu-edge" = the GPU triangle's outside
+# margin over (t |d|), "depth" = relative depth excess of the GPU's triangle
+TIE_WIDTHS: list = []
 
 
 def device_scene(V, scene, torch):
@@ -75,12 +85,16 @@ def classify(tris, o, d, gpu_ids, ora_ids, ora_t, rel=1e-5):
             delta = rel * ora_t[k] * dist_scale
             if abs(m) < delta:
                 tie = True
+                TIE_WIDTHS.append(("edge", abs(m) / (ora_t[k] * dist_scale)))
         if not tie and gpu_ids[k] >= 0:
             tg = _plane_t(tris[gpu_ids[k]], o[k], d[k])
             delta = rel * max(tg, 1e-30) * dist_scale
             m = oracle.edge_margin(tris[gpu_ids[k]], o[k], d[k])
-            if m > -delta and tg > 0 and (ora_ids[k] < 0 or tg <= ora_t[k] * (1 + 1e-5)):
+            if m > -delta and tg > 0 and (ora_ids[k] < 0 or tg <= ora_t[k] * (1 + rel)):
                 tie = True
+                TIE_WIDTHS.append(("gpu-edge", max(-m, 0.0) / (max(tg, 1e-30) * dist_scale)))
+                if ora_ids[k] >= 0:
+                    TIE_WIDTHS.append(("depth", max(tg / ora_t[k] - 1.0, 0.0)))
         if tie:
             ties += 1
         else:
