@@ -1,19 +1,28 @@
 """Benchmark of the VaFR ray-casting hot path on one GB300 (or N, one per rank).
 
-Workload (default ``terrain4k``): 3840x2160 monocular display, 100 deg vertical
-FOV, a 240-frame seeded saccade gaze trajectory, a 1,069,506-triangle scene
-(fBm terrain 512x1024 + 2,000 boxes), FP32 LP buffer and FP32 display.
+Workload (default ``objects8k``, the largest single-GPU configuration):
+binocular 7680x4320 per eye, 63 mm IPD, 100 deg vertical FOV, a 240-frame
+seeded saccade gaze trajectory per eye, a 1,998,088-triangle scene (fBm
+terrain 829x1024 + 4,000 spheres + 4,000 boxes), FP16 LP buffer and FP16
+display, FP32 shading and filter arithmetic.
 
-A step is one frame: the FP64 gaze set-up, the LP render (one ray per LP
-texel: generation + LBVH traversal + shading) and the reconstruction of the
-full-resolution display.  Inputs (scene, BVH, buffers) are resident in HBM
-before timing.  L2 is flushed (256 MiB write) between steps, outside the
-per-step CUDA events.  The GPU's own full-resolution ray cast (the paper's GT,
-one ray per display pixel) is timed the same way for the speedup.
+A step is one binocular frame: the FP64 gaze set-up of both eyes, the LP
+render of both eyes in one launch (one ray per LP texel: generation + BVH
+traversal + shading) and the reconstruction of both full-resolution displays.
+Inputs (scene, BVH, buffers) are resident in HBM before timing.  L2 is flushed
+(256 MiB write) between steps, outside the per-step CUDA events.  The GPU's own
+full-resolution ray cast (the paper's GT, one ray per display pixel) is timed
+the same way for the speedup.  On one GPU the line also carries compact
+results of the other configurations under extra keys: ``terrain4k`` (4K
+monocular, FP32), ``sweep`` (1080p ... 16K binocular batched in one CUDA
+graph, VaFR and GT per resolution) and ``serving`` (64 Poisson sessions,
+frames/s and p50/p99 latency); ``--no-extra`` leaves them out.
 
 ``--impl reference`` times the FP64 CPU oracle (the reference arm here) on the
-host cores: each step renders a bounded random sample of one frame's LP texels
-and display pixels, extrapolated to a whole frame.
+host cores over the same 240-frame trajectory: each step renders a bounded
+random sample of one frame's LP texels and display pixels; ``ms_per_step`` is
+the measured time of that sample and the whole-frame time extrapolated from it
+is reported beside it.
 
 Prints one JSON line (rank 0).
 """
@@ -40,12 +49,18 @@ UNIT = "Mpix/s"
 HERE_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 FP32_LANES_PER_SM = 128
-# FP32 operations per traversal step, counted from the kernel source: a child
-# box test is 12 slab ops (a subtract and a multiply per plane, the robust
-# form), 6 min/max (two three-input min/max and the clamps to 0 and t_max),
-# the far-bound scale, the compare and the select; a triangle test is 9 sub +
-# 18 shear ops + 9 (U,V,W) + 2 (det) + 9 (z) + 3 (T) + 1 div + 7 compares; ray
-# set-up + generation + shading ~ 60.
+# FP32 operations per unit of traversal work, in two readings.
+# Algorithmic counts (the traversal roofline's own units; `roofline.frac`):
+# 12 per child-box test (a subtract and a multiply per slab plane), 30 per
+# ray-triangle test, 20 per ray for generation and shading.
+OPS_PER_BOX_ALG = 12
+OPS_PER_TRI_ALG = 30
+OPS_PER_RAY_ALG = 20
+# Counted from the kernel source (`roofline.frac_source_count`): a child box
+# test is 12 slab ops, 6 min/max (two three-input min/max and the clamps to 0
+# and t_max), the far-bound scale, the compare and the select; a triangle test
+# is 9 sub + 18 shear ops + 9 (U,V,W) + 2 (det) + 9 (z) + 3 (T) + 1 div + 7
+# compares; ray set-up + generation + shading ~ 60.
 OPS_PER_BOX = 21
 OPS_PER_TRI = 58
 OPS_PER_RAY = 60
@@ -163,13 +178,29 @@ def _workload_desc(w):
             f"{'FP16' if w.display_fp16 else 'FP32'}")
 
 
+L2_NOTE = "GPU arm: flushed between steps (256 MiB write outside the per-step events)"
+
+
+def _config(w, args, ws):
+    """The workload description, the same dict in both arms."""
+    pt, rep, deferred = bool(args.pt), bool(args.rep), bool(args.deferred)
+    return {"workload": _workload_desc(w), "l2": L2_NOTE, "acuity": args.acuity,
+            "lp_fxaa": bool(args.fxaa),
+            "shading": f"path traced, 1 path/texel, NEE, {PT_DIFFUSE} diffuse bounces" if pt
+            else "ray cast, Lambert + ambient",
+            "binocular_mode": "VaFR_Rep (right eye warped)" if rep else "VaFR_Dup",
+            "pipeline": "deferred (visibility buffer + LP lighting)" if deferred else "ray casting",
+            "point_lights": int(args.point_lights),
+            "parallelism": f"replicas x{ws} (independent sessions, no collective)"}
+
+
 # ---------------------------------------------------------------------------
 # reference arm / CPU baseline: the FP64 oracle on the host cores
 
 
 def oracle_frame_sample(w, frame, n_tex, n_pix, bvh, lay, rng):
-    """Seconds to render n_tex LP texels + reconstruct n_pix pixels of one frame,
-    and the same scaled to a whole frame."""
+    """Seconds to render n_tex LP texels + reconstruct n_pix pixels of one frame
+    (every eye), and the same scaled to a whole frame."""
     import oracle
     d = w.displays[0]
     eyes = len(d.poses)
@@ -192,7 +223,7 @@ def oracle_frame_sample(w, frame, n_tex, n_pix, bvh, lay, rng):
     return t_lp + t_rec, frame_s
 
 
-def run_reference(args, w):
+def run_reference(args, w, ws):
     import oracle
     oracle.build()
     d = w.displays[0]
@@ -205,27 +236,29 @@ def run_reference(args, w):
     n_tex, n_pix = args.ref_texels, args.ref_pixels
     for k in range(args.warmup):
         oracle_frame_sample(w, k, n_tex, n_pix, bvh, lay, rng)
-    frame_times, cpu_s = [], 0.0
+    step_s, frame_s = [], []
     for k in range(args.steps):
-        s, f = oracle_frame_sample(w, args.warmup + k, n_tex, n_pix, bvh, lay, rng)
-        cpu_s += s
-        frame_times.append(f)
-    ft = np.array(frame_times)
+        s_, f_ = oracle_frame_sample(w, args.warmup + k, n_tex, n_pix, bvh, lay, rng)
+        step_s.append(s_)
+        frame_s.append(f_)
+    st, ft = np.array(step_s), np.array(frame_s)
     value = d.width * d.height * eyes / 1e6 / ft.mean()
     sample = (f"per step: {n_tex} random LP texels/eye (CPU BVH, FP64) + {n_pix} random display "
-              f"pixels/eye reconstructed, extrapolated to the frame's {lay.total:,} texels and "
+              f"pixels/eye reconstructed, of frame k of the {len(d.gaze)}-frame trajectory; Mpix/s "
+              f"extrapolates the sample to the frame's {lay.total:,} texels and "
               f"{d.width * d.height:,} pixels per eye; BVH build {build_s:.1f} s excluded")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(ft.mean() * 1e3),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(st.mean() * 1e3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": _workload_desc(w)},
+        "data": "synthetic", "config": _config(w, args, ws),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "p50_frame_ms": float(np.percentile(ft, 50) * 1e3),
-        "p99_frame_ms": float(np.percentile(ft, 99) * 1e3),
-        "cpu_seconds_measured": cpu_s,
+        "frame_ms_extrapolated": float(ft.mean() * 1e3),
+        "p50_frame_ms_extrapolated": float(np.percentile(ft, 50) * 1e3),
+        "p99_frame_ms_extrapolated": float(np.percentile(ft, 99) * 1e3),
+        "cpu_seconds_measured": float(st.sum()),
     }
     print(json.dumps(line))
 
@@ -452,8 +485,12 @@ def run_gpu(args, w):
     # roofline of the dominant kernel
     stats = V.vafr_traversal_stats(scene, sess, 0)
     rays = stats["rays"] * eyes
-    ops = (stats["box_tests"] * OPS_PER_BOX + stats["tri_tests"] * OPS_PER_TRI
-           + stats["rays"] * OPS_PER_RAY) * eyes
+    ops = (stats["box_tests"] * OPS_PER_BOX_ALG + stats["tri_tests"] * OPS_PER_TRI_ALG
+           + stats["rays"] * OPS_PER_RAY_ALG) * eyes
+    src_ratio = ((stats["box_tests"] * OPS_PER_BOX + stats["tri_tests"] * OPS_PER_TRI
+                  + stats["rays"] * OPS_PER_RAY) /
+                 max(stats["box_tests"] * OPS_PER_BOX_ALG + stats["tri_tests"] * OPS_PER_TRI_ALG
+                     + stats["rays"] * OPS_PER_RAY_ALG, 1))
     pt_rays = None
     if pt:
         # rays per path from one signature run (segments traced + shadow rays
@@ -507,6 +544,13 @@ def run_gpu(args, w):
     roof_render = {"kernel": render_kernel, "bound": "alu",
                    "achieved": ops / render_s / 1e12,
                    "peak": alu_peak, "unit": "TFLOP/s", "frac": ops / render_s / 1e12 / alu_peak,
+                   "ops_counted": (f"algorithmic: {OPS_PER_BOX_ALG} per child-box test, {OPS_PER_TRI_ALG} per "
+                                   f"triangle test, {OPS_PER_RAY_ALG} per ray (generation + shading), with "
+                                   "the box and triangle tests counted by an instrumented traversal"),
+                   "frac_source_count": ops * src_ratio / render_s / 1e12 / alu_peak,
+                   "ops_source_count": (f"{OPS_PER_BOX} per child-box test, {OPS_PER_TRI} per triangle test, "
+                                        f"{OPS_PER_RAY} per ray, counted from the kernel source (robust slab "
+                                        "form, watertight test with its division and compares)"),
                    "traffic": tr_render,
                    "peak_kind": (f"measured: scalar FFMA issue rate of this GPU (vafr_measure_fp32_peak; "
                                  f"paired FFMA2 {ffma2 / 1e12:.1f} T FMA/s; lane count x max clock "
@@ -541,6 +585,8 @@ def run_gpu(args, w):
         roof_render = {"kernel": "k_vbuf_raster + k_vbuf_tiles (+ k_shade_lp_vbuf)", "bound": "alu",
                        "achieved": r_ops / render_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
                        "frac": r_ops / render_s / 1e12 / alu_peak, "traffic": None,
+                       "ops_counted": "counted from the rasteriser source per pre-filter evaluation, "
+                                      "pixel past it and exact pixel-ray test",
                        "peak_kind": roof_render["peak_kind"], "ops_per_launch": r_ops,
                        "raster_counts_per_frame": rs, "avg_ms": render_s * 1e3}
     dominant = roof_render if render_s >= recon_s else roof_recon
@@ -549,19 +595,13 @@ def run_gpu(args, w):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": _workload_desc(w),
-                   "l2": "flushed between steps (256 MiB write outside the per-step events)",
-                   "acuity": args.acuity, "lp_fxaa": fxaa,
-                   "shading": f"path traced, 1 path/texel, NEE, {PT_DIFFUSE} diffuse bounces" if pt
-                   else "ray cast, Lambert + ambient",
-                   "binocular_mode": "VaFR_Rep (right eye warped)" if rep else "VaFR_Dup",
-                   "pipeline": "deferred (visibility buffer + LP lighting)" if deferred else "ray casting",
-                   "point_lights": int(args.point_lights),
-                   "tuning": ({"render_variant": tuning[0], "reconstruct_variant": tuning[1],
-                               "by": "--tuning" if args.tuning else
-                               "vafr_session_autotune on whole frames at the first gaze, before warm-up"}
-                              if tuning else "default variants (0, 0)"),
-                   "parallelism": f"replicas x{ws} (independent sessions, no collective)"},
+        "config": _config(w, args, ws),
+        "tuning": ({"render_variant": tuning[0], "reconstruct_variant": tuning[1],
+                    "by": "--tuning" if args.tuning else
+                    "vafr_session_autotune on whole frames at the first gaze, before warm-up"}
+                   if tuning else "default variants (0, 0)"),
+        "storage": {"lp": "f16" if w.lp_fp16 else "f32", "display": "f16" if w.display_fp16 else "f32",
+                    "arithmetic": "f32 (shading, filter accumulation); f64 host gaze set-up"},
         "fps": 1e3 / float(step_ms.mean()),
         "p50_frame_ms": float(np.percentile(step_ms, 50)),
         "p99_frame_ms": float(np.percentile(step_ms, 99)),
@@ -620,12 +660,11 @@ def run_gpu(args, w):
                                  "only at ray-edge ties, and display pixels whose filter footprint holds "
                                  "such a texel make the max"})
             line["precision"] = prec
-    if rank == 0:
-        print(json.dumps(line))
     V.vafr_session_destroy(sess)
     V.vafr_scene_destroy(scene)
     if dist:
         dist.destroy_process_group()
+    return line if rank == 0 else None
 
 
 def _device_scene(V, torch, w):
@@ -726,11 +765,11 @@ def run_sweep(args):
             "graph (render + reconstruct launch) per frame",
             "l2": "flushed between steps"},
             "tuning": V.vafr_batch_tuning(batch), "per_resolution": per_res}
-    print(json.dumps(line))
     V.vafr_batch_destroy(batch)
     for s in sess:
         V.vafr_session_destroy(s)
     V.vafr_scene_destroy(scene)
+    return line
 
 
 def run_serving(args):
@@ -763,8 +802,8 @@ def run_serving(args):
                        f"({w.poisson_rate_hz:.0f}/s), random-walk gaze, terrain4k scene, HBM "
                        f"budget {w.hbm_budget_bytes >> 30} GB, 2 in-flight batches"},
             "serving": sm, "clocks": clk.summary()}
-    print(json.dumps(line))
     V.vafr_scene_destroy(scene)
+    return line
 
 
 def cpu_baseline(args, w, gpu_eval=None):
@@ -847,7 +886,7 @@ def main():
     ap.add_argument("--steps", type=int, default=240)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="vafr", choices=["vafr", "reference"])
-    ap.add_argument("--workload", default="terrain4k",
+    ap.add_argument("--workload", default="objects8k",
                     choices=["random1k", "terrain4k", "objects8k", "sweep", "serving"])
     ap.add_argument("--serve-frames", type=int, default=60)
     ap.add_argument("--gt-steps", type=int, default=60)
@@ -880,6 +919,8 @@ def main():
                          "profiling runs, where the tuner's timings are distorted)")
     ap.add_argument("--fxaa", action="store_true",
                     help="run the LP-space FXAA pass (Sec. 3.4) inside each timed frame")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="leave out the terrain4k, sweep and serving summaries of the default line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -888,14 +929,46 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        run_reference(args, workload(args.workload, frames=max(args.steps + args.warmup, 1)))
+        run_reference(args, workload(args.workload), ws)
         return
     if args.workload == "sweep":
-        run_sweep(args)
-    elif args.workload == "serving":
-        run_serving(args)
-    else:
-        run_gpu(args, workload(args.workload))
+        print(json.dumps(run_sweep(args)))
+        return
+    if args.workload == "serving":
+        print(json.dumps(run_serving(args)))
+        return
+    line = run_gpu(args, workload(args.workload))
+    if line is None:
+        return
+    plain = not (args.pt or args.rep or args.deferred or args.fxaa or args.tuning or args.acuity != "paper")
+    if ws == 1 and args.workload == "objects8k" and plain and not args.no_extra:
+        line["extra_configs"] = ("terrain4k, sweep and serving: the other single-GPU configurations, "
+                                 "measured in the same process after the headline, L2 flushed between steps")
+        sub = argparse.Namespace(**vars(args))
+        sub.cpu_seconds = 0.0           # one oracle frame: the precision report, no baseline loop
+        line["terrain4k"] = _compact(run_gpu(sub, workload("terrain4k")))
+        line["sweep"] = {k: v for k, v in run_sweep(args).items()
+                         if k not in ("metric", "n_gpus", "higher_is_better", "data", "steps", "warmup")}
+        line["serving"] = {k: v for k, v in run_serving(args).items()
+                           if k not in ("metric", "n_gpus", "higher_is_better", "data")}
+    print(json.dumps(line))
+
+
+def _compact(line):
+    """The figures of a secondary configuration's line worth keeping."""
+    keep = ("value", "unit", "ms_per_step", "fps", "p50_frame_ms", "p99_frame_ms", "speedup_vs_gt",
+            "stage_ms", "tuning", "precision", "storage")
+    out = {k: line[k] for k in keep if k in line}
+    out["workload"] = line["config"]["workload"]
+    out["gt_ms_per_frame"] = line["gt"]["ms_per_frame"]
+    out["e2e_value"] = line["e2e"]["value"]
+    for key in ("roofline", "roofline_other"):
+        r = line[key]
+        out[key] = {k: r[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac",
+                                      "frac_source_count", "traffic", "avg_ms") if k in r}
+    if "cpu_baseline" in line:
+        out["cpu_oracle_one_frame"] = line["cpu_baseline"]
+    return out
 
 
 if __name__ == "__main__":

@@ -85,10 +85,13 @@ def test_reference_arm_line():
     import os
     import subprocess
     import sys
+    import time
+    t0 = time.perf_counter()
     out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
                           "--workload", "random1k", "--steps", "2", "--warmup", "0",
                           "--ref-texels", "512", "--ref-pixels", "4096"],
                          capture_output=True, text=True, timeout=600, cwd=bench.ROOT)
+    wall = time.perf_counter() - t0
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
@@ -99,3 +102,10 @@ def test_reference_arm_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    # the measured per-step time fits inside the process's own run time
+    assert d["ms_per_step"] * d["steps"] / 1e3 < wall
+    assert d["frame_ms_extrapolated"] > 0
+    # the same workload description as the GPU arm, trajectory included
+    args = bench.argparse.Namespace(pt=False, rep=False, deferred=False, fxaa=False, acuity="paper",
+                                    point_lights=0)
+    assert d["config"] == bench._config(workload("random1k"), args, 1)
