@@ -209,6 +209,18 @@ VAFR_API int vafr_scene_check(const vafr_scene* scene, void* stream);
 #define VAFR_INJECT_LOOP      2
 #define VAFR_INJECT_STACK     3
 VAFR_API int vafr_scene_inject_fault(vafr_scene* scene, int32_t kind);
+/* Host-side fault injection for tests of error recovery (no counterpart in
+ * the paper).  Arms a per-thread countdown: the batch entry points
+ * (vafr_batch_create, _render, _capture, _autotune) pass a checkpoint before
+ * each host allocation they make, and the checkpoint reached when the
+ * countdown is 0 fails as a failed allocation does: the call returns
+ * VAFR_ERR_OOM and leaves the batch as it was before the call (a captured
+ * graph, its parameters and frames stay consistent; a graph whose staging
+ * buffer had to be replaced is dropped, so vafr_batch_replay then returns
+ * INVALID_ARG instead of copying from freed memory).  The countdown then
+ * stays off until armed again.  countdown = -1 disarms it.
+ * Errors: INVALID_ARG (countdown < -1). */
+VAFR_API int vafr_debug_fail_host_alloc(int32_t countdown);
 
 /* ---- session --------------------------------------------------------------
  * vafr_session_create: validates the description and builds, in FP64 on the
@@ -500,12 +512,16 @@ VAFR_API int vafr_tuning_space(int32_t* n_render, int32_t* n_reconstruct);
  *                   same values vafr_scene_export_lbvh reports).
  *   sorted_ids_out  device, n_tris int32, triangle ids sorted by (code, id).
  *   err, err_len    optional host buffer for a message (NULL allowed).
+ * The three buffers must not share any byte (INVALID_ARG otherwise: the
+ * sort reads keys while it writes ids).
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The address is kept per device and context: after cudaDeviceReset the
+ * next call looks it up again, so it too should come before any capture.
  * Every call shares the one array: calls that overlap on the GPU (other
  * streams, other threads) race and corrupt each other's results; serialise
  * them.  No cudaMalloc, cudaFree or allocating library routine is called.
- * Errors: INVALID_ARG (size, NULL or non-device pointer), CUDA. */
+ * Errors: INVALID_ARG (size, NULL, non-device or overlapping pointers), CUDA. */
 #define VAFR_NOALLOC_MAX_TRIS 524288
 VAFR_API int vafr_morton_sort_noalloc(const float* tri_xyz, int64_t n_tris, uint32_t* codes_out,
                                       int32_t* sorted_ids_out, void* stream, char* err,

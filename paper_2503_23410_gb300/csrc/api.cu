@@ -38,9 +38,21 @@ int fail(int code, const char* fmt, ...) {
     return code;
 }
 
+// Host-allocation fault injection (vafr_debug_fail_host_alloc): the batch
+// entry points call host_alloc_point() before each host allocation they make;
+// the countdown-th call throws std::bad_alloc, exactly as a failed allocation
+// would.  Per thread, off (-1) unless a test arms it.
+thread_local int g_alloc_countdown = -1;
+
+void host_alloc_point() {
+    if (g_alloc_countdown < 0) return;
+    if (g_alloc_countdown-- == 0) throw std::bad_alloc();
+}
+
 // Entry points that allocate host memory run their body through this, so a
 // failed host allocation returns VAFR_ERR_OOM and no C++ exception leaves the
-// library.
+// library.  Their bodies change caller-visible state only after the last step
+// that can throw, so a failed call leaves every object as it was.
 template <class F>
 int guarded(F&& body) noexcept {
     try {
@@ -61,6 +73,15 @@ int guarded(F&& body) noexcept {
     } while (0)
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Two timing events destroyed on every return path.
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
 
 int check_device(int* sms) {
     int dev = 0;
@@ -111,6 +132,7 @@ struct vafr_scene {
     int alloc(T** p, size_t count) {
         const size_t b = sizeof(T) * (count ? count : 1);
         void* q = nullptr;
+        allocs.reserve(allocs.size() + 1);   // may throw; the push_back below cannot
         CUDA_TRY(cudaMalloc(&q, b));
         allocs.push_back(q);
         bytes += (int64_t)b;
@@ -185,9 +207,12 @@ struct vafr_batch {
     BigBatch* host_batch = nullptr;  // parameters of the captured launches
     // longest-first order state per frame slot (the batch's own, so batches in
     // flight on different streams never share one)
-    std::vector<LptState*> lpt;
-    std::vector<int> lpt_cap;
-    std::vector<unsigned> lpt_frames;
+    struct LptSlot {
+        LptState* state;
+        int cap;           // chunks the state holds
+        unsigned frames;   // frames rendered with it (parity)
+    };
+    std::vector<LptSlot> lpt;
     // displays in page-locked host memory: the reconstruction writes a device
     // staging buffer per frame position, which the copy engine then moves to
     // the host (faster over the CPU-GPU link than the kernel's own stores)
@@ -196,13 +221,16 @@ struct vafr_batch {
         const void* src;
         size_t bytes;
     };
-    std::vector<void*> stage;
-    std::vector<size_t> stage_cap;
+    struct StageSlot {
+        void* buf;
+        size_t cap;
+    };
+    std::vector<StageSlot> stage;
     std::vector<HostCopy> copies;   // of the last built batch
 
     ~vafr_batch() {
-        for (LptState* q : lpt) cudaFree(q);
-        for (void* q : stage) cudaFree(q);
+        for (const LptSlot& q : lpt) cudaFree(q.state);
+        for (const StageSlot& q : stage) cudaFree(q.buf);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         cudaFree(d_counter);
@@ -375,7 +403,7 @@ static int vafr_build_scene_impl(const float* tri_xyz, const float* albedo_rgb, 
     int rc = check_device(&sms);
     if (rc) return rc;
     cudaStream_t s = as_stream(stream);
-    auto* sc = new vafr_scene();
+    std::unique_ptr<vafr_scene> sc(new vafr_scene());
     cudaGetDevice(&sc->device);
     sc->sms = sms;
     sc->n = n_tris;
@@ -388,7 +416,7 @@ static int vafr_build_scene_impl(const float* tri_xyz, const float* albedo_rgb, 
 #define ALLOC(p, c)                              \
     do {                                         \
         int r_ = sc->alloc(&(p), (size_t)(c));   \
-        if (r_) { delete sc; return r_; }        \
+        if (r_) return r_;                       \
     } while (0)
     ALLOC(sc->status, 1);
     if (n > 0) {
@@ -415,7 +443,7 @@ static int vafr_build_scene_impl(const float* tri_xyz, const float* albedo_rgb, 
         ALLOC(b.albedo4, n);
     }
 #undef ALLOC
-    auto bail = [&](int code) { delete sc; return code; };
+    auto bail = [&](int code) { return code; };   // sc frees everything it holds
     if (cudaMemsetAsync(sc->status, 0, sizeof(unsigned), s) != cudaSuccess)
         return bail(fail(VAFR_ERR_CUDA, "memset status"));
     if (n > 0) {
@@ -449,7 +477,7 @@ static int vafr_build_scene_impl(const float* tri_xyz, const float* albedo_rgb, 
     d.root = n == 0 ? INT_MIN : (n == 1 ? ~0 : 0);
     for (int k = 0; k < 3; ++k) d.light[k] = (float)(light_dir[k] / ll);
     d.status = sc->status;
-    *out = sc;
+    *out = sc.release();
     return VAFR_OK;
 }
 
@@ -532,6 +560,12 @@ int vafr_scene_check(const vafr_scene* scene, void* stream) {
     return VAFR_OK;
 }
 
+int vafr_debug_fail_host_alloc(int32_t countdown) {
+    if (countdown < -1) return fail(VAFR_ERR_INVALID_ARG, "countdown %d < -1", countdown);
+    g_alloc_countdown = countdown;
+    return VAFR_OK;
+}
+
 int vafr_scene_inject_fault(vafr_scene* scene, int32_t kind) {
     if (!scene) return fail(VAFR_ERR_INVALID_ARG, "scene is NULL");
     if (kind < VAFR_INJECT_NONE || kind > VAFR_INJECT_STACK) return fail(VAFR_ERR_INVALID_ARG, "unknown kind %d", kind);
@@ -579,7 +613,7 @@ static int vafr_session_create_impl(const vafr_session_desc* desc, vafr_session*
     std::string why;
     rc = get_layout(d.acuity, &lay, &why);
     if (rc) return fail(rc, "%s", why.c_str());
-    auto* s = new vafr_session();
+    std::unique_ptr<vafr_session> s(new vafr_session());
     cudaGetDevice(&s->device);
     s->sms = sms;
     s->desc = d;
@@ -587,8 +621,7 @@ static int vafr_session_create_impl(const vafr_session_desc* desc, vafr_session*
     s->n_cols = lay->n_cols;
     s->n_texels = lay->n_texels;
     s->n_slots = lay->n_slots;
-    auto bail = [&](cudaError_t e) {
-        delete s;
+    auto bail = [&](cudaError_t e) {   // s frees what it holds
         return fail(e == cudaErrorMemoryAllocation ? VAFR_ERR_OOM : VAFR_ERR_CUDA, "session: %s",
                     cudaGetErrorString(e));
     };
@@ -601,8 +634,8 @@ static int vafr_session_create_impl(const vafr_session_desc* desc, vafr_session*
     if ((e = cudaMemset(s->d_status, 0, sizeof(unsigned))) != cudaSuccess) return bail(e);
     if (d.lp_fxaa && (e = cudaMalloc(&s->d_luma, sizeof(float) * s->n_slots * d.n_eyes)) != cudaSuccess)
         return bail(e);
-    for (int eye = 0; eye < d.n_eyes; ++eye) fill_static(s, eye);
-    *out = s;
+    for (int eye = 0; eye < d.n_eyes; ++eye) fill_static(s.get(), eye);
+    *out = s.release();
     return VAFR_OK;
 }
 
@@ -1074,21 +1107,23 @@ static int build_batch(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n,
         f.lpt = nullptr;
         if (bt->render_variant == kLptVariant && !graph) {
             if ((int)bt->lpt.size() <= i) {
-                bt->lpt.resize(i + 1, nullptr);
-                bt->lpt_cap.resize(i + 1, 0);
-                bt->lpt_frames.resize(i + 1, 0u);
+                host_alloc_point();
+                bt->lpt.resize(i + 1, vafr_batch::LptSlot{nullptr, 0, 0u});   // all or nothing
             }
+            vafr_batch::LptSlot& q = bt->lpt[i];
             const int need = lpt_chunks(s->n_texels);
-            if (bt->lpt_cap[i] < need) {   // grows only (a state in use is never freed mid-flight)
-                LptState* q = nullptr;
-                CUDA_TRY(lpt_alloc(&q, need));
-                CUDA_TRY(cudaDeviceSynchronize());   // the old state may still be in use
-                cudaFree(bt->lpt[i]);
-                bt->lpt[i] = q;
-                bt->lpt_cap[i] = need;
-                bt->lpt_frames[i] = 0u;
+            if (q.cap < need) {   // grows only (a state in use is never freed mid-flight)
+                LptState* nq = nullptr;
+                CUDA_TRY(lpt_alloc(&nq, need));
+                cudaError_t e = cudaDeviceSynchronize();   // the old state may still be in use
+                if (e != cudaSuccess) {
+                    cudaFree(nq);
+                    CUDA_TRY(e);
+                }
+                cudaFree(q.state);
+                q = vafr_batch::LptSlot{nq, need, 0u};
             }
-            CUDA_TRY(lpt_next(bt->lpt[i], bt->lpt_frames[i], st, &f.lpt));
+            CUDA_TRY(lpt_next(q.state, q.frames, st, &f.lpt));
         }
         if (s->desc.lp_fxaa) {
             if (!fr.lp_aa || !aligned(fr.lp_aa, 16) || fr.lp_aa == fr.lp)
@@ -1108,19 +1143,24 @@ static int build_batch(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n,
             int64_t lpb = 0, dpb = 0;
             vafr_session_sizes(s, &lpb, &dpb);
             if ((int)bt->stage.size() <= i) {
-                bt->stage.resize(i + 1, nullptr);
-                bt->stage_cap.resize(i + 1, 0);
+                host_alloc_point();
+                bt->stage.resize(i + 1, vafr_batch::StageSlot{nullptr, 0});   // all or nothing
             }
-            if (bt->stage_cap[i] < (size_t)dpb) {   // grows only
-                void* q = nullptr;
-                CUDA_TRY(cudaMalloc(&q, (size_t)dpb));
-                CUDA_TRY(cudaDeviceSynchronize());   // the old buffer may still be in use
-                cudaFree(bt->stage[i]);
-                bt->stage[i] = q;
-                bt->stage_cap[i] = (size_t)dpb;
+            vafr_batch::StageSlot& q = bt->stage[i];
+            if (q.cap < (size_t)dpb) {   // grows only
+                void* nq = nullptr;
+                CUDA_TRY(cudaMalloc(&nq, (size_t)dpb));
+                cudaError_t e = cudaDeviceSynchronize();   // the old buffer may still be in use
+                if (e != cudaSuccess) {
+                    cudaFree(nq);
+                    CUDA_TRY(e);
+                }
+                cudaFree(q.buf);
+                q = vafr_batch::StageSlot{nq, (size_t)dpb};
             }
-            f.disp = bt->stage[i];
-            bt->copies.push_back({fr.display, bt->stage[i], (size_t)dpb});
+            f.disp = q.buf;
+            host_alloc_point();
+            bt->copies.push_back({fr.display, q.buf, (size_t)dpb});
         }
         f.hit_ids = nullptr;
         f.work_begin = b->total_work;
@@ -1148,15 +1188,14 @@ static int vafr_batch_create_impl(const vafr_scene* scene, int32_t max_frames, v
     if (!scene || !out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
     if (max_frames <= 0 || max_frames > VAFR_MAX_BATCH)
         return fail(VAFR_ERR_INVALID_ARG, "max_frames out of range");
-    auto* bt = new vafr_batch();
+    std::unique_ptr<vafr_batch> bt(new vafr_batch());
     bt->scene = scene;
     bt->max_frames = max_frames;
-    if (cudaMalloc(&bt->d_counter, 2 * sizeof(unsigned long long)) != cudaSuccess) {
-        delete bt;
+    if (cudaMalloc(&bt->d_counter, 2 * sizeof(unsigned long long)) != cudaSuccess)
         return fail(VAFR_ERR_OOM, "batch counter");
-    }
+    host_alloc_point();
     bt->host_batch = new BigBatch();
-    *out = bt;
+    *out = bt.release();
     return VAFR_OK;
 }
 
@@ -1173,10 +1212,10 @@ int vafr_batch_destroy(vafr_batch* batch) {
 
 static int vafr_batch_render_impl(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream) {
     if (!bt) return fail(VAFR_ERR_INVALID_ARG, "batch is NULL");
-    BigBatch* b = new BigBatch();
-    int rc = build_batch(bt, frames, n, b, as_stream(stream), false);
+    host_alloc_point();
+    std::unique_ptr<BigBatch> b(new BigBatch());
+    int rc = build_batch(bt, frames, n, b.get(), as_stream(stream), false);
     if (!rc) rc = launch_batch(bt, *b, as_stream(stream));
-    delete b;
     return rc;
 }
 
@@ -1184,29 +1223,65 @@ int vafr_batch_render(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, 
     return guarded([&] { return vafr_batch_render_impl(bt, frames, n, stream); });
 }
 
+// Owner of a graph and its executable while a capture is being built; the
+// batch takes them over only when every step has succeeded.
+struct GraphParts {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~GraphParts() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
 static int vafr_batch_capture_impl(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n, void* stream) {
     if (!bt) return fail(VAFR_ERR_INVALID_ARG, "batch is NULL");
-    int rc = build_batch(bt, frames, n, bt->host_batch, as_stream(stream), true);
+    // everything is built in locals first: a failure at any step (including a
+    // host allocation) leaves the batch's previous graph, parameters and
+    // captured frames as they were, still consistent with one another
+    host_alloc_point();
+    std::unique_ptr<BigBatch> hb(new BigBatch());
+    // build_batch may replace a staging buffer the current graph copies from;
+    // if this capture then fails, that graph must not be replayed any more
+    host_alloc_point();
+    std::vector<void*> old_stage;
+    old_stage.reserve(bt->stage.size());
+    for (const vafr_batch::StageSlot& q : bt->stage) old_stage.push_back(q.buf);
+    struct StaleGraph {
+        vafr_batch* bt;
+        const std::vector<void*>& old;
+        bool committed = false;
+        ~StaleGraph() {
+            if (committed || !bt->exec) return;
+            for (size_t i = 0; i < old.size(); ++i)
+                if (i >= bt->stage.size() || bt->stage[i].buf != old[i]) {
+                    cudaGraphExecDestroy(bt->exec);
+                    bt->exec = nullptr;
+                    return;
+                }
+        }
+    } stale{bt, old_stage};
+    int rc = build_batch(bt, frames, n, hb.get(), as_stream(stream), true);
     if (rc) return rc;
-    if (bt->exec) { cudaGraphExecDestroy(bt->exec); bt->exec = nullptr; }
-    if (bt->graph) { cudaGraphDestroy(bt->graph); bt->graph = nullptr; }
+    GraphParts gp;
     cudaStream_t cs = nullptr;
     CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        rc = launch_batch(bt, *bt->host_batch, cs);
-        e = cudaStreamEndCapture(cs, &bt->graph);
+        rc = launch_batch(bt, *hb, cs);
+        e = cudaStreamEndCapture(cs, &gp.graph);
     }
     cudaStreamDestroy(cs);
     if (rc) return rc;
     CUDA_TRY(e);
-    CUDA_TRY(cudaGraphInstantiate(&bt->exec, bt->graph, 0));
+    CUDA_TRY(cudaGraphInstantiate(&gp.exec, gp.graph, 0));
     // the kernel nodes, ordered along the captured chain (memset -> render ->
     // [FXAA ->] reconstruct): a node's rank is its number of kernel ancestors
     size_t nn = 0;
-    CUDA_TRY(cudaGraphGetNodes(bt->graph, nullptr, &nn));
+    CUDA_TRY(cudaGraphGetNodes(gp.graph, nullptr, &nn));
+    host_alloc_point();
     std::vector<cudaGraphNode_t> nodes(nn);
-    CUDA_TRY(cudaGraphGetNodes(bt->graph, nodes.data(), &nn));
+    CUDA_TRY(cudaGraphGetNodes(gp.graph, nodes.data(), &nn));
     auto kernel_ancestors = [&](cudaGraphNode_t nd, auto&& self) -> int {
         size_t ndep = 0;
         if (cudaGraphNodeGetDependencies(nd, nullptr, nullptr, &ndep) != cudaSuccess) return -1;
@@ -1229,23 +1304,38 @@ static int vafr_batch_capture_impl(vafr_batch* bt, const vafr_frame_desc* frames
         if (ty != cudaGraphNodeTypeKernel) continue;
         const int r = kernel_ancestors(nd, kernel_ancestors);
         if (r < 0) return fail(VAFR_ERR_CUDA, "graph: dependency query failed");
+        host_alloc_point();
         ranked.push_back({r, nd});
     }
     std::sort(ranked.begin(), ranked.end(),
               [](const std::pair<int, cudaGraphNode_t>& a, const std::pair<int, cudaGraphNode_t>& b) {
                   return a.first < b.first;
               });
-    bt->kernel_nodes.clear();
-    bt->kernel_params.clear();
+    std::vector<cudaGraphNode_t> knodes;
+    std::vector<cudaKernelNodeParams> kparams;
     for (size_t k = 0; k < ranked.size(); ++k) {
         if (ranked[k].first != (int)k) return fail(VAFR_ERR_CUDA, "graph: kernel nodes are not a chain");
         cudaKernelNodeParams p{};
         CUDA_TRY(cudaGraphKernelNodeGetParams(ranked[k].second, &p));
-        bt->kernel_nodes.push_back(ranked[k].second);
-        bt->kernel_params.push_back(p);
+        host_alloc_point();
+        knodes.push_back(ranked[k].second);
+        kparams.push_back(p);
     }
-    if (bt->kernel_nodes.size() < 2) return fail(VAFR_ERR_CUDA, "graph: kernel nodes not found");
-    bt->captured.assign(frames, frames + n);
+    if (knodes.size() < 2) return fail(VAFR_ERR_CUDA, "graph: kernel nodes not found");
+    host_alloc_point();
+    std::vector<vafr_frame_desc> cap(frames, frames + n);
+    // commit: nothing below can fail
+    stale.committed = true;
+    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    if (bt->graph) cudaGraphDestroy(bt->graph);
+    bt->exec = gp.exec;
+    bt->graph = gp.graph;
+    gp.exec = nullptr;
+    gp.graph = nullptr;
+    *bt->host_batch = *hb;
+    bt->kernel_nodes.swap(knodes);
+    bt->kernel_params.swap(kparams);
+    bt->captured.swap(cap);
     return VAFR_OK;
 }
 
@@ -1318,10 +1408,12 @@ int vafr_session_autotune(const vafr_scene* scene, vafr_session* s, void* lp, vo
                                   static_cast<char*>(display) + (size_t)e * dpb, stream);
         return rc;
     };
-    cudaEvent_t e0, e1;
-    CUDA_TRY(cudaEventCreate(&e0));
-    CUDA_TRY(cudaEventCreate(&e1));
+    EventPair ev;
+    CUDA_TRY(cudaEventCreate(&ev.a));
+    CUDA_TRY(cudaEventCreate(&ev.b));
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     int rc = VAFR_OK;
+    const int keep_render = s->render_variant;
     auto time_frames = [&](float& ms) {
         for (int i = 0; i < warm && !rc; ++i) rc = frame();
         cudaEventRecord(e0, st);
@@ -1350,9 +1442,11 @@ int vafr_session_autotune(const vafr_scene* scene, vafr_session* s, void* lp, vo
         if (ms < best) { best = ms; best_c = v; }
     }
     s->recon_variant = best_c;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (rc) return rc;
+    if (rc) {   // a failed tuning run leaves the session's variants as they were
+        s->render_variant = keep_render;
+        s->recon_variant = keep_recon;
+        return rc;
+    }
     if (cfg_out) { cfg_out[0] = best_r; cfg_out[1] = best_c; }
     return VAFR_OK;
 }
@@ -1362,11 +1456,23 @@ static int vafr_batch_autotune_impl(vafr_batch* bt, const vafr_frame_desc* frame
     if (!bt) return fail(VAFR_ERR_INVALID_ARG, "batch is NULL");
     if (iters <= 0) iters = 3;
     cudaStream_t st = as_stream(stream);
-    cudaEvent_t e0, e1;
-    CUDA_TRY(cudaEventCreate(&e0));
-    CUDA_TRY(cudaEventCreate(&e1));
-    BigBatch* b = new BigBatch();
+    EventPair ev;
+    CUDA_TRY(cudaEventCreate(&ev.a));
+    CUDA_TRY(cudaEventCreate(&ev.b));
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
+    host_alloc_point();
+    std::unique_ptr<BigBatch> holder(new BigBatch());
+    BigBatch* b = holder.get();
     int rc = VAFR_OK;
+    // restores the batch's variants unless the tuning completes
+    struct Restore {
+        vafr_batch* bt;
+        int render, recon;
+        bool done = false;
+        ~Restore() {
+            if (!done) { bt->render_variant = render; bt->recon_variant = recon; }
+        }
+    } restore{bt, bt->render_variant, bt->recon_variant};
     auto time_it = [&](auto&& launch) -> float {
         if (launch() != cudaSuccess) return INFINITY;
         cudaEventRecord(e0, st);
@@ -1397,13 +1503,11 @@ static int vafr_batch_autotune_impl(vafr_batch* bt, const vafr_frame_desc* frame
         if (ms < best) { best = ms; best_v = v; }
     }
     bt->recon_variant = best_v;
-    delete b;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (!rc) {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = fail(VAFR_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
     }
+    restore.done = rc == VAFR_OK;
     return rc;
 }
 

@@ -14,6 +14,8 @@
 
 #include <float.h>
 
+#include <cuda.h>
+
 #include <cstring>
 #include <mutex>
 
@@ -417,25 +419,64 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocS
 
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
-NoAllocScratch* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+struct NoAllocSlot {
+    NoAllocScratch* ptr;         // device address of the array, or nullptr
+    unsigned long long ctx_id;   // context it was looked up in (0: unknown)
+};
+NoAllocSlot g_noalloc_slot[kNoAllocMaxDevices] = {};
+
+// Process-unique id of the calling thread's current context, or 0 if the
+// driver cannot say.  A device reset destroys the context and the module with
+// the array; the context that replaces it has a new id, which tells the cache
+// below to look the address up again.  The two driver calls are found
+// through the runtime, so the library needs no link against the driver.
+unsigned long long current_context_id() {
+    using GetCur = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCur get_cur = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<GetCur>(f);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_cur || !get_id || get_cur(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 // Device address of the scratch array on the current device.  In host code the
-// array's name is only a host-side stand-in, so the address is looked up once
-// per device with that device current.
+// array's name is only a host-side stand-in, so the address is looked up with
+// that device current: once per device, and again after a device reset.
 cudaError_t noalloc_scratch(NoAllocScratch** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    NoAllocSlot& slot = g_noalloc_slot[dev];
+    if (!slot.ptr || slot.ctx_id != ctx) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = static_cast<NoAllocScratch*>(p);
+        slot = NoAllocSlot{static_cast<NoAllocScratch*>(p), ctx};
     }
-    *out = g_noalloc_ptr[dev];
+    *out = slot.ptr;
     return cudaSuccess;
+}
+
+// Whether byte ranges [a, a + na) and [b, b + nb) share a byte.
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
 }
 
 }  // namespace
@@ -465,6 +506,12 @@ extern "C" VAFR_API int vafr_morton_sort_noalloc(const float* tri_xyz, int64_t n
             return report(VAFR_ERR_INVALID_ARG, "every buffer must be device memory");
         }
     }
+    // the sort reads its input keys while writing the output ids: any shared
+    // byte between the three buffers would corrupt the result silently
+    const size_t nt = (size_t)n_tris;
+    if (overlaps(codes_out, 4 * nt, sorted_ids_out, 4 * nt) || overlaps(tri_xyz, 36 * nt, codes_out, 4 * nt) ||
+        overlaps(tri_xyz, 36 * nt, sorted_ids_out, 4 * nt))
+        return report(VAFR_ERR_INVALID_ARG, "tri_xyz, codes_out and sorted_ids_out must not overlap");
     NoAllocScratch* sc = nullptr;
     cudaError_t e = noalloc_scratch(&sc);
     if (e != cudaSuccess) return report(VAFR_ERR_CUDA, cudaGetErrorString(e));

@@ -79,6 +79,7 @@ _PROTOS = {
     "vafr_scene_export_lbvh": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "vafr_scene_check": (ctypes.c_int, [_P, _P]),
     "vafr_scene_inject_fault": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "vafr_debug_fail_host_alloc": (ctypes.c_int, [ctypes.c_int32]),
     "vafr_session_create": (ctypes.c_int, [_P, _P]),
     "vafr_session_destroy": (ctypes.c_int, [_P]),
     "vafr_lp_layout": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -274,6 +275,10 @@ INJECT_NONE, INJECT_BAD_CHILD, INJECT_LOOP, INJECT_STACK = 0, 1, 2, 3
 
 def vafr_scene_inject_fault(scene: int, kind: int) -> None:
     _check(load().vafr_scene_inject_fault(scene, int(kind)))
+
+
+def vafr_debug_fail_host_alloc(countdown: int) -> None:
+    _check(load().vafr_debug_fail_host_alloc(int(countdown)))
 
 
 def vafr_session_create(desc: vafr_session_desc) -> int:
@@ -495,10 +500,31 @@ def vafr_tuning_space():
     return a.value, b.value
 
 
+def _noalloc_n(tri_xyz, codes_out, sorted_ids_out) -> int:
+    """Triangle count of vafr_morton_sort_noalloc's arguments, checked here
+    because the C entry point cannot see buffer sizes: tri_xyz is (n, 9) (or
+    flat with 9 n floats) FP32, both outputs hold at least n 32-bit integers."""
+    _require_f32(tri_xyz, "tri_xyz")
+    shape = tuple(tri_xyz.shape)
+    if len(shape) == 2 and shape[1] == 9:
+        n = int(shape[0])
+    elif len(shape) == 1 and shape[0] % 9 == 0:
+        n = int(shape[0]) // 9
+    else:
+        raise ValueError(f"tri_xyz must be (n, 9) or flat with 9 n floats, got shape {shape}")
+    for name, buf in (("codes_out", codes_out), ("sorted_ids_out", sorted_ids_out)):
+        dt = str(buf.dtype)
+        if not any(dt.endswith(t) for t in ("int32", "uint32")):
+            raise ValueError(f"{name} must hold 32-bit integers, got {dt}")
+        count = int(buf.numel()) if hasattr(buf, "numel") else int(buf.size)
+        if count < n:
+            raise ValueError(f"{name} holds {count} elements, fewer than the {n} triangles")
+    return n
+
+
 def vafr_morton_sort_noalloc(tri_xyz, codes_out, sorted_ids_out, stream=None) -> None:
     """Morton codes + stable (code, id) order without any allocation (device buffers)."""
-    _require_f32(tri_xyz, "tri_xyz")
-    n = int(tri_xyz.shape[0])
+    n = _noalloc_n(tri_xyz, codes_out, sorted_ids_out)
     msg = ctypes.create_string_buffer(256)
     rc = load().vafr_morton_sort_noalloc(ptr(tri_xyz), n, ptr(codes_out), ptr(sorted_ids_out),
                                          stream_ptr(stream), msg, len(msg))

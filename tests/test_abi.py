@@ -76,3 +76,25 @@ def test_oracle_is_not_imported_by_the_product():
                 txt = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, fn
                 assert "vafr_oracle" not in txt and "liboracle" not in txt, fn
+
+
+def test_noalloc_wrapper_checks_sizes_before_the_call():
+    """The C entry point cannot see buffer sizes, so the binding refuses a flat
+    tri_xyz whose length is not 9 n, outputs shorter than n and outputs that are
+    not 32-bit integers -- before anything reaches the library."""
+    import numpy as np
+    from paper_2503_23410_gb300 import vafr as V
+    tris = np.zeros((10, 9), np.float32)
+    ok = np.zeros(10, np.int32)
+    assert V._noalloc_n(tris, ok, ok) == 10
+    assert V._noalloc_n(tris.reshape(-1), ok, np.zeros(12, np.uint32)) == 10
+    for bad in ((tris.reshape(-1)[:89], ok, ok),          # flat, not a multiple of 9
+                (tris.reshape(30, 3), ok, ok),            # wrong shape
+                (tris, np.zeros(9, np.int32), ok),        # codes too short
+                (tris, ok, np.zeros(9, np.int32)),        # ids too short
+                (tris, np.zeros(10, np.float32), ok),     # not integers
+                (tris, ok, np.zeros(10, np.int64))):      # not 32-bit
+        with pytest.raises(ValueError):
+            V.vafr_morton_sort_noalloc(*bad)
+    with pytest.raises(TypeError):
+        V.vafr_morton_sort_noalloc(tris.astype(np.float64), ok, ok)

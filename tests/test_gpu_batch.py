@@ -211,3 +211,111 @@ def test_host_displays_equal_device_displays(V, torch_mod, setup):
         s0, bufs0, _, dpb0 = sessions[0]
         V.vafr_batch_render(b, [(s0, 0, bufs0[0][0], np.zeros(dpb0, np.uint8))])
     V.vafr_batch_destroy(b)
+
+
+def test_host_allocation_failures_leave_the_batch_usable(V, torch_mod):
+    """Every host allocation inside vafr_batch_capture and vafr_batch_render,
+    failed in turn by the fault hook, makes the call return OOM and leaves the
+    batch as it was: the graph captured before still replays the same bytes,
+    a graph whose staging buffer had to be replaced is refused instead of
+    replayed, and the next call without a fault succeeds."""
+    torch = torch_mod
+    sc = random_triangles_scene(500, seed=3)
+    h, keep = device_scene(V, sc, torch)
+    poses = eye_pair_poses(look_at_pose((0.0, 0.3, -3.2), (0, 0, 0)), 0.063)
+    made = []
+
+    def session(W, H):
+        s = V.vafr_session_create(V.make_session_desc(W, H, 100.0, poses, 0, 0))
+        for e in range(2):
+            V.vafr_set_gaze(s, e, W * 0.4, H * 0.55)
+        lpb, dpb = V.vafr_session_sizes(s)
+        lp = torch.zeros(2 * lpb, dtype=torch.uint8, device="cuda")
+        dev = torch.zeros(dpb, dtype=torch.uint8, device="cuda")
+        host = torch.zeros(dpb, dtype=torch.uint8, pin_memory=True)
+        made.append(s)
+        return s, lp, lpb, dev, host
+
+    small = session(96, 64)
+    big = session(160, 120)
+
+    def frames(x):
+        s, lp, lpb, dev, host = x
+        return [(s, 0, lp, dev), (s, 1, lp[lpb:], host)]
+
+    bt = V.vafr_batch_create(h, 4)
+    V.vafr_batch_capture(bt, frames(small))
+    V.vafr_batch_replay(bt)
+    torch.cuda.synchronize()
+    ref = (small[3].cpu().numpy().copy(), small[4].numpy().copy())
+
+    def replay_matches():
+        small[3].zero_()
+        small[4].zero_()
+        V.vafr_batch_replay(bt)
+        torch.cuda.synchronize()
+        return (np.array_equal(small[3].cpu().numpy(), ref[0]) and
+                np.array_equal(small[4].numpy(), ref[1]))
+
+    # capture of the same frames, failing at each host allocation in turn
+    failures = 0
+    for k in range(64):
+        V.vafr_debug_fail_host_alloc(k)
+        try:
+            V.vafr_batch_capture(bt, frames(small))
+            done = True
+        except V.VafrError as ex:
+            assert ex.code == V.ERR_OOM
+            done = False
+        finally:
+            V.vafr_debug_fail_host_alloc(-1)
+        assert replay_matches()
+        if done:
+            break
+        failures += 1
+    assert failures >= 3 and done
+
+    # batch renders (longest-first slots and host staging included), same way
+    V.vafr_batch_tuning(bt, (6, 0))
+    for k in range(64):
+        V.vafr_debug_fail_host_alloc(k)
+        try:
+            V.vafr_batch_render(bt, frames(small))
+            done = True
+        except V.VafrError as ex:
+            assert ex.code == V.ERR_OOM
+            done = False
+        finally:
+            V.vafr_debug_fail_host_alloc(-1)
+        if done:
+            break
+    assert done
+    torch.cuda.synchronize()
+    V.vafr_batch_tuning(bt, (0, 0))
+    assert replay_matches()
+
+    # a capture with a larger host display replaces the staging buffer the
+    # old graph copies from; failing after that drops the old graph
+    V.vafr_debug_fail_host_alloc(6)
+    try:
+        V.vafr_batch_capture(bt, frames(big))
+        captured = True
+    except V.VafrError as ex:
+        assert ex.code == V.ERR_OOM
+        captured = False
+    finally:
+        V.vafr_debug_fail_host_alloc(-1)
+    if not captured:
+        try:
+            ok = replay_matches()
+        except V.VafrError as ex:
+            assert ex.code == V.ERR_INVALID_ARG
+            ok = None
+        assert ok in (True, None)
+    V.vafr_batch_capture(bt, frames(big))        # without a fault: works
+    V.vafr_batch_replay(bt)
+    torch.cuda.synchronize()
+    V.vafr_batch_destroy(bt)
+    for s in made:
+        V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)

@@ -52,3 +52,18 @@ def test_noalloc_rejects_oversized_and_host_input(V, torch_mod):
     small = torch.empty(8, dtype=torch.int32, device="cuda")
     with pytest.raises(V.VafrError, match="device memory"):
         V.vafr_morton_sort_noalloc(host, small, small)
+
+
+def test_noalloc_rejects_overlapping_buffers(V, torch_mod):
+    """Outputs that share bytes with each other or with the input would corrupt
+    the sort silently; the entry point refuses them before any launch."""
+    torch = torch_mod
+    n = 1000
+    tris = torch.zeros((n, 9), dtype=torch.float32, device="cuda")
+    out = torch.empty(3 * n, dtype=torch.int32, device="cuda")
+    with pytest.raises(V.VafrError, match="overlap"):
+        V.vafr_morton_sort_noalloc(tris, out[:n], out[n // 2:n // 2 + n])      # outputs overlap
+    with pytest.raises(V.VafrError, match="overlap"):
+        V.vafr_morton_sort_noalloc(tris, tris.view(torch.int32).view(-1)[:n], out[:n])   # code over input
+    V.vafr_morton_sort_noalloc(tris, out[:n], out[n:2 * n])                      # adjacent: fine
+    torch.cuda.synchronize()
