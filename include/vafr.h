@@ -170,6 +170,22 @@ VAFR_API int vafr_scene_set_point_lights(vafr_scene* scene, int32_t n, const flo
 VAFR_API int vafr_scene_destroy(vafr_scene* scene);
 /* Triangle count and device bytes held by the scene. */
 VAFR_API int vafr_scene_info(const vafr_scene* scene, int64_t* n_tris, int64_t* device_bytes);
+/* Copies the tree the rays traverse to HOST buffers (either may be NULL; call
+ * with both NULL to learn n_nodes first).  It is built by PLOC over the
+ * Morton-sorted leaves (Meister and Bittner 2018) and collapsed into 4-wide
+ * nodes; the paper's acceleration structure is the driver's own (Sec. 6.1),
+ * so this is the build's choice, checked by its invariants.
+ *   n_nodes  number of 4-wide nodes; node 0 is the root.
+ *   nodes    n_nodes x 32 floats: per axis the lo then hi planes of the four
+ *            children (lo.x[4], hi.x[4], lo.y[4], hi.y[4], lo.z[4], hi.z[4]),
+ *            then four int32 child references (>= 0 node, < 0 leaf ~k,
+ *            INT32_MIN unused), then four padding words.
+ *   leaves   n_tris x 12 floats, sorted (leaf) order: v0.xyz | id bits,
+ *            v1.xyz | 0, v2.xyz | 0, vertices in lexicographic order.
+ * A scene of fewer than two triangles has no nodes.  Synchronises the
+ * device.  Errors: INVALID_ARG, CUDA. */
+VAFR_API int vafr_scene_export_tree4(const vafr_scene* scene, int64_t* n_nodes, float* nodes,
+                                     float* leaves);
 /* Copies the LBVH build products to HOST buffers (any may be NULL):
  *   codes      n     uint32 Morton codes, input triangle order
  *   sorted_ids n     int32 triangle ids in sorted (leaf) order
@@ -339,7 +355,9 @@ VAFR_API int vafr_render_full_gt_pt(const vafr_scene* scene, vafr_session* sessi
  * on one session must not overlap.
  * vafr_render_lp_rep: the whole mode: casts the left eye (eye 0) into
  *   lp_out[0], warps it into lp_out[1] and casts the right eye's holes.
- *   lp_out as vafr_render_lp with both eyes.
+ *   lp_out as vafr_render_lp with both eyes; right_tri_out (device or NULL,
+ *   one int32 per slot) receives the warp's winning triangle per right texel
+ *   as in vafr_reproject_lp, -1 where the texel was a hole and was cast.
  * vafr_reproject_lp: the warp alone, from a caller's left LP buffer and hit
  *   distances (left_depth: device, one float per slot, +inf on a miss; only
  *   texel slots are read); holes are left unwritten in right_lp_out and
@@ -350,7 +368,7 @@ VAFR_API int vafr_render_full_gt_pt(const vafr_scene* scene, vafr_session* sessi
  *   `stream`).
  * Errors: INVALID_ARG (NULL, unaligned, not binocular, gaze not set), OOM, CUDA. */
 VAFR_API int vafr_render_lp_rep(const vafr_scene* scene, vafr_session* session, void* lp_out,
-                                void* stream);
+                                int32_t* right_tri_out, void* stream);
 VAFR_API int vafr_reproject_lp(vafr_session* session, const void* left_lp, const float* left_depth,
                                void* right_lp_out, int32_t* right_tri_out, void* stream);
 VAFR_API int vafr_rep_hole_count(vafr_session* session, int64_t* holes, void* stream);

@@ -81,6 +81,7 @@ def lib():
         L.or_fxaa_lp.argtypes = [P, P, ctypes.c_int, P, ctypes.c_int, P]
         L.or_shade_points.argtypes = [P, P, P, P, P, P, i64, ctypes.c_int, P, P, P]
         L.or_reproject_lp.argtypes = [P, ctypes.c_double, P, P, P, ctypes.c_int, i64, P, P, P, P, P, P]
+        L.or_rep_probe.argtypes = [P, ctypes.c_double, P, P, P, ctypes.c_int, i64, P, P, P, i64, P, P, P]
         L.or_path_trace.argtypes = [P, P, P, P, P, P, i64, ctypes.c_uint64, ctypes.c_int, P, P, P]
         L.or_pt_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int]
         L.or_pt_uniform.restype = ctypes.c_double
@@ -452,6 +453,26 @@ def reproject_lp(layout: Layout, width, height, fov_v_deg, gaze_left, pose_left,
                           _p(layout.off_col), layout.n_cols, layout.total, ctypes.byref(vl),
                           ctypes.byref(vr), _p(lt), _p(lc), _p(out), _p(tri))
     return out, tri
+
+
+REP_PROBE_FIELDS = ("exists", "in_front", "front_margin", "n_inf", "depth_ratio", "u_span",
+                    "f_span_raw", "f_span", "cover_margin", "depth")
+
+
+def rep_probe(layout: Layout, width, height, fov_v_deg, gaze_left, pose_left, gaze_right, pose_right,
+              left_t, tids, texels, acuity: Optional[Acuity] = None, e_max: float = PAPER_E_MAX):
+    """For warped triangle tids[q] at right texel texels[q]: the quantities the
+    warp's raster decides on (REP_PROBE_FIELDS), as a dict of arrays."""
+    a = acuity or Acuity()
+    vl = _view(width, height, fov_v_deg, gaze_left, pose_left)
+    vr = _view(width, height, fov_v_deg, gaze_right, pose_right)
+    t = _c(tids, np.int32)
+    k = _c(texels, np.int64)
+    out = np.empty((t.size, 10))
+    lib().or_rep_probe(a.ptr, float(e_max), _p(_c(layout.e_col, np.float64)), _p(layout.n_col),
+                       _p(layout.off_col), layout.n_cols, layout.total, ctypes.byref(vl), ctypes.byref(vr),
+                       _p(_c(left_t, np.float64)), t.size, _p(t), _p(k), _p(out))
+    return {name: out[:, i] for i, name in enumerate(REP_PROBE_FIELDS)}
 
 
 def render_lp_rep(scene_tris, albedo, light_dir, layout, width, height, fov_v_deg, gazes, poses,

@@ -1297,6 +1297,108 @@ static void rep_raster(const or_rvert* V, const int64_t tv[3], int32_t tid, cons
     }
 }
 
+/* Test support for the warp's parity check: for query q, warped triangle
+ * q_tid[q] (numbered as right_tri) and right texel q_tex[q] (column order),
+ * out[10 q + ...] = the quantities the raster decides on, so that a test can
+ * tell a decision taken within rounding of its threshold from a genuine
+ * difference:
+ *   0 exists (1/0)      1 all vertices in front of the right eye (1/0)
+ *   2 smallest camera depth of the vertices over their distance (> 0 in front)
+ *   3 vertices at infinity (0..3)   4 zhi / zlo (finite vertices, else 0)
+ *   5 U span            6 F span before unwrapping   7 F span after
+ *   8 coverage margin of the texel centre: its signed distance to the
+ *     triangle (> 0 inside) in the plane of (U in columns, F in rows of the
+ *     texel's column), the smaller distance to an edge line
+ *   9 interpolated depth at the texel centre (inf if not computable). */
+void or_rep_probe(const or_acuity* a, double e_max, const double* e_col, const int32_t* n_col,
+                  const int64_t* off_col, int C, int64_t n_tex, const or_view* vl, const or_view* vr,
+                  const double* left_t, int64_t n_q, const int32_t* q_tid, const int64_t* q_tex,
+                  double* out) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < n_q; ++q) {
+        double* o = out + 10 * q;
+        for (int i = 0; i < 10; ++i) o[i] = 0.0;
+        o[9] = INFINITY;
+        const int32_t tid = q_tid[q];
+        if (tid < 0 || (int64_t)tid / 2 >= n_tex) continue;
+        const int64_t ia = tid / 2;
+        const int s = tid % 2;
+        int c = 0;
+        { int lo = 0, hi = C - 1; while (lo < hi) { int mid = (lo + hi + 1) / 2; if (off_col[mid] <= ia) lo = mid; else hi = mid - 1; } c = lo; }
+        int64_t tv[3];
+        if (!rep_triangle(n_col, off_col, C, c, ia - off_col[c], s, tv)) continue;
+        o[0] = 1.0;
+        or_rvert V[3];
+        double zmin = INFINITY;
+        for (int v = 0; v < 3; ++v) {
+            int cv = 0;
+            { int lo = 0, hi = C - 1; while (lo < hi) { int mid = (lo + hi + 1) / 2; if (off_col[mid] <= tv[v]) lo = mid; else hi = mid - 1; } cv = lo; }
+            rep_vertex(a, e_max, vl, vr, e_col[cv], n_col[cv], tv[v] - off_col[cv], left_t[tv[v]], &V[v]);
+            /* camera depth of the vertex in the right eye over its distance */
+            double x, y, oo[3], d[3], P[3], pc2 = 0.0, len = 0.0;
+            texel_screen_point(vl, e_col[cv], n_col[cv], tv[v] - off_col[cv], &x, &y);
+            view_ray(vl, x, y, oo, d);
+            const int inf = !(left_t[tv[v]] < INFINITY);
+            for (int k = 0; k < 3; ++k) P[k] = inf ? d[k] : oo[k] + left_t[tv[v]] * d[k] - vr->pose[4 * k + 3];
+            for (int k = 0; k < 3; ++k) { pc2 += vr->pose[8 + k] * P[k]; len += P[k] * P[k]; }
+            const double r = pc2 / sqrt(len);
+            if (r < zmin) zmin = r;
+        }
+        o[1] = (V[0].ok && V[1].ok && V[2].ok) ? 1.0 : 0.0;
+        o[2] = zmin;
+        const int ninf = V[0].inf + V[1].inf + V[2].inf;
+        o[3] = ninf;
+        if (!o[1]) continue;
+        if (ninf == 0) {
+            double zlo = fmin(V[0].z, fmin(V[1].z, V[2].z)), zhi = fmax(V[0].z, fmax(V[1].z, V[2].z));
+            o[4] = zhi / zlo;
+        }
+        double ulo = fmin(V[0].U, fmin(V[1].U, V[2].U)), uhi = fmax(V[0].U, fmax(V[1].U, V[2].U));
+        o[5] = uhi - ulo;
+        double F3[3] = {V[0].F, V[1].F, V[2].F};
+        double flo = fmin(F3[0], fmin(F3[1], F3[2])), fhi = fmax(F3[0], fmax(F3[1], F3[2]));
+        o[6] = fhi - flo;
+        if (fhi - flo > 0.5) {
+            for (int k = 0; k < 3; ++k) if (F3[k] < 0.5) F3[k] += 1.0;
+            flo = fmin(F3[0], fmin(F3[1], F3[2]));
+            fhi = fmax(F3[0], fmax(F3[1], F3[2]));
+        }
+        o[7] = fhi - flo;
+        /* the texel's column and row */
+        const int64_t k = q_tex[q];
+        int cr = 0;
+        { int lo = 0, hi = C - 1; while (lo < hi) { int mid = (lo + hi + 1) / 2; if (off_col[mid] <= k) lo = mid; else hi = mid - 1; } cr = lo; }
+        const int64_t n = n_col[cr], jj = k - off_col[cr];
+        /* signed distance of the centre (cr, f n) to the triangle (U, F n): the
+         * smaller distance to an edge line, > 0 inside; the unwrapped triangle
+         * is drawn at F and F - 1, so the centre is also tried at f + 1 */
+        const double fc = ((double)jj + 0.5) / (double)n;
+        const double area = (V[1].U - V[0].U) * (F3[2] - F3[0]) - (V[2].U - V[0].U) * (F3[1] - F3[0]);
+        const double orient = area >= 0.0 ? 1.0 : -1.0;
+        double best = -INFINITY;
+        for (int cp = 0; cp < 2; ++cp) {
+            const double px = (double)cr, py = (fc + cp) * (double)n;
+            double m = INFINITY;
+            for (int e = 0; e < 3; ++e) {
+                const int p0 = e, p1 = (e + 1) % 3;
+                const double ex = V[p1].U - V[p0].U, ey = (F3[p1] - F3[p0]) * (double)n;
+                const double len = sqrt(ex * ex + ey * ey);
+                const double dist = len > 0.0 ? orient * (ex * (py - F3[p0] * (double)n) - ey * (px - V[p0].U)) / len
+                                              : -INFINITY;
+                if (dist < m) m = dist;
+            }
+            if (m > best) best = m;
+        }
+        o[8] = best;
+        const or_rvert* vp[3] = {&V[0], &V[1], &V[2]};
+        double w[3];
+        const double f = fc;
+        if (!rep_bary(vp, F3, (double)cr, f, w) || w[0] < -0.25 || w[1] < -0.25 || w[2] < -0.25)
+            if (!rep_bary(vp, F3, (double)cr, f + 1.0, w)) continue;
+        o[9] = w[0] * V[0].z + w[1] * V[1].z + w[2] * V[2].z;
+    }
+}
+
 void or_reproject_lp(const or_acuity* a, double e_max, const double* e_col, const int32_t* n_col,
                      const int64_t* off_col, int C, int64_t n_tex, const or_view* vl, const or_view* vr,
                      const double* left_t, const double* left_rgba, double* right_rgba,

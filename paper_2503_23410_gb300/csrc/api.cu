@@ -549,6 +549,26 @@ int vafr_scene_export_lbvh(const vafr_scene* scene, uint32_t* codes, int32_t* so
     return VAFR_OK;
 }
 
+int vafr_scene_export_tree4(const vafr_scene* scene, int64_t* n_nodes, float* nodes, float* leaves) {
+    if (!scene || !n_nodes) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
+    const int64_t n = scene->n;
+    CUDA_TRY(cudaDeviceSynchronize());
+    int64_t n4 = 0;
+    if (n > 1) {   // one 4-wide node per head: the last head index plus the last flag
+        const LbvhBuffers& b = scene->buf;
+        unsigned last[2] = {0u, 0u};
+        CUDA_TRY(cudaMemcpy(&last[0], b.head_idx + (n - 2), sizeof(unsigned), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(&last[1], b.head_flag + (n - 2), sizeof(unsigned), cudaMemcpyDeviceToHost));
+        n4 = (int64_t)last[0] + last[1];
+    }
+    *n_nodes = n4;
+    if (nodes && n4 > 0)
+        CUDA_TRY(cudaMemcpy(nodes, scene->buf.nodes4, 128ull * (size_t)n4, cudaMemcpyDeviceToHost));
+    if (leaves && n > 0)
+        CUDA_TRY(cudaMemcpy(leaves, scene->buf.leaves, 48ull * (size_t)n, cudaMemcpyDeviceToHost));
+    return VAFR_OK;
+}
+
 int vafr_scene_check(const vafr_scene* scene, void* stream) {
     if (!scene) return fail(VAFR_ERR_INVALID_ARG, "scene is NULL");
     CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
@@ -799,7 +819,8 @@ int vafr_reproject_lp(vafr_session* s, const void* left_lp, const float* left_de
     return VAFR_OK;
 }
 
-int vafr_render_lp_rep(const vafr_scene* scene, vafr_session* s, void* lp_out, void* stream) {
+int vafr_render_lp_rep(const vafr_scene* scene, vafr_session* s, void* lp_out, int32_t* right_tri_out,
+                       void* stream) {
     if (!scene || !s || !lp_out) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
     if (!aligned(lp_out, 16)) return fail(VAFR_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
     if (int rc = rep_check(s)) return rc;
@@ -822,7 +843,7 @@ int vafr_render_lp_rep(const vafr_scene* scene, vafr_session* s, void* lp_out, v
     w.d[1] = s->fd[1];
     w.d[1].lp = right;
     w.n = 2;
-    RepScratch r{s->d_rep_vert, s->d_rep_zbuf, s->d_rep_holes, s->d_rep_count, nullptr};
+    RepScratch r{s->d_rep_vert, s->d_rep_zbuf, s->d_rep_holes, s->d_rep_count, right_tri_out};
     CUDA_TRY(launch_reproject(w, r, st, s->sms));
     // 3. cast the right eye's holes
     SmallBatch h{};

@@ -80,6 +80,7 @@ _PROTOS = {
     "vafr_scene_check": (ctypes.c_int, [_P, _P]),
     "vafr_scene_inject_fault": (ctypes.c_int, [_P, ctypes.c_int32]),
     "vafr_debug_fail_host_alloc": (ctypes.c_int, [ctypes.c_int32]),
+    "vafr_scene_export_tree4": (ctypes.c_int, [_P, _P, _P, _P]),
     "vafr_session_create": (ctypes.c_int, [_P, _P]),
     "vafr_session_destroy": (ctypes.c_int, [_P]),
     "vafr_lp_layout": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -92,7 +93,7 @@ _PROTOS = {
     "vafr_fxaa_lp": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     "vafr_render_lp_pt": (ctypes.c_int, [_P, _P, _I32, _P, ctypes.c_uint64, _I32, _P, _P]),
     "vafr_render_full_gt_pt": (ctypes.c_int, [_P, _P, _I32, _P, ctypes.c_uint64, _I32, _P]),
-    "vafr_render_lp_rep": (ctypes.c_int, [_P, _P, _P, _P]),
+    "vafr_render_lp_rep": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "vafr_scene_set_point_lights": (ctypes.c_int, [_P, _I32, _P, _P]),
     "vafr_render_vbuffer": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
     "vafr_vbuffer_stats": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P]),
@@ -266,6 +267,17 @@ def vafr_scene_export_lbvh(scene: int):
     return codes, ids, child[:ni], nb[:ni], lb[:n]
 
 
+def vafr_scene_export_tree4(scene: int):
+    """(nodes (n_nodes, 32) float32, leaves (n_tris, 12) float32) of the traversal tree."""
+    n, _ = vafr_scene_info(scene)
+    cnt = ctypes.c_int64()
+    _check(load().vafr_scene_export_tree4(scene, ctypes.byref(cnt), None, None))
+    nodes = np.zeros((max(cnt.value, 1), 32), np.float32)
+    leaves = np.zeros((max(n, 1), 12), np.float32)
+    _check(load().vafr_scene_export_tree4(scene, ctypes.byref(cnt), ptr(nodes), ptr(leaves)))
+    return nodes[:cnt.value], leaves[:n]
+
+
 def vafr_scene_check(scene: int, stream=None) -> int:
     return int(load().vafr_scene_check(scene, stream_ptr(stream)))
 
@@ -398,8 +410,8 @@ def vafr_shade_full_deferred(scene: int, session: int, eye: int, vbuf, display_o
                                            stream_ptr(stream)))
 
 
-def vafr_render_lp_rep(scene: int, session: int, lp_out, stream=None) -> None:
-    _check(load().vafr_render_lp_rep(scene, session, ptr(lp_out), stream_ptr(stream)))
+def vafr_render_lp_rep(scene: int, session: int, lp_out, right_tri_out=None, stream=None) -> None:
+    _check(load().vafr_render_lp_rep(scene, session, ptr(lp_out), ptr(right_tri_out), stream_ptr(stream)))
 
 
 def vafr_reproject_lp(session: int, left_lp, left_depth, right_lp_out, right_tri_out=None,

@@ -5,7 +5,8 @@ A mismatch between the GPU's hit triangle (FP32 ray, FP32 watertight test) and
 the oracle's (FP64 ray, FP64 test) is a tie when the FP64 ray passes within
 ``rel`` x (distance along the ray) of an edge of the oracle's triangle, or when
 the GPU's triangle is within that distance of being hit by the FP64 ray and
-its plane lies no farther than the oracle's hit (relative 1e-5).  Anything
+its plane lies no farther than the oracle's hit (relative ``rel``); ``rel``
+defaults to TIE_REL, a bound on the FP32 rounding of the GPU's ray and test.  Anything
 else is a genuine error.  A colour comparison skips rays that graze their
 triangle (|n.d| < 1e-5), where the face-forward flip is ambiguous.
 
@@ -73,7 +74,19 @@ def _plane_t(tri, o, d):
     return float(n @ (v0 - o)) / den
 
 
-def classify(tris, o, d, gpu_ids, ora_ids, ora_t, rel=1e-5):
+# Width of the tie window, relative to the distance along the ray t |d|.  The
+# GPU ray differs from the oracle's FP64 ray by the FP32 roundings of its
+# generation (tan e_c and the angle (2j+1)/n_c rounded to FP32, sincospi, two
+# FMAs into the camera direction, the FP32 camera rotation: at most ~25 units
+# of 2^-24 of |d| when every rounding adds up), and the FP32 watertight test
+# moves an edge by up to ~12 units of 2^-24 of the vertex distance (the
+# subtraction from the origin, the shear, the edge-function products).  The
+# window takes 64 units of 2^-24 (3.8e-6), above that sum; the widest tie
+# measured over the whole GPU suite is 8.5 units (5.0e-7).
+TIE_REL = 64.0 * 2.0 ** -24
+
+
+def classify(tris, o, d, gpu_ids, ora_ids, ora_t, rel=TIE_REL):
     """Returns (n_ties, n_errors, error_indices) over the mismatching rays."""
     mism = np.flatnonzero(gpu_ids != ora_ids)
     ties, errs = 0, []

@@ -5,8 +5,9 @@ autotuner: every result equals the single-session path bitwise."""
 import numpy as np
 import pytest
 
-from parity import device_scene
-from workloads import random_triangles_scene
+import oracle
+from parity import classify, device_scene, lp_slots
+from workloads import random_triangles_scene, workload
 from workloads.views import eye_pair_poses, look_at_pose
 
 pytestmark = pytest.mark.gpu
@@ -315,6 +316,81 @@ def test_host_allocation_failures_leave_the_batch_usable(V, torch_mod):
     V.vafr_batch_capture(bt, frames(big))        # without a fault: works
     V.vafr_batch_replay(bt)
     torch.cuda.synchronize()
+    V.vafr_batch_destroy(bt)
+    for s in made:
+        V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)
+
+
+def test_uneven_batch_against_the_oracle(V, torch_mod):
+    """One batched render launch and one reconstruct launch over displays of
+    five sizes (the resolution sweep: 1080p, 1440p, 4K, 8K and 16K per eye,
+    binocular, FP16 LP and display, the 1.07 M-triangle terrain scene)
+    compared with the FP64 oracle: every LP texel's colour (hit ids from the
+    same session's plain render, bitwise equal to the batch's, for the tie
+    classification) and 65,536 sampled display pixels per frame-eye against
+    the oracle's reconstruction of its own LP buffer, excluding pixels whose
+    filter footprint holds a tie texel."""
+    torch = torch_mod
+    w = workload("sweep", frames=2)
+    sc = w.scene
+    h, keep = device_scene(V, sc, torch)
+    frames, meta, made = [], [], []
+    for d in w.displays:
+        s = V.vafr_session_create(V.make_session_desc(d.width, d.height, d.fov_v_deg, d.poses,
+                                                      V.FMT_RGBA16F, V.FMT_RGBA16F))
+        made.append(s)
+        for e in range(2):
+            V.vafr_set_gaze(s, e, *d.gaze[1, e])
+        lpb, dpb = V.vafr_session_sizes(s)
+        lp = torch.empty(2 * lpb, dtype=torch.uint8, device="cuda")
+        dp = torch.empty(2 * dpb, dtype=torch.uint8, device="cuda")
+        for e in range(2):
+            frames.append((s, e, lp[e * lpb:], dp[e * dpb:]))
+            meta.append((d, s, e, lp[e * lpb:(e + 1) * lpb], dp[e * dpb:(e + 1) * dpb]))
+    bt = V.vafr_batch_create(h, len(frames))
+    l0 = V.vafr_kernel_launch_count()
+    V.vafr_batch_render(bt, frames)
+    assert V.vafr_kernel_launch_count() - l0 == 2          # one render + one reconstruct launch
+    torch.cuda.synchronize()
+    lay = oracle.lp_layout()
+    bvh = oracle.CpuBVH(sc.tris)
+    rng = np.random.default_rng(44)
+    tol_lp = 1e-3 + 2.0 ** -11                  # FP32 shading, FP16 storage
+    tol_px = 1e-3 + 2.0 * 2.0 ** -11            # + the FP16 display
+    for d, s, e, lp, dp in meta:
+        slot, n_slots, counts, offs = lp_slots(V, s)
+        got_lp = lp.view(torch.float16).view(-1, 4).float().cpu().numpy()[slot]
+        # hit ids of the same texels from the session's plain render
+        plp = torch.empty(2 * n_slots * 8, dtype=torch.uint8, device="cuda")
+        ids = torch.empty(2 * n_slots, dtype=torch.int32, device="cuda")
+        V.vafr_render_lp(h, s, 3, plp, ids)
+        torch.cuda.synchronize()
+        plain = plp.view(torch.float16).view(2, n_slots, 4).float().cpu().numpy()[e][slot]
+        assert np.array_equal(plain, got_lp)
+        gid = ids.cpu().numpy().reshape(2, n_slots)[e][slot]
+        gaze = d.gaze[1, e]
+        rgba, oid, ot, o, dd = oracle.render_lp(sc.tris, sc.albedo, sc.light_dir, lay, d.width, d.height,
+                                                d.fov_v_deg, gaze, d.poses[e], bvh=bvh)
+        ties, n_err, bad = classify(sc.tris, o, dd, gid, oid, ot)
+        assert n_err == 0, f"{d.width}x{d.height} eye {e}: non-tie hit differences at {bad[:8]}"
+        assert ties <= 1e-4 * lay.total
+        same = gid == oid
+        graze = oracle.grazing(sc.tris, dd, oid) < 1e-5
+        assert np.abs(got_lp[same & ~graze] - rgba[same & ~graze]).max() <= tol_lp
+        # display: sampled pixels against the oracle's reconstruction of its own
+        # LP buffer stored in FP16, where no footprint texel is a tie
+        pix = np.sort(rng.choice(d.width * d.height, 65536, replace=False))
+        ref = oracle.reconstruct(rgba.astype(np.float16).astype(np.float64), lay, d.width, d.height,
+                                 d.fov_v_deg, gaze, pix)
+        off = (~same | graze).astype(np.float64)[:, None]
+        touch = oracle.reconstruct(off, lay, d.width, d.height, d.fov_v_deg, gaze, pix)[:, 0] > 0
+        got_px = dp.view(torch.float16).view(-1, 4)[torch.from_numpy(pix).cuda()].float().cpu().numpy()
+        assert touch.mean() < 0.01
+        err = np.abs(got_px[~touch] - ref[~touch]).max()
+        print(f"batch {d.width}x{d.height} eye {e}: ties {ties}, display err {err:.2e}, "
+              f"excluded {touch.mean():.4f}")
+        assert err <= tol_px
     V.vafr_batch_destroy(bt)
     for s in made:
         V.vafr_session_destroy(s)

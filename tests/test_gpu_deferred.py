@@ -70,6 +70,73 @@ def test_vbuffer_is_the_gt_cast(V, torch_mod, name):
     V.vafr_scene_destroy(h)
 
 
+def test_lp_lighting_against_the_oracle(V, torch_mod):
+    """The LP lighting pass (Sec. 3.4 / Sec. 5: lighting at LP resolution from
+    the display-resolution G-buffer) against the FP64 oracle: each texel takes
+    the shading of the pixel under its screen point, so on a 65,536-texel
+    sample the GPU texel must equal the oracle's GT shading of the floor pixel
+    of the oracle's screen point -- hit ids exactly except ray-edge ties,
+    colours within the FP32 tolerance.  Texels within 1e-2 px of a pixel
+    boundary (where the GPU's FP32 screen point may floor to the neighbour)
+    must match the oracle at one of the two pixels."""
+    w = workload("terrain4k", frames=4)
+    d, sc = w.displays[0], w.scene
+    h, keep = device_scene(V, sc, torch_mod)
+    pos, rgb = _lights(sc, 31, 9)
+    V.vafr_scene_set_point_lights(h, pos, rgb)
+    s = V.vafr_session_create(V.make_session_desc(d.width, d.height, d.fov_v_deg, d.poses))
+    gaze = d.gaze[2, 0]
+    V.vafr_set_gaze(s, 0, *gaze)
+    W, H = d.width, d.height
+    vb = torch_mod.empty((H, W), dtype=torch_mod.int64, device="cuda")
+    V.vafr_render_vbuffer(h, s, 0, vb)
+    slot, n_slots, _, _ = lp_slots(V, s)
+    lp = torch_mod.empty((n_slots, 4), device="cuda")
+    V.vafr_shade_lp_deferred(h, s, 0, vb, lp)
+    torch_mod.cuda.synchronize()
+    assert V.vafr_session_check(s) == 0 and V.vafr_scene_check(h) == 0
+    key = vb.cpu().numpy().reshape(-1).view(np.uint64)
+    vid = np.where(key == np.uint64(2 ** 64 - 1), -1, (key & np.uint64(0xffffffff)).astype(np.int64))
+    lay = oracle.lp_layout()
+    rng = np.random.default_rng(21)
+    tex = np.sort(rng.choice(lay.total, 65536, replace=False))
+    _, _, xy = oracle.lp_rays(lay, W, H, d.fov_v_deg, gaze, d.poses[0], texels=tex)
+    # texels whose screen point lies on the display (the pass clamps the rest
+    # to the border pixel, which the same comparison covers)
+    fx, fy = np.floor(xy[:, 0]), np.floor(xy[:, 1])
+    px = np.clip(fx, 0, W - 1).astype(np.int64)
+    py = np.clip(fy, 0, H - 1).astype(np.int64)
+    got = lp.cpu().numpy()[slot][tex]
+    eps = 1e-2
+    rx, ry = xy[:, 0] - fx, xy[:, 1] - fy
+    inside = (xy[:, 0] >= eps) & (xy[:, 0] < W - eps) & (xy[:, 1] >= eps) & (xy[:, 1] < H - eps)
+    near = inside & ((rx < eps) | (rx > 1 - eps) | (ry < eps) | (ry > 1 - eps))
+    far = ~near
+    bvh = oracle.CpuBVH(sc.tris)
+    pix = py * W + px
+    orgba, oid, ot, o, dd = oracle.render_gt(sc.tris, sc.albedo, sc.light_dir, W, H, d.fov_v_deg,
+                                             d.poses[0], pixels=pix[far], bvh=bvh, point_lights=(pos, rgb))
+    tol = 1e-3 * max(1.0, float(np.abs(orgba).max()))
+    summ = compare_hits_and_colours(sc.tris, o, dd, vid[pix[far]], got[far], oid, ot, orgba, tol)
+    print("deferred LP lighting vs oracle", summ, "boundary texels", int(near.sum()))
+    # boundary texels: the oracle at the floor pixel or its neighbour across
+    # the nearer boundary, hit and colour
+    k = np.flatnonzero(near)
+    sx = np.where(rx[k] < 0.5, -1, 1) * ((rx[k] < eps) | (rx[k] > 1 - eps))
+    sy = np.where(ry[k] < 0.5, -1, 1) * ((ry[k] < eps) | (ry[k] > 1 - eps))
+    cands = [pix[k], py[k] * W + np.clip(px[k] + sx, 0, W - 1), np.clip(py[k] + sy, 0, H - 1) * W + px[k],
+             np.clip(py[k] + sy, 0, H - 1) * W + np.clip(px[k] + sx, 0, W - 1)]
+    ok = np.zeros(k.size, bool)
+    for c in cands:
+        crgba, cid, _, _, _ = oracle.render_gt(sc.tris, sc.albedo, sc.light_dir, W, H, d.fov_v_deg,
+                                               d.poses[0], pixels=c, bvh=bvh, point_lights=(pos, rgb))
+        ok |= (vid[c] == cid) & (np.abs(got[k] - crgba).max(1) <= tol)
+    # what is left are ray-edge ties at those pixels, inside the same budget
+    assert (~ok).sum() <= 1e-4 * tex.size + summ["ties"], (int((~ok).sum()), summ)
+    V.vafr_session_destroy(s)
+    V.vafr_scene_destroy(h)
+
+
 def test_point_lights_in_the_ray_cast(V, torch_mod):
     w = workload("random1k")
     d, sc = w.displays[0], w.scene

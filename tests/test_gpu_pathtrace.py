@@ -47,12 +47,18 @@ def _compare(sc, lay, got_rgba, got_sig, ref_rgba, ref_sig, seg, tex, tol):
         ties += t_
         errs += e_
     cerr = np.abs(got_rgba[same, :3] - ref_rgba[same, :3]).max(initial=0.0)
-    summ = dict(n=n, same=float(same.mean()), hit_ties=ties, hit_errors=errs,
+    # rays the oracle traced: path segments (a hit id or -1 for a miss) and
+    # shadow rays (bits 16-23 of the last signature word)
+    segs = int((ref_sig[:, :-1] >= -1).sum())
+    shadow = int(np.unpackbits(((ref_sig[:, -1] >> 16) & 0xff).astype(np.uint8)).sum())
+    n_rays = segs + shadow
+    summ = dict(n=n, rays=n_rays, same=float(same.mean()), hit_ties=ties, hit_errors=errs,
                 shadow_only=int(shadow_only.sum()), colour_err=float(cerr))
     print("path parity", summ)
     assert errs == 0, summ
-    assert ties <= 1e-3 * n, summ
-    assert shadow_only.sum() <= 5e-4 * n, summ
+    # the ray-edge tie budget, 0.01 % of the rays cast; a shadow ray whose
+    # visibility differs counts as one of its ties
+    assert ties + shadow_only.sum() <= 1e-4 * n_rays, summ
     assert cerr <= tol, summ
     return summ
 

@@ -1,16 +1,43 @@
-"""GPU VaFR_Rep (Sec. 5.1): the warp against the FP64 oracle on identical left
-inputs (oracle-rendered), and the whole mode (left cast, warp, hole cast)
-against the oracle's and against rendering the right eye directly."""
+"""GPU VaFR_Rep (Sec. 5.1) against the FP64 oracle.
+
+The warp alone is compared with the oracle's warp on identical left inputs
+(oracle-rendered): every right texel's winning warped triangle must equal the
+oracle's or differ by a classified tie -- a decision the FP32 vertices can take
+either way because the oracle's FP64 quantities lie within the FP32 error of
+its threshold (the texel centre near a triangle edge, two covering triangles at
+depths within the interpolation error, a triangle at the edge of a rejection
+rule); colours must agree on every texel where the winners agree.
+
+The whole mode (left cast, warp, hole cast) is checked as that composition:
+its left eye is the plain LP render bit for bit, its hole texels are the plain
+right-eye render bit for bit, both compared with the oracle's casts (hit ids
+exactly except ray-edge ties), and its warped texels follow the classified
+warp comparison wherever the GPU's and the oracle's left inputs agree.
+"""
 
 import numpy as np
 import pytest
 
 import oracle
-from parity import check_guards, device_scene, lp_slots, to_device_lp
+from parity import check_guards, compare_hits_and_colours, device_scene, lp_slots, to_device_lp
 from workloads import workload
 from workloads.views import eye_pair_poses
 
 pytestmark = pytest.mark.gpu
+
+# FP32 error bounds of the GPU's warp, against which oracle decisions count as
+# ties.  A vertex's screen point carries ~1e-6 relative error from the FP32 hit
+# point and camera transform (~2e-3 px at 2,000 px from the centre); the LP
+# map multiplies that by at most ~4 texels per pixel (the fovea at 4K), so
+# (U, F n) are within ~1e-2 texels: a coverage decision within 2e-2 texels of
+# the edge is a tie.  Depths interpolated with those weights differ by up to
+# ~1e-2 of the triangle's depth range (at most 10 % of its depth): 1e-3
+# relative.  Rejection rules: within 1e-4 of their threshold (relative for
+# the depth ratio and the F spans, absolute 0.05 columns for the U span, 1e-5
+# for a vertex's camera depth over distance).
+EPS_COVER = 2e-2
+EPS_DEPTH = 1e-3
+EPS_RULE = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -30,6 +57,49 @@ def setup(V, torch_mod):
     V.vafr_scene_destroy(h)
 
 
+def _probe(st, left_t, tids, tex):
+    d = st["d"]
+    return oracle.rep_probe(st["lay"], d.width, d.height, d.fov_v_deg, st["gazes"][0], st["poses"][0],
+                            st["gazes"][1], st["poses"][1], left_t, tids, tex)
+
+
+def _near_rule(p):
+    """A rejection rule (or the F unwrap) decided within rounding of its threshold."""
+    return ((np.abs(p["front_margin"]) < 1e-5) |
+            ((p["n_inf"] == 0) & (np.abs(p["depth_ratio"] / 1.1 - 1.0) < EPS_RULE)) |
+            (np.abs(p["u_span"] - 64.0) < 0.05) |
+            (np.abs(p["f_span"] / 0.25 - 1.0) < EPS_RULE) |
+            (np.abs(p["f_span_raw"] / 0.5 - 1.0) < EPS_RULE))
+
+
+def _valid(p):
+    """Exists and passes every rejection rule (FP64)."""
+    finite_ok = (p["n_inf"] == 0) & (p["depth_ratio"] <= 1.1)
+    return ((p["exists"] == 1) & (p["in_front"] == 1) & (finite_ok | (p["n_inf"] == 3)) &
+            (p["u_span"] <= 64.0) & (p["f_span"] <= 0.25))
+
+
+def classify_warp(st, left_t, gpu_tri, ora_tri, k):
+    """(ties, errors, error texels) over the right texels k whose winners differ."""
+    g, r = gpu_tri[k], ora_tri[k]
+    pg = _probe(st, left_t, np.where(g >= 0, g, -1), k)
+    pr = _probe(st, left_t, np.where(r >= 0, r, -1), k)
+    # g could win in FP32: a valid or rule-borderline triangle covering the
+    # centre or passing within EPS_COVER of it
+    g_can_win = (g >= 0) & (_valid(pg) | _near_rule(pg)) & (pg["cover_margin"] > -EPS_COVER)
+    # r could be lost in FP32: centre near its edge or a rule borderline
+    r_can_lose = (r >= 0) & ((np.abs(pr["cover_margin"]) < EPS_COVER) | _near_rule(pr))
+    depth_tie = (pg["depth"] <= pr["depth"] * (1.0 + EPS_DEPTH))
+    tie = np.where((g >= 0) & (r >= 0), g_can_win & (depth_tie | r_can_lose),
+                   np.where(g >= 0, g_can_win, r_can_lose))
+    return int(tie.sum()), int((~tie).sum()), k[~tie]
+
+
+def _summary(label, same, ties, errs, n, extra=""):
+    print(f"{label}: {n} texels, winners differ {int((~same).sum())}, classified ties {ties}, "
+          f"errors {errs}{extra}")
+
+
 def test_warp_matches_oracle(V, torch_mod, setup):
     d, sc, lay, s = setup["d"], setup["sc"], setup["lay"], setup["s"]
     rgba, ids, t, _, _ = oracle.render_lp(sc.tris, sc.albedo, sc.light_dir, lay, d.width, d.height,
@@ -46,47 +116,109 @@ def test_warp_matches_oracle(V, torch_mod, setup):
     V.vafr_reproject_lp(s, left, depth, right, tri)
     torch_mod.cuda.synchronize()
     got, gtri = right.cpu().numpy()[slot], tri.cpu().numpy()[slot]
+    left_t = t32.astype(np.float64)
     ref, rtri = oracle.reproject_lp(lay, d.width, d.height, d.fov_v_deg, setup["gazes"][0],
                                     setup["poses"][0], setup["gazes"][1], setup["poses"][1],
-                                    t32.astype(np.float64), c32.astype(np.float64))
+                                    left_t, c32.astype(np.float64))
     assert V.vafr_rep_hole_count(s) == int((gtri < 0).sum())
     same = gtri == rtri
-    print(f"warp: same triangle {same.mean():.5f}, holes gpu {(gtri < 0).mean():.4f} oracle {(rtri < 0).mean():.4f}")
-    assert same.mean() > 0.995
-    assert abs((gtri < 0).mean() - (rtri < 0).mean()) < 1e-3
+    ties, errs, bad = classify_warp(setup, left_t, gtri, rtri, np.flatnonzero(~same))
     both = same & (gtri >= 0)
     err = np.abs(got[both] - ref[both]).max(1)
-    # FP32 (U, F) of the vertices (u table, angle polynomial) vs FP64: weight
-    # errors of ~1e-4 in thin triangles; the colour tolerance is 1e-3
+    _summary("warp", same, ties, errs, lay.total, f", colour err max {err.max():.2e} "
+             f"p99.9 {np.percentile(err, 99.9):.2e}")
+    assert errs == 0, f"unclassified winner differences at right texels {bad[:10]}"
+    assert ties <= 5e-3 * lay.total
+    # every texel where the winners agree: barycentric weights from FP32
+    # vertices against FP64 (thin triangles ~1e-4 of weight), colours in [0, 1]
     assert err.max() < 1e-3 and np.percentile(err, 99.9) < 1e-4
-    # where the winners differ both are valid warps of neighbouring triangles
-    diff = ~same & (gtri >= 0) & (rtri >= 0)
-    assert np.percentile(np.abs(got[diff] - ref[diff]).max(1), 90) < 0.05
 
 
-def test_rep_mode_matches_oracle_and_direct(V, torch_mod, setup):
-    d, sc, lay, s = setup["d"], setup["sc"], setup["lay"], setup["s"]
+def test_rep_mode_is_the_composition_and_matches_oracle(V, torch_mod, setup):
+    torch = torch_mod
+    d, sc, lay, s, h = setup["d"], setup["sc"], setup["lay"], setup["s"], setup["h"]
     slot, n_slots, counts, offs = lp_slots(V, s)
-    lp = torch_mod.empty((2 * n_slots, 4), device="cuda")
-    V.vafr_render_lp_rep(setup["h"], s, lp)
-    torch_mod.cuda.synchronize()
+    lp = torch.empty((2 * n_slots, 4), device="cuda")
+    tri = torch.full((n_slots,), -9, dtype=torch.int32, device="cuda")
+    V.vafr_render_lp_rep(h, s, lp, tri)
+    # the plain casts of both eyes, with hit ids
+    plain = torch.empty((2 * n_slots, 4), device="cuda")
+    pids = torch.empty(2 * n_slots, dtype=torch.int32, device="cuda")
+    V.vafr_render_lp(h, s, 3, plain, pids)
+    torch.cuda.synchronize()
     assert V.vafr_session_check(s) == 0
     out = lp.cpu().numpy().reshape(2, n_slots, 4)
+    pl = plain.cpu().numpy().reshape(2, n_slots, 4)
+    pid = pids.cpu().numpy().reshape(2, n_slots)
     for e in range(2):
         check_guards(out[e], counts, offs)
-    left, right = out[0][slot], out[1][slot]
-    L, R, tri = oracle.render_lp_rep(sc.tris, sc.albedo, sc.light_dir, lay, d.width, d.height,
-                                     d.fov_v_deg, setup["gazes"], setup["poses"], bvh=setup["bvh"])
-    el = np.abs(left - L).max(1)
-    er = np.abs(right - R).max(1)
-    print(f"rep mode: left within 1e-3 {np.mean(el < 1e-3):.5f}, right {np.mean(er < 1e-3):.5f}, "
-          f"holes {np.mean(tri < 0):.4f}")
-    assert np.mean(el < 1e-3) > 0.9995
-    assert np.mean(er < 1e-3) > 0.99
-    # against rendering the right eye directly (VaFR_Dup): reprojection error
-    direct, _, _, _, _ = oracle.render_lp(sc.tris, sc.albedo, sc.light_dir, lay, d.width, d.height,
-                                          d.fov_v_deg, setup["gazes"][1], setup["poses"][1],
-                                          bvh=setup["bvh"])
-    ed = np.abs(right - direct)[:, :3].max(1)
+    gtri = tri.cpu().numpy()[slot]
+    holes = gtri < 0
+    assert V.vafr_rep_hole_count(s) == int(holes.sum())
+    # composition: the left eye is the plain cast, hole texels the plain right cast
+    assert np.array_equal(out[0][slot], pl[0][slot])
+    assert np.array_equal(out[1][slot][holes], pl[1][slot][holes])
+
+    # the left cast against the oracle (ids except ties, colours)
+    L_rgba, L_ids, L_t, lo, ld = oracle.render_lp(sc.tris, sc.albedo, sc.light_dir, lay, d.width, d.height,
+                                                  d.fov_v_deg, setup["gazes"][0], setup["poses"][0],
+                                                  bvh=setup["bvh"])
+    compare_hits_and_colours(sc.tris, lo, ld, pid[0][slot], out[0][slot], L_ids, L_t, L_rgba, 1e-3)
+    # the hole texels against the oracle's cast of the right eye
+    hk = np.flatnonzero(holes)
+    R_rgba, R_ids, R_t, ro, rd = oracle.render_lp(sc.tris, sc.albedo, sc.light_dir, lay, d.width, d.height,
+                                                  d.fov_v_deg, setup["gazes"][1], setup["poses"][1],
+                                                  texels=hk, bvh=setup["bvh"])
+    # the tie budget is 0.01 % of the eye's rays, here spent on the holes alone
+    compare_hits_and_colours(sc.tris, ro, rd, pid[1][slot][hk], out[1][slot][hk], R_ids, R_t, R_rgba, 1e-3,
+                             tie_budget=1e-4 * lay.total / max(hk.size, 1))
+
+    # the warped texels against the oracle's warp of the oracle's left eye,
+    # where the warped triangle's left vertices carry the same hits on both sides
+    left_t = np.where(L_ids >= 0, L_t, np.inf)
+    ref, rtri = oracle.reproject_lp(lay, d.width, d.height, d.fov_v_deg, setup["gazes"][0],
+                                    setup["poses"][0], setup["gazes"][1], setup["poses"][1], left_t, L_rgba)
+    left_diff = pid[0][slot] != L_ids
+    # left texels of triangle tid: its own texel, the next one in the column and
+    # one in the neighbouring column -- mark a triangle affected when any of the
+    # three differs; the neighbour-column vertex is found by the oracle probe's
+    # numbering, so the test uses the conservative set: the texel, its column
+    # neighbours and every texel of the adjacent columns within one angular step
+    col = np.repeat(np.arange(lay.n_cols), lay.n_col)
+    j = np.arange(lay.total) - lay.off_col[col]
+    bad_left = np.flatnonzero(left_diff)
+    affected = np.zeros(lay.total, bool)
+    for t_ in bad_left:
+        c = col[t_]
+        for c2 in (c - 1, c, c + 1):
+            if 0 <= c2 < lay.n_cols:
+                n2 = lay.n_col[c2]
+                centre = (j[t_] + 0.5) / lay.n_col[c] * n2
+                for jj in range(int(np.floor(centre)) - 2, int(np.floor(centre)) + 3):
+                    affected[lay.off_col[c2] + (jj % n2)] = True
+
+    def touches_affected(tids):
+        v = np.zeros(tids.size, bool)
+        ok = tids >= 0
+        v[ok] = affected[tids[ok] // 2]
+        return v
+
+    warped = ~holes
+    exclude = touches_affected(gtri) | touches_affected(rtri)
+    k = np.flatnonzero(warped & ~exclude & (gtri != rtri))
+    ties, errs, bad = classify_warp(setup, left_t, gtri, rtri, k)
+    same = warped & ~exclude & (gtri == rtri)
+    err = np.abs(out[1][slot][same] - ref[same]).max(1)
+    _summary("rep mode warp", gtri[warped & ~exclude] == rtri[warped & ~exclude], ties, errs,
+             int((warped & ~exclude).sum()),
+             f", excluded (left ties nearby) {int((warped & exclude).sum())}, colour err max {err.max():.2e}")
+    assert errs == 0, f"unclassified winner differences at right texels {bad[:10]}"
+    assert ties <= 5e-3 * lay.total
+    assert (warped & exclude).sum() <= 1e-3 * lay.total
+    assert err.max() < 1e-3
+
+    # against rendering the right eye directly (VaFR_Dup): the reprojection error
+    direct = pl[1][slot]
+    ed = np.abs(out[1][slot] - direct)[:, :3].max(1)
     print(f"rep vs direct: within 0.02 {np.mean(ed < 0.02):.4f}, mean abs {ed.mean():.4f}")
     assert np.mean(ed < 0.02) > 0.9

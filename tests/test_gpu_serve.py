@@ -1,6 +1,7 @@
-"""Serving on the GPU: Poisson sessions of mixed resolutions, admitted by HBM
-budget, continuously batched; each frame rendered in the mix is bitwise the
-same as that frame rendered alone."""
+"""Serving on the GPU: Poisson sessions of mixed resolutions (1080p to 8K,
+binocular), admitted by HBM budget, continuously batched; each frame rendered
+in the mix, 8K binocular sessions included, is bitwise the same as that frame
+rendered alone."""
 
 import numpy as np
 import pytest
@@ -14,14 +15,16 @@ pytestmark = pytest.mark.gpu
 
 def test_served_mix_equals_alone(V, torch_mod):
     torch = torch_mod
-    w = workload("serving", frames=6, small_scene=True)
+    w = workload("serving", frames=6)     # the serving configuration's scene (1.07 M triangles)
     h, keep = device_scene(V, w.scene, torch)
     reqs = poisson_requests(w, seed=1, n_sessions=24, rate_hz=2000.0)
-    for r in reqs:                       # keep the test small: cap at 4K
-        if r.width > 3840:
-            r.width, r.height = 3840, 2160
-            r.gaze = np.clip(r.gaze, 0, [3840, 2160])
-    watch = {3: 2, 10: 0, 17: 5}          # session -> frame to snapshot
+    big = [i for i, r in enumerate(reqs) if r.width >= 7680 and r.eyes == 2]
+    small = [i for i, r in enumerate(reqs) if r.width < 7680]
+    assert big and len(small) >= 2, "the seeded mix holds 8K binocular and smaller sessions"
+    # session -> frame to snapshot: an 8K binocular session among them
+    watch = {big[0]: 2, small[0]: 0, small[-1]: 5}
+    if len(big) > 1:
+        watch[big[-1]] = 4
     snaps = {}
 
     def on_done(sid, frame, handle):
@@ -29,7 +32,7 @@ def test_served_mix_equals_alone(V, torch_mod):
             snaps[sid] = handle["disp"].cpu().numpy().copy()
 
     be = VafrBackend(h, n_slots=2)
-    budget = 1 << 30
+    budget = 3 << 30                      # room for about five 8K binocular sessions at once
     st = Server(be, hbm_budget_bytes=budget, on_frame_done=on_done).run(reqs, time_limit_s=300)
     be.close_all()
     s = st.summary()

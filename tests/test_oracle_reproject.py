@@ -121,3 +121,61 @@ def test_affine_data_in_lp_coordinates_is_reproduced(layout, acuity):
     sel = (tri >= 0) & (Fc > 0.1) & (Fc < 0.9) & (col >= 4) & (col < layout.n_cols - 8)
     assert sel.sum() > 0.7 * layout.total
     np.testing.assert_allclose(right[sel, :3], want[sel], atol=1e-9)
+
+
+def _probe_setup(layout, seed=1, k=120):
+    """Identical eyes, hit distances putting every vertex 5 units from the eye,
+    and random interior left texels with their first triangle's own texel."""
+    gaze = (600.5, 300.25)
+    _, d, _ = oracle.lp_rays(layout, W, H, FOV, gaze, HEAD)
+    dn = np.linalg.norm(d, axis=1)
+    t = 5.0 / dn
+    col = np.repeat(np.arange(layout.n_cols), layout.n_col)
+    cand = np.flatnonzero((col > 2) & (col < layout.n_cols - 3))
+    rng = np.random.default_rng(seed)
+    tex = rng.choice(cand, k, replace=False)
+    s = rng.integers(0, 2, tex.size)
+    return gaze, t, dn, tex, 2 * tex + s, col
+
+
+def test_rep_probe_identity_view_closed_forms(layout):
+    """With identical eyes a left texel's vertex lands on its own right texel
+    centre (U = c, F = (j + 1/2)/n_c).  Every vertex 5 units away: depth ratio
+    1, depth 5 at the texel; the triangle joins columns c and c +- 1 (U span
+    1); the texel centre is a vertex, so it lies on the boundary (margin 0)."""
+    gaze, t, dn, tex, tid, col = _probe_setup(layout)
+    p = oracle.rep_probe(layout, W, H, FOV, gaze, HEAD, gaze, HEAD, t, tid, tex)
+    assert np.all(p["exists"] == 1) and np.all(p["in_front"] == 1) and np.all(p["n_inf"] == 0)
+    assert np.all(p["front_margin"] > 0)
+    np.testing.assert_allclose(p["depth_ratio"], 1.0, atol=1e-12)
+    np.testing.assert_allclose(p["u_span"], 1.0, atol=1e-8)
+    np.testing.assert_allclose(p["depth"], 5.0, atol=1e-9)
+    np.testing.assert_allclose(p["cover_margin"], 0.0, atol=1e-6)
+    assert np.all(p["f_span"] <= 0.25)
+    # a texel eight columns away is outside the triangle's U range
+    far = layout.off_col[np.minimum(col[tex] + 8, layout.n_cols - 1)]
+    q = oracle.rep_probe(layout, W, H, FOV, gaze, HEAD, gaze, HEAD, t, tid, far)
+    assert np.all(q["cover_margin"] < -1.0)
+
+
+def test_rep_probe_depths_misses_and_eyes_behind(layout):
+    gaze, t, dn, tex, tid, col = _probe_setup(layout, seed=2, k=12)
+    for k in range(tex.size):
+        tt = t.copy()
+        tt[tex[k]] = 6.0 / dn[tex[k]]          # the queried texel's own vertex at 6
+        p = oracle.rep_probe(layout, W, H, FOV, gaze, HEAD, gaze, HEAD, tt, tid[k:k + 1], tex[k:k + 1])
+        assert abs(p["depth_ratio"][0] - 1.2) < 1e-12     # 6 / 5
+        assert abs(p["depth"][0] - 6.0) < 1e-9           # the texel centre is that vertex
+        tt[tex[k]] = np.inf                       # a miss: a point at infinity
+        p = oracle.rep_probe(layout, W, H, FOV, gaze, HEAD, gaze, HEAD, tt, tid[k:k + 1], tex[k:k + 1])
+        assert p["n_inf"][0] == 1 and p["depth_ratio"][0] == 0.0
+    # a right eye turned around sees every vertex behind it
+    back = HEAD.copy()
+    back[:, 0] *= -1.0
+    back[:, 2] *= -1.0
+    p = oracle.rep_probe(layout, W, H, FOV, gaze, HEAD, gaze, back, t, tid, tex)
+    assert np.all(p["in_front"] == 0) and np.all(p["front_margin"] < 0)
+    # ids that name no triangle
+    p = oracle.rep_probe(layout, W, H, FOV, gaze, HEAD, gaze, HEAD, t, np.array([-1, 2 * layout.total]),
+                         np.array([0, 0]))
+    assert np.all(p["exists"] == 0)
