@@ -257,9 +257,19 @@ __device__ __forceinline__ void sort2(float& ta, int& ra, float& tb, int& rb) {
     ra = q;
 }
 
-// Closest hit through the 4-wide tree: test the four child boxes, test leaf
-// children at once, then continue with the nearest internal child and push the
-// others far-to-near.  Returns a fault bit (0 = fine).
+// A traversal stack entry: the child reference in the low word, its entry
+// distance in the high word (one 64-bit store and load per push and pop).
+__device__ __forceinline__ unsigned long long stack_entry(int ref, float t) {
+    return ((unsigned long long)__float_as_uint(t) << 32) | (unsigned)ref;
+}
+
+// Closest hit through the 4-wide tree: test the four child boxes, test the
+// leaf children that were hit, then continue with the nearest internal child
+// and push the others far-to-near.  The hit leaf children of a node form a bit
+// mask that one loop consumes, so a warp runs as many triangle tests per node
+// as its busiest lane needs (not one pass per child slot that any lane needs);
+// the closest-hit rule (t, then id) makes the result independent of the order.
+// Returns a fault bit (0 = fine).
 template <bool STATS, int ORDER, bool ANY = false, bool SKIP = false>
 __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
                               unsigned long long* node_visits, unsigned long long* box_tests,
@@ -272,8 +282,7 @@ __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
         test_leaf<STATS, SKIP>(sc, r, 0, h, tri_tests);
         return 0u;
     }
-    int stack[kStackSize];
-    float stack_t[kStackSize];
+    unsigned long long stack[kStackSize];
     int sp = 0;
     int node = 0;
     const int n_inner = sc.n_tris - 1;
@@ -290,26 +299,37 @@ __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
             ++*node_visits;
             *box_tests += (c0 != kEmptyRef) + (c1 != kEmptyRef) + (c2 != kEmptyRef) + (c3 != kEmptyRef);
         }
-#define VAFR_LEAF(T, C)                                                                   \
+        // hit children that are leaves (bit q for child q) leave the box list;
+        // unused slots (kEmptyRef, a zero box) leave it without a test
+        unsigned lm = 0u;
+#define VAFR_LEAF_BIT(T, C, Q)                                                            \
         if (T < INFINITY && C < 0) {                                                      \
-            if (C != kEmptyRef) {                                                         \
-                if ((unsigned)~C >= (unsigned)sc.n_tris) return kFaultBadNode;            \
-                test_leaf<STATS, SKIP>(sc, r, ~C, h, tri_tests);                          \
-            }                                                                             \
+            if (C != kEmptyRef) lm |= 1u << Q;                                            \
             T = INFINITY;                                                                 \
         }
-        VAFR_LEAF(t.x, c0)
-        VAFR_LEAF(t.y, c1)
-        VAFR_LEAF(t.z, c2)
-        VAFR_LEAF(t.w, c3)
-#undef VAFR_LEAF
+        VAFR_LEAF_BIT(t.x, c0, 0)
+        VAFR_LEAF_BIT(t.y, c1, 1)
+        VAFR_LEAF_BIT(t.z, c2, 2)
+        VAFR_LEAF_BIT(t.w, c3, 3)
+#undef VAFR_LEAF_BIT
+        const float t_entry = h.t;
+        while (lm) {
+            const int q = __ffs(lm) - 1;
+            lm &= lm - 1u;
+            const int C = q == 0 ? c0 : (q == 1 ? c1 : (q == 2 ? c2 : c3));
+            if ((unsigned)~C >= (unsigned)sc.n_tris) return kFaultBadNode;
+            test_leaf<STATS, SKIP>(sc, r, ~C, h, tri_tests);
+        }
         if (ANY && h.leaf >= 0) return 0u;   // occlusion query: any hit ends it
-        // children entering beyond an updated closest hit are dropped
-        const float lim = h.t * kFarScale;
-        if (t.x > lim) t.x = INFINITY;
-        if (t.y > lim) t.y = INFINITY;
-        if (t.z > lim) t.z = INFINITY;
-        if (t.w > lim) t.w = INFINITY;
+        // children entering beyond a closest hit found at this node are dropped
+        // (the box tests already clipped against the hit known before it)
+        if (h.t != t_entry) {
+            const float lim = h.t * kFarScale;
+            if (t.x > lim) t.x = INFINITY;
+            if (t.y > lim) t.y = INFINITY;
+            if (t.z > lim) t.z = INFINITY;
+            if (t.w > lim) t.w = INFINITY;
+        }
         if (ORDER == 0) {
             // ascending (t, ref): sorting network (0,1) (2,3) (0,2) (1,3) (1,2)
             sort2(t.x, c0, t.y, c1);
@@ -326,24 +346,27 @@ __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
         if (t.x < INFINITY) {
             if (t.w < INFINITY) {
                 if (sp >= kStackSize) return kFaultStack;
-                stack[sp] = c3; stack_t[sp] = t.w; ++sp;
+                stack[sp++] = stack_entry(c3, t.w);
             }
             if (t.z < INFINITY) {
                 if (sp >= kStackSize) return kFaultStack;
-                stack[sp] = c2; stack_t[sp] = t.z; ++sp;
+                stack[sp++] = stack_entry(c2, t.z);
             }
             if (t.y < INFINITY) {
                 if (sp >= kStackSize) return kFaultStack;
-                stack[sp] = c1; stack_t[sp] = t.y; ++sp;
+                stack[sp++] = stack_entry(c1, t.y);
             }
             node = c0;
         } else {
+            // pop, skipping entries that start beyond the current closest hit
+            const float lim2 = h.t * kFarScale;
+            unsigned long long e;
             while (true) {
                 if (sp == 0) return 0u;
-                --sp;
-                if (stack_t[sp] <= h.t * kFarScale) break;
+                e = stack[--sp];
+                if (__uint_as_float((unsigned)(e >> 32)) <= lim2) break;
             }
-            node = stack[sp];
+            node = (int)(unsigned)e;
         }
     }
 }

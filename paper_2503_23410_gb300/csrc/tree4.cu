@@ -4,7 +4,8 @@
 //
 // PLOC starts from the leaves in Morton order (the LBVH sort) and repeats:
 //   1. every cluster finds the cluster within +-radius positions whose
-//      merged box has the smallest surface area (ties: lower position);
+//      merged box has the smallest surface area (ties: the nearer position,
+//      then the partner i ^ 1, so runs of equal boxes pair up);
 //   2. mutual nearest neighbours merge into a new internal node, which takes
 //      the lower position; the other position is dropped;
 //   3. the cluster array is compacted (exclusive scans; no atomics, so the
@@ -120,17 +121,24 @@ k_ploc_nn(const float4* __restrict__ lo, const float4* __restrict__ hi, int m, i
     const int i = base + threadIdx.x;
     if (i >= m) return;
     const float4 a = slo[threadIdx.x + R], A = shi[threadIdx.x + R];
+    // Equal costs (identical boxes, e.g. duplicated geometry) go to the nearer
+    // position, then to the partner i ^ 1: a run of equal boxes then pairs up
+    // as (0,1) (2,3) ... in every round and halves, where "lower position
+    // first" would merge one pair per round and chain the tree.
+    const int pref = (i & 1) ? -1 : 1;
     float best = INFINITY;
-    int bj = -1;
+    int bj = -1, bd = 0;
     for (int d = -radius; d <= radius; ++d) {
         const int j = i + d;
         if (d == 0 || j < 0 || j >= m) continue;
         const float4 b = slo[threadIdx.x + R + d], B = shi[threadIdx.x + R + d];
         const float c = half_area(make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), 0.0f),
                                   make_float4(fmaxf(A.x, B.x), fmaxf(A.y, B.y), fmaxf(A.z, B.z), 0.0f));
-        if (c < best) {   // ascending j: ties keep the lower position
+        const int ad = d < 0 ? -d : d, abd = bd < 0 ? -bd : bd;
+        if (c < best || (c == best && (ad < abd || (ad == abd && d == pref)))) {
             best = c;
             bj = j;
+            bd = d;
         }
     }
     nbr[i] = bj;

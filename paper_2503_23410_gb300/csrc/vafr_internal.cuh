@@ -17,7 +17,7 @@ enum DeviceFault : unsigned {
     kFaultBadNode = 4u,   // child reference out of range
 };
 
-constexpr int kStackSize = 96;
+constexpr int kStackSize = 128;   // entries; a descent pushes at most 3 per 4-wide level above the last: depth <= 43
 constexpr int kEmptyRef = (int)0x80000000;   // unused slot of a 4-wide node
 constexpr int kMaxSeg = VAFR_MAX_PIVOTS - 1;
 
