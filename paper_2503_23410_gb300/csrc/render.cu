@@ -33,6 +33,10 @@ k_render_lp(const SceneDev sc, const __grid_constant__ B b) {
             Hit h;
             const unsigned fault = traverse<WIDE, false, ORDER>(sc, r, h, nullptr, nullptr, nullptr);
             if (fault) { atomicOr(f.status, fault); h.leaf = -1; h.id = -1; }
+            // shading regenerates the ray (same bits) instead of keeping its
+            // direction in registers through the traversal: with it the
+            // 64-register variants run without spills
+            lp_ray(f, (int)(w - f.work_begin), r, glo, ghi);
             store_lp(f, t, glo, ghi, shade(sc, r, h), h.leaf >= 0 ? h.id : -1);
             if (f.depth) f.depth[t] = h.leaf >= 0 ? h.t : INFINITY;
         }
@@ -311,8 +315,8 @@ cudaError_t launch_variant(const SceneDev& sc, const B& b, int variant, cudaStre
         case 1: return launch_one<256, 32, 4, 0, 1, GT>(sc, b, s, sms);
         case 2: return launch_one<128, 32, 4, 0, 1, GT>(sc, b, s, sms);
         case 3: return launch_one<128, 32, 2, 0, 1, GT>(sc, b, s, sms);
-        case 4: return launch_one<128, 32, 4, 0, 10, GT>(sc, b, s, sms);
-        default: return launch_one<128, 32, 4, 1, 10, GT>(sc, b, s, sms);
+        case 4: return launch_one<128, 32, 4, 0, 8, GT>(sc, b, s, sms);
+        default: return launch_one<128, 32, 4, 1, 8, GT>(sc, b, s, sms);
     }
 }
 }  // namespace
