@@ -308,7 +308,7 @@ template <bool GT, class B>
 cudaError_t launch_variant(const SceneDev& sc, const B& b, int variant, cudaStream_t s, int sms) {
     if (b.total_work <= 0) return cudaSuccess;
     if (variant == kLptVariant)
-        return GT ? launch_one<128, 32, 4, 1, 1, GT>(sc, b, s, sms) : launch_lpt<128, 1>(sc, b, s, sms);
+        return GT ? launch_one<128, 32, 4, 1, 1, GT>(sc, b, s, sms) : launch_lpt<128, 0>(sc, b, s, sms);
     // (threads per block, rays per warp fetch, tree width, child order, min blocks/SM)
     switch (variant) {
         case 0: return launch_one<128, 32, 4, 1, 1, GT>(sc, b, s, sms);
