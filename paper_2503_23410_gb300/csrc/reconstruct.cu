@@ -25,6 +25,8 @@
 #include "lp_map.cuh"
 #include "vafr_internal.cuh"
 
+#include <limits.h>
+
 namespace vafr {
 namespace {
 
@@ -96,6 +98,7 @@ struct ReconShared {
     int gxi, gyi;
     float gxf, gyf;
     int W, H, disp_fmt, tile_begin;
+    int n_cols;
     void* disp;
 };
 
@@ -123,6 +126,7 @@ __device__ __forceinline__ void stage_frame(const B& b, int tile, ReconShared& s
     sh.H = fd.H;
     sh.disp_fmt = fd.disp_fmt;
     sh.tile_begin = (int)fd.tile_begin;
+    sh.n_cols = fd.n_cols;
     sh.disp = fd.disp;
 }
 
@@ -218,6 +222,164 @@ k_reconstruct(const __grid_constant__ B b) {
     }
 }
 
+// ---- LP texels staged in shared memory -----------------------------------------
+// A staged tile first copies the LP texels its pixels can reach into shared
+// memory (coalesced loads of each column's row span), then filters from there.
+// The span comes from the tile's rectangle: the nearest and farthest pixel
+// centres bound the table coordinate, hence the columns (the forward map is
+// monotone in the radius); the corners bound the angle when the gaze lies
+// outside the rectangle.  Spans carry one column and one or two rows of
+// margin; a tile holding the gaze, spanning more than a quarter turn, more
+// than kStageCols columns or more texels than the buffer holds stages nothing.
+// Whatever the plan, each texel pair is read from shared memory only if its
+// slots lie inside its column's staged span, else from global memory, so the
+// texel values -- and the results -- are those of the other variants.
+constexpr int kStageCols = 64;
+constexpr int kStageBytes = 24576;    // 1,536 FP32 or 3,072 FP16 texel slots
+
+struct StagePlan {
+    int4 col[kStageCols];   // per staged column: (first slot, last slot, buffer index - slot, 0)
+    int off[kStageCols];    // buffer index of each column's first slot
+    int c_lo, n, total;     // first column, staged columns (0: none), staged slots
+};
+
+// Warp 0 plans the tile whose pixel centres span columns x0..x1, rows y0..y1.
+__device__ void stage_plan(const ReconRegs& f, const ReconShared& sh, int x0, int y0, int x1, int y1,
+                           int cap_slots, StagePlan& st) {
+    const int lane = (int)(threadIdx.x & 31);
+    // pixel-centre offsets from the gaze, computed as the pixels compute them
+    const float dxa = (float)(x0 - sh.gxi) + sh.gxf, dxb = (float)(x1 - sh.gxi) + sh.gxf;
+    const float dya = (float)(y0 - sh.gyi) + sh.gyf, dyb = (float)(y1 - sh.gyi) + sh.gyf;
+    const bool holds_gaze = dxa <= 0.0f && dxb >= 0.0f && dya <= 0.0f && dyb >= 0.0f;
+    const float nx = dxa > 0.0f ? dxa : (dxb < 0.0f ? dxb : 0.0f);
+    const float ny = dya > 0.0f ? dya : (dyb < 0.0f ? dyb : 0.0f);
+    const float fx = fmaxf(fabsf(dxa), fabsf(dxb)), fy = fmaxf(fabsf(dya), fabsf(dyb));
+    const float s0 = table_coord(f, nx, ny * ny), s1 = table_coord(f, fx, fy * fy);
+    const int p0 = (int)s0, p1 = (int)s1;
+    const float u0 = piece_eval(__ldg(f.u_tab + p0), s0 - (float)p0);
+    const float u1 = piece_eval(__ldg(f.u_tab + p1), s1 - (float)p1);
+    const int c_lo = max(__float2int_rd(u0) - 1, 0);
+    const int c_hi = min(__float2int_rd(u1) + 2, sh.n_cols - 1);
+    // the angle fractions of the corners, relative to the first, give the arc
+    const float cx[4] = {dxa, dxb, dxa, dxb}, cy[4] = {dya, dya, dyb, dyb};
+    float fr0 = 0.0f, lo = 0.0f, hi = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float fq = angle_fraction(cy[q], cx[q], fmaxf(fabsf(cx[q]), 1e-30f));
+        if (q == 0) {
+            fr0 = fq;
+        } else {
+            float d = fq - fr0;
+            d = d >= 0.5f ? d - 1.0f : (d < -0.5f ? d + 1.0f : d);
+            lo = fminf(lo, d);
+            hi = fmaxf(hi, d);
+        }
+    }
+    const bool ok = !holds_gaze && hi - lo <= 0.25f && c_hi - c_lo + 1 <= kStageCols;
+    const float flo = fr0 + lo, fhi = fr0 + hi;
+    // each lane plans columns c_lo + lane and c_lo + lane + 32
+    int cnt[2] = {0, 0};
+    int4 info[2] = {make_int4(INT_MAX, INT_MIN, 0, 0), make_int4(INT_MAX, INT_MIN, 0, 0)};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int c = c_lo + lane + 32 * h;
+        if (ok && c <= c_hi) {
+            const int4 cp = __ldg(f.col_pair + c);       // (first slot, FP32 count) of column c
+            const float nf = __int_as_float(cp.y);
+            const int n = (int)nf;
+            int jl = __float2int_rd(fmaf(flo, nf, -0.5f)) - 1;
+            int jh = __float2int_rd(fmaf(fhi, nf, -0.5f)) + 2;
+            if (jl < -1 || jh > n) {   // the arc wraps in this column: all of it, guards included
+                jl = -1;
+                jh = n;
+            }
+            info[h] = make_int4(cp.x + jl, cp.x + jh, 0, 0);
+            cnt[h] = jh - jl + 1;
+        }
+    }
+    // exclusive offsets of the counts, columns in order (lane, then lane + 32)
+    int sa = cnt[0], sb = cnt[1];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ya = __shfl_up_sync(0xffffffffu, sa, o), yb = __shfl_up_sync(0xffffffffu, sb, o);
+        if (lane >= o) {
+            sa += ya;
+            sb += yb;
+        }
+    }
+    const int ta = __shfl_sync(0xffffffffu, sa, 31), tb = __shfl_sync(0xffffffffu, sb, 31);
+    const int total = ta + tb;
+    const bool fits = ok && total <= cap_slots;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = lane + 32 * h;
+        const int off = h == 0 ? sa - cnt[0] : ta + sb - cnt[1];
+        info[h].z = off - info[h].x;
+        if (!fits) info[h] = make_int4(INT_MAX, INT_MIN, 0, 0);
+        st.col[k] = info[h];
+        st.off[k] = off;
+    }
+    if (lane == 0) {
+        st.c_lo = c_lo;
+        st.n = fits ? c_hi - c_lo + 1 : 0;
+        st.total = fits ? total : 0;
+    }
+}
+
+// The block copies the planned slots into the buffer: warp w takes columns
+// w, w + TW/32, ..., its lanes consecutive slots of the column's span.
+template <int TW>
+__device__ __forceinline__ void stage_copy(const ReconRegs& f, const StagePlan& st, unsigned char* buf) {
+    const bool h16 = f.lp_fmt == VAFR_FMT_RGBA16F;
+    const int lane = (int)(threadIdx.x & 31);
+    for (int k = (int)(threadIdx.x >> 5); k < st.n; k += TW / 32) {
+        const int4 ci = st.col[k];
+        const int n = ci.y - ci.x + 1, to = ci.x + ci.z;
+        for (int q = lane; q < n; q += 32) {
+            if (h16)
+                reinterpret_cast<uint2*>(buf)[to + q] = __ldg(reinterpret_cast<const uint2*>(f.lp) + ci.x + q);
+            else
+                reinterpret_cast<float4*>(buf)[to + q] = __ldg(reinterpret_cast<const float4*>(f.lp) + ci.x + q);
+        }
+    }
+}
+
+// Staged span of the column holding slots i, i + 1 (as an int4 of the plan).
+__device__ __forceinline__ int4 stage_info(const StagePlan* st, int c) {
+    const int k = c - st->c_lo;
+    return (unsigned)k < (unsigned)st->n ? st->col[k] : make_int4(INT_MAX, INT_MIN, 0, 0);
+}
+
+template <int LPF>
+__device__ __forceinline__ px2 load_lp_shared(const unsigned char* buf, int idx) {
+    px2 r;
+    if (LPF == VAFR_FMT_RGBA16F) {
+        const uint2 p = reinterpret_cast<const uint2*>(buf)[idx];
+        r.rg = __half22float2(*reinterpret_cast<const __half2*>(&p.x));
+        r.ba = __half22float2(*reinterpret_cast<const __half2*>(&p.y));
+    } else {
+        const float4 q = reinterpret_cast<const float4*>(buf)[idx];
+        r.rg = make_float2(q.x, q.y);
+        r.ba = make_float2(q.z, q.w);
+    }
+    return r;
+}
+
+// Texel pair (i, i + 1) of one column into (a, b) if p: from the buffer when
+// both slots are staged, else from global memory.
+template <int LPF>
+__device__ __forceinline__ void pair_staged(bool p, const void* lp, const unsigned char* buf, int4 si, int i,
+                                            px2& a, px2& b) {
+    if (!p) return;
+    if (i >= si.x && i + 1 <= si.y) {
+        a = load_lp_shared<LPF>(buf, i + si.z);
+        b = load_lp_shared<LPF>(buf, i + 1 + si.z);
+    } else {
+        a = load_lp(lp, LPF, i);
+        b = load_lp(lp, LPF, i + 1);
+    }
+}
+
 // ---- column runs ---------------------------------------------------------------
 // A thread owns one display column x and R consecutive rows; the 32 lanes of a
 // warp take 32 consecutive x, so every row store of a warp is contiguous.  Down
@@ -274,14 +436,16 @@ __device__ __forceinline__ void ld_texel_if(bool p, const void* lp, int idx, px2
 // R rows (FULL) or the first `nrows` of them, of display column x.  The
 // column's dx is fixed, so angle_fraction's dx < 0 reflection becomes the
 // per-thread FMA a * sx + ox (0.5 - a rounded once, or a exactly).
-template <int R, int LH, bool FULL, bool REUSE_U, int LPF, int DF>
+template <int R, int LH, bool FULL, bool REUSE_U, int LPF, int DF, bool STAGED = false>
 __device__ __forceinline__ void recon_run(const ReconRegs& f, void* disp, int W, int x, int y0, int nrows,
-                                          float dx, int gyi, float gyf) {
+                                          float dx, int gyi, float gyf, const StagePlan* st = nullptr,
+                                          const unsigned char* buf = nullptr, int n_cols = 0) {
     constexpr float c[8] = {VAFR_ATAN_COEFS};
     constexpr int BPP = DF == VAFR_FMT_RGBA16F ? 8 : 16;
     int piece = -1, c0_held = -2, k0 = -1, k1 = -1;
     float4 cf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     int4 cp = make_int4(0, 0x3f800000, 0, 0x3f800000);
+    int4 si0 = make_int4(INT_MAX, INT_MIN, 0, 0), si1 = si0;   // staged spans of the column pair
     px2 a0{}, b0{}, a1{}, b1{};
     const float ax = fmaxf(fabsf(dx), 1e-30f);
     const float sx = dx < 0.0f ? -1.0f : 1.0f, ox = dx < 0.0f ? 0.5f : 0.0f;
@@ -304,6 +468,10 @@ __device__ __forceinline__ void recon_run(const ReconRegs& f, void* disp, int W,
         const float uf = piece_eval(cf, t);
         const int c0 = __float2int_rd(uf);
         const float wu = uf - (float)c0;
+        if (STAGED && c0 != c0_held) {
+            si0 = stage_info(st, max(c0, 0));
+            si1 = stage_info(st, min(c0 + 1, n_cols - 1));
+        }
         ld_if(c0 != c0_held, f.col_pair + c0, cp);
         c0_held = c0;
         // angle_fraction(dy, dx, ax) with the dx reflection as one FMA
@@ -322,10 +490,15 @@ __device__ __forceinline__ void recon_run(const ReconRegs& f, void* disp, int W,
         column_index(cp.x, __int_as_float(cp.y), frac, i0, w0);
         column_index(cp.z, __int_as_float(cp.w), frac, i2, w1);
         const bool l0 = i0 != k0, l1 = i2 != k1;
-        ld_texel_if<LPF>(l0, f.lp, i0, a0);
-        ld_texel_if<LPF>(l0, f.lp, i0 + 1, b0);
-        ld_texel_if<LPF>(l1, f.lp, i2, a1);
-        ld_texel_if<LPF>(l1, f.lp, i2 + 1, b1);
+        if (STAGED) {
+            pair_staged<LPF>(l0, f.lp, buf, si0, i0, a0, b0);
+            pair_staged<LPF>(l1, f.lp, buf, si1, i2, a1, b1);
+        } else {
+            ld_texel_if<LPF>(l0, f.lp, i0, a0);
+            ld_texel_if<LPF>(l0, f.lp, i0 + 1, b0);
+            ld_texel_if<LPF>(l1, f.lp, i2, a1);
+            ld_texel_if<LPF>(l1, f.lp, i2 + 1, b1);
+        }
         k0 = i0;
         k1 = i2;
         store_px<DF>(out, 0, lerp2(lerp2(a0, b0, w0), lerp2(a1, b1, w1), wu));
@@ -393,6 +566,61 @@ cudaError_t launch_runs(const B& b, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Column-run tile (TW threads, one display column each, R rows) whose LP
+// footprint is first staged in shared memory (stage_plan / stage_copy).
+template <int TW, int R, int MINB, class B>
+__global__ void __launch_bounds__(TW, MINB)
+k_reconstruct_staged(const __grid_constant__ B b) {
+    constexpr int TX = TW, TY = R;
+    __shared__ ReconShared sh;
+    __shared__ StagePlan st;
+    __shared__ __align__(16) unsigned char buf[kStageBytes];
+    const int tile = (int)blockIdx.x;
+    if (threadIdx.x == 0) stage_frame(b, tile, sh);
+    __syncthreads();
+    const ReconRegs f = sh.r;
+    const int W = sh.W, H = sh.H;
+    const int local = tile - sh.tile_begin;
+    const int tiles_x = (W + TX - 1) / TX;
+    const int ty = local / tiles_x;
+    const int xt = (local - ty * tiles_x) * TX, yt = ty * TY;
+    if (threadIdx.x < 32) {
+        const int cap = kStageBytes / (f.lp_fmt == VAFR_FMT_RGBA16F ? 8 : 16);
+        stage_plan(f, sh, xt, yt, min(xt + TX, W) - 1, min(yt + TY, H) - 1, cap, st);
+    }
+    __syncthreads();
+    stage_copy<TW>(f, st, buf);
+    __syncthreads();
+    const int x = xt + (int)threadIdx.x;
+    const int y0 = yt;
+    if (x >= W || y0 >= H) return;
+    const int nrows = min(R, H - y0);
+    const float dx = (float)(x - sh.gxi) + sh.gxf;
+    const int gyi = sh.gyi;
+    const float gyf = sh.gyf;
+    void* const disp = sh.disp;
+    const int C = sh.n_cols;
+#define VAFR_STAGED_RUN(LPF, DF)                                                                     \
+    (nrows == R ? recon_run<R, 1, true, false, LPF, DF, true>(f, disp, W, x, y0, nrows, dx, gyi, gyf, &st, buf, C) \
+                : recon_run<R, 1, false, false, LPF, DF, true>(f, disp, W, x, y0, nrows, dx, gyi, gyf, &st, buf, C))
+    if (f.lp_fmt == VAFR_FMT_RGBA16F) {
+        if (sh.disp_fmt == VAFR_FMT_RGBA16F) VAFR_STAGED_RUN(VAFR_FMT_RGBA16F, VAFR_FMT_RGBA16F);
+        else VAFR_STAGED_RUN(VAFR_FMT_RGBA16F, VAFR_FMT_RGBA32F);
+    } else {
+        if (sh.disp_fmt == VAFR_FMT_RGBA16F) VAFR_STAGED_RUN(VAFR_FMT_RGBA32F, VAFR_FMT_RGBA16F);
+        else VAFR_STAGED_RUN(VAFR_FMT_RGBA32F, VAFR_FMT_RGBA32F);
+    }
+#undef VAFR_STAGED_RUN
+}
+
+template <int TW, int R, int MINB, class B>
+cudaError_t launch_staged(const B& b, cudaStream_t s) {
+    if (b.total_tiles <= 0) return cudaSuccess;
+    k_reconstruct_staged<TW, R, MINB, B><<<(unsigned)b.total_tiles, TW, 0, s>>>(b);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
 template <int TW, int TH, int PX, class B>
 cudaError_t launch_shape(const B& b, cudaStream_t s) {
     if (b.total_tiles <= 0) return cudaSuccess;
@@ -404,8 +632,9 @@ cudaError_t launch_shape(const B& b, cudaStream_t s) {
 }  // namespace
 
 // Tile shapes the autotuner chooses between: column runs (0-3: rows per
-// thread, lanes per warp row, minimum blocks per SM, u-table piece reuse) and
-// row tiles (4-7: pixels wide, rows, pixels per thread).
+// thread, lanes per warp row, minimum blocks per SM, u-table piece reuse), row
+// tiles (4-7: pixels wide, rows, pixels per thread) and the column run with
+// its LP footprint staged in shared memory (8).
 ReconShape recon_shape(int variant) {
     switch (variant) {
         case 0: return {128, 8, 0};
@@ -415,7 +644,8 @@ ReconShape recon_shape(int variant) {
         case 4: return {256, 4, 8};
         case 5: return {128, 8, 4};
         case 6: return {64, 8, 2};
-        default: return {128, 4, 4};
+        case 7: return {128, 4, 4};
+        default: return {128, 16, 0};
     }
 }
 
@@ -429,7 +659,8 @@ cudaError_t launch_reconstruct(const B& batch, int variant, cudaStream_t s) {
         case 4: return launch_shape<256, 4, 8>(batch, s);
         case 5: return launch_shape<128, 8, 4>(batch, s);
         case 6: return launch_shape<64, 8, 2>(batch, s);
-        default: return launch_shape<128, 4, 4>(batch, s);
+        case 7: return launch_shape<128, 4, 4>(batch, s);
+        default: return launch_staged<128, 16, 6>(batch, s);
     }
 }
 

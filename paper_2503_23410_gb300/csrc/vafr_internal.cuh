@@ -129,8 +129,9 @@ static_assert(sizeof(BigBatch) + sizeof(SceneDev) <= 32764, "batch too large for
 // variant 6 is the longest-first LP order (the GT keeps variant 0's kernel).
 constexpr int kNumRenderVariants = 7;
 constexpr int kLptVariant = 6;
-// Reconstruct variants: column-run tiles (0-3) and row tiles (4-7).
-constexpr int kNumReconVariants = 8;
+// Reconstruct variants: column-run tiles (0-3), row tiles (4-7) and the
+// column-run tile with its LP footprint staged in shared memory (8).
+constexpr int kNumReconVariants = 9;
 
 // tile width/height in pixels; pixels per thread along a row (row tiles), or 0
 // for a column-run tile (one thread per display column, `th` rows)

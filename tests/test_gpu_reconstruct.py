@@ -144,7 +144,7 @@ def test_16k_sampled(V, torch_mod, lay, disp_fmt):
     assert np.abs(got - ref).max() < tol
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 8])
 def test_8k_fp16_sampled(V, torch_mod, lay, variant):
     """One eye of the 8K binocular configuration (FP16 LP, FP16 display) in the
     reconstruct variants the autotuner picks (2 at 8K, 1 at 4K): sampled pixels
@@ -226,3 +226,16 @@ def test_render_frame_pinned_host_equals_device(V, torch_mod):
     assert torch_mod.equal(dev.cpu(), pin)
     V.vafr_session_destroy(s)
     V.vafr_scene_destroy(h)
+
+
+@pytest.mark.parametrize("W,H,fmt", [(3840, 2160, 0), (7680, 4320, 1)])
+def test_staged_tiles_equal_plain_runs_full_size(V, torch_mod, lay, W, H, fmt):
+    """Variant 8 stages each tile's LP footprint in shared memory; at the bench's
+    display sizes (4K FP32, 8K FP16) and a gaze near a corner and one in the
+    middle, every pixel equals the plain column run's bit for bit."""
+    rng = np.random.default_rng(W + fmt)
+    lp = rng.uniform(0, 1, (lay.total, 4)).astype(np.float16 if fmt else np.float32)
+    for gaze in ((W * 0.5 + 0.37, H * 0.5 - 0.21), (W * 0.07, H * 0.93)):
+        a = _recon(V, torch_mod, W, H, 100.0, gaze, lp, lp_fmt=fmt, disp_fmt=fmt, variant=2)
+        b = _recon(V, torch_mod, W, H, 100.0, gaze, lp, lp_fmt=fmt, disp_fmt=fmt, variant=8)
+        assert np.array_equal(a, b)
