@@ -179,7 +179,10 @@ VAFR_API int vafr_scene_info(const vafr_scene* scene, int64_t* n_tris, int64_t* 
  *   nodes    n_nodes x 32 floats: per axis the lo then hi planes of the four
  *            children (lo.x[4], hi.x[4], lo.y[4], hi.y[4], lo.z[4], hi.z[4]),
  *            then four int32 child references (>= 0 node, < 0 leaf ~k,
- *            INT32_MIN unused), then four padding words.
+ *            INT32_MIN unused), then four uint32 slot keys (q for an internal
+ *            child in slot q, 0xFFFFFFFF otherwise).  Internal children take
+ *            the first slots and are consecutive nodes (slot q's reference is
+ *            slot 0's + q); leaves follow; unused slots come last.
  *   leaves   n_tris x 12 floats, sorted (leaf) order: v0.xyz | id bits,
  *            v1.xyz | 0, v2.xyz | 0, vertices in lexicographic order.
  * A scene of fewer than two triangles has no nodes.  Synchronises the
@@ -200,20 +203,22 @@ VAFR_API int vafr_scene_export_lbvh(const vafr_scene* scene, uint32_t* codes, in
 VAFR_API int vafr_scene_check(const vafr_scene* scene, void* stream);
 
 /* Failure injection for tests of the device status words, made on the host:
- * rewrites the child references of the root of the scene's 4-wide tree in
- * device memory (the node boxes stay), so that the traversal's own checks
+ * rewrites the child references and slot keys of the root of the scene's
+ * 4-wide tree in device memory (the node boxes stay), so that the traversal's own checks
  * stop the affected rays and report the fault through the session status word
  * of the launch (vafr_session_check) instead of touching memory out of range.
- *   VAFR_INJECT_NONE        restore the references saved by the first injection
- *   VAFR_INJECT_BAD_CHILD   every used slot names inner node n_tris + 4, past
- *                           the last one: the node check fails (VAFR_ERR_DEVICE)
+ *   VAFR_INJECT_NONE        restore the references and keys saved by the first
+ *                           injection
+ *   VAFR_INJECT_BAD_CHILD   every used slot becomes an internal child from
+ *                           inner node n_tris + 4 on, past the last one: the
+ *                           node check fails (VAFR_ERR_DEVICE)
  *   VAFR_INJECT_LOOP        slot 0 names the root itself, the other slots are
  *                           emptied: a ray entering slot 0's box cycles without
  *                           growing its stack until the iteration limit of
  *                           4 n_tris + 64 node visits (VAFR_ERR_TIMEOUT)
  *   VAFR_INJECT_STACK       every used slot names the root: a ray entering two
  *                           or more of the root's boxes pushes at every visit
- *                           until the 96-entry stack would overflow (status
+ *                           until the 128-entry stack would overflow (status
  *                           bit 1); a ray entering one box cycles as above
  *                           (bit 2, which takes precedence: VAFR_ERR_TIMEOUT)
  * The check's error message ("session status 0x..") carries the bits:

@@ -118,8 +118,9 @@ struct vafr_scene {
     LbvhBuffers buf{};
     SceneDev dev{};
     unsigned* status = nullptr;
-    bool injected = false;         // vafr_scene_inject_fault: root references saved
-    int4 root_refs{};
+    int n_nodes4 = 0;              // 4-wide nodes of the traversal tree
+    bool injected = false;         // vafr_scene_inject_fault: root references and keys saved
+    int4 root_refs{}, root_keys{};
     float4* d_plights = nullptr;   // point lights (vafr_scene_set_point_lights)
     // deferred path scratch (first use): triangle id -> leaf, large-triangle list
     int* d_leaf_of = nullptr;
@@ -462,7 +463,7 @@ static int vafr_build_scene_impl(const float* tri_xyz, const float* albedo_rgb, 
             void* scratch = nullptr;
             e = cudaMalloc(&scratch, tree4_scratch_bytes(n));
             if (e != cudaSuccess) return bail(fail(VAFR_ERR_OOM, "traversal tree scratch"));
-            e = tree4_build(b, scratch, kPlocRadius, s);
+            e = tree4_build(b, scratch, kPlocRadius, s, &sc->n_nodes4);
             cudaFree(scratch);
             if (e != cudaSuccess)
                 return bail(fail(VAFR_ERR_CUDA, "traversal tree build: %s", cudaGetErrorString(e)));
@@ -553,14 +554,7 @@ int vafr_scene_export_tree4(const vafr_scene* scene, int64_t* n_nodes, float* no
     if (!scene || !n_nodes) return fail(VAFR_ERR_INVALID_ARG, "NULL argument");
     const int64_t n = scene->n;
     CUDA_TRY(cudaDeviceSynchronize());
-    int64_t n4 = 0;
-    if (n > 1) {   // one 4-wide node per head: the last head index plus the last flag
-        const LbvhBuffers& b = scene->buf;
-        unsigned last[2] = {0u, 0u};
-        CUDA_TRY(cudaMemcpy(&last[0], b.head_idx + (n - 2), sizeof(unsigned), cudaMemcpyDeviceToHost));
-        CUDA_TRY(cudaMemcpy(&last[1], b.head_flag + (n - 2), sizeof(unsigned), cudaMemcpyDeviceToHost));
-        n4 = (int64_t)last[0] + last[1];
-    }
+    const int64_t n4 = n > 1 ? scene->n_nodes4 : 0;
     *n_nodes = n4;
     if (nodes && n4 > 0)
         CUDA_TRY(cudaMemcpy(nodes, scene->buf.nodes4, 128ull * (size_t)n4, cudaMemcpyDeviceToHost));
@@ -591,22 +585,37 @@ int vafr_scene_inject_fault(vafr_scene* scene, int32_t kind) {
     if (kind < VAFR_INJECT_NONE || kind > VAFR_INJECT_STACK) return fail(VAFR_ERR_INVALID_ARG, "unknown kind %d", kind);
     if (scene->n < 2) return fail(VAFR_ERR_INVALID_ARG, "a one-triangle scene has no tree");
     // the root is 4-wide node 0; its child references are the node's 7th float4
+    // and its slot keys the 8th (slot q's internal child is reference 0 + key)
     int4* refs = reinterpret_cast<int4*>(scene->buf.nodes4 + 6);
+    int4* keys = reinterpret_cast<int4*>(scene->buf.nodes4 + 7);
     CUDA_TRY(cudaDeviceSynchronize());
     if (!scene->injected) {
         if (kind == VAFR_INJECT_NONE) return VAFR_OK;
         CUDA_TRY(cudaMemcpy(&scene->root_refs, refs, sizeof(int4), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(&scene->root_keys, keys, sizeof(int4), cudaMemcpyDeviceToHost));
         scene->injected = true;
     }
-    int4 v = scene->root_refs;
+    int4 v = scene->root_refs, w = scene->root_keys;
     int* c = &v.x;
+    int* q = &w.x;
     const int bad = (int)(scene->n + 4);   // inner nodes are 0 .. n - 2
     for (int k = 0; k < 4; ++k) {
-        if (kind == VAFR_INJECT_BAD_CHILD && c[k] != kEmptyRef) c[k] = bad;
-        if (kind == VAFR_INJECT_LOOP) c[k] = k == 0 ? 0 : kEmptyRef;
-        if (kind == VAFR_INJECT_STACK && c[k] != kEmptyRef) c[k] = 0;
+        const bool used = c[k] != kEmptyRef;
+        if (kind == VAFR_INJECT_BAD_CHILD && used) {   // every used slot an internal child out of range
+            c[k] = bad;
+            q[k] = k;
+        }
+        if (kind == VAFR_INJECT_LOOP) {   // the root's only child is the root
+            c[k] = k == 0 ? 0 : kEmptyRef;
+            q[k] = k == 0 ? 0 : -1;
+        }
+        if (kind == VAFR_INJECT_STACK && used) {   // every used slot leads back to the root
+            c[k] = 0;
+            q[k] = 0;
+        }
     }
     CUDA_TRY(cudaMemcpy(refs, &v, sizeof(int4), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(keys, &w, sizeof(int4), cudaMemcpyHostToDevice));
     if (kind == VAFR_INJECT_NONE) scene->injected = false;
     return VAFR_OK;
 }

@@ -247,28 +247,34 @@ __device__ unsigned traverse2(const SceneDev& sc, const Ray& r, Hit& h,
     }
 }
 
-__device__ __forceinline__ void sort2(float& ta, int& ra, float& tb, int& rb) {
-    const bool sw = tb < ta;
-    const float t = sw ? tb : ta;
-    const int q = sw ? rb : ra;
-    tb = sw ? ta : tb;
-    rb = sw ? ra : rb;
-    ta = t;
-    ra = q;
+// Ascending order of two sort keys (one integer minimum and one maximum).
+__device__ __forceinline__ void sort2(unsigned& a, unsigned& b) {
+    const unsigned lo = min(a, b);
+    b = max(a, b);
+    a = lo;
 }
 
-// A traversal stack entry: the child reference in the low word, its entry
-// distance in the high word (one 64-bit store and load per push and pop).
-__device__ __forceinline__ unsigned long long stack_entry(int ref, float t) {
-    return ((unsigned long long)__float_as_uint(t) << 32) | (unsigned)ref;
+// Sort key of child slot q: its entry distance t >= 0 (+inf for a miss) as
+// bits without the sign (a -0 entry is 0), whose unsigned order is the order
+// of t, with the two low bits replaced by q for an internal child (key word
+// q); a leaf or unused slot has key word all ones and sorts after every miss.
+// Keys below kKeyMiss are hit internal children; dropping two bits of t only
+// reorders children whose distances agree within 4 ulp, and a stack entry's
+// distance, rounded down, only culls later.
+constexpr unsigned kKeyMiss = 0x7f800000u;
+__device__ __forceinline__ unsigned child_key(float t, unsigned word) {
+    return (__float_as_uint(t) & 0x7ffffffcu) | word;
 }
 
 // Closest hit through the 4-wide tree: test the four child boxes, test the
 // leaf children that were hit, then continue with the nearest internal child
-// and push the others far-to-near.  The hit leaf children of a node form a bit
-// mask that one loop consumes, so a warp runs as many triangle tests per node
-// as its busiest lane needs (not one pass per child slot that any lane needs);
-// the closest-hit rule (t, then id) makes the result independent of the order.
+// and push the others far-to-near.  Internal children are ordered by integer
+// keys (entry distance bits and slot); they are consecutive nodes, so the
+// slot in a key's low bits gives the child's index.  The hit leaf children of
+// a node form a bit mask that one loop consumes, so a warp runs as many
+// triangle tests per node as its busiest lane needs (not one pass per child
+// slot that any lane needs); the closest-hit rule (t, then id) makes the
+// result independent of the order.
 // Returns a fault bit (0 = fine).
 template <bool STATS, int ORDER, bool ANY = false, bool SKIP = false>
 __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
@@ -293,20 +299,19 @@ __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
         const float4* nd = sc.nodes4 + 8ll * node;
         float4 t = slab4(nd, r, h.t);
         const float4 rf = __ldg(nd + 6);
-        int c0 = __float_as_int(rf.x), c1 = __float_as_int(rf.y), c2 = __float_as_int(rf.z),
-            c3 = __float_as_int(rf.w);
+        const uint4 kw = __ldg(reinterpret_cast<const uint4*>(nd + 7));
+        const int c0 = __float_as_int(rf.x), c1 = __float_as_int(rf.y), c2 = __float_as_int(rf.z),
+                  c3 = __float_as_int(rf.w);
         if (STATS) {
             ++*node_visits;
             *box_tests += (c0 != kEmptyRef) + (c1 != kEmptyRef) + (c2 != kEmptyRef) + (c3 != kEmptyRef);
         }
-        // hit children that are leaves (bit q for child q) leave the box list;
-        // unused slots (kEmptyRef, a zero box) leave it without a test
+        // hit children that are leaves (bit q for child q): references below 0
+        // other than kEmptyRef (INT_MIN: an unused slot with a zero box)
+        static_assert(kEmptyRef == INT_MIN, "the leaf test below relies on kEmptyRef");
         unsigned lm = 0u;
 #define VAFR_LEAF_BIT(T, C, Q)                                                            \
-        if (T < INFINITY && C < 0) {                                                      \
-            if (C != kEmptyRef) lm |= 1u << Q;                                            \
-            T = INFINITY;                                                                 \
-        }
+        if (T < INFINITY && (unsigned)C > (unsigned)kEmptyRef) lm |= 1u << Q;
         VAFR_LEAF_BIT(t.x, c0, 0)
         VAFR_LEAF_BIT(t.y, c1, 1)
         VAFR_LEAF_BIT(t.z, c2, 2)
@@ -330,33 +335,33 @@ __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
             if (t.z > lim) t.z = INFINITY;
             if (t.w > lim) t.w = INFINITY;
         }
+        unsigned k0 = child_key(t.x, kw.x), k1 = child_key(t.y, kw.y), k2 = child_key(t.z, kw.z),
+                 k3 = child_key(t.w, kw.w);
         if (ORDER == 0) {
-            // ascending (t, ref): sorting network (0,1) (2,3) (0,2) (1,3) (1,2)
-            sort2(t.x, c0, t.y, c1);
-            sort2(t.z, c2, t.w, c3);
-            sort2(t.x, c0, t.z, c2);
-            sort2(t.y, c1, t.w, c3);
-            sort2(t.y, c1, t.z, c2);
+            // ascending: sorting network (0,1) (2,3) (0,2) (1,3) (1,2)
+            sort2(k0, k1);
+            sort2(k2, k3);
+            sort2(k0, k2);
+            sort2(k1, k3);
+            sort2(k1, k2);
         } else {
             // nearest first, the rest in slot order: (0,1) (2,3) (0,2)
-            sort2(t.x, c0, t.y, c1);
-            sort2(t.z, c2, t.w, c3);
-            sort2(t.x, c0, t.z, c2);
+            sort2(k0, k1);
+            sort2(k2, k3);
+            sort2(k0, k2);
         }
-        if (t.x < INFINITY) {
-            if (t.w < INFINITY) {
-                if (sp >= kStackSize) return kFaultStack;
-                stack[sp++] = stack_entry(c3, t.w);
+        if (k0 < kKeyMiss) {
+            // a stack entry: the child's entry distance (key bits) high, its index low
+#define VAFR_PUSH(K)                                                                      \
+            if (K < kKeyMiss) {                                                           \
+                if (sp >= kStackSize) return kFaultStack;                                 \
+                stack[sp++] = ((unsigned long long)(K & ~3u) << 32) | (unsigned)(c0 + (int)(K & 3u)); \
             }
-            if (t.z < INFINITY) {
-                if (sp >= kStackSize) return kFaultStack;
-                stack[sp++] = stack_entry(c2, t.z);
-            }
-            if (t.y < INFINITY) {
-                if (sp >= kStackSize) return kFaultStack;
-                stack[sp++] = stack_entry(c1, t.y);
-            }
-            node = c0;
+            VAFR_PUSH(k3)
+            VAFR_PUSH(k2)
+            VAFR_PUSH(k1)
+#undef VAFR_PUSH
+            node = c0 + (int)(k0 & 3u);
         } else {
             // pop, skipping entries that start beyond the current closest hit
             const float lim2 = h.t * kFarScale;

@@ -220,48 +220,95 @@ __device__ __forceinline__ void box_of(int ref, const float* __restrict__ node_b
     for (int k = 0; k < 6; ++k) b[k] = p[k];
 }
 
-// head_idx: exclusive scan of the head flags (4-wide node index of each head).
-__global__ void k_pack_nodes4(const int2* __restrict__ child, const float* __restrict__ node_box,
-                              const float* __restrict__ leaf_box, const unsigned* __restrict__ flag,
-                              const unsigned* __restrict__ head_idx, int n_inner,
-                              float4* __restrict__ nodes4) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_inner || !flag[i]) return;
-    int ref[4];
-    float box[4][6];
-    int m = 0;
+// The 4-wide children of head i: its binary children that are leaves and the
+// two children of each internal one (heads, at the next even depth, or
+// leaves).  Internal children come first (ni of them), then the leaves: m in
+// all.  Each head's internal children get consecutive 4-wide indices, so the
+// child in slot q < ni is the slot-0 child + q.
+__device__ __forceinline__ void children4(const int2* __restrict__ child, int i, int ref[4], int& m, int& ni) {
+    int tmp[4];
+    m = 0;
     const int2 c = child[i];
     const int cs[2] = {c.x, c.y};
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
-        const int ca = cs[a];
-        if (ca < 0) {
-            box_of(ca, node_box, leaf_box, box[m]);
-            ref[m++] = ca;
+        if (cs[a] < 0) {
+            tmp[m++] = cs[a];
         } else {
-            const int2 g = child[ca];
-            const int gs[2] = {g.x, g.y};
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                box_of(gs[q], node_box, leaf_box, box[m]);
-                ref[m++] = gs[q] < 0 ? gs[q] : (int)head_idx[gs[q]];
-            }
+            const int2 g = child[cs[a]];
+            tmp[m++] = g.x;
+            tmp[m++] = g.y;
         }
     }
-    for (int k = m; k < 4; ++k) {
-        ref[k] = kEmptyRef;
+    ni = 0;
+    for (int q = 0; q < m; ++q)
+        if (tmp[q] >= 0) ref[ni++] = tmp[q];
+    int k = ni;
+    for (int q = 0; q < m; ++q)
+        if (tmp[q] < 0) ref[k++] = tmp[q];
+}
+
+// Internal-child count of every head (0 elsewhere).
+__global__ void k_count4(const int2* __restrict__ child, const unsigned* __restrict__ flag, int n_inner,
+                         unsigned* __restrict__ cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inner) return;
+    int ref[4], m = 0, ni = 0;
+    if (flag[i]) children4(child, i, ref, m, ni);
+    cnt[i] = (unsigned)ni;
+}
+
+// 4-wide index of every head: 0 for the root, 1 + off[h] + k for the k-th
+// internal child of head h (off: exclusive scan of the counts).
+__global__ void k_number4(const int2* __restrict__ child, const unsigned* __restrict__ flag,
+                          const unsigned* __restrict__ off, int n_inner, unsigned* __restrict__ idx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inner || !flag[i]) return;
+    if (i == 0) idx[0] = 0u;
+    int ref[4], m, ni;
+    children4(child, i, ref, m, ni);
+    for (int k = 0; k < ni; ++k)
+        if ((unsigned)ref[k] < (unsigned)n_inner) idx[ref[k]] = 1u + off[i] + (unsigned)k;
+}
+
+// Node of head i at idx[i]: six planes of the four child boxes, the child
+// references (internal 4-wide indices, ~leaf, kEmptyRef for unused slots with
+// a zero box) and the slot keys: q for an internal child in slot q, all ones
+// for the others (the traversal sorts (entry distance | key) as integers).
+__global__ void k_pack_nodes4(const int2* __restrict__ child, const float* __restrict__ node_box,
+                              const float* __restrict__ leaf_box, const unsigned* __restrict__ flag,
+                              const unsigned* __restrict__ off, const unsigned* __restrict__ idx, int n_inner,
+                              float4* __restrict__ nodes4) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inner || !flag[i]) return;
+    const unsigned self = idx[i];
+    if (self >= (unsigned)n_inner) return;   // unnumbered: a malformed binary tree
+    int ref[4], m, ni;
+    children4(child, i, ref, m, ni);
+    float box[4][6];
+    int out[4];
+    unsigned key[4];
+    for (int k = 0; k < 4; ++k) {
+        if (k < m) {
+            box_of(ref[k], node_box, leaf_box, box[k]);
+            out[k] = k < ni ? (int)(1u + off[i] + (unsigned)k) : ref[k];
+        } else {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) box[k][q] = 0.0f;
+            for (int q = 0; q < 6; ++q) box[k][q] = 0.0f;
+            out[k] = kEmptyRef;
+        }
+        key[k] = k < ni ? (unsigned)k : 0xffffffffu;
     }
-    float4* o = nodes4 + 8ll * head_idx[i];
+    float4* o = nodes4 + 8ll * self;
 #pragma unroll
     for (int q = 0; q < 6; ++q) {   // lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the four children
         const int comp = (q >> 1) + ((q & 1) ? 3 : 0);
         o[q] = make_float4(box[0][comp], box[1][comp], box[2][comp], box[3][comp]);
     }
-    o[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]),
-                       __int_as_float(ref[3]));
-    o[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    o[6] = make_float4(__int_as_float(out[0]), __int_as_float(out[1]), __int_as_float(out[2]),
+                       __int_as_float(out[3]));
+    o[7] = make_float4(__uint_as_float(key[0]), __uint_as_float(key[1]), __uint_as_float(key[2]),
+                       __uint_as_float(key[3]));
 }
 
 }  // namespace
@@ -273,9 +320,10 @@ size_t tree4_scratch_bytes(int n) {
            (size_t)scan_scratch_elems((int)N) * sizeof(unsigned) + 20 * 256;
 }
 
-cudaError_t tree4_build(const LbvhBuffers& b, void* scratch, int radius, cudaStream_t s) {
+cudaError_t tree4_build(const LbvhBuffers& b, void* scratch, int radius, cudaStream_t s, int* n_nodes4) {
     if (radius < 1 || radius > kPlocRadiusMax) return cudaErrorInvalidValue;
     const int n = b.n;
+    *n_nodes4 = 0;
     if (n <= 1) return cudaSuccess;
     const int n_inner = n - 1;
     // carve the scratch block
@@ -338,20 +386,36 @@ cudaError_t tree4_build(const LbvhBuffers& b, void* scratch, int radius, cudaStr
         std::swap(lo, lo2);
         std::swap(hi, hi2);
     }
-    cudaFreeHost(hostv);
-    if (e != cudaSuccess) return e;
-    if (node_base != n_inner) return cudaErrorUnknown;
-    k_renumber<<<blocks_for(n_inner, kThreads), kThreads, 0, s>>>(child, nbox, n_inner, child2, nbox2, parent);
-    k_depth_heads<<<blocks_for(n_inner, kThreads), kThreads, 0, s>>>(parent, n_inner, b.head_flag);
-    count_launch(2);
-    e = cudaMemcpyAsync(b.head_idx, b.head_flag, sizeof(unsigned) * (size_t)n_inner, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = exclusive_scan(b.head_idx, n_inner, sums, s);
-    if (e != cudaSuccess) return e;
-    k_pack_nodes4<<<blocks_for(n_inner, kThreads), kThreads, 0, s>>>(child2, nbox2, b.leaf_box, b.head_flag,
-                                                                      b.head_idx, n_inner, b.nodes4);
-    count_launch(1);
-    e = cudaGetLastError();
+    if (e == cudaSuccess && node_base != n_inner) e = cudaErrorUnknown;
+    if (e != cudaSuccess) {
+        cudaFreeHost(hostv);
+        return e;
+    }
+    // collapse: heads at even depth, their internal-child counts (in `pos`,
+    // free after the rounds) scanned into offsets, then numbering and packing
+    const int g = blocks_for(n_inner, kThreads);
+    k_renumber<<<g, kThreads, 0, s>>>(child, nbox, n_inner, child2, nbox2, parent);
+    k_depth_heads<<<g, kThreads, 0, s>>>(parent, n_inner, b.head_flag);
+    k_count4<<<g, kThreads, 0, s>>>(child2, b.head_flag, n_inner, pos);
+    count_launch(3);
+    e = cudaMemcpyAsync(hostv + 0, pos + (n_inner - 1), sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = exclusive_scan(pos, n_inner, sums, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hostv + 1, pos + (n_inner - 1), sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.head_idx, 0xff, sizeof(unsigned) * (size_t)n_inner, s);
+    if (e == cudaSuccess) {
+        k_number4<<<g, kThreads, 0, s>>>(child2, b.head_flag, pos, n_inner, b.head_idx);
+        k_pack_nodes4<<<g, kThreads, 0, s>>>(child2, nbox2, b.leaf_box, b.head_flag, pos, b.head_idx, n_inner,
+                                            b.nodes4);
+        count_launch(2);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the caller frees the scratch next
+    if (e == cudaSuccess) {
+        const long long n4 = 1ll + hostv[0] + hostv[1];   // the root and every head's internal children
+        if (n4 > n_inner) e = cudaErrorUnknown;
+        else *n_nodes4 = (int)n4;
+    }
+    cudaFreeHost(hostv);
     return e;
 }
 

@@ -30,7 +30,10 @@ constexpr int kMaxSeg = VAFR_MAX_PIVOTS - 1;
 // Leaf k (sorted order): three float4 (v0.xyz | id), (v1.xyz | 0), (v2.xyz | 0).
 // 4-wide node j (128 B, eight float4): lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of
 // children 0..3, then their refs (>= 0 4-wide node, < 0 leaf ~k, kEmptyRef
-// unused), then padding.  4-wide node 0 is the root.
+// unused), then the slot keys (q for an internal child in slot q, all ones
+// otherwise).  Internal children take the first slots and consecutive
+// indices (slot q's node = slot 0's + q); leaves follow, unused slots last.
+// 4-wide node 0 is the root.
 struct SceneDev {
     const float4* nodes;
     const float4* nodes4;
@@ -212,7 +215,7 @@ struct LbvhBuffers {
     float* leaf_box;        // n x 6
     float4* nodes;          // (n-1) x 4
     unsigned* head_flag;    // n-1: internal node at even depth
-    unsigned* head_idx;     // n-1: its 4-wide node index
+    unsigned* head_idx;     // n-1: its 4-wide node index (each node's internal children consecutive)
     float4* nodes4;         // (n-1) x 8 (upper bound on the 4-wide node count)
     float4* leaves;         // n x 3
     float4* albedo4;        // n
@@ -220,11 +223,12 @@ struct LbvhBuffers {
 size_t lbvh_sort_blocks(int n);
 cudaError_t lbvh_build(const LbvhBuffers& b, cudaStream_t s);
 // Traversal tree (tree4.cu): PLOC over the sorted leaves, collapsed to 4-wide
-// nodes in b.nodes4.  `scratch` holds tree4_scratch_bytes(n) device bytes and
-// may be freed when the call returns (it synchronises `s`).
+// nodes in b.nodes4 (*n_nodes4 of them).  `scratch` holds
+// tree4_scratch_bytes(n) device bytes and may be freed when the call returns
+// (it synchronises `s`).
 constexpr int kPlocRadius = 8;
 size_t tree4_scratch_bytes(int n);
-cudaError_t tree4_build(const LbvhBuffers& b, void* scratch, int radius, cudaStream_t s);
+cudaError_t tree4_build(const LbvhBuffers& b, void* scratch, int radius, cudaStream_t s, int* n_nodes4);
 
 // FP32 issue rate (peak.cu): FMAs per second of scalar FFMA and of paired
 // FFMA2 (two FMAs each) over the whole device; `sink` holds num_sms * 8 floats.

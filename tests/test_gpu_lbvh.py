@@ -66,7 +66,8 @@ MAX_DEPTH = 1 + 128 // 3
 def check_tree4(nodes, leaves, tris):
     """Invariants of the exported traversal tree, checked level by level from
     the root: every node is reached exactly once and every leaf exactly once
-    (a tree over all triangles); each node has 2-4 children with unused slots
+    (a tree over all triangles); each node has 2-4 children, internal ones
+    first (consecutive nodes, slot keys 0, 1, ...), then leaves, unused slots
     last; every child box is the exact FP32 union of its subtree's vertices
     (a leaf's box is its triangle's min/max, a node's box the min/max of its
     own children's boxes); leaves hold their triangle's vertices; the depth
@@ -82,6 +83,7 @@ def check_tree4(nodes, leaves, tris):
     assert np.array_equal(np.take_along_axis(src, order[:, :, None], 1), v)
     leaf_lo, leaf_hi = v.min(1), v.max(1)
     refs = nodes[:, 24:28].copy().view(np.int32)
+    keys = nodes[:, 28:32].copy().view(np.uint32)
     lo = np.stack([nodes[:, 0:4], nodes[:, 8:12], nodes[:, 16:20]], -1)
     hi = np.stack([nodes[:, 4:8], nodes[:, 12:16], nodes[:, 20:24]], -1)
     used = refs != EMPTY
@@ -90,6 +92,12 @@ def check_tree4(nodes, leaves, tris):
     node_ref = used & (refs >= 0)
     leaf_ref = used & (refs < 0)
     assert np.all(refs[node_ref] < n4) and np.all(~refs[leaf_ref] < n)
+    # internal children first, consecutive nodes, each slot's key its slot
+    # number (all ones for leaves and unused slots)
+    assert np.all(node_ref[:, 1:] <= node_ref[:, :-1]), "a leaf or unused slot before an internal child"
+    slot = np.arange(4)
+    assert np.all(~node_ref | (refs == refs[:, :1] + slot)), "internal children are not consecutive nodes"
+    assert np.array_equal(keys, np.where(node_ref, slot, 0xFFFFFFFF).astype(np.uint32)), "slot keys"
     # boxes: leaf children
     lk = ~refs[leaf_ref]
     assert np.array_equal(lo[leaf_ref], leaf_lo[lk]) and np.array_equal(hi[leaf_ref], leaf_hi[lk])
