@@ -439,7 +439,6 @@ static int vafr_build_scene_impl(const float* tri_xyz, const float* albedo_rgb, 
         ALLOC(b.nodes, 4ll * (n > 1 ? n - 1 : 1));
         ALLOC(b.head_flag, n > 1 ? n - 1 : 1);
         ALLOC(b.head_idx, n > 1 ? n - 1 : 1);
-        ALLOC(b.nodes4, 8ll * (n > 1 ? n - 1 : 1));
         ALLOC(b.leaves, 3ll * n);
         ALLOC(b.albedo4, n);
     }
@@ -460,11 +459,18 @@ static int vafr_build_scene_impl(const float* tri_xyz, const float* albedo_rgb, 
         e = lbvh_build(b, s);
         if (e != cudaSuccess) return bail(fail(VAFR_ERR_CUDA, "lbvh build: %s", cudaGetErrorString(e)));
         if (n > 1) {
-            void* scratch = nullptr;
-            e = cudaMalloc(&scratch, tree4_scratch_bytes(n));
+            struct Scratch {   // freed on every way out, a thrown bad_alloc included
+                void* p = nullptr;
+                ~Scratch() { if (p) cudaFree(p); }
+            } scratch;
+            e = cudaMalloc(&scratch.p, tree4_scratch_bytes(n));
             if (e != cudaSuccess) return bail(fail(VAFR_ERR_OOM, "traversal tree scratch"));
-            e = tree4_build(b, scratch, kPlocRadius, s, &sc->n_nodes4);
-            cudaFree(scratch);
+            e = tree4_build(b, scratch.p, kPlocRadius, s, &sc->n_nodes4);
+            if (e != cudaSuccess)
+                return bail(fail(VAFR_ERR_CUDA, "traversal tree build: %s", cudaGetErrorString(e)));
+            const int r4 = sc->alloc(&b.nodes4, 16ll * sc->n_nodes4);
+            if (r4) return r4;
+            e = tree4_pack(b, scratch.p, sc->n_nodes4, s);
             if (e != cudaSuccess)
                 return bail(fail(VAFR_ERR_CUDA, "traversal tree build: %s", cudaGetErrorString(e)));
         }
@@ -556,8 +562,20 @@ int vafr_scene_export_tree4(const vafr_scene* scene, int64_t* n_nodes, float* no
     CUDA_TRY(cudaDeviceSynchronize());
     const int64_t n4 = n > 1 ? scene->n_nodes4 : 0;
     *n_nodes = n4;
-    if (nodes && n4 > 0)
-        CUDA_TRY(cudaMemcpy(nodes, scene->buf.nodes4, 128ull * (size_t)n4, cudaMemcpyDeviceToHost));
+    if (nodes && n4 > 0) {   // device nodes hold each axis as lo, hi, hi, lo: export lo, hi
+        std::vector<float4> dev((size_t)n4 * 16);
+        CUDA_TRY(cudaMemcpy(dev.data(), scene->buf.nodes4, 256ull * (size_t)n4, cudaMemcpyDeviceToHost));
+        float4* o = reinterpret_cast<float4*>(nodes);
+        for (int64_t j = 0; j < n4; ++j) {
+            const float4* d = dev.data() + 16 * j;
+            for (int a = 0; a < 3; ++a) {
+                o[8 * j + 2 * a] = d[4 * a];
+                o[8 * j + 2 * a + 1] = d[4 * a + 1];
+            }
+            o[8 * j + 6] = d[12];
+            o[8 * j + 7] = d[13];
+        }
+    }
     if (leaves && n > 0)
         CUDA_TRY(cudaMemcpy(leaves, scene->buf.leaves, 48ull * (size_t)n, cudaMemcpyDeviceToHost));
     return VAFR_OK;
@@ -586,8 +604,8 @@ int vafr_scene_inject_fault(vafr_scene* scene, int32_t kind) {
     if (scene->n < 2) return fail(VAFR_ERR_INVALID_ARG, "a one-triangle scene has no tree");
     // the root is 4-wide node 0; its child references are the node's 7th float4
     // and its slot keys the 8th (slot q's internal child is reference 0 + key)
-    int4* refs = reinterpret_cast<int4*>(scene->buf.nodes4 + 6);
-    int4* keys = reinterpret_cast<int4*>(scene->buf.nodes4 + 7);
+    int4* refs = reinterpret_cast<int4*>(scene->buf.nodes4 + 12);
+    int4* keys = reinterpret_cast<int4*>(scene->buf.nodes4 + 13);
     CUDA_TRY(cudaDeviceSynchronize());
     if (!scene->injected) {
         if (kind == VAFR_INJECT_NONE) return VAFR_OK;

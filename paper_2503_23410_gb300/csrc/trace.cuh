@@ -47,10 +47,11 @@ __device__ __forceinline__ void ray_setup(Ray& r) {
     r.ix = safe_inv(r.dx);
     r.iy = safe_inv(r.dy);
     r.iz = safe_inv(r.dz);
-    // a 4-wide node stores lo then hi per axis: the near plane is hi when 1/d < 0
-    r.nx = r.ix < 0.0f ? 1 : 0;
-    r.ny = r.iy < 0.0f ? 3 : 2;
-    r.nz = r.iz < 0.0f ? 5 : 4;
+    // a 4-wide node stores lo, hi, hi, lo per axis: (near, far) is (hi, lo)
+    // from the axis's third float4 when 1/d < 0, (lo, hi) from its first otherwise
+    r.nx = r.ix < 0.0f ? 2 : 0;
+    r.ny = r.iy < 0.0f ? 6 : 4;
+    r.nz = r.iz < 0.0f ? 10 : 8;
     const float ax = fabsf(r.dx), ay = fabsf(r.dy), az = fabsf(r.dz);
     const int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
     int kx = kz == 2 ? 0 : kz + 1;
@@ -93,6 +94,13 @@ __device__ __forceinline__ float2 slab2(float4 nx, float4 ny, float4 nz, const R
     return make_float2(tnl <= tfl * kFarScale ? tnl : INFINITY, tnr <= tfr * kFarScale ? tnr : INFINITY);
 }
 
+// Two float4 from one 32-byte aligned address (one 256-bit load).
+__device__ __forceinline__ void ldg256(const float4* p, float4& a, float4& b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
 // Three-input FP32 minimum / maximum (one PTX instruction on sm_100 and later;
 // same NaN rule as fminf / fmaxf).
 __device__ __forceinline__ float max3f(float a, float b, float c) {
@@ -110,12 +118,15 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
 // the same robust evaluation as slab2.  Each axis's near and far planes are
 // chosen per ray by the sign of 1/d (the near plane of every box is then its
 // lo side, or its hi side, for all four children at once), so each child needs
-// only the max of three near distances and the min of three far ones.
+// only the max of three near distances and the min of three far ones.  The
+// node stores each axis as lo, hi, hi, lo: the ray's (near, far) pair is one
+// 256-bit load at a 32-byte offset fixed per ray.
 // Returns the entry distances, +inf for a miss.
 __device__ __forceinline__ float4 slab4(const float4* __restrict__ nd, const Ray& r, float tmax) {
-    const float4 nxp = __ldg(nd + r.nx), fxp = __ldg(nd + (r.nx ^ 1));
-    const float4 nyp = __ldg(nd + r.ny), fyp = __ldg(nd + (r.ny ^ 1));
-    const float4 nzp = __ldg(nd + r.nz), fzp = __ldg(nd + (r.nz ^ 1));
+    float4 nxp, fxp, nyp, fyp, nzp, fzp;
+    ldg256(nd + r.nx, nxp, fxp);
+    ldg256(nd + r.ny, nyp, fyp);
+    ldg256(nd + r.nz, nzp, fzp);
     const float2 ix = make_float2(r.ix, r.ix), iy = make_float2(r.iy, r.iy), iz = make_float2(r.iz, r.iz);
     const float2 xna = __fmul2_rn(sub2(nxp.x, nxp.y, r.ox), ix), xnb = __fmul2_rn(sub2(nxp.z, nxp.w, r.ox), ix);
     const float2 xfa = __fmul2_rn(sub2(fxp.x, fxp.y, r.ox), ix), xfb = __fmul2_rn(sub2(fxp.z, fxp.w, r.ox), ix);
@@ -296,10 +307,12 @@ __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
     while (true) {
         if (--budget == 0u) return kFaultWatchdog;
         if ((unsigned)node >= (unsigned)n_inner) return kFaultBadNode;
-        const float4* nd = sc.nodes4 + 8ll * node;
+        const float4* nd = sc.nodes4 + 16ll * node;
         float4 t = slab4(nd, r, h.t);
-        const float4 rf = __ldg(nd + 6);
-        const uint4 kw = __ldg(reinterpret_cast<const uint4*>(nd + 7));
+        float4 rf, kwf;
+        ldg256(nd + 12, rf, kwf);
+        const uint4 kw = make_uint4(__float_as_uint(kwf.x), __float_as_uint(kwf.y), __float_as_uint(kwf.z),
+                                    __float_as_uint(kwf.w));
         const int c0 = __float_as_int(rf.x), c1 = __float_as_int(rf.y), c2 = __float_as_int(rf.z),
                   c3 = __float_as_int(rf.w);
         if (STATS) {

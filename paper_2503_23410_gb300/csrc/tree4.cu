@@ -278,11 +278,11 @@ __global__ void k_number4(const int2* __restrict__ child, const unsigned* __rest
 __global__ void k_pack_nodes4(const int2* __restrict__ child, const float* __restrict__ node_box,
                               const float* __restrict__ leaf_box, const unsigned* __restrict__ flag,
                               const unsigned* __restrict__ off, const unsigned* __restrict__ idx, int n_inner,
-                              float4* __restrict__ nodes4) {
+                              int n_nodes4, float4* __restrict__ nodes4) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_inner || !flag[i]) return;
     const unsigned self = idx[i];
-    if (self >= (unsigned)n_inner) return;   // unnumbered: a malformed binary tree
+    if (self >= (unsigned)n_nodes4) return;   // unnumbered: a malformed binary tree
     int ref[4], m, ni;
     children4(child, i, ref, m, ni);
     float box[4][6];
@@ -299,16 +299,21 @@ __global__ void k_pack_nodes4(const int2* __restrict__ child, const float* __res
         }
         key[k] = k < ni ? (unsigned)k : 0xffffffffu;
     }
-    float4* o = nodes4 + 8ll * self;
+    float4* o = nodes4 + 16ll * self;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {   // lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the four children
-        const int comp = (q >> 1) + ((q & 1) ? 3 : 0);
-        o[q] = make_float4(box[0][comp], box[1][comp], box[2][comp], box[3][comp]);
+    for (int a = 0; a < 3; ++a) {   // per axis: lo, hi, hi, lo of the four children
+        const float4 lo = make_float4(box[0][a], box[1][a], box[2][a], box[3][a]);
+        const float4 hi = make_float4(box[0][a + 3], box[1][a + 3], box[2][a + 3], box[3][a + 3]);
+        o[4 * a] = lo;
+        o[4 * a + 1] = hi;
+        o[4 * a + 2] = hi;
+        o[4 * a + 3] = lo;
     }
-    o[6] = make_float4(__int_as_float(out[0]), __int_as_float(out[1]), __int_as_float(out[2]),
-                       __int_as_float(out[3]));
-    o[7] = make_float4(__uint_as_float(key[0]), __uint_as_float(key[1]), __uint_as_float(key[2]),
-                       __uint_as_float(key[3]));
+    o[12] = make_float4(__int_as_float(out[0]), __int_as_float(out[1]), __int_as_float(out[2]),
+                        __int_as_float(out[3]));
+    o[13] = make_float4(__uint_as_float(key[0]), __uint_as_float(key[1]), __uint_as_float(key[2]),
+                        __uint_as_float(key[3]));
+    o[14] = o[15] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
 }  // namespace
@@ -320,36 +325,73 @@ size_t tree4_scratch_bytes(int n) {
            (size_t)scan_scratch_elems((int)N) * sizeof(unsigned) + 20 * 256;
 }
 
-cudaError_t tree4_build(const LbvhBuffers& b, void* scratch, int radius, cudaStream_t s, int* n_nodes4) {
-    if (radius < 1 || radius > kPlocRadiusMax) return cudaErrorInvalidValue;
-    const int n = b.n;
-    *n_nodes4 = 0;
-    if (n <= 1) return cudaSuccess;
+// The scratch block's arrays.  tree4_build leaves the binary tree in child2 /
+// nbox2 (root = 0) and the heads' internal-child offsets in pos for
+// tree4_pack.
+struct Tree4Scratch {
+    int *C, *C2;
+    float4 *lo, *hi, *lo2, *hi2;
+    int* nbr;
+    unsigned *keep, *pos, *merge, *moff;
+    int2 *child, *child2;
+    float *nbox, *nbox2;
+    int32_t* parent;
+    unsigned* sums;
+};
+
+static Tree4Scratch carve(void* scratch, int n) {
     const int n_inner = n - 1;
-    // carve the scratch block
     char* p = static_cast<char*>(scratch);
     auto take = [&](size_t bytes) {
         char* q = p;
         p += (bytes + 255) & ~(size_t)255;
         return q;
     };
-    int* C = reinterpret_cast<int*>(take(sizeof(int) * n));
-    int* C2 = reinterpret_cast<int*>(take(sizeof(int) * n));
-    float4* lo = reinterpret_cast<float4*>(take(sizeof(float4) * n));
-    float4* hi = reinterpret_cast<float4*>(take(sizeof(float4) * n));
-    float4* lo2 = reinterpret_cast<float4*>(take(sizeof(float4) * n));
-    float4* hi2 = reinterpret_cast<float4*>(take(sizeof(float4) * n));
-    int* nbr = reinterpret_cast<int*>(take(sizeof(int) * n));
-    unsigned* keep = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * n));
-    unsigned* pos = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * n));
-    unsigned* merge = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * n));
-    unsigned* moff = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * n));
-    int2* child = reinterpret_cast<int2*>(take(sizeof(int2) * n_inner));
-    int2* child2 = reinterpret_cast<int2*>(take(sizeof(int2) * n_inner));
-    float* nbox = reinterpret_cast<float*>(take(sizeof(float) * 6 * n_inner));
-    float* nbox2 = reinterpret_cast<float*>(take(sizeof(float) * 6 * n_inner));
-    int32_t* parent = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * n_inner));
-    unsigned* sums = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * scan_scratch_elems(n)));
+    Tree4Scratch t;
+    t.C = reinterpret_cast<int*>(take(sizeof(int) * n));
+    t.C2 = reinterpret_cast<int*>(take(sizeof(int) * n));
+    t.lo = reinterpret_cast<float4*>(take(sizeof(float4) * n));
+    t.hi = reinterpret_cast<float4*>(take(sizeof(float4) * n));
+    t.lo2 = reinterpret_cast<float4*>(take(sizeof(float4) * n));
+    t.hi2 = reinterpret_cast<float4*>(take(sizeof(float4) * n));
+    t.nbr = reinterpret_cast<int*>(take(sizeof(int) * n));
+    t.keep = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * n));
+    t.pos = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * n));
+    t.merge = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * n));
+    t.moff = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * n));
+    t.child = reinterpret_cast<int2*>(take(sizeof(int2) * n_inner));
+    t.child2 = reinterpret_cast<int2*>(take(sizeof(int2) * n_inner));
+    t.nbox = reinterpret_cast<float*>(take(sizeof(float) * 6 * n_inner));
+    t.nbox2 = reinterpret_cast<float*>(take(sizeof(float) * 6 * n_inner));
+    t.parent = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * n_inner));
+    t.sums = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * scan_scratch_elems(n)));
+    return t;
+}
+
+cudaError_t tree4_build(const LbvhBuffers& b, void* scratch, int radius, cudaStream_t s, int* n_nodes4) {
+    if (radius < 1 || radius > kPlocRadiusMax) return cudaErrorInvalidValue;
+    const int n = b.n;
+    *n_nodes4 = 0;
+    if (n <= 1) return cudaSuccess;
+    const int n_inner = n - 1;
+    const Tree4Scratch sc = carve(scratch, n);
+    int* C = sc.C;
+    int* C2 = sc.C2;
+    float4* lo = sc.lo;
+    float4* hi = sc.hi;
+    float4* lo2 = sc.lo2;
+    float4* hi2 = sc.hi2;
+    int* nbr = sc.nbr;
+    unsigned* keep = sc.keep;
+    unsigned* pos = sc.pos;
+    unsigned* merge = sc.merge;
+    unsigned* moff = sc.moff;
+    int2* child = sc.child;
+    int2* child2 = sc.child2;
+    float* nbox = sc.nbox;
+    float* nbox2 = sc.nbox2;
+    int32_t* parent = sc.parent;
+    unsigned* sums = sc.sums;
     unsigned* hostv = nullptr;
     cudaError_t e = cudaMallocHost(&hostv, 4 * sizeof(unsigned));
     if (e != cudaSuccess) return e;
@@ -392,7 +434,8 @@ cudaError_t tree4_build(const LbvhBuffers& b, void* scratch, int radius, cudaStr
         return e;
     }
     // collapse: heads at even depth, their internal-child counts (in `pos`,
-    // free after the rounds) scanned into offsets, then numbering and packing
+    // free after the rounds) scanned into offsets, then the numbering; the
+    // caller allocates the nodes and tree4_pack writes them
     const int g = blocks_for(n_inner, kThreads);
     k_renumber<<<g, kThreads, 0, s>>>(child, nbox, n_inner, child2, nbox2, parent);
     k_depth_heads<<<g, kThreads, 0, s>>>(parent, n_inner, b.head_flag);
@@ -404,18 +447,30 @@ cudaError_t tree4_build(const LbvhBuffers& b, void* scratch, int radius, cudaStr
     if (e == cudaSuccess) e = cudaMemsetAsync(b.head_idx, 0xff, sizeof(unsigned) * (size_t)n_inner, s);
     if (e == cudaSuccess) {
         k_number4<<<g, kThreads, 0, s>>>(child2, b.head_flag, pos, n_inner, b.head_idx);
-        k_pack_nodes4<<<g, kThreads, 0, s>>>(child2, nbox2, b.leaf_box, b.head_flag, pos, b.head_idx, n_inner,
-                                            b.nodes4);
-        count_launch(2);
+        count_launch(1);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the caller frees the scratch next
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the count is read next
     if (e == cudaSuccess) {
         const long long n4 = 1ll + hostv[0] + hostv[1];   // the root and every head's internal children
         if (n4 > n_inner) e = cudaErrorUnknown;
         else *n_nodes4 = (int)n4;
     }
     cudaFreeHost(hostv);
+    return e;
+}
+
+cudaError_t tree4_pack(const LbvhBuffers& b, void* scratch, int n_nodes4, cudaStream_t s) {
+    const int n = b.n;
+    if (n <= 1) return cudaSuccess;
+    const int n_inner = n - 1;
+    const Tree4Scratch sc = carve(scratch, n);
+    k_pack_nodes4<<<blocks_for(n_inner, kThreads), kThreads, 0, s>>>(sc.child2, sc.nbox2, b.leaf_box, b.head_flag,
+                                                                      sc.pos, b.head_idx, n_inner, n_nodes4,
+                                                                      b.nodes4);
+    count_launch(1);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the caller frees the scratch next
     return e;
 }
 

@@ -28,12 +28,13 @@ constexpr int kMaxSeg = VAFR_MAX_PIVOTS - 1;
 //   n[2] = (L.lo.z, R.lo.z, L.hi.z, R.hi.z)
 //   n[3] = (L ref, R ref, -, -) as int bits; ref >= 0 internal, < 0 leaf ~k
 // Leaf k (sorted order): three float4 (v0.xyz | id), (v1.xyz | 0), (v2.xyz | 0).
-// 4-wide node j (128 B, eight float4): lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of
-// children 0..3, then their refs (>= 0 4-wide node, < 0 leaf ~k, kEmptyRef
-// unused), then the slot keys (q for an internal child in slot q, all ones
-// otherwise).  Internal children take the first slots and consecutive
-// indices (slot q's node = slot 0's + q); leaves follow, unused slots last.
-// 4-wide node 0 is the root.
+// 4-wide node j (256 B, sixteen float4): per axis the planes lo, hi, hi, lo of
+// children 0..3 (so the (near, far) pair of either ray direction is one
+// 32-byte aligned load), then their refs (>= 0 4-wide node, < 0 leaf ~k,
+// kEmptyRef unused), then the slot keys (q for an internal child in slot q,
+// all ones otherwise), then padding.  Internal children take the first slots
+// and consecutive indices (slot q's node = slot 0's + q); leaves follow,
+// unused slots last.  4-wide node 0 is the root.
 struct SceneDev {
     const float4* nodes;
     const float4* nodes4;
@@ -216,19 +217,22 @@ struct LbvhBuffers {
     float4* nodes;          // (n-1) x 4
     unsigned* head_flag;    // n-1: internal node at even depth
     unsigned* head_idx;     // n-1: its 4-wide node index (each node's internal children consecutive)
-    float4* nodes4;         // (n-1) x 8 (upper bound on the 4-wide node count)
+    float4* nodes4;         // n_nodes4 x 16 (allocated once tree4_build has counted them)
     float4* leaves;         // n x 3
     float4* albedo4;        // n
 };
 size_t lbvh_sort_blocks(int n);
 cudaError_t lbvh_build(const LbvhBuffers& b, cudaStream_t s);
-// Traversal tree (tree4.cu): PLOC over the sorted leaves, collapsed to 4-wide
-// nodes in b.nodes4 (*n_nodes4 of them).  `scratch` holds
-// tree4_scratch_bytes(n) device bytes and may be freed when the call returns
-// (it synchronises `s`).
+// Traversal tree (tree4.cu): PLOC over the sorted leaves, collapsed to
+// 4-wide nodes.  tree4_build clusters, numbers the nodes and returns their
+// count; the caller allocates b.nodes4 (16 float4 per node) and tree4_pack
+// writes them.  `scratch` holds tree4_scratch_bytes(n) device bytes, carries
+// the binary tree from the first call to the second and may be freed after
+// it (both synchronise `s`).
 constexpr int kPlocRadius = 8;
 size_t tree4_scratch_bytes(int n);
 cudaError_t tree4_build(const LbvhBuffers& b, void* scratch, int radius, cudaStream_t s, int* n_nodes4);
+cudaError_t tree4_pack(const LbvhBuffers& b, void* scratch, int n_nodes4, cudaStream_t s);
 
 // FP32 issue rate (peak.cu): FMAs per second of scalar FFMA and of paired
 // FFMA2 (two FMAs each) over the whole device; `sink` holds num_sms * 8 floats.
