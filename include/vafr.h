@@ -210,7 +210,7 @@ VAFR_API int vafr_scene_check(const vafr_scene* scene, void* stream);
  *   VAFR_INJECT_NONE        restore the references and keys saved by the first
  *                           injection
  *   VAFR_INJECT_BAD_CHILD   every used slot becomes an internal child from
- *                           inner node n_tris + 4 on, past the last one: the
+ *                           the first index past the last 4-wide node on: the
  *                           node check fails (VAFR_ERR_DEVICE)
  *   VAFR_INJECT_LOOP        slot 0 names the root itself, the other slots are
  *                           emptied: a ray entering slot 0's box cycles without

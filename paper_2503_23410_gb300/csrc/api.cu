@@ -478,6 +478,7 @@ static int vafr_build_scene_impl(const float* tri_xyz, const float* albedo_rgb, 
     SceneDev& d = sc->dev;
     d.nodes = b.nodes;
     d.nodes4 = b.nodes4;
+    d.n_nodes4 = sc->n_nodes4;
     d.leaves = b.leaves;
     d.albedo = b.albedo4;
     d.n_tris = n;
@@ -616,7 +617,7 @@ int vafr_scene_inject_fault(vafr_scene* scene, int32_t kind) {
     int4 v = scene->root_refs, w = scene->root_keys;
     int* c = &v.x;
     int* q = &w.x;
-    const int bad = (int)(scene->n + 4);   // inner nodes are 0 .. n - 2
+    const int bad = scene->n_nodes4;   // one past the last 4-wide node
     for (int k = 0; k < 4; ++k) {
         const bool used = c[k] != kEmptyRef;
         if (kind == VAFR_INJECT_BAD_CHILD && used) {   // every used slot an internal child out of range

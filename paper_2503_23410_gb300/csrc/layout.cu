@@ -132,22 +132,36 @@ int32_t float_bits(int32_t n) {
     return b;
 }
 
-uint32_t spread16(uint32_t x) {
-    x &= 0xffffu;
-    x = (x | (x << 8)) & 0x00ff00ffu;
-    x = (x | (x << 4)) & 0x0f0f0f0fu;
-    x = (x | (x << 2)) & 0x33333333u;
-    x = (x | (x << 1)) & 0x55555555u;
-    return x;
+// Position of cell (x, y) of a 2^16 x 2^16 grid along the Hilbert curve:
+// from the coarsest level down, each level adds its quadrant's rank (0-3 in
+// curve order) and turns the remaining coordinates into that quadrant's
+// frame (a transpose, mirrored for the last quadrant).
+uint32_t hilbert16(uint32_t x, uint32_t y) {
+    uint32_t d = 0;
+    for (uint32_t s = 1u << 15; s > 0; s >>= 1) {
+        const uint32_t rx = (x & s) ? 1u : 0u, ry = (y & s) ? 1u : 0u;
+        d += s * s * ((3u * rx) ^ ry);
+        if (ry == 0) {
+            if (rx == 1) {
+                x = (s - 1) - (x & (s - 1)) + (x & ~(s - 1));
+                y = (s - 1) - (y & (s - 1)) + (y & ~(s - 1));
+            }
+            const uint32_t t = x;
+            x = y;
+            y = t;
+        }
+    }
+    return d;
 }
 
-// Processing order of the LP texels: Morton order of each texel's screen
+// Processing order of the LP texels: Hilbert order of each texel's screen
 // direction relative to the gaze, (tan e_c cos phi_j, tan e_c sin phi_j), so the
-// 32 rays a warp takes are spatial neighbours.  This direction depends on the
-// acuity model only, never on the display size or the gaze.
+// 32 rays a warp takes are spatial neighbours (the curve has no long jumps
+// between consecutive cells).  This direction depends on the acuity model
+// only, never on the display size or the gaze.
 void build_work_order(const LayoutTables& L, std::vector<int2>& work) {
     const double X = std::tan(L.map.e_max * M_PI / 180.0) * 1.0001;
-    // (Morton key, slot, column); the slot breaks ties, so the order is a function
+    // (Hilbert key, slot, column); the slot breaks ties, so the order is a function
     std::vector<std::pair<uint32_t, int2>> key;
     key.reserve(L.n_texels);
     for (int c = 0; c < L.n_cols; ++c) {
@@ -157,7 +171,7 @@ void build_work_order(const LayoutTables& L, std::vector<int2>& work) {
             const double x = te * std::cos(ph), y = te * std::sin(ph);
             const uint32_t qx = (uint32_t)std::min(65535.0, std::max(0.0, (x + X) / (2 * X) * 65535.0));
             const uint32_t qy = (uint32_t)std::min(65535.0, std::max(0.0, (y + X) / (2 * X) * 65535.0));
-            key.push_back({(spread16(qx) << 1) | spread16(qy), make_int2((int)(L.off_col[c] + j), c)});
+            key.push_back({hilbert16(qx, qy), make_int2((int)(L.off_col[c] + j), c)});
         }
     }
     std::sort(key.begin(), key.end(), [](const std::pair<uint32_t, int2>& a, const std::pair<uint32_t, int2>& b) {

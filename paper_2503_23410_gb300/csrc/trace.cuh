@@ -302,11 +302,10 @@ __device__ unsigned traverse4(const SceneDev& sc, const Ray& r, Hit& h,
     unsigned long long stack[kStackSize];
     int sp = 0;
     int node = 0;
-    const int n_inner = sc.n_tris - 1;
     unsigned budget = 4u * (unsigned)sc.n_tris + 64u;
     while (true) {
         if (--budget == 0u) return kFaultWatchdog;
-        if ((unsigned)node >= (unsigned)n_inner) return kFaultBadNode;
+        if ((unsigned)node >= (unsigned)sc.n_nodes4) return kFaultBadNode;   // the nodes are allocated at their count
         const float4* nd = sc.nodes4 + 16ll * node;
         float4 t = slab4(nd, r, h.t);
         float4 rf, kwf;

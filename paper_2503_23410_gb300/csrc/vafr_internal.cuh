@@ -38,6 +38,7 @@ constexpr int kMaxSeg = VAFR_MAX_PIVOTS - 1;
 struct SceneDev {
     const float4* nodes;
     const float4* nodes4;
+    int n_nodes4;           // 4-wide nodes (the traversal's bound on a child index)
     const float4* leaves;
     const float4* albedo;   // original triangle order (rgb, 0)
     int root;               // 0 (internal), ~0 (single leaf) or INT_MIN (empty)
