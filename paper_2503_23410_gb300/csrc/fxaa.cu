@@ -25,7 +25,7 @@
 //   7 blend   texel + max(offset, subpix) (neighbour - texel), every channel.
 // Luma and every branch decision use FP32 in one fixed order (no contraction),
 // offsets and the blend FP32.  Two passes, one thread per texel in the
-// frame's screen-space Morton order: the luma of every slot into a scratch
+// frame's screen-space Hilbert order: the luma of every slot into a scratch
 // array, then the filter, which reads lumas (4 bytes) for its neighbourhood
 // and search and colours only for the texel and its blend partner.  The
 // output (a second LP buffer) gets the guard copies too.

@@ -479,7 +479,7 @@ __device__ __forceinline__ int find_frame(const B& b, long long w, bool tiles) {
 }
 
 // LP ray of the frame's work item k (Eqs. 3, 10, 11): work items visit the
-// texels in screen-space Morton order; texel t = (c, j) sits at distance
+// texels in screen-space Hilbert order; texel t = (c, j) sits at distance
 // r = tan(e_c)/c_r from the gaze at angle phi = (j + 0.5) 360/n_c, so its
 // camera direction is (tan(e_c) cos(phi) + gx, -tan(e_c) sin(phi) + gy, 1).
 // Returns the texel's slot; `guard_lo` / `guard_hi` get the guard slots that
