@@ -70,7 +70,7 @@ PT_DIFFUSE = 3        # the paper's maximum diffuse bounces (Sec. 8.1)
 # is the pixel ray (15), the shear set-up (3 abs, 5 compares/selects, 2 divides
 # + 1 reciprocal, 9 selects = 20), the watertight test on eye-relative
 # vertices (50) and the key (3).
-LPT_VARIANT = 6      # render variant: longest-first chunk order (k_render_lp_lpt)
+LPT_VARIANTS = (6, 7)   # render variants in longest-first chunk order (k_render_lp_lpt)
 OPS_PER_PREFILTER = 13
 OPS_PER_PIXEL_TEST = 88
 
@@ -361,7 +361,16 @@ def run_gpu(args, w):
         if evs:
             evs[-1].record()
 
+    # The GT cast is timed in its own fastest kernel, whichever variant the
+    # VaFR frames use (the longest-first variants cast the GT with variant
+    # 0's kernel, which is not the fastest GT cast on every scene).
+    gt_variant = None
+
     def gt_frame(k, evs=None):
+        vafr_cfg = None
+        if gt_variant is not None:
+            vafr_cfg = V.vafr_session_tuning(sess)
+            V.vafr_session_tuning(sess, (gt_variant, vafr_cfg[1]))
         if evs:
             evs[0].record()
         for e in range(eyes):
@@ -374,6 +383,32 @@ def run_gpu(args, w):
                 V.vafr_render_full_gt(scene, sess, e, disp[e * dp_b:])
         if evs:
             evs[1].record()
+        if vafr_cfg is not None:
+            V.vafr_session_tuning(sess, vafr_cfg)
+
+    if not (pt or deferred):
+        # pick it: every plain-order render variant casts one untimed and two
+        # timed GT frames (CUDA events), the fastest is kept
+        vafr_cfg = V.vafr_session_tuning(sess)
+        best = None
+        for v in range(V.vafr_tuning_space()[0]):
+            if v in LPT_VARIANTS:
+                continue
+            V.vafr_session_tuning(sess, (v, vafr_cfg[1]))
+            for e in range(eyes):
+                V.vafr_render_full_gt(scene, sess, e, disp[e * dp_b:])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(2):
+                for e in range(eyes):
+                    V.vafr_render_full_gt(scene, sess, e, disp[e * dp_b:])
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if best is None or ms < best[0]:
+                best = (ms, v)
+        V.vafr_session_tuning(sess, vafr_cfg)
+        gt_variant = best[1]
 
     def timed(fn, K, n_ev):
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(K)]
@@ -527,7 +562,7 @@ def run_gpu(args, w):
     # traffic lines were captured with the paper's acuity model; another model
     # changes the ray count and the LP buffer, so it needs captures of its own
     traffic_key = args.workload if args.acuity == "paper" else f"{args.workload}+{args.acuity}"
-    lpt = bool(tuning) and tuning[0] == LPT_VARIANT
+    lpt = bool(tuning) and tuning[0] in LPT_VARIANTS
     if pt:
         tr_render, _ = _traffic("path_lp", [os.path.join(csrc, f) for f in ("pathtrace.cu", "trace.cuh")],
                                 traffic_key)
@@ -607,7 +642,11 @@ def run_gpu(args, w):
         "p99_frame_ms": float(np.percentile(step_ms, 99)),
         "gt": {"fps": 1e3 / gt_mean, "ms_per_frame": gt_mean,
                "mpix_per_s": mpix_frame * 1e3 / gt_mean, "rays_per_frame": W_ * H_ * eyes,
-               "steps": gt_steps},
+               "steps": gt_steps,
+               "render_variant": (gt_variant if gt_variant is not None else
+                                  V.vafr_session_tuning(sess)[0]),
+               "variant_by": ("fastest plain-order variant on 2 GT frames, picked before warm-up"
+                              if gt_variant is not None else "the VaFR frames' variant")},
         "speedup_vs_gt": gt_mean / float(step_ms.mean()),
         "stage_ms": dict({"render_lp": float(render_ms.mean()), "reconstruct": float(recon_ms.mean())},
                          **({"fxaa_lp": float(per[:, 1].mean())} if fxaa else {})),

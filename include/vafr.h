@@ -270,15 +270,16 @@ VAFR_API int vafr_session_sizes(const vafr_session* session, int64_t* lp_bytes_p
                        int64_t* display_bytes_per_eye);
 /* Reads (set = 0) or writes (set = 1) the kernel variants used by this
  * session's single-session calls: cfg[0] render variant, cfg[1] reconstruct
- * tile shape (see vafr_tuning_space).  Render variant 6 takes the LP work in
- * chunks of 32 rays and renders the chunks that were slowest in the session's
- * previous frame first, so a launch does not end waiting for slow chunks that
- * happened to come last.  Results do not depend on the choice.
+ * tile shape (see vafr_tuning_space).  Render variants 6 and 7 take the LP
+ * work in chunks of 32 rays and render the chunks that were slowest in the
+ * session's previous frame first, so a launch does not end waiting for slow
+ * chunks that happened to come last (7 keeps fewer registers, 7 blocks per
+ * SM).  Results do not depend on the choice.
  * Errors: INVALID_ARG (NULL, variant out of range). */
 VAFR_API int vafr_session_tuning(vafr_session* session, int32_t set, int32_t cfg[2]);
 /* Picks the session's kernel variants by timing whole frames at the current
- * gaze: every render variant renders `warm` untimed frames (variant 6, the
- * longest-first order, needs two frames of history) and then `iters` timed
+ * gaze: every render variant renders `warm` untimed frames (variants 6 and 7,
+ * the longest-first order, need two frames of history) and then `iters` timed
  * frames (render_lp of all eyes + reconstruct of every eye, CUDA events on
  * `stream`); then every reconstruct variant is timed the same way with the
  * chosen render variant.  The fastest pair is kept and written to cfg_out
@@ -496,11 +497,11 @@ VAFR_API int vafr_measure_fp32_peak(double out[2], void* stream);
  *                       each, CUDA events) and keeps the fastest.
  *   vafr_batch_tuning   reads (set = 0) or writes (set = 1) the choice:
  *                       cfg[0] render variant, cfg[1] reconstruct variant.
- * With render variant 6 (longest-first order) vafr_batch_render keeps one
+ * With render variant 6 or 7 (longest-first order) vafr_batch_render keeps one
  * order state per frame position of the batch (the first render at a
  * position, or one whose session has more LP texels than before, allocates
  * it and synchronises the device); captured graphs and the autotuner's
- * timings run variant 6 without an order (chunks in work order).
+ * timings run variants 6 and 7 without an order (chunks in work order).
  * A batch owns device state that its launches use: the render's work
  * counter, the order states and one staging buffer per host display.  Keep
  * at most one render or replay of a batch in flight at a time (for frames in

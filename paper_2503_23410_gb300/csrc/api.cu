@@ -770,7 +770,7 @@ int vafr_render_lp(const vafr_scene* scene, vafr_session* s, int32_t eye_mask, v
         f.lp = static_cast<char*>(lp_out) + (size_t)b.n * s->n_slots * bpp;
         f.hit_ids = hit_ids_out ? hit_ids_out + (size_t)b.n * s->n_slots : nullptr;
         f.work_begin = b.total_work;
-        if (s->render_variant == kLptVariant)
+        if (is_lpt_variant(s->render_variant))
             CUDA_TRY(lpt_next(s->d_lpt[eye], s->lpt_frames[eye], as_stream(stream), &f.lpt));
         b.total_work += s->n_texels;
         b.d[b.n++] = f;
@@ -1154,7 +1154,7 @@ static int build_batch(vafr_batch* bt, const vafr_frame_desc* frames, int32_t n,
         f.lp = fr.lp;
         f.lp_aa = nullptr;
         f.lpt = nullptr;
-        if (bt->render_variant == kLptVariant && !graph) {
+        if (is_lpt_variant(bt->render_variant) && !graph) {
             if ((int)bt->lpt.size() <= i) {
                 host_alloc_point();
                 bt->lpt.resize(i + 1, vafr_batch::LptSlot{nullptr, 0, 0u});   // all or nothing

@@ -83,8 +83,10 @@ __device__ __forceinline__ LptState* lpt_state(const FrameDesc& f, int& p) {
 // The LP render in chunks of 32 work items: first the listed chunks of every
 // frame (counter [1]), then all chunks in work order (counter [0]) except the
 // listed ones.
-template <int TPB, int ORDER, class B>
-__global__ void __launch_bounds__(TPB)
+// REGEN: the shading regenerates the ray (same bits) instead of keeping it
+// through the traversal, which with MINB = 7 fits 7 blocks per SM.
+template <int TPB, int ORDER, class B, bool REGEN = false, int MINB = 1>
+__global__ void __launch_bounds__(TPB, MINB)
 k_render_lp_lpt(const SceneDev sc, const __grid_constant__ B b) {
     // Everything the fetch needs lives in shared memory and is re-read there,
     // so the traversal keeps the registers of the plain kernel (a register cap
@@ -170,6 +172,7 @@ k_render_lp_lpt(const SceneDev sc, const __grid_constant__ B b) {
             Hit h;
             const unsigned fault = traverse<4, false, ORDER>(sc, r, h, nullptr, nullptr, nullptr);
             if (fault) { atomicOr(f.status, fault); h.leaf = -1; h.id = -1; }
+            if (REGEN) lp_ray(f, local, r, glo, ghi);
             store_lp(f, t, glo, ghi, shade(sc, r, h), h.leaf >= 0 ? h.id : -1);
             if (f.depth) f.depth[t] = h.leaf >= 0 ? h.t : INFINITY;
         }
@@ -282,9 +285,9 @@ cudaError_t launch_one(const SceneDev& sc, const B& b, cudaStream_t s, int num_s
     return cudaGetLastError();
 }
 
-template <int TPB, int ORDER, class B>
+template <int TPB, int ORDER, bool REGEN = false, int MINB = 1, class B>
 cudaError_t launch_lpt(const SceneDev& sc, const B& b, cudaStream_t s, int num_sms) {
-    auto kern = k_render_lp_lpt<TPB, ORDER, B>;
+    auto kern = k_render_lp_lpt<TPB, ORDER, B, REGEN, MINB>;
     // the kernel's few bytes of shared memory must not shrink the L1 the
     // traversal lives in: ask for the smallest shared-memory carveout
     static const cudaError_t carve =
@@ -307,8 +310,10 @@ cudaError_t launch_lpt(const SceneDev& sc, const B& b, cudaStream_t s, int num_s
 template <bool GT, class B>
 cudaError_t launch_variant(const SceneDev& sc, const B& b, int variant, cudaStream_t s, int sms) {
     if (b.total_work <= 0) return cudaSuccess;
-    if (variant == kLptVariant)
-        return GT ? launch_one<128, 32, 4, 1, 1, GT>(sc, b, s, sms) : launch_lpt<128, 0>(sc, b, s, sms);
+    if (is_lpt_variant(variant)) {
+        if (GT) return launch_one<128, 32, 4, 1, 1, GT>(sc, b, s, sms);
+        return variant == kLptVariant ? launch_lpt<128, 0>(sc, b, s, sms) : launch_lpt<128, 0, true, 7>(sc, b, s, sms);
+    }
     // (threads per block, rays per warp fetch, tree width, child order, min blocks/SM)
     switch (variant) {
         case 0: return launch_one<128, 32, 4, 1, 1, GT>(sc, b, s, sms);

@@ -131,9 +131,13 @@ static_assert(sizeof(BigBatch) + sizeof(SceneDev) <= 32764, "batch too large for
 
 // ---- launch interfaces ---------------------------------------------------------
 // Render variants: threads per block, tree width, child order, register cap;
-// variant 6 is the longest-first LP order (the GT keeps variant 0's kernel).
-constexpr int kNumRenderVariants = 7;
+// variants 6 and 7 are the longest-first LP order (7: the ray regenerated for
+// shading and at most 72 registers, 7 blocks per SM); the GT keeps variant 0's
+// kernel for both.
+constexpr int kNumRenderVariants = 8;
 constexpr int kLptVariant = 6;
+constexpr int kLptVariantLean = 7;
+__host__ __device__ constexpr bool is_lpt_variant(int v) { return v == kLptVariant || v == kLptVariantLean; }
 // Reconstruct variants: column-run tiles (0-3), row tiles (4-7) and the
 // column-run tile with its LP footprint staged in shared memory (8).
 constexpr int kNumReconVariants = 9;

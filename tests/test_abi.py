@@ -42,7 +42,7 @@ def test_host_only_entry_points(lib):
     assert list(a.pivot_ecc_deg[:5]) == [0, 10, 20, 30, 60]
     assert list(a.pivot_cpd[:5]) == [40, 10, 6, 5, 4]
     assert a.e_max_deg == 60
-    assert V.vafr_tuning_space() == (7, 9)
+    assert V.vafr_tuning_space() == (8, 9)
     assert V.vafr_error_string(0) == "ok"
     assert "invalid" in V.vafr_error_string(V.ERR_INVALID_ARG)
     assert V.vafr_version() >= 10000

@@ -124,14 +124,15 @@ def test_batch_rejects_bad_frames(V, torch_mod, setup):
     V.vafr_batch_destroy(b)
 
 
-def test_longest_first_order_keeps_results(V, torch_mod, setup):
-    """Render variant 6 renders the previous frame's slowest chunks first: the
-    LP buffers and displays stay bitwise those of the plain order, frame after
-    frame (the order is rebuilt from each frame's costs), across gaze changes,
-    in the single-session path and in a replayed graph."""
+@pytest.mark.parametrize("lpt", [6, 7])
+def test_longest_first_order_keeps_results(V, torch_mod, setup, lpt):
+    """Render variants 6 and 7 render the previous frame's slowest chunks
+    first: the LP buffers and displays stay bitwise those of the plain order,
+    frame after frame (the order is rebuilt from each frame's costs), across
+    gaze changes, in the single-session path and in a replayed graph."""
     h, sessions, _ = setup
     for s, *_ in sessions:
-        V.vafr_session_tuning(s, (6, 0))
+        V.vafr_session_tuning(s, (lpt, 0))
     try:
         for it in range(3):
             got = _single(V, torch_mod, h, sessions)
@@ -139,7 +140,7 @@ def test_longest_first_order_keeps_results(V, torch_mod, setup):
                 V.vafr_session_tuning(s, (0, 0))
             ref = _single(V, torch_mod, h, sessions)
             for s, *_ in sessions:
-                V.vafr_session_tuning(s, (6, 0))
+                V.vafr_session_tuning(s, (lpt, 0))
             for (lp, d), (rlp, rd) in zip(got, ref):
                 assert np.array_equal(lp, rlp)
                 assert np.array_equal(d, rd)
@@ -150,7 +151,7 @@ def test_longest_first_order_keeps_results(V, torch_mod, setup):
         for s, *_ in sessions:
             V.vafr_session_tuning(s, (0, 0))
     b = V.vafr_batch_create(h, 16)
-    V.vafr_batch_tuning(b, (6, 0))
+    V.vafr_batch_tuning(b, (lpt, 0))
     V.vafr_batch_capture(b, _frames(sessions))
     for it in range(3):
         for k, (s, bufs, lpb, dpb) in enumerate(sessions):

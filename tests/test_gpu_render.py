@@ -291,13 +291,14 @@ def objects8k(V, torch_mod):
     V.vafr_scene_destroy(h)
 
 
-@pytest.mark.parametrize("frame,variant", [(0, 4), (150, 4), (150, 2), (150, 6)])
+@pytest.mark.parametrize("frame,variant", [(0, 4), (150, 4), (150, 2), (150, 6), (150, 7)])
 def test_lp_objects8k_binocular_sampled(V, torch_mod, lay, objects8k, frame, variant):
     """The 8K binocular workload at full size (1,998,088 triangles, FP16 LP, both
     eyes in one launch, each eye on its own gaze trajectory) in the render
-    variant the autotuner picks for it (4, capped at 64 registers), the
-    uncapped plain order (2) and the longest-first order (6): sampled texels
-    of both eyes against the oracle's CPU-BVH cast."""
+    variants the autotuner picks for it (4: plain order capped at 64
+    registers; 7: longest-first order at 7 blocks per SM), the uncapped plain
+    order (2) and the longest-first order (6): sampled texels of both eyes
+    against the oracle's CPU-BVH cast."""
     w, h, bvh = objects8k
     d, sc = w.displays[0], w.scene
     s = _session(V, d.width, d.height, d.fov_v_deg, d.poses, lp_fmt=1, disp_fmt=1)
